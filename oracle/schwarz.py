@@ -1,0 +1,278 @@
+"""Two-level ORAS preconditioner (Eq. 2lvl, Eq. oras) in FP64.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+What the paper fixes (section "Domain decomposition preconditioner"):
+
+* ``M1^{-1} = sum_i R_i^T D_i A_i^{-1} R_i`` (Eq. oras) over an overlapping
+  decomposition, ``R_i`` Boolean restrictions, ``D_i`` diagonal partition of
+  unity, ``A_i`` local Helmholtz operators with absorbing conditions on the
+  subdomain interfaces (the "optimized" in ORAS; RAS uses Dirichlet).
+* ``M^{-1} = M1^{-1} (I - A Q) + Q``, ``Q = Z E^{-1} Z^T``, ``E = Z^T A Z``
+  (Eq. 2lvl), ``Z^T`` the interpolation from the fine space to a coarse space.
+* Local problems are solved exactly by a direct solver.
+
+Readings taken where the paper is silent:
+
+* Box subdomains on the grid: axis ``a`` is cut into ``p_a`` cores at
+  ``floor(t n_a / p_a)``; each box is its core grown by ``overlap`` nodes on
+  every side that is not a global face.
+* ``D_i`` is the Boolean owner partition of unity: 1 on the core, 0 on the
+  overlap, so ``sum_i R_i^T D_i R_i = I``.
+* Absorbing interface condition: a stencil neighbour ``q`` of row ``p`` that
+  lies outside the box across an interface face is replaced by the clamped
+  in-box node times ``rho_p = exp(i k_p h)`` per crossed face, ``k_p`` at the
+  row node.  This is exact for waves ``exp(i k |x_a - x_mid|)`` leaving the
+  box along each axis; the tests pin it by that identity.  ``mode="ras"``
+  drops those neighbours instead (Dirichlet).
+* Coarse space: nodes at fine indices ``r J_a``, ``J_a = 0..ceil((n_a-1)/r)``,
+  trilinear hats ``Z[i, J] = prod_a max(0, 1 - |i_a - r J_a| / r)``; ``E`` is
+  solved exactly (the paper's 10 inner GMRES iterations on the coarse level
+  are not reproduced).
+
+Local solves have two independent routes: ``scipy.sparse.linalg.splu`` (the
+paper's sparse direct solver) and the plane-by-plane block-tridiagonal LU
+with dense Schur-complement inverses
+``S_0 = D_0, S_k = D_k - L_k S_{k-1}^{-1} U_{k-1}`` and the sweeps
+``y_k = S_k^{-1}(b_k - L_k y_{k-1})``, ``x_k = y_k - S_k^{-1} U_k x_{k+1}``.
+Pinned against ``numpy.linalg.solve`` of the dense ``A_i``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .discretization import Problem, neighbour_coefficients, assemble_A
+
+
+@dataclass
+class Box:
+    """One subdomain; all triples are in (x, y, z) order, half-open ranges."""
+
+    core_lo: tuple
+    core_hi: tuple
+    lo: tuple
+    hi: tuple
+
+    @property
+    def dims(self):
+        return tuple(self.hi[a] - self.lo[a] for a in range(3))
+
+    @property
+    def size(self):
+        d = self.dims
+        return d[0] * d[1] * d[2]
+
+
+def decompose(dims, parts, overlap):
+    """Box decomposition of a grid ``dims = (nx, ny, nz)`` into ``parts = (px, py, pz)``."""
+    cuts = [[(t * dims[a]) // parts[a] for t in range(parts[a] + 1)] for a in range(3)]
+    boxes = []
+    for tz in range(parts[2]):
+        for ty in range(parts[1]):
+            for tx in range(parts[0]):
+                t = (tx, ty, tz)
+                clo = tuple(cuts[a][t[a]] for a in range(3))
+                chi = tuple(cuts[a][t[a] + 1] for a in range(3))
+                lo = tuple(max(0, clo[a] - overlap) if clo[a] > 0 else 0 for a in range(3))
+                hi = tuple(min(dims[a], chi[a] + overlap) if chi[a] < dims[a] else dims[a] for a in range(3))
+                boxes.append(Box(clo, chi, lo, hi))
+    return boxes
+
+
+def box_global_indices(box: Box, dims):
+    """Global flat indices of the box nodes, local order ``(k, j, i)`` with i fastest."""
+    nx, ny, _ = dims
+    k, j, i = np.meshgrid(np.arange(box.lo[2], box.hi[2]), np.arange(box.lo[1], box.hi[1]),
+                          np.arange(box.lo[0], box.hi[0]), indexing="ij")
+    return ((k * ny + j) * nx + i).ravel()
+
+
+def restriction(box: Box, dims) -> sp.csr_matrix:
+    """Boolean ``R_i`` (local size x global size)."""
+    g = box_global_indices(box, dims)
+    n = dims[0] * dims[1] * dims[2]
+    return sp.csr_matrix((np.ones(g.size), (np.arange(g.size), g)), shape=(g.size, n))
+
+
+def partition_of_unity(box: Box) -> np.ndarray:
+    """Boolean owner weights ``diag(D_i)``: 1 on core nodes, 0 on overlap nodes."""
+    k, j, i = np.meshgrid(np.arange(box.lo[2], box.hi[2]), np.arange(box.lo[1], box.hi[1]),
+                          np.arange(box.lo[0], box.hi[0]), indexing="ij")
+    own = ((i >= box.core_lo[0]) & (i < box.core_hi[0]) & (j >= box.core_lo[1]) & (j < box.core_hi[1])
+           & (k >= box.core_lo[2]) & (k < box.core_hi[2]))
+    return own.ravel().astype(np.float64)
+
+
+def local_operator(prob: Problem, box: Box, mode: str = "oras", coef=None) -> sp.csr_matrix:
+    """``A_i``: the rows of A for the box nodes with absorbing (or Dirichlet) interface folding."""
+    if coef is None:
+        coef = neighbour_coefficients(prob)
+    bx, by, bz = box.dims
+    k, j, i = np.meshgrid(np.arange(bz), np.arange(by), np.arange(bx), indexing="ij")
+    gi, gj, gk = i + box.lo[0], j + box.lo[1], k + box.lo[2]
+    rho = np.exp(1j * (prob.omega / np.asarray(prob.c, dtype=np.complex128)[gk, gj, gi]) * prob.h)
+    row = ((k * by + j) * bx + i)
+    rows, cols, vals = [], [], []
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                c = coef[dz + 1, dy + 1, dx + 1][gk, gj, gi]
+                qi, qj, qk = i + dx, j + dy, k + dz
+                crossed = ((qi < 0) | (qi >= bx)).astype(int) + ((qj < 0) | (qj >= by)).astype(int) \
+                    + ((qk < 0) | (qk >= bz)).astype(int)
+                # neighbours outside the global grid already carry a zero coefficient
+                ci, cj, ck = np.clip(qi, 0, bx - 1), np.clip(qj, 0, by - 1), np.clip(qk, 0, bz - 1)
+                if mode == "oras":
+                    v = c * rho ** crossed
+                elif mode == "ras":
+                    v = np.where(crossed > 0, 0.0, c)
+                else:
+                    raise ValueError(mode)
+                rows.append(row.ravel())
+                cols.append(((ck * by + cj) * bx + ci).ravel())
+                vals.append(v.ravel())
+    n = bx * by * bz
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    A.eliminate_zeros()
+    return A
+
+
+# ---------------------------------------------------------------------------
+# Plane-by-plane block-tridiagonal LU (second route for the local solves)
+# ---------------------------------------------------------------------------
+
+def plane_blocks(Ai: sp.spmatrix, m: int, nplanes: int):
+    """Dense ``(D_k, L_k, U_k)`` of a local operator ordered plane by plane."""
+    A = Ai.tocsr()
+    D, L, U = [], [], []
+    for kk in range(nplanes):
+        s = slice(kk * m, (kk + 1) * m)
+        D.append(A[s, s].toarray())
+        L.append(A[s, (kk - 1) * m:kk * m].toarray() if kk > 0 else None)
+        U.append(A[s, (kk + 1) * m:(kk + 2) * m].toarray() if kk < nplanes - 1 else None)
+    return D, L, U
+
+
+def plane_factor(D, L, U):
+    """Dense Schur-complement inverses ``G_k = S_k^{-1}``."""
+    G = []
+    for kk in range(len(D)):
+        S = D[kk] if kk == 0 else D[kk] - L[kk] @ G[kk - 1] @ U[kk - 1]
+        G.append(np.linalg.inv(S))
+    return G
+
+
+def plane_solve(G, L, U, b):
+    """Forward and backward plane sweeps; ``b`` is ``[nplanes*m]`` or ``[nplanes*m, nrhs]``."""
+    nplanes = len(G)
+    m = G[0].shape[0]
+    bb = b.reshape((nplanes, m) + b.shape[1:])
+    y = np.empty_like(bb, dtype=np.complex128)
+    for kk in range(nplanes):
+        rhs = bb[kk] if kk == 0 else bb[kk] - L[kk] @ y[kk - 1]
+        y[kk] = G[kk] @ rhs
+    x = np.empty_like(y)
+    x[-1] = y[-1]
+    for kk in range(nplanes - 2, -1, -1):
+        x[kk] = y[kk] - G[kk] @ (U[kk] @ x[kk + 1])
+    return x.reshape(b.shape)
+
+
+# ---------------------------------------------------------------------------
+# Coarse space
+# ---------------------------------------------------------------------------
+
+def coarse_dims(dims, r):
+    return tuple(-(-(dims[a] - 1) // r) + 1 for a in range(3))
+
+
+def hat_1d(n: int, r: int) -> sp.csr_matrix:
+    nc = -(-(n - 1) // r) + 1
+    i = np.arange(n)[:, None]
+    J = np.arange(nc)[None, :]
+    w = np.maximum(0.0, 1.0 - np.abs(i - r * J) / r)
+    return sp.csr_matrix(w)
+
+
+def coarse_basis(dims, r) -> sp.csr_matrix:
+    """``Z`` (fine size x coarse size), trilinear hats; index ``(k*ny + j)*nx + i`` on both grids."""
+    Zx, Zy, Zz = hat_1d(dims[0], r), hat_1d(dims[1], r), hat_1d(dims[2], r)
+    return sp.kron(Zz, sp.kron(Zy, Zx, format="csr"), format="csr")
+
+
+# ---------------------------------------------------------------------------
+# The preconditioner
+# ---------------------------------------------------------------------------
+
+class ORAS:
+    """``M^{-1}`` of Eq. (2lvl) (or Eq. (oras) alone when ``coarse_ratio == 0``)."""
+
+    def __init__(self, prob: Problem, parts, overlap, coarse_ratio=0, mode="oras", local="splu"):
+        self.prob = prob
+        self.dims = (prob.nx, prob.ny, prob.nz)
+        self.boxes = decompose(self.dims, parts, overlap)
+        coef = neighbour_coefficients(prob)
+        self.A = assemble_A(prob)
+        self.local = local
+        self.idx, self.pu, self.Ai, self.solvers = [], [], [], []
+        for box in self.boxes:
+            Ai = local_operator(prob, box, mode, coef)
+            self.idx.append(box_global_indices(box, self.dims))
+            self.pu.append(partition_of_unity(box))
+            self.Ai.append(Ai)
+            if local == "splu":
+                self.solvers.append(spla.splu(Ai.tocsc()))
+            elif local == "planes":
+                m = box.dims[0] * box.dims[1]
+                D, L, U = plane_blocks(Ai, m, box.dims[2])
+                self.solvers.append((plane_factor(D, L, U), L, U))
+            else:
+                raise ValueError(local)
+        self.coarse_ratio = coarse_ratio
+        if coarse_ratio:
+            self.Z = coarse_basis(self.dims, coarse_ratio)
+            self.E = (self.Z.T @ self.A @ self.Z).tocsc()
+            self.E_lu = spla.splu(self.E)
+
+    def local_solve(self, i, r):
+        if self.local == "splu":
+            return self.solvers[i].solve(r)
+        G, L, U = self.solvers[i]
+        return plane_solve(G, L, U, r)
+
+    def apply_one_level(self, v):
+        """``sum_i R_i^T D_i A_i^{-1} R_i v`` for ``v`` of shape ``[N]`` or ``[N, nrhs]``."""
+        out = np.zeros(v.shape, dtype=np.complex128)
+        for i in range(len(self.boxes)):
+            xi = self.local_solve(i, np.ascontiguousarray(v[self.idx[i]]))
+            d = self.pu[i] if v.ndim == 1 else self.pu[i][:, None]
+            out[self.idx[i]] += d * xi
+        return out
+
+    def coarse_correction(self, v):
+        """``Q v = Z E^{-1} Z^T v``."""
+        return self.Z @ self.E_lu.solve(np.asarray(self.Z.T @ v))
+
+    def apply(self, v):
+        v = np.asarray(v, dtype=np.complex128)
+        if not self.coarse_ratio:
+            return self.apply_one_level(v)
+        q = self.coarse_correction(v)
+        return self.apply_one_level(v - self.A @ q) + q
+
+
+def direct_solve_planes(prob: Problem, B):
+    """Exact ``A^{-1} B`` by the plane-by-plane block LU of the whole grid (one box, no folding).
+
+    ``B`` is ``[N]`` or ``[N, nrhs]``.  Used as the reference solution of
+    small problems; pinned against ``splu`` and ``numpy.linalg.solve``.
+    """
+    A = assemble_A(prob)
+    m = prob.nx * prob.ny
+    D, L, U = plane_blocks(A, m, prob.nz)
+    G = plane_factor(D, L, U)
+    return plane_solve(G, L, U, np.asarray(B, dtype=np.complex128))

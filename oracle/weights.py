@@ -1,0 +1,74 @@
+"""Least-squares fit of the 27-point mixed-grid stencil weights (FP64).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+The paper states that the stiffness and consistent-mass weights are computed
+by least-squares minimisation of the numerical dispersion and anisotropy
+(section "Tetrahedral finite elements versus 27-point finite-differences"),
+but prints no values.  Reading taken: minimise the normalised phase-velocity
+error ``1 - sqrt(-L_hat(kappa)/M_hat(kappa)) / |kappa|`` of plane waves over
+``G`` = 4..30 grid points per wavelength and propagation directions in one
+octant, with ``w1 = 1 - w2 - w3`` and ``wm1 = 1 - 6 wm2 - 12 wm3 - 8 wm4`` so
+both weight sets sum to one, and every weight kept non-negative (each set is
+a convex combination of stencils; the unconstrained minimum has negative
+weights and no smaller error).  ``L_hat``/``M_hat`` are the Laplacian and mass
+parts of the symbol in :func:`oracle.discretization.symbol`.
+
+Parity: the fitted values themselves are unpinned (the paper prints none);
+what is pinned is that the fit reduces the maximum phase-velocity error far
+below the 7-point stencil's over the fitted range.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.optimize import least_squares
+
+from .discretization import stencil_coefficients
+
+
+def _sample_directions(n_theta=7, n_phi=7):
+    th = np.linspace(0.0, np.pi / 2, n_theta)
+    ph = np.linspace(0.0, np.pi / 2, n_phi)
+    dirs = []
+    for t in th:
+        for p in ph:
+            dirs.append((np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)))
+    return np.array(dirs)
+
+
+def phase_velocity_ratio(weights, G, direction) -> float:
+    """``v_phase / c`` of a plane wave with ``G`` points per wavelength (h = 1)."""
+    a2, a3, m0, m1, m2, m3 = stencil_coefficients(weights)
+    kap = 2.0 * np.pi / G
+    s = [2.0 * (np.cos(kap * d) - 1.0) for d in direction]
+    s1 = s[0] + s[1] + s[2]
+    s2 = s[0] * s[1] + s[0] * s[2] + s[1] * s[2]
+    s3 = s[0] * s[1] * s[2]
+    L = s1 + a2 * s2 + a3 * s3
+    M = m0 + m1 * s1 + m2 * s2 + m3 * s3
+    return np.sqrt(max(-L / M, 0.0)) / kap
+
+
+def full_weights(p):
+    w2, w3, wm2, wm3, wm4 = p
+    return (1.0 - w2 - w3, w2, w3, 1.0 - 6.0 * wm2 - 12.0 * wm3 - 8.0 * wm4, wm2, wm3, wm4)
+
+
+def dispersion_residuals(weights, G_values=None, directions=None):
+    if G_values is None:
+        G_values = 1.0 / np.linspace(1.0 / 30.0, 1.0 / 4.0, 24)
+    if directions is None:
+        directions = _sample_directions()
+    return np.array([1.0 - phase_velocity_ratio(weights, G, d) for G in G_values for d in directions])
+
+
+def fit_weights(G_min=4.0, G_max=30.0):
+    """Fit ``(w1, w2, w3, wm1, wm2, wm3, wm4)``; returns a 7-tuple of floats."""
+    G_values = 1.0 / np.linspace(1.0 / G_max, 1.0 / G_min, 24)
+    directions = _sample_directions()
+    p0 = np.array([0.5, 0.1, 0.08, 0.005, 0.001])
+    lower = [0.0, 0.0, 0.0, 0.0, 0.0]
+    upper = [1.0, 1.0, 1.0 / 6.0, 1.0 / 12.0, 1.0 / 8.0]
+    res = least_squares(lambda p: dispersion_residuals(full_weights(p), G_values, directions), p0,
+                        bounds=(lower, upper), xtol=1e-14, ftol=1e-14, gtol=1e-14, max_nfev=4000)
+    return tuple(float(v) for v in full_weights(res.x))

@@ -1,0 +1,149 @@
+"""Pins of the oracle's discretisation (Eq. eq1, the 27-point mixed-grid stencil)."""
+import numpy as np
+import scipy.sparse as sp
+import pytest
+
+from oracle.discretization import (Problem, WEIGHTS_7PT, apply_A, assemble_A, neighbour_coefficients, symbol,
+                                   stencil_coefficients, pml_xi)
+from oracle.weights import fit_weights, dispersion_residuals, phase_velocity_ratio
+from paper_2103_14921_gb300 import synth
+
+
+def _prob(n=(9, 8, 7), weights=WEIGHTS_7PT, npml=0, c=None, top_pml=False, f=5.0, h=25.0):
+    nx, ny, nz = n
+    if c is None:
+        c = synth.homogeneous(nx, ny, nz, 1500.0)
+    return Problem(nx, ny, nz, h, f, c, npml=npml, top_pml=top_pml, weights=weights)
+
+
+def test_seven_point_equals_textbook_laplacian():
+    """w1 = 1, wm1 = 1 without PML: the Kronecker-sum Laplacian plus diag(k^2)."""
+    nx, ny, nz = 9, 8, 7
+    c = synth.linear_gradient(nx, ny, nz, 25.0) * (1 - 0.01j)
+    prob = _prob((nx, ny, nz), c=c)
+    h = prob.h
+
+    def lap1(n):
+        return sp.diags([np.ones(n - 1), -2 * np.ones(n), np.ones(n - 1)], [-1, 0, 1]) / h ** 2
+
+    I = lambda n: sp.identity(n)
+    L = (sp.kron(I(nz), sp.kron(I(ny), lap1(nx))) + sp.kron(I(nz), sp.kron(lap1(ny), I(nx)))
+         + sp.kron(lap1(nz), sp.kron(I(ny), I(nx))))
+    A_text = (L + sp.diags(prob.k2().ravel())).toarray()
+    A = assemble_A(prob).toarray()
+    assert np.allclose(A, A_text, rtol=0, atol=1e-14 * np.abs(A_text).max())
+    u = synth.random_complex((nz, ny, nx), 4)
+    assert np.allclose(apply_A(prob, u).ravel(), A_text @ u.ravel(), rtol=1e-13, atol=0)
+
+
+def test_rotated_system_form_equals_product_form():
+    """Interior rows: the stencil written per rotated coordinate system (Operto et al. form)."""
+    w = synth.random_weights(11)
+    w1, w2, w3, wm1, wm2, wm3, wm4 = w
+    nx, ny, nz = 8, 7, 6
+    c = synth.linear_gradient(nx, ny, nz, 25.0, c0=1500.0, alpha=3.0) * (1 - 0.02j)
+    prob = _prob((nx, ny, nz), weights=w, c=c)
+    u = synth.random_complex((nz, ny, nx), 5)
+    k2 = prob.k2()
+    h = prob.h
+    got = apply_A(prob, u)
+    upad = np.pad(u, 1)
+    wpad = np.pad(k2 * u, 1)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                F = E = C = 0
+                Fw = Ew = Cw = 0
+                for dz in (-1, 0, 1):
+                    for dy in (-1, 0, 1):
+                        for dx in (-1, 0, 1):
+                            nnz = abs(dx) + abs(dy) + abs(dz)
+                            v = upad[k + 1 + dz, j + 1 + dy, i + 1 + dx]
+                            vw = wpad[k + 1 + dz, j + 1 + dy, i + 1 + dx]
+                            if nnz == 1:
+                                F += v; Fw += vw
+                            elif nnz == 2:
+                                E += v; Ew += vw
+                            elif nnz == 3:
+                                C += v; Cw += vw
+                u0 = u[k, j, i]
+                lap = (w1 * (F - 6 * u0) + (w2 / 3) * ((F - 6 * u0) + (E - 12 * u0) / 2)
+                       + w3 * (C - 8 * u0) / 4) / h ** 2
+                mass = wm1 * k2[k, j, i] * u0 + wm2 * Fw + wm3 * Ew + wm4 * Cw
+                assert abs(got[k, j, i] - (lap + mass)) <= 1e-12 * (abs(lap) + abs(mass))
+
+
+def test_plane_wave_symbol_interior():
+    """``A exp(i kappa.x) = A_hat(kappa) exp(i kappa.x)`` on interior unstretched nodes."""
+    w = fit_weights()
+    prob = _prob((10, 9, 8), weights=w)
+    k2 = complex(prob.k2()[0, 0, 0])
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        kappa = rng.uniform(-np.pi / prob.h, np.pi / prob.h, 3)
+        k, j, i = np.meshgrid(np.arange(8), np.arange(9), np.arange(10), indexing="ij")
+        u = np.exp(1j * (kappa[0] * i * prob.h + kappa[1] * j * prob.h + kappa[2] * (k + 1) * prob.h))
+        got = apply_A(prob, u)[1:-1, 1:-1, 1:-1]
+        want = symbol(prob, kappa, k2) * u[1:-1, 1:-1, 1:-1]
+        assert np.allclose(got, want, rtol=1e-11, atol=1e-11 * np.abs(want).max())
+
+
+def test_assembled_equals_matrix_free_with_pml_and_attenuation():
+    nx, ny, nz = 14, 13, 12
+    c = synth.linear_gradient(nx, ny, nz, 25.0, Q=50.0)
+    for top in (False, True):
+        prob = _prob((nx, ny, nz), weights=synth.random_weights(2), npml=4, c=c, top_pml=top)
+        A = assemble_A(prob)
+        U = synth.random_complex((nz, ny, nx, 3), 6)
+        got = apply_A(prob, U).reshape(-1, 3)
+        want = A @ U.reshape(-1, 3)
+        assert np.linalg.norm(got - want) <= 1e-14 * np.linalg.norm(want)
+        # 27 nonzeros per interior row
+        assert A.getnnz(axis=1).max() == 27
+
+
+def test_neighbour_coefficients_zero_at_ghosts_and_dirichlet_top():
+    prob = _prob((6, 5, 4), weights=synth.random_weights(3), npml=2)
+    coef = neighbour_coefficients(prob)
+    assert np.all(coef[0, :, :, 0] == 0)       # no coupling to the Dirichlet ghost plane
+    assert np.all(coef[:, :, 2, :, :, -1] == 0)
+    assert np.abs(coef[1, 1, 1]).min() > 0
+
+
+def test_pml_stretching_profile():
+    """xi = 1 inside, 1 + i gamma0 (d/L)^2 / omega in the layers, symmetric, growing outwards."""
+    n, h, npml, omega, cref, R = 30, 25.0, 8, 2 * np.pi * 5, 2000.0, 1e-3
+    xn, xh = pml_xi(n, h, npml, True, True, omega, cref, R)
+    L = npml * h
+    g0 = 1.5 * cref / L * np.log(1 / R)
+    assert np.allclose(xn[npml:n - npml], 1.0)
+    assert np.isclose(xn[0], 1 + 1j * g0 / omega)            # d = L at the outermost node
+    assert np.allclose(xn, xn[::-1])
+    assert np.allclose(xh, xh[::-1])
+    assert np.all(np.diff(xn[:npml + 1].imag) < 0)
+    # no high layer requested -> no stretch there
+    xn2, _ = pml_xi(n, h, npml, False, True, omega, cref, R)
+    assert np.allclose(xn2[:n - npml], 1.0)
+
+
+def test_fitted_weights_reduce_dispersion():
+    """The fitted stencil keeps |1 - v_ph/c| small over 4..30 points per wavelength."""
+    w = fit_weights()
+    assert abs(sum(w[:3]) - 1) < 1e-12
+    assert abs(w[3] + 6 * w[4] + 12 * w[5] + 8 * w[6] - 1) < 1e-12
+    assert min(w) >= 0
+    err_fit = np.abs(dispersion_residuals(w)).max()
+    err_7 = np.abs(dispersion_residuals(WEIGHTS_7PT)).max()
+    assert err_fit < 0.006
+    assert err_7 > 0.05
+    # consistency: v_ph / c -> 1 for well-resolved waves in any direction
+    for d in [(1, 0, 0), (0.6, 0.8, 0), (0.48, 0.6, 0.64)]:
+        assert abs(1 - phase_velocity_ratio(w, 200.0, d)) < 1e-4
+
+
+def test_stencil_coefficient_identities():
+    # the mass weights summing to one give m0 = 1
+    w = synth.random_weights(9)
+    a2, a3, m0, m1, m2, m3 = stencil_coefficients(w)
+    assert abs(m0 - 1) < 1e-12
+    assert a2 >= 0 and a3 >= 0
