@@ -1,0 +1,189 @@
+/*
+ * helm.h -- C ABI of the GB300 ORAS-GMRES solver for the 27-point
+ * finite-difference Helmholtz problem.
+ *
+ * The method (Dolean, Jolivet, Tournier, Combe, Operto, Riffo, EAGE 2021,
+ * arXiv 2103.14921):
+ *   - Eq. (eqh)/(eq1): (Delta + k^2(x)) u = b, k = omega / c(x), c complex in
+ *     viscous media, discretised as A u = b with absorbing layers on the
+ *     vertical and bottom faces and a homogeneous Dirichlet top.
+ *   - The 27-point mixed-grid stencil (rotated-coordinate Laplacians plus a
+ *     consistent mass term, weights fitted on numerical dispersion).
+ *   - Eq. (2lvl): M^{-1} = M1^{-1}(I - A Q) + Q, Q = Z E^{-1} Z^T, E = Z^T A Z.
+ *   - Eq. (oras): M1^{-1} = sum_i R_i^T D_i A_i^{-1} R_i with absorbing
+ *     conditions on the subdomain interfaces.
+ *   - GMRES, flexible when the preconditioner varies.
+ *
+ * Conventions shared by every call:
+ *   - Grid vectors are complex, interleaved (re, im), point-major and
+ *     right-hand-side-minor: element (i, j, k, r) of an nrhs-column vector is
+ *     at offset ((k * ny + j) * nx + i) * nrhs + r.  Node (i, j, k) sits at
+ *     x = i h, y = j h, depth z = (k + 1) h; the Dirichlet plane is the ghost
+ *     k = -1.
+ *   - "complex128" = two doubles, "complex64" = two floats.
+ *   - Unless stated otherwise a pointer argument may point to device memory
+ *     or to host memory (pinned or pageable); host buffers are staged through
+ *     device memory inside the call.  Caller-owned buffers are never retained
+ *     after a call returns.
+ *   - All work is ordered on the CUDA stream given to helm_create.  Calls are
+ *     synchronous with respect to the host unless stated otherwise.
+ *   - Errors are returned as status codes; nothing aborts, throws or traps.
+ *     helm_last_error() gives the message of the last failure on a context.
+ *   - Handles are owned by the library until the matching destroy call.  A
+ *     grid must outlive the ORAS handles built on it; a context must outlive
+ *     its grids.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int helm_status;
+#define HELM_OK          0
+#define HELM_EINVAL      1  /* invalid argument or unsupported combination            */
+#define HELM_ENOMEM      2  /* device allocation failed or HBM budget exceeded        */
+#define HELM_ENOTCONV    3  /* maxit reached; best iterate and residual still written */
+#define HELM_ESINGULAR   4  /* zero pivot in a plane Schur-complement inverse         */
+#define HELM_ENONFINITE  5  /* NaN/Inf in a right-hand side or a residual             */
+#define HELM_ETIMEOUT    6  /* a bounded device wait expired                          */
+#define HELM_EBUSY       7  /* resource in use (request queue full)                   */
+#define HELM_ECUDA       8  /* CUDA runtime error                                     */
+#define HELM_ENOTFOUND   9  /* unknown ticket or index out of range                  */
+
+typedef struct helm_ctx_s*  helm_ctx;
+typedef struct helm_grid_s* helm_grid;
+typedef struct helm_oras_s* helm_oras;
+
+/* Top boundary: the paper's homogeneous Dirichlet condition, or an absorbing
+ * layer (used to compare against whole-space closed-form solutions). */
+#define HELM_TOP_DIRICHLET 0
+#define HELM_TOP_PML       1
+
+/* Arithmetic of a kernel family.  FP64: complex128 throughout.  FP32:
+ * complex64 storage and arithmetic.  TF32: complex64 storage, plane products
+ * on the tensor cores in TF32 with FP32 accumulation.  TF32X3: the same with
+ * the three-product split (hi*hi + hi*lo + lo*hi) for near-FP32 accuracy. */
+#define HELM_PREC_FP64   0
+#define HELM_PREC_FP32   1
+#define HELM_PREC_TF32   2
+#define HELM_PREC_TF32X3 3
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, ordering all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * `hbm_budget_bytes` caps the device memory the context may allocate
+ * (0 = no cap).  Returns HELM_ECUDA if the device cannot be used. */
+helm_status helm_create(helm_ctx* out, int device, void* cuda_stream, size_t hbm_budget_bytes);
+void        helm_destroy(helm_ctx ctx);
+/* Message of the last failure on this context ("" if none).  Valid until the
+ * next call on the context.  ctx may be NULL (then: last failure of helm_create). */
+const char* helm_last_error(helm_ctx ctx);
+/* Bytes of device memory currently held by the context. */
+size_t      helm_bytes_in_use(helm_ctx ctx);
+/* Number of CUDA kernel launches the library has issued on this context. */
+uint64_t    helm_launch_count(helm_ctx ctx);
+
+/* ------------------------------------------------------------ grid / model */
+
+typedef struct {
+    int    nx, ny, nz;    /* unknown nodes per axis (each >= 2)                              */
+    double h;             /* grid spacing, metres                                             */
+    double freq_hz;       /* frequency; omega = 2 pi freq_hz                                  */
+    int    npml;          /* absorbing-layer thickness in nodes (0 = none)                    */
+    double pml_R;         /* nominal layer reflection; gamma0 = 3 c_ref/(2 L) ln(1/R)         */
+    int    top_bc;        /* HELM_TOP_DIRICHLET or HELM_TOP_PML                               */
+    double weights[7];    /* w1, w2, w3, wm1, wm2, wm3, wm4 of the mixed-grid stencil;
+                             w1+w2+w3 = 1 and wm1+6wm2+12wm3+8wm4 = 1 (checked, 1e-9)       */
+} helm_grid_desc;
+
+/* Fit the stencil weights by least squares on the normalised phase-velocity
+ * error 1 - sqrt(-L(kappa)/M(kappa))/|kappa| of plane waves over G_min..G_max
+ * grid points per wavelength and directions in one octant, all weights kept
+ * non-negative (the paper: "least-squares minimisation of the numerical
+ * dispersion and anisotropy").  Host-only; writes weights_out[7]. */
+helm_status helm_fit_weights(double G_min, double G_max, double weights_out[7]);
+
+/* Set up one problem: copies the wave speed c (complex128 [nz][ny][nx],
+ * device or host) and builds k^2 = (omega/c)^2 and the stretched 1-D
+ * difference tables of the absorbing layers (separable PML, xi = 1 + i
+ * gamma(d)/omega, gamma = gamma0 (d/L)^2, c_ref = max Re c).  Eq. (eqh). */
+helm_status helm_setup_grid(helm_ctx ctx, const helm_grid_desc* desc, const void* c, helm_grid* out);
+void        helm_destroy_grid(helm_grid g);
+
+/* y = A u (Eq. eq1), matrix-free 27-point stencil, nrhs columns.
+ * prec = HELM_PREC_FP64: u, y complex128; prec = HELM_PREC_FP32: complex64.
+ * u and y must not overlap.  Device pointers only. */
+helm_status helm_apply(helm_grid g, int prec, const void* u, void* y, int nrhs);
+
+/* ----------------------------------------------------------- ORAS factors */
+
+typedef struct {
+    int px, py, pz;       /* boxes per axis; axis a is cut at floor(t n_a / p_a)            */
+    int overlap;          /* nodes added on every interior side of each core (>= 1)         */
+    int coarse_ratio;     /* 0 = one level (Eq. oras); r >= 2 = trilinear coarse grid (Eq. 2lvl) */
+    int interface_bc;     /* 0 = absorbing (ORAS, rho = exp(i k_p h) folding); 1 = Dirichlet (RAS) */
+    int factor_prec;      /* HELM_PREC_FP64, _FP32, _TF32 or _TF32X3 for the fine local factors;
+                             the coarse factors are always FP64                                     */
+} helm_oras_desc;
+
+/* Build the ORAS preconditioner: box decomposition, local operators A_i with
+ * absorbing interface folding, and for every box the plane-by-plane block LU
+ * S_0 = D_0, S_k = D_k - L_k S_{k-1}^{-1} U_{k-1} with the dense complex
+ * inverses S_k^{-1} kept resident; with coarse_ratio > 0 also Z, E = Z^T A Z
+ * and E's plane factors in FP64.  Eq. (2lvl), Eq. (oras).
+ * Returns HELM_ESINGULAR if a pivot vanishes, HELM_ENOMEM past the budget. */
+helm_status oras_factor(helm_grid g, const helm_oras_desc* desc, helm_oras* out);
+void        oras_destroy(helm_oras o);
+
+/* out = M^{-1} v (Eq. 2lvl, or Eq. oras without a coarse level).
+ * v, out: complex128, nrhs columns, device pointers. */
+helm_status oras_apply(helm_oras o, const void* v, void* out, int nrhs);
+
+/* Sizes of the decomposition: number of boxes, and for box `box` its origin
+ * lo[3] and extent dims[3] in (x, y, z) order.  box < 0 fills only nboxes. */
+helm_status oras_box_info(helm_oras o, int box, int* nboxes, int lo[3], int dims[3]);
+
+/* Copy S_k^{-1} of box `box`, plane `plane` to `out` as a complex128 m x m
+ * row-major matrix (m = dims[0]*dims[1], in-plane index j*dims[0]+i).
+ * Device or host pointer. */
+helm_status oras_plane_inverse(helm_oras o, int box, int plane, void* out);
+
+/* Seconds spent in oras_factor (device time of the setup kernels). */
+double      oras_setup_seconds(helm_oras o);
+
+/* ---------------------------------------------------------------- Krylov */
+
+typedef struct {
+    double tol;           /* stop when ||b - A x||_2 / ||b||_2 <= tol (per column)           */
+    int    restart;       /* Krylov dimension per cycle (1..200)                              */
+    int    maxit;         /* total iteration cap per column                                   */
+    int    flexible;      /* 1 = FGMRES (keeps Z_j = M^{-1} v_j), 0 = right-preconditioned GMRES */
+    int    basis_prec;    /* HELM_PREC_FP64 (complex128 basis) or HELM_PREC_FP32 (complex64)  */
+} helm_gmres_desc;
+
+typedef struct {
+    int    iterations;    /* Krylov iterations taken                                          */
+    int    converged;     /* 1 if the true relative residual <= tol                          */
+    double true_relres;   /* FP64 ||b - A x|| / ||b|| at exit                                 */
+    double est_relres;    /* last Givens residual estimate                                    */
+} helm_rhs_stats;
+
+/* Solve A x = b for nrhs columns with right-preconditioned (F)GMRES(m),
+ * x0 = 0, independent Krylov spaces per column, CGS2 Arnoldi with FP64
+ * accumulation, complex Givens rotations, FP64 true residual at every cycle
+ * end (restart if above tol).  b, x complex128 [N][nrhs]; device or host.
+ * stats (host array of nrhs, may be NULL) receives per-column results.
+ * Returns HELM_ENOTCONV (x still written) if some column missed tol. */
+helm_status gmres_solve(helm_oras o, const void* b, void* x, int nrhs, const helm_gmres_desc* desc,
+                        helm_rhs_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

@@ -1,0 +1,128 @@
+// 27-point mixed-grid Helmholtz stencil y = A u (Eq. eq1), matrix-free, multi-RHS.
+//
+// The mixed-grid stencil (rotated-coordinate Laplacians with weights w1..w3
+// plus a consistent mass term with weights wm1..wm4) is applied in its exact
+// product form with 1-D second differences:
+//   A u = h^-2 [sum D_a + a2 sum_{a<b} D_a D_b + a3 D_x D_y D_z] u
+//       + [m0 + m1 sum P_a + m2 sum P_a P_b + m3 P_x P_y P_z] (k^2 u)
+// with a2 = w2/6 + w3/2, a3 = w3/4, m0 = wm1+6wm2+12wm3+8wm4,
+// m1 = wm2+4wm3+4wm4, m2 = wm3+2wm4, m3 = wm4.  D_a is the 3-point second
+// difference stretched by the absorbing layer (coefficients cm, c0, cp per
+// node, from the grid's 1-D tables); P_a is the plain (1, -2, 1).  Ghost
+// neighbours (outside the grid, including the Dirichlet plane above k = 0)
+// contribute zero.
+//
+// The coefficient of neighbour (dx, dy, dz) is a tensor product of the 1-D
+// coefficients; per (dy, dz) pair the two partial sums
+//   A = e_y e_z + a2 (Y e_z + e_y Z) + a3 Y Z,  B = Y e_z + e_y Z + a2 Y Z
+// give the Laplacian coefficient X_dx A + [dx == 0] B, and likewise for the
+// real mass coefficient.  Each thread owns one node and RCH consecutive
+// right-hand sides (rhs fastest across threads, so warps read contiguous
+// memory); the coefficient is formed once per neighbour and reused for the
+// RCH columns.
+#include "internal.h"
+
+namespace {
+
+template <typename T, int RCH>
+__global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict__ u, cplx<T>* __restrict__ y,
+                                                      const cplx<T>* __restrict__ k2,
+                                                      const cplx<T>* __restrict__ tab, int nx, int ny, int nz,
+                                                      int nrhs, StencilW w) {
+    const int nch = nrhs / RCH;
+    const long long total = (long long)nx * ny * nz * nch;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int ch = (int)(t % nch);
+    const long long p = t / nch;
+    const int i = (int)(p % nx);
+    const long long tmp = p / nx;
+    const int j = (int)(tmp % ny);
+    const int k = (int)(tmp / ny);
+
+    const cplx<T>* tx = tab + 3 * i;
+    const cplx<T>* ty = tab + 3 * (nx + j);
+    const cplx<T>* tz = tab + 3 * (nx + ny + k);
+    cplx<T> X[3], Y[3], Z[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) { X[d] = tx[d]; Y[d] = ty[d]; Z[d] = tz[d]; }
+
+    const T a2 = (T)w.a2, a3 = (T)w.a3, m0 = (T)w.m0, m1 = (T)w.m1, m2 = (T)w.m2, m3 = (T)w.m3;
+    const T ih2 = (T)w.inv_h2;
+    const cplx<T> zero = mk<T>(0, 0);
+    cplx<T> acc[RCH];
+#pragma unroll
+    for (int r = 0; r < RCH; ++r) acc[r] = zero;
+
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int kk = k + dz;
+        if (kk < 0 || kk >= nz) continue;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int jj = j + dy;
+            if (jj < 0 || jj >= ny) continue;
+            const cplx<T> Yd = Y[dy + 1], Zd = Z[dz + 1];
+            const cplx<T> yz = Yd * Zd;
+            const cplx<T> ye = (dz == 0) ? Yd : zero;       // Y e_z
+            const cplx<T> ez = (dy == 0) ? Zd : zero;       // e_y Z
+            const T ee = (dy == 0 && dz == 0) ? (T)1 : (T)0;
+            cplx<T> Ac = a3 * yz + a2 * (ye + ez);
+            Ac.x += ee;
+            const cplx<T> Bc = ye + ez + a2 * yz;
+            const T Py = (dy == 0) ? (T)-2 : (T)1, Pz = (dz == 0) ? (T)-2 : (T)1;
+            const T pe = (dz == 0) ? Py : (T)0;
+            const T ep = (dy == 0) ? Pz : (T)0;
+            const T pp = Py * Pz;
+            const T Am = m1 * ee + m2 * (pe + ep) + m3 * pp;
+            const T Bm = m0 * ee + m1 * (pe + ep) + m2 * pp;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int ii = i + dx;
+                if (ii < 0 || ii >= nx) continue;
+                cplx<T> lap = X[dx + 1] * Ac;
+                T mass = ((dx == 0) ? (T)-2 : (T)1) * Am;
+                if (dx == 0) { lap = lap + Bc; mass += Bm; }
+                const long long q = ((long long)kk * ny + jj) * nx + ii;
+                const cplx<T> kq = k2[q];
+                cplx<T> coef = mk<T>(lap.x * ih2 + mass * kq.x, lap.y * ih2 + mass * kq.y);
+                const cplx<T>* uq = u + q * nrhs + (long long)ch * RCH;
+#pragma unroll
+                for (int r = 0; r < RCH; ++r) cmac(acc[r], coef, uq[r]);
+            }
+        }
+    }
+    cplx<T>* yp = y + p * nrhs + (long long)ch * RCH;
+#pragma unroll
+    for (int r = 0; r < RCH; ++r) yp[r] = acc[r];
+}
+
+template <typename T, int RCH>
+void launch_t(const cplx<T>* u, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab, const helm_grid_desc& d, int nrhs,
+              const StencilW& w, cudaStream_t s) {
+    const long long total = (long long)d.nx * d.ny * d.nz * (nrhs / RCH);
+    const int threads = 256;
+    const long long blocks = (total + threads - 1) / threads;
+    stencil_kernel<T, RCH><<<(unsigned)blocks, threads, 0, s>>>(u, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w);
+}
+
+template <typename T>
+void dispatch(const cplx<T>* u, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab, const helm_grid_desc& d, int nrhs,
+              const StencilW& w, cudaStream_t s) {
+    if (nrhs % 4 == 0) launch_t<T, 4>(u, y, k2, tab, d, nrhs, w, s);
+    else if (nrhs % 2 == 0) launch_t<T, 2>(u, y, k2, tab, d, nrhs, w, s);
+    else launch_t<T, 1>(u, y, k2, tab, d, nrhs, w, s);
+}
+
+}  // namespace
+
+helm_status launch_stencil(helm_grid g, int prec, const void* u, void* y, int nrhs, cudaStream_t s) {
+    if (nrhs <= 0) return HELM_OK;
+    if (prec == HELM_PREC_FP64) {
+        dispatch<double>((const c128*)u, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, s);
+    } else {
+        dispatch<float>((const c64*)u, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, s);
+    }
+    HELM_LAUNCH_CHECK(g->ctx, "stencil_kernel");
+    return HELM_OK;
+}

@@ -1,0 +1,257 @@
+"""ctypes binding of ``libhelm.so`` (argument marshalling only).
+
+Names follow ``include/helm.h``.  Arrays are torch tensors; the binding
+passes their data pointers and the current CUDA stream.  All computation
+happens in the CUDA library; if the library is missing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libhelm.so")
+_lib = None
+_finalizing = False
+
+
+def _mark_finalizing():
+    global _finalizing
+    _finalizing = True
+
+
+import atexit as _atexit
+_atexit.register(_mark_finalizing)   # handles still alive at exit are left to process teardown
+
+OK, EINVAL, ENOMEM, ENOTCONV, ESINGULAR, ENONFINITE, ETIMEOUT, EBUSY, ECUDA, ENOTFOUND = range(10)
+TOP_DIRICHLET, TOP_PML = 0, 1
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_TF32X3 = 0, 1, 2, 3
+PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3}
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"helm status {status}: {msg}")
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double), ("freq_hz", C.c_double),
+                ("npml", C.c_int), ("pml_R", C.c_double), ("top_bc", C.c_int), ("weights", C.c_double * 7)]
+
+
+class OrasDesc(C.Structure):
+    _fields_ = [("px", C.c_int), ("py", C.c_int), ("pz", C.c_int), ("overlap", C.c_int), ("coarse_ratio", C.c_int),
+                ("interface_bc", C.c_int), ("factor_prec", C.c_int)]
+
+
+class GmresDesc(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("flexible", C.c_int),
+                ("basis_prec", C.c_int)]
+
+
+class RhsStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("true_relres", C.c_double),
+                ("est_relres", C.c_double)]
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_2103_14921_gb300.build.build()")
+    L = C.CDLL(_LIB_PATH)
+    vp, i32, st = C.c_void_p, C.c_int, C.c_int
+    sig = {
+        "helm_create": (st, [C.POINTER(vp), i32, vp, C.c_size_t]),
+        "helm_destroy": (None, [vp]),
+        "helm_last_error": (C.c_char_p, [vp]),
+        "helm_bytes_in_use": (C.c_size_t, [vp]),
+        "helm_launch_count": (C.c_uint64, [vp]),
+        "helm_fit_weights": (st, [C.c_double, C.c_double, C.POINTER(C.c_double)]),
+        "helm_setup_grid": (st, [vp, C.POINTER(GridDesc), vp, C.POINTER(vp)]),
+        "helm_destroy_grid": (None, [vp]),
+        "helm_apply": (st, [vp, i32, vp, vp, i32]),
+        "oras_factor": (st, [vp, C.POINTER(OrasDesc), C.POINTER(vp)]),
+        "oras_destroy": (None, [vp]),
+        "oras_apply": (st, [vp, vp, vp, i32]),
+        "oras_box_info": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+        "oras_plane_inverse": (st, [vp, i32, i32, vp]),
+        "oras_setup_seconds": (C.c_double, [vp]),
+        "gmres_solve": (st, [vp, vp, vp, i32, C.POINTER(GmresDesc), C.POINTER(RhsStats)]),
+    }
+    for name, (res, args) in sig.items():
+        if hasattr(L, name):
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+    _lib = L
+    return L
+
+
+def fit_weights(G_min=4.0, G_max=30.0):
+    """Stencil weights fitted by the library (host computation)."""
+    out = (C.c_double * 7)()
+    st = lib().helm_fit_weights(G_min, G_max, out)
+    if st:
+        raise HelmError(st, "helm_fit_weights")
+    return tuple(out)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    def __init__(self, device=0, stream=None, budget_bytes=0):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self._h = C.c_void_p()
+        st = lib().helm_create(C.byref(self._h), device, C.c_void_p(stream), budget_bytes)
+        if st:
+            raise HelmError(st, lib().helm_last_error(None).decode())
+        self.device = device
+
+    def check(self, st, what=""):
+        if st:
+            raise HelmError(st, f"{what}: {lib().helm_last_error(self._h).decode()}")
+
+    @property
+    def bytes_in_use(self):
+        return lib().helm_bytes_in_use(self._h)
+
+    @property
+    def launches(self):
+        return lib().helm_launch_count(self._h)
+
+    def close(self):
+        if self._h:
+            lib().helm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        if _finalizing:
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Grid:
+    """``helm_setup_grid``: one problem (grid, medium, frequency)."""
+
+    def __init__(self, ctx: Context, nx, ny, nz, h, freq_hz, c, npml=8, top_bc=TOP_DIRICHLET, pml_R=1e-3,
+                 weights=None):
+        import torch
+        if weights is None:
+            weights = fit_weights()
+        d = GridDesc(nx, ny, nz, h, freq_hz, npml, pml_R, top_bc, (C.c_double * 7)(*weights))
+        self.ctx = ctx
+        self.desc = d
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        if isinstance(c, np.ndarray):
+            c = torch.from_numpy(np.ascontiguousarray(c, dtype=np.complex128))
+        c = c.contiguous()
+        assert c.dtype == torch.complex128 and c.numel() == self.n
+        self._h = C.c_void_p()
+        ctx.check(lib().helm_setup_grid(ctx._h, C.byref(d), _ptr(c), C.byref(self._h)), "helm_setup_grid")
+
+    def apply(self, u, y=None, prec=PREC_FP64):
+        """``y = A u``; u is a CUDA tensor ``[nz, ny, nx, nrhs]`` complex128 (FP64) or complex64 (FP32)."""
+        import torch
+        want = torch.complex128 if prec == PREC_FP64 else torch.complex64
+        assert u.is_cuda and u.dtype == want and u.is_contiguous()
+        nrhs = u.numel() // self.n
+        if y is None:
+            y = torch.empty_like(u)
+        self.ctx.check(lib().helm_apply(self._h, prec, _ptr(u), _ptr(y), nrhs), "helm_apply")
+        return y
+
+    def close(self):
+        if self._h:
+            lib().helm_destroy_grid(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        if _finalizing:
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Oras:
+    """``oras_factor``: the two-level ORAS preconditioner with resident plane factors."""
+
+    def __init__(self, grid: Grid, parts, overlap, coarse_ratio=0, interface_bc=0, factor_prec=PREC_FP64):
+        d = OrasDesc(parts[0], parts[1], parts[2], overlap, coarse_ratio, interface_bc, factor_prec)
+        self.grid = grid
+        self.ctx = grid.ctx
+        self.desc = d
+        self._h = C.c_void_p()
+        self.ctx.check(lib().oras_factor(grid._h, C.byref(d), C.byref(self._h)), "oras_factor")
+
+    @property
+    def setup_seconds(self):
+        return lib().oras_setup_seconds(self._h)
+
+    def box_info(self, box):
+        nb = C.c_int()
+        lo = (C.c_int * 3)()
+        dims = (C.c_int * 3)()
+        self.ctx.check(lib().oras_box_info(self._h, box, C.byref(nb), lo, dims), "oras_box_info")
+        return nb.value, tuple(lo), tuple(dims)
+
+    def plane_inverse(self, box, plane):
+        import torch
+        _, _, dims = self.box_info(box)
+        m = dims[0] * dims[1]
+        out = torch.empty((m, m), dtype=torch.complex128, device="cuda")
+        self.ctx.check(lib().oras_plane_inverse(self._h, box, plane, _ptr(out)), "oras_plane_inverse")
+        return out
+
+    def apply(self, v, out=None):
+        import torch
+        assert v.is_cuda and v.dtype == torch.complex128 and v.is_contiguous()
+        nrhs = v.numel() // self.grid.n
+        if out is None:
+            out = torch.empty_like(v)
+        self.ctx.check(lib().oras_apply(self._h, _ptr(v), _ptr(out), nrhs), "oras_apply")
+        return out
+
+    def solve(self, b, x=None, tol=1e-6, restart=30, maxit=1000, flexible=True, basis_prec=PREC_FP64,
+              allow_notconv=False):
+        """``gmres_solve``; b is complex128 ``[nz, ny, nx, nrhs]`` (CUDA or pinned/pageable CPU tensor)."""
+        import torch
+        assert b.dtype == torch.complex128 and b.is_contiguous()
+        nrhs = b.numel() // self.grid.n
+        if x is None:
+            x = torch.empty_like(b)
+        d = GmresDesc(tol, restart, maxit, 1 if flexible else 0, basis_prec)
+        stats = (RhsStats * max(nrhs, 1))()
+        st = lib().gmres_solve(self._h, _ptr(b), _ptr(x), nrhs, C.byref(d), stats)
+        if st and not (allow_notconv and st == ENOTCONV):
+            self.ctx.check(st, "gmres_solve")
+        return x, [dict(iterations=s.iterations, converged=bool(s.converged), true_relres=s.true_relres,
+                        est_relres=s.est_relres) for s in stats[:nrhs]]
+
+    def close(self):
+        if self._h:
+            lib().oras_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        if _finalizing:
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
