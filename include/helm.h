@@ -89,6 +89,17 @@ size_t      helm_bytes_in_use(helm_ctx ctx);
 /* Number of CUDA kernel launches the library has issued on this context. */
 uint64_t    helm_launch_count(helm_ctx ctx);
 
+/* Per-kernel-family timing with CUDA events recorded on the context's stream
+ * around every launch of the instrumented families ("stencil", "sweep_gemv",
+ * "sweep_prep", "gj_update", "gj_panel", "arnoldi").  on = 1 enables (and
+ * clears the counters), 0 disables.  helm_profile_query synchronizes the
+ * stream and returns, for family `name`, the launches recorded, their summed
+ * device time in milliseconds and their summed algorithmic bytes (the data a
+ * launch must move at least once, as stated in each kernel's description).
+ * Returns HELM_ENOTFOUND for a family with no recorded launch. */
+helm_status helm_profile_enable(helm_ctx ctx, int on);
+helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launches, double* ms, double* bytes);
+
 /* ------------------------------------------------------------ grid / model */
 
 typedef struct {

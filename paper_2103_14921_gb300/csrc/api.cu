@@ -170,7 +170,7 @@ static void axis_table(int n, double h, int npml, bool low, bool high, double om
     }
 }
 
-static bool is_device_pointer(const void* p) {
+bool is_device_pointer(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -255,6 +255,10 @@ extern "C" helm_status helm_setup_grid(helm_ctx ctx, const helm_grid_desc* d, co
 
 extern "C" void helm_destroy_grid(helm_grid g) {
     if (!g) return;
+    if (g->refs > 0) {
+        g->destroy_pending = true;   // freed when its last ORAS handle is destroyed
+        return;
+    }
     helm_ctx ctx = g->ctx;
     cudaStreamSynchronize(ctx->stream);
     const long long n = g->n;

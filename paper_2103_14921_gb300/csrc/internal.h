@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -37,6 +38,21 @@ typedef cplx<float> c64;
 
 // ----------------------------------------------------------------- objects
 
+// Event-pair timing of instrumented kernel families (helm_profile_*).
+struct ProfRecord {
+    cudaEvent_t a, b;
+    double bytes;
+    int family;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<std::string> names;
+    std::vector<ProfRecord> pending;
+    std::vector<cudaEvent_t> pool;
+    std::vector<uint64_t> launches;
+    std::vector<double> ms, bytes;
+};
+
 struct helm_ctx_s {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -47,7 +63,13 @@ struct helm_ctx_s {
     int sm_count = 0;
     int children = 0;          // live grids; helm_destroy defers the delete until they are gone
     bool destroy_pending = false;
+    Profiler prof;
 };
+
+// Bracket one launch of an instrumented family with events on the context's stream.
+int prof_begin(helm_ctx ctx, const char* family);   // returns a token (-1 when profiling is off)
+void prof_end(helm_ctx ctx, int token, double bytes);
+void prof_drain(helm_ctx ctx);                       // fold completed records into the totals
 
 // Stencil weights in product form (see stencil.cu).
 struct StencilW {
@@ -68,6 +90,52 @@ struct helm_grid_s {
     c64* tabf = nullptr;
     std::vector<c128> htab;    // host copy of the tables
     int refs = 0;              // ORAS handles built on this grid
+    bool destroy_pending = false;   // helm_destroy_grid called while ORAS handles were alive
+};
+
+// One box of a plane-by-plane block LU (a fine subdomain, or the whole coarse grid).
+struct BoxInfo {
+    int lo[3], dims[3];        // origin and extent in (x, y, z)
+    int core_lo[3], core_hi[3];
+    int m;                     // dims[0] * dims[1]: unknowns per z-plane
+    int pad;
+    long long loc_off;         // index of the box's first node in the concatenated local vectors
+    long long fac_off;         // index of the first entry of S_0^{-1} in the factor storage
+};
+
+// Plane-by-plane block LU of a set of boxes: the local operators as 27
+// coefficients per node and the dense inverses S_k^{-1}, all resident.
+struct PlaneSet {
+    int prec = HELM_PREC_FP64;  // FP64 -> complex128 storage, otherwise complex64
+    int nbox = 0, m_max = 0, bz_max = 0;
+    long long nloc = 0;         // total local nodes
+    size_t fac_entries = 0;     // total factor entries
+    std::vector<BoxInfo> hbox;
+    BoxInfo* dbox = nullptr;
+    void* coef = nullptr;       // [nloc][27] in the set's precision
+    void* G = nullptr;          // factors, per box: bz planes of m x m row-major
+    size_t esize() const { return prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64); }
+};
+
+struct helm_oras_s {
+    helm_grid g = nullptr;
+    helm_oras_desc d{};
+    PlaneSet fine, coarse;
+    int cdims[3] = {0, 0, 0};
+    long long nc = 0;
+    int* owner = nullptr;       // device: per axis owner part index, [nx + ny + nz]
+    int* cuts = nullptr;        // device: per axis cut positions, [px+1 + py+1 + pz+1]
+    double setup_s = 0;
+    // apply scratch (grown on demand)
+    int cap_nrhs = 0;
+    void* loc = nullptr;        // local vectors, fine factor precision
+    void* rbuf = nullptr;       // sweep right-hand sides, nbox * m_max * nrhs
+    c128* cvec = nullptr;       // coarse vector
+    c128* crbuf = nullptr;
+    void* qf = nullptr;         // fine coarse-correction vector (work precision)
+    void* tf = nullptr;         // fine residual v - A q (work precision)
+    int cap_wp = -1;
+    size_t scratch_bytes = 0;
 };
 
 // ----------------------------------------------------------------- helpers
@@ -96,5 +164,16 @@ void dev_free(helm_ctx ctx, void* p, size_t bytes);
 // ----------------------------------------------------------------- kernels (launchers)
 
 helm_status launch_stencil(helm_grid g, int prec, const void* u, void* y, int nrhs, cudaStream_t s);
+// y = b - A u (same precisions as launch_stencil)
+helm_status launch_stencil_sub(helm_grid g, int prec, const void* u, const void* b, void* y, int nrhs, cudaStream_t s);
+// out = M^{-1} v on vectors of precision wp (HELM_PREC_FP64: complex128, HELM_PREC_FP32: complex64), device pointers.
+helm_status oras_apply_wp(helm_oras o, int wp, const void* v, void* out, int nrhs);
+bool is_device_pointer(const void* p);
 helm_status launch_k2(helm_grid g);
 helm_status launch_max_real(helm_ctx ctx, const c128* v, long long n, double* host_out);
+
+// plane-by-plane block LU (planelu.cu)
+helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P);
+void planeset_free(helm_ctx ctx, PlaneSet& P);
+helm_status planeset_factor(helm_ctx ctx, PlaneSet& P, int* singular);
+helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st);

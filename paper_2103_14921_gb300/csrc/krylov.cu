@@ -1,0 +1,502 @@
+// Right-preconditioned restarted GMRES / flexible GMRES (the paper's Krylov
+// solver, with M^{-1} of Eq. 2lvl), one independent Krylov space per
+// right-hand side, all right-hand sides batched in every kernel.
+//
+//   x0 = 0, r = b, beta = ||r||, v_0 = r / beta, g = beta e_0
+//   for j = 0 .. restart-1:
+//     z_j = M^{-1} v_j ; w = A z_j
+//     CGS2: h = V^H w, w -= V h, h' = V^H w, w -= V h', h += h' (FP64 sums)
+//     h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
+//     complex Givens rotations (real cosine) on column j, g updated,
+//     |g_{j+1}| / ||b|| <= tol stops that column's cycle
+//   y = R^{-1} g ; x += Z y (FGMRES) or x += M^{-1} (V y) (GMRES)
+//   true residual ||b - A x|| / ||b|| in FP64; restart the columns above tol.
+//
+// Vectors (basis V, Z, w) are complex128 or complex64 (basis_prec); x, the
+// true residual, the Hessenberg matrix, the rotations and every reduction
+// are FP64.  Reductions are two-pass (per-block partials, then a fixed-order
+// sum), so results do not depend on scheduling.
+#include <math.h>
+#include <string.h>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+constexpr int IC = 8;   // basis vectors handled per pass of a dot-product kernel
+
+// Number of reduction blocks: the grid stride (blocks x 256) must be a multiple
+// of nrhs so that every thread only ever touches one right-hand side.
+inline int red_blocks(helm_ctx ctx, long long elems, int nrhs) {
+    int a = RED_THREADS, b = nrhs;
+    while (b) { const int t = a % b; a = b; b = t; }
+    const long long q = nrhs / a;   // nrhs / gcd(256, nrhs)
+    long long nb = (elems + RED_THREADS - 1) / RED_THREADS;
+    const long long cap = std::max(q, ((long long)std::max(1, ctx->sm_count) * 8 / q) * q);
+    nb = ((nb + q - 1) / q) * q;
+    return (int)std::min(nb, cap);
+}
+
+template <typename T> __device__ __forceinline__ c128 widen(cplx<T> a) { return mk<double>((double)a.x, (double)a.y); }
+
+// partial[blk][i][r] = sum over this block's elements of conj(V_i[e]) w[e], i in [i0, i0+ni)
+// With a block of 256 consecutive thread ids every r = e % nrhs appears; each thread keeps one r.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
+                                                           const cplx<T>* __restrict__ w, long long n_el, int nrhs,
+                                                           int i0, int ni, c128* __restrict__ partial, int ldp) {
+    __shared__ c128 s[RED_THREADS];
+    const long long t = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
+    const long long stride = (long long)gridDim.x * RED_THREADS;
+    for (int ib = 0; ib < ni; ib += IC) {
+        c128 acc[IC];
+#pragma unroll
+        for (int q = 0; q < IC; ++q) acc[q] = mk<double>(0, 0);
+        for (long long e = t; e < n_el; e += stride) {
+            const c128 wv = widen(w[e]);
+#pragma unroll
+            for (int q = 0; q < IC; ++q)
+                if (ib + q < ni) cmac_conj(acc[q], widen(V[(long long)(i0 + ib + q) * vstride + e]), wv);
+        }
+        for (int q = 0; q < IC && ib + q < ni; ++q) {
+            s[threadIdx.x] = acc[q];
+            __syncthreads();
+            if (threadIdx.x < min(nrhs, RED_THREADS)) {
+                c128 sum = mk<double>(0, 0);
+                for (int u = threadIdx.x; u < RED_THREADS; u += nrhs) sum = sum + s[u];
+                const int r = (int)(((long long)blockIdx.x * RED_THREADS + threadIdx.x) % nrhs);
+                partial[((long long)blockIdx.x * ldp + (i0 + ib + q)) * nrhs + r] = sum;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// out[i][r] (+)= sum_blk partial[blk][i][r], fixed order
+__global__ void finish_dots(const c128* __restrict__ partial, int nblk, int ldp, int ni, int nrhs,
+                            c128* __restrict__ H, int ldh_i, int ldh_r, int col, int accumulate) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ni * nrhs) return;
+    const int i = e / nrhs, r = e % nrhs;
+    c128 sum = mk<double>(0, 0);
+    for (int b = 0; b < nblk; ++b) sum = sum + partial[((long long)b * ldp + i) * nrhs + r];
+    c128* dst = H + (long long)r * ldh_r + (long long)i * ldh_i + col;
+    *dst = accumulate ? *dst + sum : sum;
+}
+
+// w[e] -= sum_{i<ni} V_i[e] h_i[r]   (h from H column col, last pass's values only: hsrc)
+template <typename T>
+__global__ void update_kernel(const cplx<T>* __restrict__ V, long long vstride, cplx<T>* __restrict__ w, long long n_el,
+                              int nrhs, int ni, const c128* __restrict__ hsrc) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % nrhs);
+        c128 acc = widen(w[e]);
+        for (int i = 0; i < ni; ++i) {
+            const c128 h = hsrc[(long long)i * nrhs + r];
+            const c128 v = widen(V[(long long)i * vstride + e]);
+            acc.x -= h.x * v.x - h.y * v.y;
+            acc.y -= h.x * v.y + h.y * v.x;
+        }
+        w[e] = mk<T>((T)acc.x, (T)acc.y);
+    }
+}
+
+// partial[blk][r] = sum |v[e]|^2 over this block's elements
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) norm2_kernel(const cplx<T>* __restrict__ v, long long n_el, int nrhs,
+                                                            double* __restrict__ partial) {
+    __shared__ double s[RED_THREADS];
+    const long long t = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
+    const long long stride = (long long)gridDim.x * RED_THREADS;
+    double acc = 0.0;
+    for (long long e = t; e < n_el; e += stride) {
+        const c128 a = widen(v[e]);
+        acc += a.x * a.x + a.y * a.y;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < min(nrhs, RED_THREADS)) {
+        double sum = 0.0;
+        for (int u = threadIdx.x; u < RED_THREADS; u += nrhs) sum += s[u];
+        const int r = (int)(((long long)blockIdx.x * RED_THREADS + threadIdx.x) % nrhs);
+        partial[(long long)blockIdx.x * nrhs + r] = sum;
+    }
+}
+
+__global__ void finish_norm2(const double* __restrict__ partial, int nblk, int nrhs, double* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    double sum = 0.0;
+    for (int b = 0; b < nblk; ++b) sum += partial[(long long)b * nrhs + r];
+    out[r] = sqrt(sum);
+}
+
+// dst[e] = src[e] * scale[r]  (scale = 0 -> zero)
+template <typename TS, typename TD>
+__global__ void scale_copy(const cplx<TS>* __restrict__ src, cplx<TD>* __restrict__ dst, long long n_el, int nrhs,
+                           const double* __restrict__ scale) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
+        const double s = scale[e % nrhs];
+        const cplx<TS> a = src[e];
+        dst[e] = mk<TD>((TD)(s * (double)a.x), (TD)(s * (double)a.y));
+    }
+}
+
+// Per-rhs solver state (FP64), one thread per rhs.
+struct RhsState {
+    double bnorm;
+    int active;       // column still iterating this cycle
+    int steps;        // Krylov steps taken in this cycle
+    int iters;        // total iterations
+    int done;         // finished (converged or out of iterations)
+    double est;       // last residual estimate (relative)
+};
+
+// Start of a cycle: inv[r] = 1/beta for active columns, g = beta e_0.
+__global__ void cycle_start(RhsState* __restrict__ S, const double* __restrict__ beta, double* __restrict__ inv,
+                            c128* __restrict__ g, int m, int nrhs) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    RhsState& s = S[r];
+    s.steps = 0;
+    s.active = !s.done && beta[r] > 0.0;
+    inv[r] = s.active ? 1.0 / beta[r] : 0.0;
+    for (int i = 0; i <= m; ++i) g[(long long)r * (m + 1) + i] = mk<double>(0, 0);
+    g[(long long)r * (m + 1)] = mk<double>(s.active ? beta[r] : 0.0, 0.0);
+}
+
+// Column j of H for every rhs: apply earlier rotations, make a new one, update g and the estimate.
+// H[r][i][j] is (m+1) x m per rhs; hnorm[r] = ||w|| = H[j+1][j]; inv[r] <- 1/hnorm (or 0).
+__global__ void givens_step(RhsState* __restrict__ S, c128* __restrict__ H, double* __restrict__ cs,
+                            c128* __restrict__ sn, c128* __restrict__ g, const double* __restrict__ hnorm,
+                            double* __restrict__ inv, int j, int m, int nrhs, double tol, int maxit,
+                            int* __restrict__ running) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    RhsState& s = S[r];
+    if (!s.active) {
+        inv[r] = 0.0;
+        return;
+    }
+    c128* h = H + (long long)r * (m + 1) * m;
+    double* c = cs + (long long)r * m;
+    c128* sv = sn + (long long)r * m;
+    c128* gg = g + (long long)r * (m + 1);
+    const double hn = hnorm[r];
+    h[(long long)(j + 1) * m + j] = mk<double>(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+        const c128 a = h[(long long)i * m + j], b = h[(long long)(i + 1) * m + j];
+        const c128 si = sv[i];
+        const c128 sb = si * b;
+        const c128 csa = mk<double>(c[i] * a.x, c[i] * a.y);
+        h[(long long)i * m + j] = csa + sb;
+        // -conj(s) a + c b
+        const c128 sca = mk<double>(si.x * a.x + si.y * a.y, si.x * a.y - si.y * a.x);
+        h[(long long)(i + 1) * m + j] = mk<double>(c[i] * b.x - sca.x, c[i] * b.y - sca.y);
+    }
+    const c128 a = h[(long long)j * m + j], b = h[(long long)(j + 1) * m + j];
+    const double na = hypot(a.x, a.y), nbv = hypot(b.x, b.y);
+    double cc;
+    c128 ss;
+    if (nbv == 0.0) {
+        cc = 1.0;
+        ss = mk<double>(0, 0);
+    } else if (na == 0.0) {
+        cc = 0.0;
+        ss = mk<double>(b.x / nbv, -b.y / nbv);
+    } else {
+        const double t = hypot(na, nbv);
+        cc = na / t;
+        const c128 ua = mk<double>(a.x / na, a.y / na);
+        const c128 cb = mk<double>(b.x / t, -b.y / t);
+        ss = ua * cb;
+    }
+    c[j] = cc;
+    sv[j] = ss;
+    h[(long long)j * m + j] = mk<double>(cc * a.x, cc * a.y) + ss * b;
+    h[(long long)(j + 1) * m + j] = mk<double>(0, 0);
+    const c128 gj = gg[j];
+    gg[j + 1] = mk<double>(-(ss.x * gj.x + ss.y * gj.y), -(ss.x * gj.y - ss.y * gj.x));
+    gg[j] = mk<double>(cc * gj.x, cc * gj.y);
+    s.steps = j + 1;
+    s.iters += 1;
+    s.est = hypot(gg[j + 1].x, gg[j + 1].y) / s.bnorm;
+    const bool stop = s.est <= tol || hn == 0.0 || s.iters >= maxit || j + 1 >= m;
+    inv[r] = (hn > 0.0 && !stop) ? 1.0 / hn : 0.0;
+    if (stop) s.active = 0;
+    else atomicAdd(running, 1);
+}
+
+// y = R^{-1} g for the steps taken this cycle (upper-triangular back substitution).
+__global__ void back_substitute(const RhsState* __restrict__ S, const c128* __restrict__ H, const c128* __restrict__ g,
+                                c128* __restrict__ y, int m, int nrhs) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    const int nsteps = S[r].steps;
+    const c128* h = H + (long long)r * (m + 1) * m;
+    const c128* gg = g + (long long)r * (m + 1);
+    for (int i = 0; i < m; ++i) y[(long long)i * nrhs + r] = mk<double>(0, 0);
+    for (int i = nsteps - 1; i >= 0; --i) {
+        c128 acc = gg[i];
+        for (int k = i + 1; k < nsteps; ++k) {
+            const c128 p = h[(long long)i * m + k] * y[(long long)k * nrhs + r];
+            acc = acc - p;
+        }
+        const c128 d = h[(long long)i * m + i];
+        const double den = d.x * d.x + d.y * d.y;
+        y[(long long)i * nrhs + r] =
+            den > 0 ? mk<double>((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den) : mk<double>(0, 0);
+    }
+}
+
+// x[e] += sum_i Zb_i[e] y_i[r]  (FP64 accumulation into complex128 x)   -- or u = sum_i Zb_i y_i (into TU)
+template <typename T, typename TO, bool ACC>
+__global__ void combine_kernel(const cplx<T>* __restrict__ Zb, long long zstride, const c128* __restrict__ y,
+                               cplx<TO>* __restrict__ x, long long n_el, int nrhs, int ni) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % nrhs);
+        c128 acc = ACC ? widen(x[e]) : mk<double>(0, 0);
+        for (int i = 0; i < ni; ++i) cmac(acc, widen(Zb[(long long)i * zstride + e]), y[(long long)i * nrhs + r]);
+        x[e] = mk<TO>((TO)acc.x, (TO)acc.y);
+    }
+}
+
+// x += u (u widened to FP64)
+template <typename T>
+__global__ void accum_widen(const cplx<T>* __restrict__ u, c128* __restrict__ x, long long n_el) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x)
+        x[e] = x[e] + widen(u[e]);
+}
+
+__global__ void finite_check(const c128* __restrict__ v, long long n_el, int* __restrict__ bad) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(v[e].x) || !isfinite(v[e].y)) atomicOr(bad, 1);
+}
+
+// ------------------------------------------------------------------ host driver
+
+struct Work {
+    helm_ctx ctx;
+    std::vector<std::pair<void*, size_t>> allocs;
+    helm_status alloc(void** p, size_t bytes, const char* what) {
+        helm_status rc = dev_alloc(ctx, p, bytes, what);
+        if (!rc && *p) allocs.push_back({*p, bytes});
+        return rc;
+    }
+    ~Work() {
+        cudaStreamSynchronize(ctx->stream);
+        for (auto& a : allocs) dev_free(ctx, a.first, a.second);
+    }
+};
+
+template <typename T>
+helm_status solve_t(helm_oras o, const c128* b, c128* x, int nrhs, const helm_gmres_desc& D, helm_rhs_stats* stats) {
+    helm_grid g = o->g;
+    helm_ctx ctx = g->ctx;
+    cudaStream_t st = ctx->stream;
+    const int wp = sizeof(T) == 8 ? HELM_PREC_FP64 : HELM_PREC_FP32;
+    const int m = D.restart;
+    const long long N = g->n;
+    const long long nel = N * nrhs;
+    const bool flex = D.flexible != 0;
+    Work W{ctx};
+    cplx<T>*V = nullptr, *Zb = nullptr, *w = nullptr, *u = nullptr;
+    c128 *r = nullptr, *H = nullptr, *sn = nullptr, *gv = nullptr, *y = nullptr, *part = nullptr, *hpass = nullptr;
+    double *cs = nullptr, *dpart = nullptr, *beta = nullptr, *inv = nullptr, *hn = nullptr;
+    RhsState* S = nullptr;
+    int* running = nullptr;
+    const int nblk = red_blocks(ctx, nel, nrhs);
+    const int ldp = m + 1;
+    HELM_TRY(W.alloc((void**)&V, (size_t)(m + 1) * nel * sizeof(cplx<T>), "Krylov basis V"));
+    if (flex) HELM_TRY(W.alloc((void**)&Zb, (size_t)m * nel * sizeof(cplx<T>), "Krylov basis Z"));
+    HELM_TRY(W.alloc((void**)&w, nel * sizeof(cplx<T>), "Arnoldi vector"));
+    HELM_TRY(W.alloc((void**)&u, nel * sizeof(cplx<T>), "preconditioned vector"));
+    HELM_TRY(W.alloc((void**)&r, nel * sizeof(c128), "residual"));
+    HELM_TRY(W.alloc((void**)&H, (size_t)nrhs * (m + 1) * m * sizeof(c128), "Hessenberg"));
+    HELM_TRY(W.alloc((void**)&sn, (size_t)nrhs * m * sizeof(c128), "Givens sines"));
+    HELM_TRY(W.alloc((void**)&cs, (size_t)nrhs * m * sizeof(double), "Givens cosines"));
+    HELM_TRY(W.alloc((void**)&gv, (size_t)nrhs * (m + 1) * sizeof(c128), "Givens rhs"));
+    HELM_TRY(W.alloc((void**)&y, (size_t)nrhs * m * sizeof(c128), "least-squares solution"));
+    HELM_TRY(W.alloc((void**)&part, (size_t)nblk * ldp * nrhs * sizeof(c128), "dot partials"));
+    HELM_TRY(W.alloc((void**)&hpass, (size_t)ldp * nrhs * sizeof(c128), "dot pass"));
+    HELM_TRY(W.alloc((void**)&dpart, (size_t)nblk * nrhs * sizeof(double), "norm partials"));
+    HELM_TRY(W.alloc((void**)&beta, nrhs * sizeof(double), "norms"));
+    HELM_TRY(W.alloc((void**)&inv, nrhs * sizeof(double), "inverse norms"));
+    HELM_TRY(W.alloc((void**)&hn, nrhs * sizeof(double), "new norms"));
+    HELM_TRY(W.alloc((void**)&S, nrhs * sizeof(RhsState), "rhs state"));
+    HELM_TRY(W.alloc((void**)&running, 2 * sizeof(int), "running flag"));
+    const unsigned eg = (unsigned)std::min<long long>((nel + 255) / 256, (long long)ctx->sm_count * 16);
+    const unsigned rg = (unsigned)((nrhs + 127) / 128);
+
+    auto norms = [&](const auto* vec, double* out) {
+        norm2_kernel<<<nblk, RED_THREADS, 0, st>>>(vec, nel, nrhs, dpart);
+        finish_norm2<<<rg, 128, 0, st>>>(dpart, nblk, nrhs, out);
+        ctx->launches += 2;
+    };
+    auto dots_into = [&](const cplx<T>* Vb, const cplx<T>* vec, int ni, c128* dst, int ldh_i, int ldh_r, int col,
+                         int accumulate) {
+        const int tk = prof_begin(ctx, "arnoldi");
+        dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, nrhs, 0, ni, part, ldp);
+        prof_end(ctx, tk, (double)(ni + 1) * nel * sizeof(cplx<T>));
+        finish_dots<<<(ni * nrhs + 127) / 128, 128, 0, st>>>(part, nblk, ldp, ni, nrhs, dst, ldh_i, ldh_r, col,
+                                                             accumulate);
+        ctx->launches += 2;
+    };
+
+    // ||b||, finite check
+    {
+        int* bad = running + 1;
+        cudaMemsetAsync(bad, 0, sizeof(int), st);
+        finite_check<<<eg, 256, 0, st>>>(b, nel, bad);
+        ctx->launches++;
+        int hbad = 0;
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+        HELM_CUDA(ctx, cudaStreamSynchronize(st));
+        if (hbad) return set_error(ctx, HELM_ENONFINITE, "gmres_solve: right-hand side has NaN/Inf");
+    }
+    norms(b, beta);
+    std::vector<double> hb(nrhs);
+    HELM_CUDA(ctx, cudaMemcpyAsync(hb.data(), beta, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<RhsState> hs(nrhs);
+    for (int i = 0; i < nrhs; ++i) {
+        hs[i] = RhsState{hb[i], 0, 0, 0, hb[i] == 0.0 ? 1 : 0, 0.0};
+    }
+    HELM_CUDA(ctx, cudaMemcpyAsync(S, hs.data(), nrhs * sizeof(RhsState), cudaMemcpyHostToDevice, st));
+    HELM_CUDA(ctx, cudaMemsetAsync(x, 0, nel * sizeof(c128), st));
+    HELM_CUDA(ctx, cudaMemcpyAsync(r, b, nel * sizeof(c128), cudaMemcpyDeviceToDevice, st));
+    std::vector<double> true_rel(nrhs, 0.0);
+
+    for (int cycle = 0;; ++cycle) {
+        // beta = ||r||, v_0 = r / beta
+        norms(r, beta);
+        cycle_start<<<rg, 128, 0, st>>>(S, beta, inv, gv, m, nrhs);
+        scale_copy<double, T><<<eg, 256, 0, st>>>(r, V, nel, nrhs, inv);
+        ctx->launches += 2;
+        int jdone = 0;
+        for (int j = 0; j < m; ++j) {
+            cplx<T>* vj = V + (long long)j * nel;
+            cplx<T>* zj = flex ? Zb + (long long)j * nel : u;
+            HELM_TRY(oras_apply_wp(o, wp, vj, zj, nrhs));
+            HELM_TRY(launch_stencil(g, wp, zj, w, nrhs, st));
+            // CGS2, column j of H for every rhs: H[r][i][j]
+            dots_into(V, w, j + 1, hpass, nrhs, 1, 0, 0);
+            {
+                const int tk = prof_begin(ctx, "arnoldi");
+                update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, nrhs, j + 1, hpass);
+                prof_end(ctx, tk, (double)(j + 3) * nel * sizeof(cplx<T>));
+            }
+            ctx->launches++;
+            // pass-1 coefficients into H column j
+            finish_dots<<<((j + 1) * nrhs + 127) / 128, 128, 0, st>>>(part, nblk, ldp, j + 1, nrhs, H, m, (m + 1) * m,
+                                                                     j, 0);
+            ctx->launches++;
+            dots_into(V, w, j + 1, hpass, nrhs, 1, 0, 0);
+            {
+                const int tk = prof_begin(ctx, "arnoldi");
+                update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, nrhs, j + 1, hpass);
+                prof_end(ctx, tk, (double)(j + 3) * nel * sizeof(cplx<T>));
+            }
+            ctx->launches++;
+            finish_dots<<<((j + 1) * nrhs + 127) / 128, 128, 0, st>>>(part, nblk, ldp, j + 1, nrhs, H, m, (m + 1) * m,
+                                                                     j, 1);
+            ctx->launches++;
+            norms(w, hn);
+            cudaMemsetAsync(running, 0, sizeof(int), st);
+            givens_step<<<rg, 128, 0, st>>>(S, H, cs, sn, gv, hn, inv, j, m, nrhs, D.tol, D.maxit, running);
+            scale_copy<T, T><<<eg, 256, 0, st>>>(w, V + (long long)(j + 1) * nel, nel, nrhs, inv);
+            ctx->launches += 2;
+            int hrun = 0;
+            HELM_CUDA(ctx, cudaMemcpyAsync(&hrun, running, sizeof(int), cudaMemcpyDeviceToHost, st));
+            HELM_CUDA(ctx, cudaStreamSynchronize(st));
+            HELM_CUDA(ctx, cudaGetLastError());
+            jdone = j + 1;
+            if (hrun == 0) break;
+        }
+        // x update with the steps taken in this cycle
+        back_substitute<<<rg, 128, 0, st>>>(S, H, gv, y, m, nrhs);
+        ctx->launches++;
+        if (flex) {
+            combine_kernel<T, double, true><<<eg, 256, 0, st>>>(Zb, nel, y, x, nel, nrhs, jdone);
+            ctx->launches++;
+        } else {
+            combine_kernel<T, T, false><<<eg, 256, 0, st>>>(V, nel, y, w, nel, nrhs, jdone);
+            ctx->launches++;
+            HELM_TRY(oras_apply_wp(o, wp, w, u, nrhs));
+            accum_widen<T><<<eg, 256, 0, st>>>(u, x, nel);
+            ctx->launches++;
+        }
+        // true residual r = b - A x (FP64)
+        HELM_TRY(launch_stencil_sub(g, HELM_PREC_FP64, x, b, r, nrhs, st));
+        norms(r, beta);
+        HELM_CUDA(ctx, cudaMemcpyAsync(hs.data(), S, nrhs * sizeof(RhsState), cudaMemcpyDeviceToHost, st));
+        std::vector<double> rn(nrhs);
+        HELM_CUDA(ctx, cudaMemcpyAsync(rn.data(), beta, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA(ctx, cudaStreamSynchronize(st));
+        bool any = false;
+        for (int i = 0; i < nrhs; ++i) {
+            if (hs[i].done) continue;
+            true_rel[i] = hs[i].bnorm > 0 ? rn[i] / hs[i].bnorm : 0.0;
+            if (!std::isfinite(true_rel[i])) return set_error(ctx, HELM_ENONFINITE, "gmres_solve: residual is NaN/Inf");
+            if (true_rel[i] <= D.tol || hs[i].iters >= D.maxit) hs[i].done = 1;
+            else any = true;
+        }
+        HELM_CUDA(ctx, cudaMemcpyAsync(S, hs.data(), nrhs * sizeof(RhsState), cudaMemcpyHostToDevice, st));
+        if (!any) break;
+    }
+    HELM_CUDA(ctx, cudaStreamSynchronize(st));
+    bool all = true;
+    for (int i = 0; i < nrhs; ++i) {
+        const bool conv = true_rel[i] <= D.tol;
+        all = all && conv;
+        if (stats) stats[i] = helm_rhs_stats{hs[i].iters, conv ? 1 : 0, true_rel[i], hs[i].est};
+    }
+    if (!all) return set_error(ctx, HELM_ENOTCONV, "gmres_solve: some columns did not reach tol within maxit");
+    return HELM_OK;
+}
+
+}  // namespace
+
+extern "C" helm_status gmres_solve(helm_oras o, const void* b, void* x, int nrhs, const helm_gmres_desc* d,
+                                   helm_rhs_stats* stats) {
+    if (!o) return HELM_EINVAL;
+    helm_ctx ctx = o->g->ctx;
+    if (!b || !x || !d || nrhs < 0) return set_error(ctx, HELM_EINVAL, "gmres_solve: invalid argument");
+    if (!(d->tol > 0) || d->restart < 1 || d->restart > 200 || d->maxit < 1 ||
+        (d->basis_prec != HELM_PREC_FP64 && d->basis_prec != HELM_PREC_FP32))
+        return set_error(ctx, HELM_EINVAL, "gmres_solve: invalid solver description");
+    if (nrhs == 0) return HELM_OK;
+    if (nrhs > 256) return set_error(ctx, HELM_EINVAL, "gmres_solve: at most 256 right-hand sides per call");
+    HELM_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t bytes = (size_t)o->g->n * nrhs * sizeof(c128);
+    const bool bdev = is_device_pointer(b), xdev = is_device_pointer(x);
+    c128 *bd = (c128*)b, *xd = (c128*)x;
+    void* stage_b = nullptr;
+    void* stage_x = nullptr;
+    if (!bdev) {
+        HELM_TRY(dev_alloc(ctx, &stage_b, bytes, "staged b"));
+        HELM_CUDA(ctx, cudaMemcpyAsync(stage_b, b, bytes, cudaMemcpyHostToDevice, st));
+        bd = (c128*)stage_b;
+    }
+    if (!xdev) {
+        helm_status rc = dev_alloc(ctx, &stage_x, bytes, "staged x");
+        if (rc) {
+            dev_free(ctx, stage_b, bytes);
+            return rc;
+        }
+        xd = (c128*)stage_x;
+    }
+    helm_status rc = d->basis_prec == HELM_PREC_FP64 ? solve_t<double>(o, bd, xd, nrhs, *d, stats)
+                                                     : solve_t<float>(o, bd, xd, nrhs, *d, stats);
+    if (!xdev && (rc == HELM_OK || rc == HELM_ENOTCONV)) {
+        cudaError_t e = cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_check(ctx, e, "copy x to host");
+    }
+    cudaStreamSynchronize(st);
+    dev_free(ctx, stage_b, bytes);
+    dev_free(ctx, stage_x, bytes);
+    return rc;
+}

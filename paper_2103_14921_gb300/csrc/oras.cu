@@ -1,16 +1,536 @@
-// ORAS preconditioner (Eq. oras, Eq. 2lvl): placeholder entry points until the
-// local factorisation kernels land.
+// Two-level ORAS preconditioner (Eq. 2lvl, Eq. oras):
+//   M^{-1} v = M1^{-1} (v - A Q v) + Q v,  Q = Z E^{-1} Z^T,  E = Z^T A Z,
+//   M1^{-1}  = sum_i R_i^T D_i A_i^{-1} R_i.
+//
+// * Box subdomains: axis a is cut into p_a cores at floor(t n_a / p_a); each
+//   box is its core grown by `overlap` nodes on every side that is not a
+//   global face.  R_i is the Boolean gather of the box nodes; D_i is the
+//   owner partition of unity (1 on the core, 0 on the overlap), so the sum
+//   over boxes reduces to a gather from each node's owner box: deterministic,
+//   no atomics.
+// * A_i: the rows of A for the box nodes; a stencil neighbour outside the box
+//   across an interface face is folded onto the clamped in-box node times
+//   rho_p = exp(i k_p h) per crossed face (k_p = omega / c at the row node),
+//   an absorbing condition exact for waves leaving the box normally.  With
+//   interface_bc = 1 the neighbour is dropped instead (RAS).
+// * Coarse space: nodes at fine indices r J, trilinear hats; E = Z^T A Z is a
+//   27-point operator on the coarse grid, assembled by probing A with Z e_c
+//   for the 27 colours c = J mod 3, and factored plane by plane in FP64.
+// * Local solves and the coarse solve use the plane-by-plane block LU of
+//   planelu.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "coef.cuh"
 #include "internal.h"
 
-extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc*, helm_oras* out) {
-    if (out) *out = nullptr;
-    return set_error(g ? g->ctx : nullptr, HELM_EINVAL, "oras_factor: not built yet");
+namespace {
+
+// ------------------------------------------------------------------ local operators
+
+// coef_out[(loc_off + l) * 27 + d'] = sum over offsets d folding onto d' of A_row(d) * rho^crossed
+template <typename TO>
+__global__ void build_local_coef(const BoxInfo* __restrict__ boxes, const c128* __restrict__ tab,
+                                 const c128* __restrict__ k2, const c128* __restrict__ c, int nx, int ny, int nz,
+                                 StencilW w, double omega, double h, int dirichlet, cplx<TO>* __restrict__ out) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const long long nl = (long long)B.m * B.dims[2];
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (long long)gridDim.x * blockDim.x) {
+        const int li = (int)(l % B.dims[0]);
+        const int lj = (int)((l / B.dims[0]) % B.dims[1]);
+        const int lk = (int)(l / B.m);
+        const int gi = B.lo[0] + li, gj = B.lo[1] + lj, gk = B.lo[2] + lk;
+        c128 a[27], loc[27];
+        global_row_coef27(tab, k2, nx, ny, nz, w, gi, gj, gk, a);
+        for (int d = 0; d < 27; ++d) loc[d] = mk<double>(0, 0);
+        const c128 cv = c[((long long)gk * ny + gj) * nx + gi];
+        const double den = cv.x * cv.x + cv.y * cv.y;
+        const double kr = omega * cv.x / den, ki = -omega * cv.y / den;   // k = omega / c
+        const double mag = exp(-ki * h);
+        c128 rho = mk<double>(mag * cos(kr * h), mag * sin(kr * h));
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const c128 v = a[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+                    if (v.x == 0.0 && v.y == 0.0) continue;
+                    const int qi = li + dx, qj = lj + dy, qk = lk + dz;
+                    int crossed = 0;
+                    int cx = dx, cy = dy, cz = dz;
+                    if (qi < 0 || qi >= B.dims[0]) { crossed++; cx = 0; }
+                    if (qj < 0 || qj >= B.dims[1]) { crossed++; cy = 0; }
+                    if (qk < 0 || qk >= B.dims[2]) { crossed++; cz = 0; }
+                    c128 val = v;
+                    if (crossed) {
+                        if (dirichlet) continue;
+                        for (int t = 0; t < crossed; ++t) val = val * rho;
+                    }
+                    const int dd = (cz + 1) * 9 + (cy + 1) * 3 + (cx + 1);
+                    loc[dd] = loc[dd] + val;
+                }
+        cplx<TO>* o = out + (B.loc_off + l) * 27;
+        for (int d = 0; d < 27; ++d) o[d] = mk<TO>((TO)loc[d].x, (TO)loc[d].y);
+    }
 }
-extern "C" void oras_destroy(helm_oras) {}
-extern "C" helm_status oras_apply(helm_oras, const void*, void*, int) { return HELM_EINVAL; }
-extern "C" helm_status oras_box_info(helm_oras, int, int*, int*, int*) { return HELM_EINVAL; }
-extern "C" helm_status oras_plane_inverse(helm_oras, int, int, void*) { return HELM_EINVAL; }
-extern "C" double oras_setup_seconds(helm_oras) { return 0.0; }
-extern "C" helm_status gmres_solve(helm_oras, const void*, void*, int, const helm_gmres_desc*, helm_rhs_stats*) {
-    return HELM_EINVAL;
+
+// ------------------------------------------------------------------ restriction / prolongation
+
+// loc[(loc_off + l) * nrhs + r] = v[g(l) * nrhs + r]   (R_i v for every box)
+template <typename TV, typename TL>
+__global__ void restrict_boxes(const BoxInfo* __restrict__ boxes, const cplx<TV>* __restrict__ v,
+                               cplx<TL>* __restrict__ loc, int nx, int ny, int nrhs) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const long long total = (long long)B.m * B.dims[2] * nrhs;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long l = e / nrhs;
+        const int r = (int)(e % nrhs);
+        const int li = (int)(l % B.dims[0]);
+        const int lj = (int)((l / B.dims[0]) % B.dims[1]);
+        const int lk = (int)(l / B.m);
+        const long long g = ((long long)(B.lo[2] + lk) * ny + (B.lo[1] + lj)) * nx + (B.lo[0] + li);
+        const cplx<TV> x = v[g * nrhs + r];
+        loc[(B.loc_off + l) * nrhs + r] = mk<TL>((TL)x.x, (TL)x.y);
+    }
 }
+
+// out[g] = loc[owner box of g][local index of g] (+ q[g])     (sum_i R_i^T D_i x_i with Boolean owner PU)
+template <typename TL, typename TV, bool ADDQ>
+__global__ void prolong_owner(const BoxInfo* __restrict__ boxes, const int* __restrict__ owner,
+                              const cplx<TL>* __restrict__ loc, const cplx<TV>* __restrict__ q, cplx<TV>* __restrict__ out,
+                              int nx, int ny, int nz, int px, int py, int nrhs) {
+    const long long total = (long long)nx * ny * nz * nrhs;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long g = e / nrhs;
+        const int r = (int)(e % nrhs);
+        const int i = (int)(g % nx);
+        const int j = (int)((g / nx) % ny);
+        const int k = (int)(g / ((long long)nx * ny));
+        const int b = (owner[nx + ny + k] * py + owner[nx + j]) * px + owner[i];
+        const BoxInfo& B = boxes[b];
+        const long long l = ((long long)(k - B.lo[2]) * B.dims[1] + (j - B.lo[1])) * B.dims[0] + (i - B.lo[0]);
+        const cplx<TL> x = loc[(B.loc_off + l) * nrhs + r];
+        cplx<TV> y = mk<TV>((TV)x.x, (TV)x.y);
+        if (ADDQ) y = y + q[e];
+        out[e] = y;
+    }
+}
+
+// ------------------------------------------------------------------ coarse space
+
+__device__ __forceinline__ double hat(int i, int J, int r) {
+    const double t = fabs((double)(i - r * J)) / r;
+    return t < 1.0 ? 1.0 - t : 0.0;
+}
+
+// cv[J * nrhs + rr] = sum_i Z[i, J] v[i * nrhs + rr]   (Z^T v, FP64 accumulation)
+template <typename TV>
+__global__ void coarse_restrict(const cplx<TV>* __restrict__ v, c128* __restrict__ cv, int nx, int ny, int nz, int cx,
+                                int cy, int cz, int r, int nrhs) {
+    const long long total = (long long)cx * cy * cz * nrhs;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long J = e / nrhs;
+        const int rr = (int)(e % nrhs);
+        const int Jx = (int)(J % cx), Jy = (int)((J / cx) % cy), Jz = (int)(J / ((long long)cx * cy));
+        c128 acc = mk<double>(0, 0);
+        for (int k = max(0, r * Jz - r + 1); k <= min(nz - 1, r * Jz + r - 1); ++k) {
+            const double wz = hat(k, Jz, r);
+            for (int j = max(0, r * Jy - r + 1); j <= min(ny - 1, r * Jy + r - 1); ++j) {
+                const double wyz = wz * hat(j, Jy, r);
+                for (int i = max(0, r * Jx - r + 1); i <= min(nx - 1, r * Jx + r - 1); ++i) {
+                    const double wt = wyz * hat(i, Jx, r);
+                    const cplx<TV> x = v[(((long long)k * ny + j) * nx + i) * nrhs + rr];
+                    acc.x += wt * (double)x.x;
+                    acc.y += wt * (double)x.y;
+                }
+            }
+        }
+        cv[e] = acc;
+    }
+}
+
+// q[i * nrhs + rr] = sum_J Z[i, J] cv[J * nrhs + rr]   (trilinear interpolation)
+template <typename TV>
+__global__ void coarse_prolong(const c128* __restrict__ cv, cplx<TV>* __restrict__ q, int nx, int ny, int nz, int cx,
+                               int cy, int cz, int r, int nrhs) {
+    const long long total = (long long)nx * ny * nz * nrhs;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long g = e / nrhs;
+        const int rr = (int)(e % nrhs);
+        const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((long long)nx * ny));
+        const int I0 = i / r, J0 = j / r, K0 = k / r;
+        c128 acc = mk<double>(0, 0);
+        for (int Kz = K0; Kz <= min(K0 + 1, cz - 1); ++Kz) {
+            const double wz = hat(k, Kz, r);
+            if (wz == 0.0) continue;
+            for (int Jy = J0; Jy <= min(J0 + 1, cy - 1); ++Jy) {
+                const double wyz = wz * hat(j, Jy, r);
+                if (wyz == 0.0) continue;
+                for (int Ix = I0; Ix <= min(I0 + 1, cx - 1); ++Ix) {
+                    const double wt = wyz * hat(i, Ix, r);
+                    if (wt == 0.0) continue;
+                    const c128 x = cv[(((long long)Kz * cy + Jy) * cx + Ix) * nrhs + rr];
+                    acc.x += wt * x.x;
+                    acc.y += wt * x.y;
+                }
+            }
+        }
+        q[e] = mk<TV>((TV)acc.x, (TV)acc.y);
+    }
+}
+
+// Probe vectors: zc[i * 27 + c] = (Z e_c)_i, e_c = indicator of the coarse nodes of colour c = (J mod 3).
+__global__ void coarse_probe_vectors(c128* __restrict__ zc, int nx, int ny, int nz, int cx, int cy, int cz, int r) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((long long)nx * ny));
+        const int idx[3] = {i, j, k};
+        const int cdim[3] = {cx, cy, cz};
+        double wa[3][3];
+        for (int a = 0; a < 3; ++a) {
+            wa[a][0] = wa[a][1] = wa[a][2] = 0.0;
+            const int J0 = idx[a] / r;
+            for (int J = J0; J <= min(J0 + 1, cdim[a] - 1); ++J) wa[a][J % 3] += hat(idx[a], J, r);
+        }
+        for (int c = 0; c < 27; ++c) {
+            const int c0 = c % 3, c1 = (c / 3) % 3, c2 = c / 9;
+            zc[g * 27 + c] = mk<double>(wa[0][c0] * wa[1][c1] * wa[2][c2], 0.0);
+        }
+    }
+}
+
+// E27[J * 27 + d] = probe[J][colour(J + d)] for neighbours inside the coarse grid, else 0.
+__global__ void coarse_gather_E(const c128* __restrict__ probe, c128* __restrict__ E27, int cx, int cy, int cz) {
+    const long long nc = (long long)cx * cy * cz;
+    for (long long J = (long long)blockIdx.x * blockDim.x + threadIdx.x; J < nc; J += (long long)gridDim.x * blockDim.x) {
+        const int Jx = (int)(J % cx), Jy = (int)((J / cx) % cy), Jz = (int)(J / ((long long)cx * cy));
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int d = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                    const int X = Jx + dx, Y = Jy + dy, Zc = Jz + dz;
+                    c128 v = mk<double>(0, 0);
+                    if (X >= 0 && X < cx && Y >= 0 && Y < cy && Zc >= 0 && Zc < cz) {
+                        const int col = (X % 3) + 3 * (Y % 3) + 9 * (Zc % 3);
+                        v = probe[J * 27 + col];
+                    }
+                    E27[J * 27 + d] = v;
+                }
+    }
+}
+
+inline unsigned grid_for(long long n, int threads = 256, long long cap = 152LL * 16) {
+    long long b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ factor
+
+extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_oras* out) {
+    if (!g || !d || !out) return set_error(g ? g->ctx : nullptr, HELM_EINVAL, "oras_factor: NULL argument");
+    helm_ctx ctx = g->ctx;
+    *out = nullptr;
+    const int n[3] = {g->d.nx, g->d.ny, g->d.nz};
+    const int p[3] = {d->px, d->py, d->pz};
+    for (int a = 0; a < 3; ++a)
+        if (p[a] < 1 || p[a] > n[a]) return set_error(ctx, HELM_EINVAL, "oras_factor: bad number of boxes");
+    if (d->overlap < 0 || d->coarse_ratio < 0)
+        return set_error(ctx, HELM_EINVAL, "oras_factor: bad overlap or coarse ratio");
+    if (d->interface_bc != 0 && d->interface_bc != 1) return set_error(ctx, HELM_EINVAL, "oras_factor: bad interface_bc");
+    if (d->factor_prec < HELM_PREC_FP64 || d->factor_prec > HELM_PREC_TF32X3)
+        return set_error(ctx, HELM_EINVAL, "oras_factor: bad factor_prec");
+    HELM_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+
+    helm_oras o = new helm_oras_s();
+    o->g = g;
+    o->d = *d;
+    g->refs++;
+    helm_status rc = HELM_OK;
+    auto fail = [&](helm_status s) {
+        oras_destroy(o);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return s;
+    };
+
+    // --- box decomposition
+    std::vector<int> cuts;
+    std::vector<int> owner(n[0] + n[1] + n[2]);
+    int base = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int t = 0; t <= p[a]; ++t) cuts.push_back((int)((long long)t * n[a] / p[a]));
+        for (int t = 0; t < p[a]; ++t) {
+            const int c0 = (int)((long long)t * n[a] / p[a]), c1 = (int)((long long)(t + 1) * n[a] / p[a]);
+            for (int i = c0; i < c1; ++i) owner[base + i] = t;
+        }
+        base += n[a];
+    }
+    o->fine.prec = d->factor_prec == HELM_PREC_FP64 ? HELM_PREC_FP64 : HELM_PREC_FP32;
+    for (int tz = 0; tz < p[2]; ++tz)
+        for (int ty = 0; ty < p[1]; ++ty)
+            for (int tx = 0; tx < p[0]; ++tx) {
+                BoxInfo b{};
+                const int t[3] = {tx, ty, tz};
+                for (int a = 0; a < 3; ++a) {
+                    const int c0 = (int)((long long)t[a] * n[a] / p[a]), c1 = (int)((long long)(t[a] + 1) * n[a] / p[a]);
+                    if (c1 <= c0) return fail(set_error(ctx, HELM_EINVAL, "oras_factor: empty box core"));
+                    b.core_lo[a] = c0;
+                    b.core_hi[a] = c1;
+                    b.lo[a] = c0 > 0 ? std::max(0, c0 - d->overlap) : 0;
+                    const int hi = c1 < n[a] ? std::min(n[a], c1 + d->overlap) : n[a];
+                    b.dims[a] = hi - b.lo[a];
+                }
+                o->fine.hbox.push_back(b);
+            }
+    if ((rc = planeset_alloc(ctx, o->fine))) return fail(rc);
+    if ((rc = dev_alloc(ctx, (void**)&o->owner, owner.size() * sizeof(int), "owner table"))) return fail(rc);
+    if ((rc = cuda_check(ctx, cudaMemcpy(o->owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice),
+                         "owner copy")))
+        return fail(rc);
+
+    // --- local operators with absorbing interface folding
+    {
+        long long mx = 0;
+        for (auto& b : o->fine.hbox) mx = std::max(mx, (long long)b.m * b.dims[2]);
+        const dim3 grid(grid_for(mx, 128, 4096), o->fine.nbox);
+        if (o->fine.prec == HELM_PREC_FP64)
+            build_local_coef<double><<<grid, 128, 0, st>>>(o->fine.dbox, g->tab, g->k2, g->c, n[0], n[1], n[2], g->w,
+                                                           g->omega, g->d.h, d->interface_bc, (c128*)o->fine.coef);
+        else
+            build_local_coef<float><<<grid, 128, 0, st>>>(o->fine.dbox, g->tab, g->k2, g->c, n[0], n[1], n[2], g->w,
+                                                          g->omega, g->d.h, d->interface_bc, (c64*)o->fine.coef);
+        ctx->launches++;
+        if ((rc = cuda_check(ctx, cudaGetLastError(), "build_local_coef"))) return fail(rc);
+    }
+    int singular = 0;
+    if ((rc = planeset_factor(ctx, o->fine, &singular))) return fail(rc);
+    if (singular) return fail(set_error(ctx, HELM_ESINGULAR, "oras_factor: zero pivot in a local plane factor"));
+
+    // --- coarse level
+    if (d->coarse_ratio > 0) {
+        const int r = d->coarse_ratio;
+        for (int a = 0; a < 3; ++a) o->cdims[a] = (n[a] - 1 + r - 1) / r + 1;
+        o->nc = (long long)o->cdims[0] * o->cdims[1] * o->cdims[2];
+        const long long N = g->n;
+        c128 *zc = nullptr, *az = nullptr, *probe = nullptr;
+        auto cfree = [&]() {
+            dev_free(ctx, zc, N * 27 * sizeof(c128));
+            dev_free(ctx, az, N * 27 * sizeof(c128));
+            dev_free(ctx, probe, o->nc * 27 * sizeof(c128));
+        };
+        if ((rc = dev_alloc(ctx, (void**)&zc, N * 27 * sizeof(c128), "coarse probes")) ||
+            (rc = dev_alloc(ctx, (void**)&az, N * 27 * sizeof(c128), "coarse probes A")) ||
+            (rc = dev_alloc(ctx, (void**)&probe, o->nc * 27 * sizeof(c128), "coarse probe results"))) {
+            cfree();
+            return fail(rc);
+        }
+        coarse_probe_vectors<<<grid_for(N), 256, 0, st>>>(zc, n[0], n[1], n[2], o->cdims[0], o->cdims[1], o->cdims[2],
+                                                          r);
+        ctx->launches++;
+        if ((rc = launch_stencil(g, HELM_PREC_FP64, zc, az, 27, st))) { cfree(); return fail(rc); }
+        coarse_restrict<double><<<grid_for(o->nc * 27), 256, 0, st>>>(az, probe, n[0], n[1], n[2], o->cdims[0],
+                                                                       o->cdims[1], o->cdims[2], r, 27);
+        ctx->launches++;
+        BoxInfo cb{};
+        for (int a = 0; a < 3; ++a) {
+            cb.lo[a] = 0;
+            cb.dims[a] = o->cdims[a];
+            cb.core_lo[a] = 0;
+            cb.core_hi[a] = o->cdims[a];
+        }
+        o->coarse.prec = HELM_PREC_FP64;
+        o->coarse.hbox.push_back(cb);
+        if ((rc = planeset_alloc(ctx, o->coarse))) { cfree(); return fail(rc); }
+        coarse_gather_E<<<grid_for(o->nc), 256, 0, st>>>(probe, (c128*)o->coarse.coef, o->cdims[0], o->cdims[1],
+                                                         o->cdims[2]);
+        ctx->launches++;
+        rc = cuda_check(ctx, cudaStreamSynchronize(st), "coarse operator");
+        cfree();
+        if (rc) return fail(rc);
+        if ((rc = planeset_factor(ctx, o->coarse, &singular))) return fail(rc);
+        if (singular) return fail(set_error(ctx, HELM_ESINGULAR, "oras_factor: zero pivot in the coarse factor"));
+    }
+    cudaEventRecord(e1, st);
+    if ((rc = cuda_check(ctx, cudaEventSynchronize(e1), "oras_factor"))) return fail(rc);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    o->setup_s = ms * 1e-3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *out = o;
+    return HELM_OK;
+}
+
+static void free_scratch(helm_oras o) {
+    helm_ctx ctx = o->g->ctx;
+    if (!o->cap_nrhs) return;
+    const size_t fe = o->fine.esize();
+    const size_t we = o->cap_wp == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+    const int R = o->cap_nrhs;
+    dev_free(ctx, o->loc, (size_t)o->fine.nloc * R * fe);
+    dev_free(ctx, o->rbuf, (size_t)o->fine.nbox * o->fine.m_max * R * fe);
+    dev_free(ctx, o->cvec, (size_t)o->nc * R * sizeof(c128));
+    dev_free(ctx, o->crbuf, (size_t)o->coarse.m_max * R * sizeof(c128));
+    dev_free(ctx, o->qf, (size_t)o->g->n * R * we);
+    dev_free(ctx, o->tf, (size_t)o->g->n * R * we);
+    o->loc = o->rbuf = o->qf = o->tf = nullptr;
+    o->cvec = o->crbuf = nullptr;
+    o->cap_nrhs = 0;
+}
+
+static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
+    if (o->cap_nrhs >= nrhs && o->cap_wp == wp) return HELM_OK;
+    helm_ctx ctx = o->g->ctx;
+    cudaStreamSynchronize(ctx->stream);
+    free_scratch(o);
+    const size_t fe = o->fine.esize();
+    const size_t we = wp == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+    o->cap_nrhs = nrhs;
+    o->cap_wp = wp;
+    const int R = nrhs;
+    HELM_TRY(dev_alloc(ctx, &o->loc, (size_t)o->fine.nloc * R * fe, "local vectors"));
+    HELM_TRY(dev_alloc(ctx, &o->rbuf, (size_t)o->fine.nbox * o->fine.m_max * R * fe, "sweep buffer"));
+    if (o->nc) {
+        HELM_TRY(dev_alloc(ctx, (void**)&o->cvec, (size_t)o->nc * R * sizeof(c128), "coarse vector"));
+        HELM_TRY(dev_alloc(ctx, (void**)&o->crbuf, (size_t)o->coarse.m_max * R * sizeof(c128), "coarse sweep buffer"));
+        HELM_TRY(dev_alloc(ctx, &o->qf, (size_t)o->g->n * R * we, "coarse correction"));
+        HELM_TRY(dev_alloc(ctx, &o->tf, (size_t)o->g->n * R * we, "coarse residual"));
+    }
+    return HELM_OK;
+}
+
+// ------------------------------------------------------------------ apply
+
+namespace {
+
+template <typename TV, typename TL>
+helm_status apply_t(helm_oras o, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
+    helm_grid g = o->g;
+    helm_ctx ctx = g->ctx;
+    cudaStream_t st = ctx->stream;
+    const int wp = sizeof(TV) == 8 ? HELM_PREC_FP64 : HELM_PREC_FP32;
+    const long long N = g->n;
+    const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
+    const cplx<TV>* src = v;
+    const cplx<TV>* q = nullptr;
+    if (o->nc) {
+        const int r = o->d.coarse_ratio;
+        const int cx = o->cdims[0], cy = o->cdims[1], cz = o->cdims[2];
+        coarse_restrict<TV><<<grid_for(o->nc * nrhs), 256, 0, st>>>(v, o->cvec, nx, ny, nz, cx, cy, cz, r, nrhs);
+        ctx->launches++;
+        HELM_TRY(planeset_solve(ctx, o->coarse, o->cvec, o->crbuf, nrhs, st));
+        coarse_prolong<TV><<<grid_for(N * nrhs), 256, 0, st>>>(o->cvec, (cplx<TV>*)o->qf, nx, ny, nz, cx, cy, cz, r,
+                                                                nrhs);
+        ctx->launches++;
+        HELM_TRY(launch_stencil_sub(g, wp, o->qf, v, o->tf, nrhs, st));   // t = v - A q
+        src = (const cplx<TV>*)o->tf;
+        q = (const cplx<TV>*)o->qf;
+    }
+    long long mx = 0;
+    for (auto& b : o->fine.hbox) mx = std::max(mx, (long long)b.m * b.dims[2] * nrhs);
+    restrict_boxes<TV, TL><<<dim3(grid_for(mx, 256, 4096), o->fine.nbox), 256, 0, st>>>(o->fine.dbox, src,
+                                                                                         (cplx<TL>*)o->loc, nx, ny, nrhs);
+    ctx->launches++;
+    HELM_TRY(planeset_solve(ctx, o->fine, o->loc, o->rbuf, nrhs, st));
+    if (q)
+        prolong_owner<TL, TV, true><<<grid_for(N * nrhs), 256, 0, st>>>(
+            o->fine.dbox, o->owner, (const cplx<TL>*)o->loc, q, out, nx, ny, nz, o->d.px, o->d.py, nrhs);
+    else
+        prolong_owner<TL, TV, false><<<grid_for(N * nrhs), 256, 0, st>>>(
+            o->fine.dbox, o->owner, (const cplx<TL>*)o->loc, nullptr, out, nx, ny, nz, o->d.px, o->d.py, nrhs);
+    ctx->launches++;
+    return cuda_check(ctx, cudaGetLastError(), "oras apply");
+}
+
+}  // namespace
+
+helm_status oras_apply_wp(helm_oras o, int wp, const void* v, void* out, int nrhs) {
+    HELM_TRY(ensure_scratch(o, wp, nrhs));
+    const bool f64 = o->fine.prec == HELM_PREC_FP64;
+    if (wp == HELM_PREC_FP64) {
+        if (f64) return apply_t<double, double>(o, (const c128*)v, (c128*)out, nrhs);
+        return apply_t<double, float>(o, (const c128*)v, (c128*)out, nrhs);
+    }
+    if (f64) return apply_t<float, double>(o, (const c64*)v, (c64*)out, nrhs);
+    return apply_t<float, float>(o, (const c64*)v, (c64*)out, nrhs);
+}
+
+extern "C" helm_status oras_apply(helm_oras o, const void* v, void* out, int nrhs) {
+    if (!o) return HELM_EINVAL;
+    helm_ctx ctx = o->g->ctx;
+    if (!v || !out || nrhs < 0) return set_error(ctx, HELM_EINVAL, "oras_apply: invalid argument");
+    if (nrhs == 0) return HELM_OK;
+    if (v == out) return set_error(ctx, HELM_EINVAL, "oras_apply: v and out must differ");
+    HELM_CUDA(ctx, cudaSetDevice(ctx->device));
+    HELM_TRY(oras_apply_wp(o, HELM_PREC_FP64, v, out, nrhs));
+    return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "oras_apply");
+}
+
+extern "C" void oras_destroy(helm_oras o) {
+    if (!o) return;
+    helm_ctx ctx = o->g->ctx;
+    cudaStreamSynchronize(ctx->stream);
+    free_scratch(o);
+    planeset_free(ctx, o->fine);
+    planeset_free(ctx, o->coarse);
+    const int n = o->g->d.nx + o->g->d.ny + o->g->d.nz;
+    dev_free(ctx, o->owner, n * sizeof(int));
+    helm_grid g = o->g;
+    delete o;
+    if (--g->refs == 0 && g->destroy_pending) helm_destroy_grid(g);
+}
+
+extern "C" helm_status oras_box_info(helm_oras o, int box, int* nboxes, int lo[3], int dims[3]) {
+    if (!o) return HELM_EINVAL;
+    if (nboxes) *nboxes = o->fine.nbox;
+    if (box < 0) return HELM_OK;
+    if (box >= o->fine.nbox) return set_error(o->g->ctx, HELM_ENOTFOUND, "oras_box_info: box out of range");
+    for (int a = 0; a < 3; ++a) {
+        if (lo) lo[a] = o->fine.hbox[box].lo[a];
+        if (dims) dims[a] = o->fine.hbox[box].dims[a];
+    }
+    return HELM_OK;
+}
+
+namespace {
+__global__ void widen_c64(const c64* __restrict__ a, c128* __restrict__ b, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = mk<double>(a[i].x, a[i].y);
+}
+}  // namespace
+
+extern "C" helm_status oras_plane_inverse(helm_oras o, int box, int plane, void* out) {
+    if (!o || !out) return HELM_EINVAL;
+    helm_ctx ctx = o->g->ctx;
+    if (box < 0 || box >= o->fine.nbox) return set_error(ctx, HELM_ENOTFOUND, "oras_plane_inverse: bad box");
+    const BoxInfo& B = o->fine.hbox[box];
+    if (plane < 0 || plane >= B.dims[2]) return set_error(ctx, HELM_ENOTFOUND, "oras_plane_inverse: bad plane");
+    const long long mm = (long long)B.m * B.m;
+    const size_t off = B.fac_off + (size_t)plane * mm;
+    const bool dev = is_device_pointer(out);
+    c128* tmp = nullptr;
+    c128* dst = (c128*)out;
+    if (!dev) {
+        HELM_TRY(dev_alloc(ctx, (void**)&tmp, mm * sizeof(c128), "plane inverse staging"));
+        dst = tmp;
+    }
+    if (o->fine.prec == HELM_PREC_FP64) {
+        cudaMemcpyAsync(dst, (c128*)o->fine.G + off, mm * sizeof(c128), cudaMemcpyDeviceToDevice, ctx->stream);
+    } else {
+        widen_c64<<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>((c64*)o->fine.G + off, dst, mm);
+        ctx->launches++;
+    }
+    if (!dev) cudaMemcpyAsync(out, tmp, mm * sizeof(c128), cudaMemcpyDeviceToHost, ctx->stream);
+    helm_status rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "oras_plane_inverse");
+    if (tmp) dev_free(ctx, tmp, mm * sizeof(c128));
+    return rc;
+}
+
+extern "C" double oras_setup_seconds(helm_oras o) { return o ? o->setup_s : 0.0; }

@@ -1,0 +1,599 @@
+// Plane-by-plane block LU of the local operators (the exact local solves
+// A_i^{-1} of Eq. oras, and of the coarse operator E of Eq. 2lvl).
+//
+// A box with nx_l x ny_l x nz_l nodes is ordered plane by plane (z slowest);
+// its operator is block tridiagonal with m x m blocks (m = nx_l ny_l): D_k
+// (in-plane couplings), L_k (to plane k-1) and U_k (to plane k+1), each a
+// 9-point in-plane pattern taken from the 27 stored coefficients of every
+// node.  Factorisation, batched over boxes and sequential over planes:
+//   S_0 = D_0,  S_k = D_k - L_k S_{k-1}^{-1} U_{k-1},  G_k = S_k^{-1} (dense).
+// Solve (forward then backward sweeps):
+//   y_k = G_k (b_k - L_k y_{k-1}),   x_k = y_k - G_k (U_k x_{k+1}).
+//
+// Kernels:
+//   schur_gu     T = G_{k-1} U_{k-1}      (9 complex MACs per entry)
+//   schur_lt     S = D_k - L_k T          (9 complex MACs per entry)
+//   gj_panel     Gauss-Jordan with partial pivoting on an nb-column panel,
+//                whole-row swaps applied at once
+//   gj_update    rank-nb update of the columns outside the panel
+//   gj_store     undo the column permutation, store G_k
+//   sweep_prep   b_k - L_k y_{k-1}  or  U_k x_{k+1}
+//   sweep_gemv   G_k times the prepared plane, nrhs columns (warp per row)
+//
+// Blocked in-place Gauss-Jordan: with the pivot-row swaps applied to whole
+// rows immediately, after the panel [j0, j1) has been eliminated the panel
+// columns hold W[:, j0:j1] of the accumulated elimination transform, and the
+// other columns B become W B = B + (W[:, j0:j1] - I[:, j0:j1]) B[j0:j1, :]
+// (rows j0..j1 of B are copied out first).  At the end the columns are
+// swapped back in reverse pivot order.
+#include "internal.h"
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T cabs2(cplx<T> a) { return a.x * a.x + a.y * a.y; }
+template <typename T> __device__ __forceinline__ cplx<T> cinv(cplx<T> a) {
+    const T d = a.x * a.x + a.y * a.y;
+    return mk<T>(a.x / d, -a.y / d);
+}
+template <typename S, typename T> __device__ __forceinline__ cplx<T> ccast(cplx<S> a) { return mk<T>((T)a.x, (T)a.y); }
+
+// ------------------------------------------------------------------ Schur update
+
+template <typename T>
+__global__ void schur_init(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ coef, cplx<T>* __restrict__ S,
+                           int m_max, int k) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m;
+    if (k >= B.dims[2]) return;
+    cplx<T>* Sb = S + (size_t)blockIdx.y * m_max * m_max;
+    const int bx = B.dims[0];
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * m;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(e / m), q = (int)(e % m);
+        const int dx = q % bx - p % bx, dy = q / bx - p / bx;
+        cplx<T> v = mk<T>(0, 0);
+        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1)
+            v = coef[(B.loc_off + (long long)k * m + p) * 27 + 9 + (dy + 1) * 3 + (dx + 1)];
+        Sb[e] = v;
+    }
+}
+
+// Tm = G_{k-1} U_{k-1}:  Tm[a][q] = sum_d G[a][q-d] * U(node q-d of plane k-1, offset (d, +1))
+template <typename T>
+__global__ void schur_gu(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ coef,
+                         const cplx<T>* __restrict__ G, cplx<T>* __restrict__ Tm, int m_max, int k) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m;
+    if (k >= B.dims[2]) return;
+    const int bx = B.dims[0], by = B.dims[1];
+    const cplx<T>* Gp = G + B.fac_off + (size_t)(k - 1) * m * m;
+    cplx<T>* Tb = Tm + (size_t)blockIdx.y * m_max * m_max;
+    const cplx<T>* cU = coef + (B.loc_off + (long long)(k - 1) * m) * 27 + 18;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * m;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(e / m), q = (int)(e % m);
+        const int qx = q % bx, qy = q / bx;
+        cplx<T> acc = mk<T>(0, 0);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int py = qy - dy;
+            if (py < 0 || py >= by) continue;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int px = qx - dx;
+                if (px < 0 || px >= bx) continue;
+                const int p = py * bx + px;
+                cmac(acc, Gp[(size_t)a * m + p], cU[(long long)p * 27 + (dy + 1) * 3 + (dx + 1)]);
+            }
+        }
+        Tb[e] = acc;
+    }
+}
+
+// S = D_k - L_k Tm:  S[p][q] = D_k[p][q] - sum_d L(node p of plane k, offset (d, -1)) * Tm[p+d][q]
+template <typename T>
+__global__ void schur_lt(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ coef,
+                         const cplx<T>* __restrict__ Tm, cplx<T>* __restrict__ S, int m_max, int k) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m;
+    if (k >= B.dims[2]) return;
+    const int bx = B.dims[0], by = B.dims[1];
+    const cplx<T>* Tb = Tm + (size_t)blockIdx.y * m_max * m_max;
+    cplx<T>* Sb = S + (size_t)blockIdx.y * m_max * m_max;
+    const cplx<T>* cK = coef + (B.loc_off + (long long)k * m) * 27;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * m;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(e / m), q = (int)(e % m);
+        const int px = p % bx, py = p / bx;
+        const int dxq = q % bx - px, dyq = q / bx - py;
+        cplx<T> acc = mk<T>(0, 0);
+        if (dxq >= -1 && dxq <= 1 && dyq >= -1 && dyq <= 1) acc = cK[(long long)p * 27 + 9 + (dyq + 1) * 3 + (dxq + 1)];
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int ny_ = py + dy;
+            if (ny_ < 0 || ny_ >= by) continue;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int nx_ = px + dx;
+                if (nx_ < 0 || nx_ >= bx) continue;
+                const cplx<T> l = cK[(long long)p * 27 + (dy + 1) * 3 + (dx + 1)];
+                const cplx<T> t = Tb[(size_t)(ny_ * bx + nx_) * m + q];
+                acc.x -= l.x * t.x - l.y * t.y;
+                acc.y -= l.x * t.y + l.y * t.x;
+            }
+        }
+        Sb[e] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ Gauss-Jordan
+
+constexpr int GJ_THREADS = 512;
+
+// One CTA per box: eliminate panel columns [j0, j1) with partial pivoting.
+template <typename T>
+__global__ void __launch_bounds__(GJ_THREADS) gj_panel(const BoxInfo* __restrict__ boxes, cplx<T>* __restrict__ S,
+                                                       int* __restrict__ perm, cplx<T>* __restrict__ rows,
+                                                       int* __restrict__ flag, int m_max, int nb, int j0, int k) {
+    const BoxInfo B = boxes[blockIdx.x];
+    const int m = B.m;
+    if (k >= B.dims[2] || j0 >= m) return;
+    const int j1 = min(m, j0 + nb);
+    cplx<T>* A = S + (size_t)blockIdx.x * m_max * m_max;
+    int* pv = perm + (size_t)blockIdx.x * m_max;
+    __shared__ T s_val[GJ_THREADS / 32];
+    __shared__ int s_idx[GJ_THREADS / 32];
+    __shared__ int s_piv;
+    __shared__ cplx<T> s_row[64];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+    for (int c = j0; c < j1; ++c) {
+        // pivot search over rows c..m-1 (ties -> smallest index)
+        T best = (T)-1;
+        int bi = m;
+        for (int r = c + tid; r < m; r += GJ_THREADS) {
+            const T v = cabs2(A[(size_t)r * m + c]);
+            if (v > best) { best = v; bi = r; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            T bv = s_val[0];
+            int bidx = s_idx[0];
+            for (int w = 1; w < GJ_THREADS / 32; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bidx)) { bv = s_val[w]; bidx = s_idx[w]; }
+            if (!(bv > (T)0) || bidx >= m) {
+                atomicOr(flag, 1);
+                bidx = c;
+            }
+            s_piv = bidx;
+            pv[c] = bidx;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != c) {
+            for (int j = tid; j < m; j += GJ_THREADS) {
+                const cplx<T> t = A[(size_t)c * m + j];
+                A[(size_t)c * m + j] = A[(size_t)p * m + j];
+                A[(size_t)p * m + j] = t;
+            }
+            __syncthreads();
+        }
+        cplx<T> piv = A[(size_t)c * m + c];
+        if (!(cabs2(piv) > (T)0)) piv = mk<T>((T)1, (T)0);   // singular: flagged above, keep going finite
+        const cplx<T> inv = cinv(piv);
+        if (tid < j1 - j0) {
+            const int j = j0 + tid;
+            s_row[tid] = (j == c) ? inv : A[(size_t)c * m + j] * inv;
+        }
+        __syncthreads();
+        for (int r = tid; r < m; r += GJ_THREADS) {
+            cplx<T>* Ar = A + (size_t)r * m;
+            if (r == c) {
+                for (int jj = 0; jj < j1 - j0; ++jj) Ar[j0 + jj] = s_row[jj];
+                continue;
+            }
+            const cplx<T> f = Ar[c];
+            for (int jj = 0; jj < j1 - j0; ++jj) {
+                const int j = j0 + jj;
+                if (j == c) {
+                    const cplx<T> v = f * inv;
+                    Ar[c] = mk<T>(-v.x, -v.y);
+                } else {
+                    const cplx<T> s = s_row[jj];
+                    Ar[j].x -= f.x * s.x - f.y * s.y;
+                    Ar[j].y -= f.x * s.y + f.y * s.x;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // copy rows j0..j1 (all columns) for the trailing update
+    cplx<T>* Rb = rows + (size_t)blockIdx.x * 64 * m_max;
+    for (long long e = tid; e < (long long)(j1 - j0) * m; e += GJ_THREADS) {
+        const int i = (int)(e / m), j = (int)(e % m);
+        Rb[(size_t)i * m + j] = A[(size_t)(j0 + i) * m + j];
+    }
+}
+
+// Columns outside the panel: A[r][j] = [r not in panel] A[r][j] + sum_c W[r][c] Rows[c][j].
+// 64 x 64 output tile per CTA, 16 x 16 threads, 4 x 4 outputs per thread.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) gj_update(const BoxInfo* __restrict__ boxes, cplx<T>* __restrict__ S,
+                                                 const cplx<T>* __restrict__ rows, int m_max, int j0, int k) {
+    const BoxInfo B = boxes[blockIdx.z];
+    const int m = B.m;
+    if (k >= B.dims[2] || j0 >= m) return;
+    const int nbw = min(NB, m - j0);
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+    if (r0 >= m || c0 >= m) return;
+    if (c0 >= j0 && c0 + 64 <= j0 + nbw) return;   // tile entirely inside the panel
+    cplx<T>* A = S + (size_t)blockIdx.z * m_max * m_max;
+    const cplx<T>* Rb = rows + (size_t)blockIdx.z * 64 * m_max;
+    __shared__ cplx<T> sW[64][NB + 1];
+    __shared__ cplx<T> sR[NB][64 + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 64 * NB; e += 256) {
+        const int r = e / NB, c = e % NB;
+        sW[r][c] = (r0 + r < m && c < nbw) ? A[(size_t)(r0 + r) * m + j0 + c] : mk<T>(0, 0);
+        const int cc = e / 64, jj = e % 64;
+        sR[cc][jj] = (cc < nbw && c0 + jj < m) ? Rb[(size_t)cc * m + c0 + jj] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    const int tx = tid % 16, ty = tid / 16;
+    cplx<T> acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = mk<T>(0, 0);
+    for (int c = 0; c < nbw; ++c) {
+        cplx<T> w[4], rr[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) w[a] = sW[ty + 16 * a][c];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rr[b] = sR[c][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cmac(acc[a][b], w[a], rr[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = r0 + ty + 16 * a;
+        if (r >= m) continue;
+        const bool in_panel_row = r >= j0 && r < j0 + nbw;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int j = c0 + tx + 16 * b;
+            if (j >= m || (j >= j0 && j < j0 + nbw)) continue;
+            cplx<T>* dst = A + (size_t)r * m + j;
+            const cplx<T> base = in_panel_row ? mk<T>(0, 0) : *dst;
+            *dst = base + acc[a][b];
+        }
+    }
+}
+
+// Undo the column swaps (reverse pivot order) and write G_k.
+template <typename T>
+__global__ void gj_store(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ S, const int* __restrict__ perm,
+                         cplx<T>* __restrict__ G, int m_max, int k) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m;
+    if (k >= B.dims[2]) return;
+    extern __shared__ int s_pos[];
+    const int* pv = perm + (size_t)blockIdx.y * m_max;
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < m; ++j) s_pos[j] = j;
+        for (int c = m - 1; c >= 0; --c) {
+            const int p = pv[c];
+            const int t = s_pos[c];
+            s_pos[c] = s_pos[p];
+            s_pos[p] = t;
+        }
+    }
+    __syncthreads();
+    const cplx<T>* A = S + (size_t)blockIdx.y * m_max * m_max;
+    cplx<T>* Gk = G + B.fac_off + (size_t)k * m * m;
+    const int rows_per = (m + gridDim.x - 1) / gridDim.x;
+    const int ra = blockIdx.x * rows_per, rb = min(m, ra + rows_per);
+    for (long long e = (long long)ra * m + threadIdx.x; e < (long long)rb * m; e += blockDim.x) {
+        const int r = (int)(e / m), j = (int)(e % m);
+        Gk[e] = A[(size_t)r * m + s_pos[j]];
+    }
+}
+
+// ------------------------------------------------------------------ sweeps
+
+// FWD: rb = b_k - L_k y_{k-1} (k > 0) or b_0;  BWD: rb = U_k x_{k+1} (k < bz-1).
+template <typename T, bool FWD>
+__global__ void sweep_prep(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ coef,
+                           const cplx<T>* __restrict__ loc, cplx<T>* __restrict__ rbuf, int m_max, int nrhs, int s) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m, bz = B.dims[2], bx = B.dims[0], by = B.dims[1];
+    const int k = FWD ? s : bz - 1 - s;
+    if (k < 0 || k >= bz) return;
+    if (!FWD && k == bz - 1) return;
+    cplx<T>* rb = rbuf + (size_t)blockIdx.y * m_max * nrhs;
+    const long long plane = B.loc_off + (long long)k * m;
+    const long long nbr = FWD ? plane - m : plane + m;
+    const int off = FWD ? 0 : 18;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * nrhs;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(e / nrhs), r = (int)(e % nrhs);
+        cplx<T> acc = mk<T>(0, 0);
+        if (FWD) acc = loc[(plane + p) * nrhs + r];
+        if (FWD && k == 0) {
+            rb[e] = acc;
+            continue;
+        }
+        const int px = p % bx, py = p / bx;
+        const cplx<T>* cp = coef + (plane + p) * 27 + off;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int qy = py + dy;
+            if (qy < 0 || qy >= by) continue;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int qx = px + dx;
+                if (qx < 0 || qx >= bx) continue;
+                const cplx<T> c = cp[(dy + 1) * 3 + (dx + 1)];
+                const cplx<T> v = loc[(nbr + qy * bx + qx) * nrhs + r];
+                if (FWD) {
+                    acc.x -= c.x * v.x - c.y * v.y;
+                    acc.y -= c.x * v.y + c.y * v.x;
+                } else {
+                    cmac(acc, c, v);
+                }
+            }
+        }
+        rb[e] = acc;
+    }
+}
+
+// loc[plane k][row][r0 + r] = (FWD ? 0 : loc[...]) +/- sum_kk G_k[row][kk] rb[kk][r0 + r]
+// One warp per row; the rhs chunk of rb is staged in shared memory as [RN][m].
+template <typename T, int RN, bool FWD>
+__global__ void __launch_bounds__(256) sweep_gemv(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ G,
+                                                  const cplx<T>* __restrict__ rbuf, cplx<T>* __restrict__ loc,
+                                                  int m_max, int nrhs, int s, int rows_per_cta) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m, bz = B.dims[2];
+    const int k = FWD ? s : bz - 1 - s;
+    if (k < 0 || k >= bz) return;
+    if (!FWD && k == bz - 1) return;
+    const int row_a = blockIdx.x * rows_per_cta;
+    if (row_a >= m) return;
+    const int row_b = min(m, row_a + rows_per_cta);
+    const int r0 = blockIdx.z * RN;
+    const int rn = min(RN, nrhs - r0);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);   // [RN][m]
+    const cplx<T>* rb = rbuf + (size_t)blockIdx.y * m_max * nrhs;
+    for (int e = threadIdx.x; e < m * RN; e += blockDim.x) {
+        const int kk = e / RN, r = e % RN;
+        rs[r * m + kk] = (r < rn) ? rb[(size_t)kk * nrhs + r0 + r] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const cplx<T>* Gk = G + B.fac_off + (size_t)k * m * m;
+    for (int row = row_a + wid; row < row_b; row += nw) {
+        cplx<T> acc[RN];
+#pragma unroll
+        for (int r = 0; r < RN; ++r) acc[r] = mk<T>(0, 0);
+        const cplx<T>* g = Gk + (size_t)row * m;
+        for (int kk = lane; kk < m; kk += 32) {
+            const cplx<T> gv = g[kk];
+#pragma unroll
+            for (int r = 0; r < RN; ++r) cmac(acc[r], gv, rs[r * m + kk]);
+        }
+#pragma unroll
+        for (int r = 0; r < RN; ++r) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+            }
+        }
+        cplx<T>* dst = loc + (B.loc_off + (long long)k * m + row) * nrhs + r0;
+#pragma unroll
+        for (int r = 0; r < RN; ++r) {
+            if (lane == r && r < rn) {
+                if (FWD) dst[r] = acc[r];
+                else dst[r] = dst[r] - acc[r];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+template <typename T>
+helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
+    cudaStream_t st = ctx->stream;
+    const int nb = sizeof(T) == 4 ? 32 : 16;
+    const size_t mm = (size_t)P.m_max * P.m_max;
+    cplx<T>*S = nullptr, *Tm = nullptr, *rows = nullptr;
+    int *perm = nullptr, *flag = nullptr;
+    helm_status rc = HELM_OK;
+    auto cleanup = [&]() {
+        dev_free(ctx, S, P.nbox * mm * sizeof(cplx<T>));
+        dev_free(ctx, Tm, P.nbox * mm * sizeof(cplx<T>));
+        dev_free(ctx, rows, (size_t)P.nbox * 64 * P.m_max * sizeof(cplx<T>));
+        dev_free(ctx, perm, (size_t)P.nbox * P.m_max * sizeof(int));
+        dev_free(ctx, flag, sizeof(int));
+    };
+    if ((rc = dev_alloc(ctx, (void**)&S, P.nbox * mm * sizeof(cplx<T>), "factor work S")) ||
+        (rc = dev_alloc(ctx, (void**)&Tm, P.nbox * mm * sizeof(cplx<T>), "factor work T")) ||
+        (rc = dev_alloc(ctx, (void**)&rows, (size_t)P.nbox * 64 * P.m_max * sizeof(cplx<T>), "factor rows")) ||
+        (rc = dev_alloc(ctx, (void**)&perm, (size_t)P.nbox * P.m_max * sizeof(int), "pivots")) ||
+        (rc = dev_alloc(ctx, (void**)&flag, sizeof(int), "singular flag"))) {
+        cleanup();
+        return rc;
+    }
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    const cplx<T>* coef = (const cplx<T>*)P.coef;
+    cplx<T>* G = (cplx<T>*)P.G;
+    const int m = P.m_max;
+    const unsigned eblocks = (unsigned)std::min<long long>(((long long)m * m + 255) / 256, 4096);
+    const dim3 egrid(eblocks, P.nbox);
+    const int tiles = (m + 63) / 64;
+    for (int k = 0; k < P.bz_max; ++k) {
+        if (k == 0) {
+            schur_init<T><<<egrid, 256, 0, st>>>(P.dbox, coef, S, m, k);
+            ctx->launches++;
+        } else {
+            schur_gu<T><<<egrid, 256, 0, st>>>(P.dbox, coef, G, Tm, m, k);
+            schur_lt<T><<<egrid, 256, 0, st>>>(P.dbox, coef, Tm, S, m, k);
+            ctx->launches += 2;
+        }
+        double ub = 0;
+        for (const auto& b : P.hbox)
+            if (k < b.dims[2]) ub += 2.0 * b.m * b.m * sizeof(cplx<T>);
+        for (int j0 = 0; j0 < m; j0 += nb) {
+            int t = prof_begin(ctx, "gj_panel");
+            gj_panel<T><<<P.nbox, GJ_THREADS, 0, st>>>(P.dbox, S, perm, rows, flag, m, nb, j0, k);
+            prof_end(ctx, t, 0.0);
+            t = prof_begin(ctx, "gj_update");
+            if (sizeof(T) == 4)
+                gj_update<T, 32><<<dim3(tiles, tiles, P.nbox), 256, 0, st>>>(P.dbox, S, rows, m, j0, k);
+            else
+                gj_update<T, 16><<<dim3(tiles, tiles, P.nbox), 256, 0, st>>>(P.dbox, S, rows, m, j0, k);
+            prof_end(ctx, t, ub);
+            ctx->launches += 2;
+        }
+        gj_store<T><<<dim3(std::max(1, std::min(64, m / 16)), P.nbox), 256, m * sizeof(int), st>>>(P.dbox, S, perm,
+                                                                                                    G, m, k);
+        ctx->launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_check(ctx, e, "plane factorisation launch");
+        }
+    }
+    int hflag = 0;
+    cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    rc = cuda_check(ctx, cudaStreamSynchronize(st), "plane factorisation");
+    cleanup();
+    *singular = hflag;
+    return rc;
+}
+
+template <typename T, int RN>
+void launch_sweep_rn(const PlaneSet& P, cplx<T>* loc, cplx<T>* rbuf, int nrhs, cudaStream_t st, helm_ctx ctx) {
+    const int m = P.m_max;
+    const int rows_per = 64;
+    const dim3 ggrid((m + rows_per - 1) / rows_per, P.nbox, (nrhs + RN - 1) / RN);
+    const size_t smem = (size_t)RN * m * sizeof(cplx<T>);
+    const unsigned pblocks = (unsigned)std::min<long long>(((long long)m * nrhs + 255) / 256, 1024);
+    const dim3 pgrid(pblocks, P.nbox);
+    const cplx<T>* coef = (const cplx<T>*)P.coef;
+    const cplx<T>* G = (const cplx<T>*)P.G;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[0]) {
+        cudaFuncSetAttribute(sweep_gemv<T, RN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(sweep_gemv<T, RN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set[0] = true;
+    }
+    // algorithmic bytes of one step: every active box reads its m x m factor plane once,
+    // the prepared plane (m x nrhs) and writes (backward: also reads) its output plane;
+    // the preparation reads 1 + 9 planes of coefficients and vectors, writes one plane.
+    const double es = sizeof(cplx<T>);
+    auto step_bytes = [&](int s, bool fwd, double& gemv, double& prep) {
+        gemv = prep = 0;
+        for (const auto& b : P.hbox) {
+            const int bz = b.dims[2];
+            const bool act = fwd ? s < bz : (s >= 1 && s <= bz - 1);
+            if (!act) continue;
+            gemv += ((double)b.m * b.m + (fwd ? 2.0 : 3.0) * b.m * nrhs) * es;
+            prep += ((double)b.m * 9 + (fwd ? 3.0 : 2.0) * b.m * nrhs) * es;
+        }
+    };
+    double gb, pb;
+    for (int s = 0; s < P.bz_max; ++s) {
+        step_bytes(s, true, gb, pb);
+        int t = prof_begin(ctx, "sweep_prep");
+        sweep_prep<T, true><<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, rbuf, m, nrhs, s);
+        prof_end(ctx, t, pb);
+        t = prof_begin(ctx, "sweep_gemv");
+        sweep_gemv<T, RN, true><<<ggrid, 256, smem, st>>>(P.dbox, G, rbuf, loc, m, nrhs, s, rows_per);
+        prof_end(ctx, t, gb);
+    }
+    for (int s = 1; s < P.bz_max; ++s) {
+        step_bytes(s, false, gb, pb);
+        int t = prof_begin(ctx, "sweep_prep");
+        sweep_prep<T, false><<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, rbuf, m, nrhs, s);
+        prof_end(ctx, t, pb);
+        t = prof_begin(ctx, "sweep_gemv");
+        sweep_gemv<T, RN, false><<<ggrid, 256, smem, st>>>(P.dbox, G, rbuf, loc, m, nrhs, s, rows_per);
+        prof_end(ctx, t, gb);
+    }
+    ctx->launches += 4 * P.bz_max - 2;
+}
+
+template <typename T>
+helm_status solve_t(helm_ctx ctx, const PlaneSet& P, cplx<T>* loc, cplx<T>* rbuf, int nrhs, cudaStream_t st) {
+    const size_t per = (size_t)P.m_max * sizeof(cplx<T>);
+    const size_t cap = 200 * 1024;
+    int rn = 16;
+    while (rn > 1 && (rn > nrhs * 2 || rn * per > cap)) rn >>= 1;
+    while (rn > 1 && rn >= 2 * nrhs) rn >>= 1;
+    if (rn * per > cap) return set_error(ctx, HELM_EINVAL, "plane size %d too large for the sweep kernel", P.m_max);
+    switch (rn) {
+        case 16: launch_sweep_rn<T, 16>(P, loc, rbuf, nrhs, st, ctx); break;
+        case 8: launch_sweep_rn<T, 8>(P, loc, rbuf, nrhs, st, ctx); break;
+        case 4: launch_sweep_rn<T, 4>(P, loc, rbuf, nrhs, st, ctx); break;
+        case 2: launch_sweep_rn<T, 2>(P, loc, rbuf, nrhs, st, ctx); break;
+        default: launch_sweep_rn<T, 1>(P, loc, rbuf, nrhs, st, ctx); break;
+    }
+    return cuda_check(ctx, cudaGetLastError(), "plane sweeps");
+}
+
+}  // namespace
+
+helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P) {
+    P.nbox = (int)P.hbox.size();
+    P.m_max = 0;
+    P.bz_max = 0;
+    long long loc = 0;
+    size_t fac = 0;
+    for (auto& b : P.hbox) {
+        b.m = b.dims[0] * b.dims[1];
+        b.loc_off = loc;
+        b.fac_off = (long long)fac;
+        loc += (long long)b.m * b.dims[2];
+        fac += (size_t)b.m * b.m * b.dims[2];
+        P.m_max = std::max(P.m_max, b.m);
+        P.bz_max = std::max(P.bz_max, b.dims[2]);
+    }
+    P.nloc = loc;
+    P.fac_entries = fac;
+    HELM_TRY(dev_alloc(ctx, (void**)&P.dbox, P.nbox * sizeof(BoxInfo), "box table"));
+    HELM_CUDA(ctx, cudaMemcpy(P.dbox, P.hbox.data(), P.nbox * sizeof(BoxInfo), cudaMemcpyHostToDevice));
+    HELM_TRY(dev_alloc(ctx, &P.coef, (size_t)P.nloc * 27 * P.esize(), "local operator coefficients"));
+    HELM_TRY(dev_alloc(ctx, &P.G, P.fac_entries * P.esize(), "plane factors"));
+    return HELM_OK;
+}
+
+void planeset_free(helm_ctx ctx, PlaneSet& P) {
+    dev_free(ctx, P.dbox, P.nbox * sizeof(BoxInfo));
+    dev_free(ctx, P.coef, (size_t)P.nloc * 27 * P.esize());
+    dev_free(ctx, P.G, P.fac_entries * P.esize());
+    P.dbox = nullptr;
+    P.coef = P.G = nullptr;
+}
+
+helm_status planeset_factor(helm_ctx ctx, PlaneSet& P, int* singular) {
+    if (P.prec == HELM_PREC_FP64) return factor_t<double>(ctx, P, singular);
+    return factor_t<float>(ctx, P, singular);
+}
+
+helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st) {
+    if (P.prec == HELM_PREC_FP64) return solve_t<double>(ctx, P, (c128*)loc, (c128*)rbuf, nrhs, st);
+    return solve_t<float>(ctx, P, (c64*)loc, (c64*)rbuf, nrhs, st);
+}

@@ -1,0 +1,93 @@
+// helm_profile_*: CUDA-event timing of instrumented kernel families on the
+// context's stream, with the algorithmic bytes each launch declares.
+#include <string.h>
+
+#include "internal.h"
+
+static int family_index(Profiler& P, const char* name) {
+    for (size_t i = 0; i < P.names.size(); ++i)
+        if (P.names[i] == name) return (int)i;
+    P.names.push_back(name);
+    P.launches.push_back(0);
+    P.ms.push_back(0.0);
+    P.bytes.push_back(0.0);
+    return (int)P.names.size() - 1;
+}
+
+static cudaEvent_t take_event(Profiler& P) {
+    if (!P.pool.empty()) {
+        cudaEvent_t e = P.pool.back();
+        P.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_drain(helm_ctx ctx) {
+    Profiler& P = ctx->prof;
+    if (P.pending.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : P.pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            P.launches[r.family] += 1;
+            P.ms[r.family] += ms;
+            P.bytes[r.family] += r.bytes;
+        }
+        P.pool.push_back(r.a);
+        P.pool.push_back(r.b);
+    }
+    P.pending.clear();
+}
+
+int prof_begin(helm_ctx ctx, const char* family) {
+    Profiler& P = ctx->prof;
+    if (!P.on) return -1;
+    if (P.pending.size() > 4096) prof_drain(ctx);
+    ProfRecord r;
+    r.family = family_index(P, family);
+    r.a = take_event(P);
+    r.b = take_event(P);
+    r.bytes = 0;
+    cudaEventRecord(r.a, ctx->stream);
+    P.pending.push_back(r);
+    return (int)P.pending.size() - 1;
+}
+
+void prof_end(helm_ctx ctx, int token, double bytes) {
+    if (token < 0) return;
+    Profiler& P = ctx->prof;
+    P.pending[token].bytes = bytes;
+    cudaEventRecord(P.pending[token].b, ctx->stream);
+}
+
+extern "C" helm_status helm_profile_enable(helm_ctx ctx, int on) {
+    if (!ctx) return HELM_EINVAL;
+    prof_drain(ctx);
+    Profiler& P = ctx->prof;
+    P.on = on != 0;
+    if (P.on)
+        for (size_t i = 0; i < P.names.size(); ++i) {
+            P.launches[i] = 0;
+            P.ms[i] = 0;
+            P.bytes[i] = 0;
+        }
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launches, double* ms,
+                                          double* bytes) {
+    if (!ctx || !name) return HELM_EINVAL;
+    prof_drain(ctx);
+    Profiler& P = ctx->prof;
+    for (size_t i = 0; i < P.names.size(); ++i)
+        if (P.names[i] == name && P.launches[i] > 0) {
+            if (launches) *launches = P.launches[i];
+            if (ms) *ms = P.ms[i];
+            if (bytes) *bytes = P.bytes[i];
+            return HELM_OK;
+        }
+    return set_error(ctx, HELM_ENOTFOUND, "helm_profile_query: no launches recorded for %s", name);
+}

@@ -24,8 +24,9 @@
 
 namespace {
 
-template <typename T, int RCH>
-__global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict__ u, cplx<T>* __restrict__ y,
+template <typename T, int RCH, bool SUB>
+__global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict__ u, const cplx<T>* __restrict__ b,
+                                                      cplx<T>* __restrict__ y,
                                                       const cplx<T>* __restrict__ k2,
                                                       const cplx<T>* __restrict__ tab, int nx, int ny, int nz,
                                                       int nrhs, StencilW w) {
@@ -93,36 +94,56 @@ __global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict_
         }
     }
     cplx<T>* yp = y + p * nrhs + (long long)ch * RCH;
+    if (SUB) {
+        const cplx<T>* bp = b + p * nrhs + (long long)ch * RCH;
 #pragma unroll
-    for (int r = 0; r < RCH; ++r) yp[r] = acc[r];
+        for (int r = 0; r < RCH; ++r) yp[r] = bp[r] - acc[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < RCH; ++r) yp[r] = acc[r];
+    }
 }
 
-template <typename T, int RCH>
-void launch_t(const cplx<T>* u, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab, const helm_grid_desc& d, int nrhs,
-              const StencilW& w, cudaStream_t s) {
+template <typename T, int RCH, bool SUB>
+void launch_t(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab,
+              const helm_grid_desc& d, int nrhs, const StencilW& w, cudaStream_t s) {
     const long long total = (long long)d.nx * d.ny * d.nz * (nrhs / RCH);
     const int threads = 256;
     const long long blocks = (total + threads - 1) / threads;
-    stencil_kernel<T, RCH><<<(unsigned)blocks, threads, 0, s>>>(u, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w);
+    stencil_kernel<T, RCH, SUB><<<(unsigned)blocks, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w);
 }
 
-template <typename T>
-void dispatch(const cplx<T>* u, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab, const helm_grid_desc& d, int nrhs,
-              const StencilW& w, cudaStream_t s) {
-    if (nrhs % 4 == 0) launch_t<T, 4>(u, y, k2, tab, d, nrhs, w, s);
-    else if (nrhs % 2 == 0) launch_t<T, 2>(u, y, k2, tab, d, nrhs, w, s);
-    else launch_t<T, 1>(u, y, k2, tab, d, nrhs, w, s);
+template <typename T, bool SUB>
+void dispatch(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab,
+              const helm_grid_desc& d, int nrhs, const StencilW& w, cudaStream_t s) {
+    if (nrhs % 4 == 0) launch_t<T, 4, SUB>(u, b, y, k2, tab, d, nrhs, w, s);
+    else if (nrhs % 2 == 0) launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, s);
+    else launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, s);
+}
+
+template <bool SUB>
+helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void* y, int nrhs, cudaStream_t s) {
+    if (nrhs <= 0) return HELM_OK;
+    // algorithmic bytes: read u (and b), write y, read k^2 once
+    const double es = prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+    const double bytes = (double)g->n * es * ((SUB ? 3.0 : 2.0) * nrhs + 1.0);
+    const int tok = prof_begin(g->ctx, "stencil");
+    if (prec == HELM_PREC_FP64) {
+        dispatch<double, SUB>((const c128*)u, (const c128*)b, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, s);
+    } else {
+        dispatch<float, SUB>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, s);
+    }
+    prof_end(g->ctx, tok, bytes);
+    HELM_LAUNCH_CHECK(g->ctx, "stencil_kernel");
+    return HELM_OK;
 }
 
 }  // namespace
 
 helm_status launch_stencil(helm_grid g, int prec, const void* u, void* y, int nrhs, cudaStream_t s) {
-    if (nrhs <= 0) return HELM_OK;
-    if (prec == HELM_PREC_FP64) {
-        dispatch<double>((const c128*)u, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, s);
-    } else {
-        dispatch<float>((const c64*)u, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, s);
-    }
-    HELM_LAUNCH_CHECK(g->ctx, "stencil_kernel");
-    return HELM_OK;
+    return launch_any<false>(g, prec, u, nullptr, y, nrhs, s);
+}
+
+helm_status launch_stencil_sub(helm_grid g, int prec, const void* u, const void* b, void* y, int nrhs, cudaStream_t s) {
+    return launch_any<true>(g, prec, u, b, y, nrhs, s);
 }

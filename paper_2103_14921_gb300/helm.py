@@ -72,6 +72,9 @@ def lib():
         "helm_last_error": (C.c_char_p, [vp]),
         "helm_bytes_in_use": (C.c_size_t, [vp]),
         "helm_launch_count": (C.c_uint64, [vp]),
+        "helm_profile_enable": (st, [vp, i32]),
+        "helm_profile_query": (st, [vp, C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
         "helm_fit_weights": (st, [C.c_double, C.c_double, C.POINTER(C.c_double)]),
         "helm_setup_grid": (st, [vp, C.POINTER(GridDesc), vp, C.POINTER(vp)]),
         "helm_destroy_grid": (None, [vp]),
@@ -128,6 +131,19 @@ class Context:
     @property
     def launches(self):
         return lib().helm_launch_count(self._h)
+
+    def profile(self, on=True):
+        """Enable (and clear) or disable per-kernel-family event timing."""
+        self.check(lib().helm_profile_enable(self._h, 1 if on else 0), "helm_profile_enable")
+
+    def profile_query(self, family):
+        """``(launches, total_ms, total_algorithmic_bytes)`` of a kernel family, or None."""
+        n, ms, b = C.c_uint64(), C.c_double(), C.c_double()
+        st = lib().helm_profile_query(self._h, family.encode(), C.byref(n), C.byref(ms), C.byref(b))
+        if st == ENOTFOUND:
+            return None
+        self.check(st, "helm_profile_query")
+        return n.value, ms.value, b.value
 
     def close(self):
         if self._h:

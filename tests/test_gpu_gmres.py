@@ -1,0 +1,137 @@
+"""GPU (F)GMRES with ORAS against the FP64 oracle, through the C ABI.
+
+Bars: converged solutions within 10 x tol (relative L2) of the oracle's
+direct solution, and the oracle-evaluated FP64 relative residual of the GPU
+solution <= tol (reported together, as the two can differ by the condition
+number).
+"""
+import numpy as np
+import pytest
+
+from oracle.discretization import Problem, apply_A, assemble_A
+from oracle.schwarz import ORAS, direct_solve_planes
+from oracle.krylov import gmres
+from oracle.analytic import green_linear_gradient, node_coordinates, relative_l2_misfit, comparison_mask
+from paper_2103_14921_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2103_14921_gb300 import build, helm
+    build.build()
+    return helm.Context(0)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _problem(ctx, dims, f=5.0, npml=4, Q=None, top=False):
+    from paper_2103_14921_gb300 import helm
+    nx, ny, nz = dims
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 0.6, Q=Q)
+    w = helm.fit_weights()
+    grid = helm.Grid(ctx, nx, ny, nz, 25.0, f, c, npml=npml, top_bc=helm.TOP_PML if top else helm.TOP_DIRICHLET,
+                     weights=w)
+    prob = Problem(nx, ny, nz, 25.0, f, c, npml=npml, top_pml=top, weights=w)
+    return grid, prob
+
+
+def _residual(prob, x, b):
+    return np.linalg.norm(apply_A(prob, x) - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("flexible", [True, False])
+def test_fp64_gmres_matches_oracle_solution_and_iterations(ctx, flexible):
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (24, 22, 20)
+    grid, prob = _problem(ctx, dims)
+    pos = [(12, 11, 3), (5, 17, 9)]
+    b = synth.point_sources(*dims, 25.0, pos)
+    tol = 1e-8
+    o = helm.Oras(grid, (2, 2, 2), 2)
+    x, stats = o.solve(torch.from_numpy(b).cuda(), tol=tol, restart=30, flexible=flexible)
+    x = x.cpu().numpy()
+    xs = direct_solve_planes(prob, b.reshape(-1, 2)).reshape(b.shape)
+    M = ORAS(prob, (2, 2, 2), 2)
+    A = assemble_A(prob)
+    for r in range(2):
+        assert stats[r]["converged"]
+        assert _rel(x[..., r], xs[..., r]) <= 10 * tol
+        assert _residual(prob, x[..., r], b[..., r]) <= tol
+        _, info = gmres(lambda v: A @ v, b[..., r].ravel(), M.apply, tol=tol, restart=30, flexible=flexible)
+        assert abs(stats[r]["iterations"] - info["iterations"]) <= 1
+
+
+def test_two_level_fgmres_restarts_and_mixed_precision(ctx):
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (28, 26, 24)
+    grid, prob = _problem(ctx, dims, f=6.0, Q=100.0)
+    rng_pos = synth.source_plane_positions(28, 26, 4, 3, 4, 7)
+    b = synth.point_sources(*dims, 25.0, rng_pos)
+    xs = direct_solve_planes(prob, b.reshape(-1, 4)).reshape(b.shape)
+    tol = 1e-6
+    for fprec, bprec in [(helm.PREC_FP64, helm.PREC_FP64), (helm.PREC_FP32, helm.PREC_FP32)]:
+        o = helm.Oras(grid, (2, 2, 2), 2, coarse_ratio=4, factor_prec=fprec)
+        x, stats = o.solve(torch.from_numpy(b).cuda(), tol=tol, restart=8, basis_prec=bprec)
+        x = x.cpu().numpy()
+        for r in range(4):
+            assert stats[r]["converged"], stats[r]
+            assert _residual(prob, x[..., r], b[..., r]) <= tol
+            assert _rel(x[..., r], xs[..., r]) <= 10 * tol
+
+
+def test_host_buffers_and_zero_rhs(ctx):
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (16, 16, 14)
+    grid, prob = _problem(ctx, dims, npml=3)
+    b = synth.point_sources(*dims, 25.0, [(8, 8, 4), (3, 4, 5), (9, 9, 9)])
+    b[..., 1] = 0.0                                # a zero column gives x = 0 with no iterations
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    o = helm.Oras(grid, (2, 1, 2), 1, coarse_ratio=3)
+    _, stats = o.solve(bh, xh, tol=1e-7, restart=20)
+    x = xh.numpy()
+    assert stats[1]["iterations"] == 0 and np.all(x[..., 1] == 0)
+    for r in (0, 2):
+        assert _residual(prob, x[..., r], b[..., r]) <= 1e-7
+
+
+def test_notconv_and_nonfinite_are_reported(ctx):
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (16, 16, 14)
+    grid, prob = _problem(ctx, dims, npml=3)
+    b = synth.point_sources(*dims, 25.0, [(8, 8, 4)])
+    o = helm.Oras(grid, (2, 2, 2), 1)
+    x, stats = o.solve(torch.from_numpy(b).cuda(), tol=1e-12, restart=3, maxit=4, allow_notconv=True)
+    assert not stats[0]["converged"] and stats[0]["iterations"] == 4
+    assert np.isfinite(stats[0]["true_relres"]) and stats[0]["true_relres"] < 1
+    bad = b.copy()
+    bad[0, 0, 0, 0] = np.nan
+    with pytest.raises(helm.HelmError) as e:
+        o.solve(torch.from_numpy(bad).cuda())
+    assert e.value.status == helm.ENONFINITE
+
+
+def test_linear_gradient_one_level_matches_closed_form(ctx):
+    """48^3, c = 1500 + 0.6 z, 3 Hz, one-level ORAS 2x2x2 overlap 2, FP64 GMRES(30) to 1e-6, PML top."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    n, h, f = 48, 25.0, 3.0
+    grid, prob = _problem(ctx, (n, n, n), f=f, npml=8, top=True)
+    s = (24, 24, 24)
+    b = synth.point_sources(n, n, n, h, [s])
+    o = helm.Oras(grid, (2, 2, 2), 2)
+    x, stats = o.solve(torch.from_numpy(b).cuda(), tol=1e-6, restart=30, flexible=False)
+    assert stats[0]["converged"]
+    u = x.cpu().numpy()[..., 0]
+    X, Y, Z = node_coordinates(n, n, n, h)
+    G = green_linear_gradient(X, Y, Z, (s[0] * h, s[1] * h, (s[2] + 1) * h), 2 * np.pi * f, 1500.0, 0.6)
+    mask = comparison_mask(n, n, n, 8, True, s, 4)
+    assert relative_l2_misfit(u, -G, mask) <= 0.05
