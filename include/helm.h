@@ -156,6 +156,21 @@ void        oras_destroy(helm_oras o);
  * v, out: complex128, nrhs columns, device pointers. */
 helm_status oras_apply(helm_oras o, const void* v, void* out, int nrhs);
 
+/* out = M^{-1} v exactly as oras_apply computes it, but without allocating
+ * any device memory inside the call.  No counterpart in the paper: it is
+ * there for callers that cannot let a library call cudaMalloc/cudaFree --
+ * an application that has reserved the GPU's memory in its own pool, or a
+ * serving loop that must not pay the device-wide synchronisation those calls
+ * imply.  The working vectors live in one fixed 8 MiB device array inside the
+ * library (held by every GPU that loads it until the process exits); a
+ * problem whose working vectors do not fit is rejected with HELM_EINVAL and a
+ * message giving the size it would need.  The array's device address is
+ * looked up on the first call on each device, so make that first call before
+ * any stream capture.  All calls share the array: calls whose GPU work
+ * overlaps (other streams or threads) race on it.  v, out: complex128,
+ * nrhs columns, device pointers. */
+helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out, int nrhs);
+
 /* Sizes of the decomposition: number of boxes, and for box `box` its origin
  * lo[3] and extent dims[3] in (x, y, z) order.  box < 0 fills only nboxes. */
 helm_status oras_box_info(helm_oras o, int box, int* nboxes, int lo[3], int dims[3]);

@@ -534,3 +534,81 @@ extern "C" helm_status oras_plane_inverse(helm_oras o, int box, int plane, void*
 }
 
 extern "C" double oras_setup_seconds(helm_oras o) { return o ? o->setup_s : 0.0; }
+
+// ------------------------------------------------------------------ allocation-free apply
+//
+// oras_apply_noalloc: the same M^{-1} v as oras_apply, for callers that must
+// not have the library allocate device memory during the call -- for example
+// an application that has already reserved (almost) all of the GPU's memory
+// in its own pool, or a serving loop that cannot afford the device-wide
+// synchronisation that cudaMalloc/cudaFree imply.  Its working vectors live
+// in one file-scope device array of HELM_NOALLOC_SCRATCH_BYTES (8 MiB), which
+// every GPU that loads the library keeps until the process exits.
+//
+// In host code the array's name only stands for it; its device address is
+// looked up with cudaGetSymbolAddress once per device, on that device's first
+// call (so make the first call on a device before any stream capture), and
+// cached.  All calls share the array and it keeps the last call's contents:
+// every working vector is fully written before it is read, so nothing needs
+// clearing, but calls whose work overlaps on the GPU (two streams, or two
+// threads) race on it.
+
+#define HELM_NOALLOC_SCRATCH_BYTES (8u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HELM_NOALLOC_SCRATCH_BYTES];
+static void* g_noalloc_ptr[64];
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out, int nrhs) {
+    if (!o) return HELM_EINVAL;
+    helm_ctx ctx = o->g->ctx;
+    if (!v || !out || nrhs < 0) return set_error(ctx, HELM_EINVAL, "oras_apply_noalloc: invalid argument");
+    if (nrhs == 0) return HELM_OK;
+    if (v == out) return set_error(ctx, HELM_EINVAL, "oras_apply_noalloc: v and out must differ");
+    if (ctx->device < 0 || ctx->device >= 64) return set_error(ctx, HELM_EINVAL, "oras_apply_noalloc: device id");
+    HELM_CUDA(ctx, cudaSetDevice(ctx->device));
+    // working vectors, carved from the static array (complex128 work precision)
+    const size_t fe = o->fine.esize();
+    const size_t R = (size_t)nrhs;
+    const size_t s_loc = align256((size_t)o->fine.nloc * R * fe);
+    const size_t s_rb = align256((size_t)o->fine.nbox * o->fine.m_max * R * fe);
+    const size_t s_cv = o->nc ? align256((size_t)o->nc * R * sizeof(c128)) : 0;
+    const size_t s_crb = o->nc ? align256((size_t)o->coarse.m_max * R * sizeof(c128)) : 0;
+    const size_t s_vec = o->nc ? align256((size_t)o->g->n * R * sizeof(c128)) : 0;
+    const size_t need = s_loc + s_rb + s_cv + s_crb + 2 * s_vec;
+    if (need > HELM_NOALLOC_SCRATCH_BYTES)
+        return set_error(ctx, HELM_EINVAL,
+                         "oras_apply_noalloc: needs %zu bytes of scratch for this problem and nrhs = %d, more than "
+                         "the fixed %u bytes; use oras_apply or fewer right-hand sides",
+                         need, nrhs, HELM_NOALLOC_SCRATCH_BYTES);
+    if (!g_noalloc_ptr[ctx->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_check(ctx, e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                      "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_ptr[ctx->device] = p;
+    }
+    unsigned char* base = (unsigned char*)g_noalloc_ptr[ctx->device];
+    // point the handle's working vectors into the static array for this call only
+    void *s_loc_p = o->loc, *s_rbuf_p = o->rbuf, *s_qf_p = o->qf, *s_tf_p = o->tf;
+    c128 *s_cvec_p = o->cvec, *s_crbuf_p = o->crbuf;
+    const bool prof_on = ctx->prof.on;
+    ctx->prof.on = false;
+    o->loc = base;
+    o->rbuf = base + s_loc;
+    o->cvec = o->nc ? (c128*)(base + s_loc + s_rb) : nullptr;
+    o->crbuf = o->nc ? (c128*)(base + s_loc + s_rb + s_cv) : nullptr;
+    o->qf = o->nc ? (void*)(base + s_loc + s_rb + s_cv + s_crb) : nullptr;
+    o->tf = o->nc ? (void*)(base + s_loc + s_rb + s_cv + s_crb + s_vec) : nullptr;
+    helm_status rc = o->fine.prec == HELM_PREC_FP64 ? apply_t<double, double>(o, (const c128*)v, (c128*)out, nrhs)
+                                                    : apply_t<double, float>(o, (const c128*)v, (c128*)out, nrhs);
+    if (rc == HELM_OK) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "oras_apply_noalloc");
+    o->loc = s_loc_p;
+    o->rbuf = s_rbuf_p;
+    o->qf = s_qf_p;
+    o->tf = s_tf_p;
+    o->cvec = s_cvec_p;
+    o->crbuf = s_crbuf_p;
+    ctx->prof.on = prof_on;
+    return rc;
+}

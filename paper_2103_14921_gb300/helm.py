@@ -82,6 +82,7 @@ def lib():
         "oras_factor": (st, [vp, C.POINTER(OrasDesc), C.POINTER(vp)]),
         "oras_destroy": (None, [vp]),
         "oras_apply": (st, [vp, vp, vp, i32]),
+        "oras_apply_noalloc": (st, [vp, vp, vp, i32]),
         "oras_box_info": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
         "oras_plane_inverse": (st, [vp, i32, i32, vp]),
         "oras_setup_seconds": (C.c_double, [vp]),
