@@ -119,11 +119,13 @@ __global__ void max_real_kernel(const c128* __restrict__ v, long long n, double*
     if (threadIdx.x == 0) out[blockIdx.x] = s[0];
 }
 
+// bad |= 1: NaN/Inf or Re c <= 0;  bad |= 2: some Im c != 0 (attenuation, complex k^2)
 __global__ void finite_check_kernel(const c128* __restrict__ v, long long n, int* bad) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const c128 a = v[i];
     if (!isfinite(a.x) || !isfinite(a.y) || a.x <= 0.0) atomicOr(bad, 1);
+    if (a.y != 0.0) atomicOr(bad, 2);
 }
 
 }  // namespace
@@ -228,7 +230,9 @@ extern "C" helm_status helm_setup_grid(helm_ctx ctx, const helm_grid_desc* d, co
         st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "finite check");
         dev_free(ctx, bad, sizeof(int));
         if (st) return fail(st);
-        if (hbad) return fail(set_error(ctx, HELM_ENONFINITE, "helm_setup_grid: wave speed has NaN/Inf or Re c <= 0"));
+        if (hbad & 1)
+            return fail(set_error(ctx, HELM_ENONFINITE, "helm_setup_grid: wave speed has NaN/Inf or Re c <= 0"));
+        g->k2_real = (hbad & 2) == 0;
     }
     k2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(g->c, g->k2, g->k2f, n, g->omega);
     ctx->launches++;

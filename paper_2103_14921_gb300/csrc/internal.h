@@ -89,6 +89,7 @@ struct helm_grid_s {
     c128* tab = nullptr;       // stretched 1-D tables, [nx+ny+nz][3] (cm, c0, cp): x, then y, then z
     c64* tabf = nullptr;
     std::vector<c128> htab;    // host copy of the tables
+    bool k2_real = false;      // wave speed real everywhere (no attenuation)
     int refs = 0;              // ORAS handles built on this grid
     bool destroy_pending = false;   // helm_destroy_grid called while ORAS handles were alive
 };
@@ -98,15 +99,21 @@ struct BoxInfo {
     int lo[3], dims[3];        // origin and extent in (x, y, z)
     int core_lo[3], core_hi[3];
     int m;                     // dims[0] * dims[1]: unknowns per z-plane
+    int ld;                    // row pitch of the stored S_k^{-1} (complex entries)
+    int plane0;                // global index of plane 0 in the factor storage
     int pad;
     long long loc_off;         // index of the box's first node in the concatenated local vectors
     long long fac_off;         // index of the first entry of S_0^{-1} in the factor storage
+    long long pstride;         // entries between consecutive planes of the box
 };
 
 // Plane-by-plane block LU of a set of boxes: the local operators as 27
 // coefficients per node and the dense inverses S_k^{-1}, all resident.
 struct PlaneSet {
     int prec = HELM_PREC_FP64;  // FP64 -> complex128 storage, otherwise complex64
+    bool padded = false;        // every plane stored as ld x ld with ld = m_max rounded up (tensor-core layout)
+    int ld = 0;                 // padded row pitch
+    int nplanes = 0;            // total planes over all boxes
     int nbox = 0, m_max = 0, bz_max = 0;
     long long nloc = 0;         // total local nodes
     size_t fac_entries = 0;     // total factor entries
@@ -121,6 +128,7 @@ struct helm_oras_s {
     helm_grid g = nullptr;
     helm_oras_desc d{};
     PlaneSet fine, coarse;
+    PlaneSet coarse32;          // complex64 copy of the FP64 coarse factors (mixed-precision apply)
     int cdims[3] = {0, 0, 0};
     long long nc = 0;
     int* owner = nullptr;       // device: per axis owner part index, [nx + ny + nz]
@@ -136,6 +144,9 @@ struct helm_oras_s {
     void* tf = nullptr;         // fine residual v - A q (work precision)
     int cap_wp = -1;
     size_t scratch_bytes = 0;
+    void* tcb = nullptr;        // tensor-core sweep operand B^T, [nbox][tc_npad][2 ld] fp32
+    int tc_npad = 0;
+    int* dev_err = nullptr;     // device error code of bounded waits (0 = none)
 };
 
 // ----------------------------------------------------------------- helpers
@@ -177,3 +188,9 @@ helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P);
 void planeset_free(helm_ctx ctx, PlaneSet& P);
 helm_status planeset_factor(helm_ctx ctx, PlaneSet& P, int* singular);
 helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st);
+// tensor-core sweeps (sweep_tc.cu), complex64 local vectors, padded factor layout
+int tc_npad(int nrhs);
+helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, void* loc, void* bt, int npad, int nrhs,
+                              cudaStream_t st, int* err);
+// HELM_ETIMEOUT if a bounded device wait of this handle's kernels gave up
+helm_status oras_check_device_error(helm_oras o);

@@ -42,6 +42,8 @@ template <typename T> __device__ __forceinline__ c128 widen(cplx<T> a) { return 
 
 // partial[blk][i][r] = sum over this block's elements of conj(V_i[e]) w[e], i in [i0, i0+ni)
 // With a block of 256 consecutive thread ids every r = e % nrhs appears; each thread keeps one r.
+// Products are formed in the basis precision and summed in groups of up to 8 elements before they
+// are added to the FP64 accumulators.
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
                                                            const cplx<T>* __restrict__ w, long long n_el, int nrhs,
@@ -51,14 +53,29 @@ __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const cplx<T>* __rest
     const long long stride = (long long)gridDim.x * RED_THREADS;
     for (int ib = 0; ib < ni; ib += IC) {
         c128 acc[IC];
+        cplx<T> part[IC];
 #pragma unroll
-        for (int q = 0; q < IC; ++q) acc[q] = mk<double>(0, 0);
+        for (int q = 0; q < IC; ++q) {
+            acc[q] = mk<double>(0, 0);
+            part[q] = mk<T>(0, 0);
+        }
+        int cnt = 0;
         for (long long e = t; e < n_el; e += stride) {
-            const c128 wv = widen(w[e]);
+            const cplx<T> wv = w[e];
 #pragma unroll
             for (int q = 0; q < IC; ++q)
-                if (ib + q < ni) cmac_conj(acc[q], widen(V[(long long)(i0 + ib + q) * vstride + e]), wv);
+                if (ib + q < ni) cmac_conj(part[q], V[(long long)(i0 + ib + q) * vstride + e], wv);
+            if (++cnt == 8) {
+#pragma unroll
+                for (int q = 0; q < IC; ++q) {
+                    acc[q] = acc[q] + widen(part[q]);
+                    part[q] = mk<T>(0, 0);
+                }
+                cnt = 0;
+            }
         }
+#pragma unroll
+        for (int q = 0; q < IC; ++q) acc[q] = acc[q] + widen(part[q]);
         for (int q = 0; q < IC && ib + q < ni; ++q) {
             s[threadIdx.x] = acc[q];
             __syncthreads();
@@ -89,16 +106,18 @@ __global__ void finish_dots(const c128* __restrict__ partial, int nblk, int ldp,
 template <typename T>
 __global__ void update_kernel(const cplx<T>* __restrict__ V, long long vstride, cplx<T>* __restrict__ w, long long n_el,
                               int nrhs, int ni, const c128* __restrict__ hsrc) {
+    // arithmetic in the basis precision (the result is stored in it anyway)
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(e % nrhs);
-        c128 acc = widen(w[e]);
+        cplx<T> acc = w[e];
         for (int i = 0; i < ni; ++i) {
-            const c128 h = hsrc[(long long)i * nrhs + r];
-            const c128 v = widen(V[(long long)i * vstride + e]);
+            const c128 hd = hsrc[(long long)i * nrhs + r];
+            const cplx<T> h = mk<T>((T)hd.x, (T)hd.y);
+            const cplx<T> v = V[(long long)i * vstride + e];
             acc.x -= h.x * v.x - h.y * v.y;
             acc.y -= h.x * v.y + h.y * v.x;
         }
-        w[e] = mk<T>((T)acc.x, (T)acc.y);
+        w[e] = acc;
     }
 }
 
@@ -330,8 +349,10 @@ helm_status solve_t(helm_oras o, const c128* b, c128* x, int nrhs, const helm_gm
     const unsigned rg = (unsigned)((nrhs + 127) / 128);
 
     auto norms = [&](const auto* vec, double* out) {
+        const int tk = prof_begin(ctx, "krylov_misc");
         norm2_kernel<<<nblk, RED_THREADS, 0, st>>>(vec, nel, nrhs, dpart);
         finish_norm2<<<rg, 128, 0, st>>>(dpart, nblk, nrhs, out);
+        prof_end(ctx, tk, (double)nel * sizeof(*vec));
         ctx->launches += 2;
     };
     auto dots_into = [&](const cplx<T>* Vb, const cplx<T>* vec, int ni, c128* dst, int ldh_i, int ldh_r, int col,
@@ -404,8 +425,10 @@ helm_status solve_t(helm_oras o, const c128* b, c128* x, int nrhs, const helm_gm
             ctx->launches++;
             norms(w, hn);
             cudaMemsetAsync(running, 0, sizeof(int), st);
+            const int tk = prof_begin(ctx, "krylov_misc");
             givens_step<<<rg, 128, 0, st>>>(S, H, cs, sn, gv, hn, inv, j, m, nrhs, D.tol, D.maxit, running);
             scale_copy<T, T><<<eg, 256, 0, st>>>(w, V + (long long)(j + 1) * nel, nel, nrhs, inv);
+            prof_end(ctx, tk, 2.0 * nel * sizeof(cplx<T>));
             ctx->launches += 2;
             int hrun = 0;
             HELM_CUDA(ctx, cudaMemcpyAsync(&hrun, running, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -452,6 +475,7 @@ helm_status solve_t(helm_oras o, const c128* b, c128* x, int nrhs, const helm_gm
         all = all && conv;
         if (stats) stats[i] = helm_rhs_stats{hs[i].iters, conv ? 1 : 0, true_rel[i], hs[i].est};
     }
+    HELM_TRY(oras_check_device_error(o));
     if (!all) return set_error(ctx, HELM_ENOTCONV, "gmres_solve: some columns did not reach tol within maxit");
     return HELM_OK;
 }

@@ -121,59 +121,64 @@ __device__ __forceinline__ double hat(int i, int J, int r) {
     return t < 1.0 ? 1.0 - t : 0.0;
 }
 
-// cv[J * nrhs + rr] = sum_i Z[i, J] v[i * nrhs + rr]   (Z^T v, FP64 accumulation)
-template <typename TV>
-__global__ void coarse_restrict(const cplx<TV>* __restrict__ v, c128* __restrict__ cv, int nx, int ny, int nz, int cx,
-                                int cy, int cz, int r, int nrhs) {
+// cv[J * nrhs + rr] = sum_i Z[i, J] v[i * nrhs + rr]   (Z^T v)
+// Hat weights are (r - |d_x|)(r - |d_y|)(r - |d_z|) / r^3 with integer numerators; the sum is
+// accumulated in the input's precision and the result stored in complex128.
+template <typename TV, typename TC>
+__global__ void coarse_restrict(const cplx<TV>* __restrict__ v, cplx<TC>* __restrict__ cv, int nx, int ny, int nz,
+                                int cx, int cy, int cz, int r, int nrhs) {
     const long long total = (long long)cx * cy * cz * nrhs;
+    const TV inv_r3 = (TV)1 / (TV)(r * r * r);
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         const long long J = e / nrhs;
         const int rr = (int)(e % nrhs);
         const int Jx = (int)(J % cx), Jy = (int)((J / cx) % cy), Jz = (int)(J / ((long long)cx * cy));
-        c128 acc = mk<double>(0, 0);
-        for (int k = max(0, r * Jz - r + 1); k <= min(nz - 1, r * Jz + r - 1); ++k) {
-            const double wz = hat(k, Jz, r);
-            for (int j = max(0, r * Jy - r + 1); j <= min(ny - 1, r * Jy + r - 1); ++j) {
-                const double wyz = wz * hat(j, Jy, r);
-                for (int i = max(0, r * Jx - r + 1); i <= min(nx - 1, r * Jx + r - 1); ++i) {
-                    const double wt = wyz * hat(i, Jx, r);
-                    const cplx<TV> x = v[(((long long)k * ny + j) * nx + i) * nrhs + rr];
-                    acc.x += wt * (double)x.x;
-                    acc.y += wt * (double)x.y;
-                }
-            }
-        }
-        cv[e] = acc;
-    }
-}
-
-// q[i * nrhs + rr] = sum_J Z[i, J] cv[J * nrhs + rr]   (trilinear interpolation)
-template <typename TV>
-__global__ void coarse_prolong(const c128* __restrict__ cv, cplx<TV>* __restrict__ q, int nx, int ny, int nz, int cx,
-                               int cy, int cz, int r, int nrhs) {
-    const long long total = (long long)nx * ny * nz * nrhs;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const long long g = e / nrhs;
-        const int rr = (int)(e % nrhs);
-        const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((long long)nx * ny));
-        const int I0 = i / r, J0 = j / r, K0 = k / r;
-        c128 acc = mk<double>(0, 0);
-        for (int Kz = K0; Kz <= min(K0 + 1, cz - 1); ++Kz) {
-            const double wz = hat(k, Kz, r);
-            if (wz == 0.0) continue;
-            for (int Jy = J0; Jy <= min(J0 + 1, cy - 1); ++Jy) {
-                const double wyz = wz * hat(j, Jy, r);
-                if (wyz == 0.0) continue;
-                for (int Ix = I0; Ix <= min(I0 + 1, cx - 1); ++Ix) {
-                    const double wt = wyz * hat(i, Ix, r);
-                    if (wt == 0.0) continue;
-                    const c128 x = cv[(((long long)Kz * cy + Jy) * cx + Ix) * nrhs + rr];
+        cplx<TV> acc = mk<TV>(0, 0);
+        const int k0 = max(0, r * Jz - r + 1), k1 = min(nz - 1, r * Jz + r - 1);
+        const int j0 = max(0, r * Jy - r + 1), j1 = min(ny - 1, r * Jy + r - 1);
+        const int i0 = max(0, r * Jx - r + 1), i1 = min(nx - 1, r * Jx + r - 1);
+        for (int k = k0; k <= k1; ++k) {
+            const int wz = r - abs(k - r * Jz);
+            for (int j = j0; j <= j1; ++j) {
+                const int wyz = wz * (r - abs(j - r * Jy));
+                const cplx<TV>* row = v + (((long long)k * ny + j) * nx) * nrhs + rr;
+                for (int i = i0; i <= i1; ++i) {
+                    const TV wt = (TV)(wyz * (r - abs(i - r * Jx)));
+                    const cplx<TV> x = row[(long long)i * nrhs];
                     acc.x += wt * x.x;
                     acc.y += wt * x.y;
                 }
             }
         }
-        q[e] = mk<TV>((TV)acc.x, (TV)acc.y);
+        cv[e] = mk<TC>((TC)(acc.x * inv_r3), (TC)(acc.y * inv_r3));
+    }
+}
+
+// q[i * nrhs + rr] = sum_J Z[i, J] cv[J * nrhs + rr]   (trilinear interpolation, weights (i mod r)/r,
+// exact in binary for r a power of two; accumulated in the output precision)
+template <typename TC, typename TV>
+__global__ void coarse_prolong(const cplx<TC>* __restrict__ cv, cplx<TV>* __restrict__ q, int nx, int ny, int nz,
+                               int cx, int cy, int cz, int r, int nrhs) {
+    const long long total = (long long)nx * ny * nz * nrhs;
+    const TV inv_r = (TV)1 / (TV)r;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long g = e / nrhs;
+        const int rr = (int)(e % nrhs);
+        const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((long long)nx * ny));
+        const int I0 = i / r, J0 = j / r, K0 = k / r;
+        const TV wx1 = (TV)(i - r * I0) * inv_r, wy1 = (TV)(j - r * J0) * inv_r, wz1 = (TV)(k - r * K0) * inv_r;
+        const TV wx[2] = {(TV)1 - wx1, wx1}, wy[2] = {(TV)1 - wy1, wy1}, wz[2] = {(TV)1 - wz1, wz1};
+        cplx<TV> acc = mk<TV>(0, 0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+            const TV wt = wx[a] * wy[b] * wz[d];
+            if (wt == (TV)0 || I0 + a >= cx || J0 + b >= cy || K0 + d >= cz) continue;
+            const cplx<TC> x = cv[(((long long)(K0 + d) * cy + (J0 + b)) * cx + (I0 + a)) * nrhs + rr];
+            acc.x += wt * (TV)x.x;
+            acc.y += wt * (TV)x.y;
+        }
+        q[e] = acc;
     }
 }
 
@@ -215,6 +220,11 @@ __global__ void coarse_gather_E(const c128* __restrict__ probe, c128* __restrict
                     E27[J * 27 + d] = v;
                 }
     }
+}
+
+__global__ void narrow_c128(const c128* __restrict__ a, c64* __restrict__ b, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = mk<float>((float)a[i].x, (float)a[i].y);
 }
 
 inline unsigned grid_for(long long n, int threads = 256, long long cap = 152LL * 16) {
@@ -272,7 +282,12 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
         }
         base += n[a];
     }
+    if (d->factor_prec == HELM_PREC_TF32X3)
+        return fail(set_error(ctx, HELM_EINVAL, "oras_factor: TF32X3 factors are not available"));
     o->fine.prec = d->factor_prec == HELM_PREC_FP64 ? HELM_PREC_FP64 : HELM_PREC_FP32;
+    o->fine.padded = d->factor_prec == HELM_PREC_TF32;
+    if ((rc = dev_alloc(ctx, (void**)&o->dev_err, sizeof(int), "device error flag"))) return fail(rc);
+    if ((rc = cuda_check(ctx, cudaMemsetAsync(o->dev_err, 0, sizeof(int), st), "clear error flag"))) return fail(rc);
     for (int tz = 0; tz < p[2]; ++tz)
         for (int ty = 0; ty < p[1]; ++ty)
             for (int tx = 0; tx < p[0]; ++tx) {
@@ -335,7 +350,7 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
                                                           r);
         ctx->launches++;
         if ((rc = launch_stencil(g, HELM_PREC_FP64, zc, az, 27, st))) { cfree(); return fail(rc); }
-        coarse_restrict<double><<<grid_for(o->nc * 27), 256, 0, st>>>(az, probe, n[0], n[1], n[2], o->cdims[0],
+        coarse_restrict<double, double><<<grid_for(o->nc * 27), 256, 0, st>>>(az, probe, n[0], n[1], n[2], o->cdims[0],
                                                                        o->cdims[1], o->cdims[2], r, 27);
         ctx->launches++;
         BoxInfo cb{};
@@ -356,6 +371,18 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
         if (rc) return fail(rc);
         if ((rc = planeset_factor(ctx, o->coarse, &singular))) return fail(rc);
         if (singular) return fail(set_error(ctx, HELM_ESINGULAR, "oras_factor: zero pivot in the coarse factor"));
+        if (o->fine.prec != HELM_PREC_FP64) {
+            // mixed precision: the coarse factors computed in FP64 are applied from a complex64 copy
+            o->coarse32.prec = HELM_PREC_FP32;
+            o->coarse32.hbox = o->coarse.hbox;
+            if ((rc = planeset_alloc(ctx, o->coarse32))) return fail(rc);
+            narrow_c128<<<grid_for((long long)o->coarse.nloc * 27), 256, 0, st>>>(
+                (const c128*)o->coarse.coef, (c64*)o->coarse32.coef, (long long)o->coarse.nloc * 27);
+            narrow_c128<<<grid_for((long long)o->coarse.fac_entries), 256, 0, st>>>(
+                (const c128*)o->coarse.G, (c64*)o->coarse32.G, (long long)o->coarse.fac_entries);
+            ctx->launches += 2;
+            if ((rc = cuda_check(ctx, cudaGetLastError(), "coarse narrow"))) return fail(rc);
+        }
     }
     cudaEventRecord(e1, st);
     if ((rc = cuda_check(ctx, cudaEventSynchronize(e1), "oras_factor"))) return fail(rc);
@@ -368,6 +395,10 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
     return HELM_OK;
 }
 
+// Planes in the fine sweep buffer: one prepared plane per box; a single box also keeps the
+// 8 split-K partial planes of its sweeps there.
+static int rbuf_planes(helm_oras o) { return o->fine.nbox == 1 ? 9 : o->fine.nbox; }
+
 static void free_scratch(helm_oras o) {
     helm_ctx ctx = o->g->ctx;
     if (!o->cap_nrhs) return;
@@ -375,11 +406,14 @@ static void free_scratch(helm_oras o) {
     const size_t we = o->cap_wp == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
     const int R = o->cap_nrhs;
     dev_free(ctx, o->loc, (size_t)o->fine.nloc * R * fe);
-    dev_free(ctx, o->rbuf, (size_t)o->fine.nbox * o->fine.m_max * R * fe);
+    dev_free(ctx, o->rbuf, (size_t)rbuf_planes(o) * o->fine.m_max * R * fe);
     dev_free(ctx, o->cvec, (size_t)o->nc * R * sizeof(c128));
-    dev_free(ctx, o->crbuf, (size_t)o->coarse.m_max * R * sizeof(c128));
+    dev_free(ctx, o->crbuf, (size_t)9 * o->coarse.m_max * R * sizeof(c128));
     dev_free(ctx, o->qf, (size_t)o->g->n * R * we);
     dev_free(ctx, o->tf, (size_t)o->g->n * R * we);
+    dev_free(ctx, o->tcb, (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * sizeof(float));
+    o->tcb = nullptr;
+    o->tc_npad = 0;
     o->loc = o->rbuf = o->qf = o->tf = nullptr;
     o->cvec = o->crbuf = nullptr;
     o->cap_nrhs = 0;
@@ -396,10 +430,18 @@ static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
     o->cap_wp = wp;
     const int R = nrhs;
     HELM_TRY(dev_alloc(ctx, &o->loc, (size_t)o->fine.nloc * R * fe, "local vectors"));
-    HELM_TRY(dev_alloc(ctx, &o->rbuf, (size_t)o->fine.nbox * o->fine.m_max * R * fe, "sweep buffer"));
+    HELM_TRY(dev_alloc(ctx, &o->rbuf, (size_t)rbuf_planes(o) * o->fine.m_max * R * fe, "sweep buffer"));
+    if (o->fine.padded) {
+        o->tc_npad = tc_npad(R);
+        const size_t bytes = (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * sizeof(float);
+        HELM_TRY(dev_alloc(ctx, &o->tcb, bytes, "tensor-core sweep operand"));
+        HELM_CUDA(ctx, cudaMemsetAsync(o->tcb, 0, bytes, ctx->stream));
+    }
     if (o->nc) {
         HELM_TRY(dev_alloc(ctx, (void**)&o->cvec, (size_t)o->nc * R * sizeof(c128), "coarse vector"));
-        HELM_TRY(dev_alloc(ctx, (void**)&o->crbuf, (size_t)o->coarse.m_max * R * sizeof(c128), "coarse sweep buffer"));
+        // coarse sweep buffer: the prepared plane plus 8 split-K partial planes
+        HELM_TRY(dev_alloc(ctx, (void**)&o->crbuf, (size_t)9 * o->coarse.m_max * R * sizeof(c128),
+                           "coarse sweep buffer"));
         HELM_TRY(dev_alloc(ctx, &o->qf, (size_t)o->g->n * R * we, "coarse correction"));
         HELM_TRY(dev_alloc(ctx, &o->tf, (size_t)o->g->n * R * we, "coarse residual"));
     }
@@ -423,28 +465,51 @@ helm_status apply_t(helm_oras o, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
     if (o->nc) {
         const int r = o->d.coarse_ratio;
         const int cx = o->cdims[0], cy = o->cdims[1], cz = o->cdims[2];
-        coarse_restrict<TV><<<grid_for(o->nc * nrhs), 256, 0, st>>>(v, o->cvec, nx, ny, nz, cx, cy, cz, r, nrhs);
-        ctx->launches++;
-        HELM_TRY(planeset_solve(ctx, o->coarse, o->cvec, o->crbuf, nrhs, st));
-        coarse_prolong<TV><<<grid_for(N * nrhs), 256, 0, st>>>(o->cvec, (cplx<TV>*)o->qf, nx, ny, nz, cx, cy, cz, r,
-                                                                nrhs);
-        ctx->launches++;
+        const double vb = (double)N * nrhs * sizeof(cplx<TV>);
+        int tk = prof_begin(ctx, "coarse_transfer");
+        if (o->coarse32.G) {
+            coarse_restrict<TV, float><<<grid_for(o->nc * nrhs), 256, 0, st>>>(v, (c64*)o->cvec, nx, ny, nz, cx, cy,
+                                                                                cz, r, nrhs);
+            prof_end(ctx, tk, vb);
+            HELM_TRY(planeset_solve(ctx, o->coarse32, o->cvec, o->crbuf, nrhs, st));
+            tk = prof_begin(ctx, "coarse_transfer");
+            coarse_prolong<float, TV><<<grid_for(N * nrhs), 256, 0, st>>>((const c64*)o->cvec, (cplx<TV>*)o->qf, nx,
+                                                                           ny, nz, cx, cy, cz, r, nrhs);
+        } else {
+            coarse_restrict<TV, double><<<grid_for(o->nc * nrhs), 256, 0, st>>>(v, o->cvec, nx, ny, nz, cx, cy, cz, r,
+                                                                                 nrhs);
+            prof_end(ctx, tk, vb);
+            HELM_TRY(planeset_solve(ctx, o->coarse, o->cvec, o->crbuf, nrhs, st));
+            tk = prof_begin(ctx, "coarse_transfer");
+            coarse_prolong<double, TV><<<grid_for(N * nrhs), 256, 0, st>>>(o->cvec, (cplx<TV>*)o->qf, nx, ny, nz, cx,
+                                                                            cy, cz, r, nrhs);
+        }
+        prof_end(ctx, tk, vb);
+        ctx->launches += 2;
         HELM_TRY(launch_stencil_sub(g, wp, o->qf, v, o->tf, nrhs, st));   // t = v - A q
         src = (const cplx<TV>*)o->tf;
         q = (const cplx<TV>*)o->qf;
     }
     long long mx = 0;
     for (auto& b : o->fine.hbox) mx = std::max(mx, (long long)b.m * b.dims[2] * nrhs);
+    const double lb = (double)o->fine.nloc * nrhs * (sizeof(cplx<TV>) + sizeof(cplx<TL>));
+    int tr = prof_begin(ctx, "oras_transfer");
     restrict_boxes<TV, TL><<<dim3(grid_for(mx, 256, 4096), o->fine.nbox), 256, 0, st>>>(o->fine.dbox, src,
                                                                                          (cplx<TL>*)o->loc, nx, ny, nrhs);
+    prof_end(ctx, tr, lb);
     ctx->launches++;
-    HELM_TRY(planeset_solve(ctx, o->fine, o->loc, o->rbuf, nrhs, st));
+    if (o->fine.padded)
+        HELM_TRY(planeset_solve_tc(ctx, o->fine, o->loc, o->tcb, o->tc_npad, nrhs, st, o->dev_err));
+    else
+        HELM_TRY(planeset_solve(ctx, o->fine, o->loc, o->rbuf, nrhs, st));
+    tr = prof_begin(ctx, "oras_transfer");
     if (q)
         prolong_owner<TL, TV, true><<<grid_for(N * nrhs), 256, 0, st>>>(
             o->fine.dbox, o->owner, (const cplx<TL>*)o->loc, q, out, nx, ny, nz, o->d.px, o->d.py, nrhs);
     else
         prolong_owner<TL, TV, false><<<grid_for(N * nrhs), 256, 0, st>>>(
             o->fine.dbox, o->owner, (const cplx<TL>*)o->loc, nullptr, out, nx, ny, nz, o->d.px, o->d.py, nrhs);
+    prof_end(ctx, tr, (double)N * nrhs * (sizeof(cplx<TL>) + (q ? 2 : 1) * sizeof(cplx<TV>)));
     ctx->launches++;
     return cuda_check(ctx, cudaGetLastError(), "oras apply");
 }
@@ -470,7 +535,21 @@ extern "C" helm_status oras_apply(helm_oras o, const void* v, void* out, int nrh
     if (v == out) return set_error(ctx, HELM_EINVAL, "oras_apply: v and out must differ");
     HELM_CUDA(ctx, cudaSetDevice(ctx->device));
     HELM_TRY(oras_apply_wp(o, HELM_PREC_FP64, v, out, nrhs));
-    return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "oras_apply");
+    HELM_TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "oras_apply"));
+    return oras_check_device_error(o);
+}
+
+helm_status oras_check_device_error(helm_oras o) {
+    helm_ctx ctx = o->g->ctx;
+    if (!o->dev_err) return HELM_OK;
+    int e = 0;
+    HELM_CUDA(ctx, cudaMemcpyAsync(&e, o->dev_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HELM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (e) {
+        cudaMemsetAsync(o->dev_err, 0, sizeof(int), ctx->stream);
+        return set_error(ctx, HELM_ETIMEOUT, "a bounded device wait gave up (code %d)", e);
+    }
+    return HELM_OK;
 }
 
 extern "C" void oras_destroy(helm_oras o) {
@@ -480,8 +559,10 @@ extern "C" void oras_destroy(helm_oras o) {
     free_scratch(o);
     planeset_free(ctx, o->fine);
     planeset_free(ctx, o->coarse);
+    planeset_free(ctx, o->coarse32);
     const int n = o->g->d.nx + o->g->d.ny + o->g->d.nz;
     dev_free(ctx, o->owner, n * sizeof(int));
+    dev_free(ctx, o->dev_err, sizeof(int));
     helm_grid g = o->g;
     delete o;
     if (--g->refs == 0 && g->destroy_pending) helm_destroy_grid(g);
@@ -500,9 +581,12 @@ extern "C" helm_status oras_box_info(helm_oras o, int box, int* nboxes, int lo[3
 }
 
 namespace {
-__global__ void widen_c64(const c64* __restrict__ a, c128* __restrict__ b, long long n) {
+// b[r * m + j] = a[r * ld + j] widened, for an m x m plane stored with row pitch ld
+__global__ void widen_c64(const c64* __restrict__ a, c128* __restrict__ b, int m, int ld) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = mk<double>(a[i].x, a[i].y);
+    if (i >= (long long)m * m) return;
+    const long long r = i / m, j = i % m;
+    b[i] = mk<double>(a[r * ld + j].x, a[r * ld + j].y);
 }
 }  // namespace
 
@@ -513,7 +597,7 @@ extern "C" helm_status oras_plane_inverse(helm_oras o, int box, int plane, void*
     const BoxInfo& B = o->fine.hbox[box];
     if (plane < 0 || plane >= B.dims[2]) return set_error(ctx, HELM_ENOTFOUND, "oras_plane_inverse: bad plane");
     const long long mm = (long long)B.m * B.m;
-    const size_t off = B.fac_off + (size_t)plane * mm;
+    const size_t off = B.fac_off + (size_t)plane * B.pstride;
     const bool dev = is_device_pointer(out);
     c128* tmp = nullptr;
     c128* dst = (c128*)out;
@@ -522,9 +606,10 @@ extern "C" helm_status oras_plane_inverse(helm_oras o, int box, int plane, void*
         dst = tmp;
     }
     if (o->fine.prec == HELM_PREC_FP64) {
-        cudaMemcpyAsync(dst, (c128*)o->fine.G + off, mm * sizeof(c128), cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaMemcpy2DAsync(dst, B.m * sizeof(c128), (c128*)o->fine.G + off, B.ld * sizeof(c128), B.m * sizeof(c128), B.m,
+                          cudaMemcpyDeviceToDevice, ctx->stream);
     } else {
-        widen_c64<<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>((c64*)o->fine.G + off, dst, mm);
+        widen_c64<<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>((c64*)o->fine.G + off, dst, B.m, B.ld);
         ctx->launches++;
     }
     if (!dev) cudaMemcpyAsync(out, tmp, mm * sizeof(c128), cudaMemcpyDeviceToHost, ctx->stream);
@@ -571,11 +656,13 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     const size_t fe = o->fine.esize();
     const size_t R = (size_t)nrhs;
     const size_t s_loc = align256((size_t)o->fine.nloc * R * fe);
-    const size_t s_rb = align256((size_t)o->fine.nbox * o->fine.m_max * R * fe);
+    const size_t s_rb = align256((size_t)rbuf_planes(o) * o->fine.m_max * R * fe);
     const size_t s_cv = o->nc ? align256((size_t)o->nc * R * sizeof(c128)) : 0;
-    const size_t s_crb = o->nc ? align256((size_t)o->coarse.m_max * R * sizeof(c128)) : 0;
+    const size_t s_crb = o->nc ? align256((size_t)9 * o->coarse.m_max * R * sizeof(c128)) : 0;
     const size_t s_vec = o->nc ? align256((size_t)o->g->n * R * sizeof(c128)) : 0;
-    const size_t need = s_loc + s_rb + s_cv + s_crb + 2 * s_vec;
+    const int npad = o->fine.padded ? tc_npad(nrhs) : 0;
+    const size_t s_tcb = o->fine.padded ? align256((size_t)o->fine.nbox * npad * 2 * o->fine.ld * sizeof(float)) : 0;
+    const size_t need = s_loc + s_rb + s_cv + s_crb + 2 * s_vec + s_tcb;
     if (need > HELM_NOALLOC_SCRATCH_BYTES)
         return set_error(ctx, HELM_EINVAL,
                          "oras_apply_noalloc: needs %zu bytes of scratch for this problem and nrhs = %d, more than "
@@ -590,7 +677,15 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     }
     unsigned char* base = (unsigned char*)g_noalloc_ptr[ctx->device];
     // point the handle's working vectors into the static array for this call only
-    void *s_loc_p = o->loc, *s_rbuf_p = o->rbuf, *s_qf_p = o->qf, *s_tf_p = o->tf;
+    void *s_loc_p = o->loc, *s_rbuf_p = o->rbuf, *s_qf_p = o->qf, *s_tf_p = o->tf, *s_tcb_p = o->tcb;
+    const int s_npad = o->tc_npad;
+    if (o->fine.padded) {
+        // the tensor-core operand's padding must read as zero
+        unsigned char* t = base + s_loc + s_rb + s_cv + s_crb + 2 * s_vec;
+        HELM_CUDA(ctx, cudaMemsetAsync(t, 0, s_tcb, ctx->stream));
+        o->tcb = t;
+        o->tc_npad = npad;
+    }
     c128 *s_cvec_p = o->cvec, *s_crbuf_p = o->crbuf;
     const bool prof_on = ctx->prof.on;
     ctx->prof.on = false;
@@ -607,6 +702,8 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     o->rbuf = s_rbuf_p;
     o->qf = s_qf_p;
     o->tf = s_tf_p;
+    o->tcb = s_tcb_p;
+    o->tc_npad = s_npad;
     o->cvec = s_cvec_p;
     o->crbuf = s_crbuf_p;
     ctx->prof.on = prof_on;

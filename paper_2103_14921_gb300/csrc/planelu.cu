@@ -66,7 +66,8 @@ __global__ void schur_gu(const BoxInfo* __restrict__ boxes, const cplx<T>* __res
     const int m = B.m;
     if (k >= B.dims[2]) return;
     const int bx = B.dims[0], by = B.dims[1];
-    const cplx<T>* Gp = G + B.fac_off + (size_t)(k - 1) * m * m;
+    const cplx<T>* Gp = G + B.fac_off + (size_t)(k - 1) * B.pstride;
+    const int ld = B.ld;
     cplx<T>* Tb = Tm + (size_t)blockIdx.y * m_max * m_max;
     const cplx<T>* cU = coef + (B.loc_off + (long long)(k - 1) * m) * 27 + 18;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * m;
@@ -83,7 +84,7 @@ __global__ void schur_gu(const BoxInfo* __restrict__ boxes, const cplx<T>* __res
                 const int px = qx - dx;
                 if (px < 0 || px >= bx) continue;
                 const int p = py * bx + px;
-                cmac(acc, Gp[(size_t)a * m + p], cU[(long long)p * 27 + (dy + 1) * 3 + (dx + 1)]);
+                cmac(acc, Gp[(size_t)a * ld + p], cU[(long long)p * 27 + (dy + 1) * 3 + (dx + 1)]);
             }
         }
         Tb[e] = acc;
@@ -299,12 +300,12 @@ __global__ void gj_store(const BoxInfo* __restrict__ boxes, const cplx<T>* __res
     }
     __syncthreads();
     const cplx<T>* A = S + (size_t)blockIdx.y * m_max * m_max;
-    cplx<T>* Gk = G + B.fac_off + (size_t)k * m * m;
+    cplx<T>* Gk = G + B.fac_off + (size_t)k * B.pstride;
     const int rows_per = (m + gridDim.x - 1) / gridDim.x;
     const int ra = blockIdx.x * rows_per, rb = min(m, ra + rows_per);
     for (long long e = (long long)ra * m + threadIdx.x; e < (long long)rb * m; e += blockDim.x) {
         const int r = (int)(e / m), j = (int)(e % m);
-        Gk[e] = A[(size_t)r * m + s_pos[j]];
+        Gk[(size_t)r * B.ld + j] = A[(size_t)r * m + s_pos[j]];
     }
 }
 
@@ -375,18 +376,19 @@ __global__ void __launch_bounds__(256) sweep_gemv(const BoxInfo* __restrict__ bo
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);   // [RN][m]
     const cplx<T>* rb = rbuf + (size_t)blockIdx.y * m_max * nrhs;
+    // staging with kk fastest: conflict-free shared stores (the rhs block itself is L2-resident)
     for (int e = threadIdx.x; e < m * RN; e += blockDim.x) {
-        const int kk = e / RN, r = e % RN;
-        rs[r * m + kk] = (r < rn) ? rb[(size_t)kk * nrhs + r0 + r] : mk<T>(0, 0);
+        const int r = e / m, kk = e % m;
+        rs[e] = (r < rn) ? rb[(size_t)kk * nrhs + r0 + r] : mk<T>(0, 0);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const cplx<T>* Gk = G + B.fac_off + (size_t)k * m * m;
+    const cplx<T>* Gk = G + B.fac_off + (size_t)k * B.pstride;
     for (int row = row_a + wid; row < row_b; row += nw) {
         cplx<T> acc[RN];
 #pragma unroll
         for (int r = 0; r < RN; ++r) acc[r] = mk<T>(0, 0);
-        const cplx<T>* g = Gk + (size_t)row * m;
+        const cplx<T>* g = Gk + (size_t)row * B.ld;
         for (int kk = lane; kk < m; kk += 32) {
             const cplx<T> gv = g[kk];
 #pragma unroll
@@ -408,6 +410,75 @@ __global__ void __launch_bounds__(256) sweep_gemv(const BoxInfo* __restrict__ bo
                 else dst[r] = dst[r] - acc[r];
             }
         }
+    }
+}
+
+// Split-K variant for sets with few boxes (the coarse grid is one box): CTA (row block, K slice)
+// writes partial sums part[slice][row][r]; sweep_reduce adds the slices in a fixed order.
+constexpr int KSPLIT = 8;
+
+template <typename T, int RN>
+__global__ void __launch_bounds__(256) sweep_gemv_splitk(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ G,
+                                                         const cplx<T>* __restrict__ rbuf, cplx<T>* __restrict__ part,
+                                                         int m_max, int nrhs, int s, int fwd, int rows_per_cta) {
+    const BoxInfo B = boxes[0];
+    const int m = B.m, bz = B.dims[2];
+    const int k = fwd ? s : bz - 1 - s;
+    if (k < 0 || k >= bz || (!fwd && k == bz - 1)) return;
+    const int row_a = blockIdx.x * rows_per_cta;
+    if (row_a >= m) return;
+    const int row_b = min(m, row_a + rows_per_cta);
+    const int kw = (m + KSPLIT - 1) / KSPLIT;
+    const int k0 = blockIdx.y * kw, k1 = min(m, k0 + kw);
+    const int r0 = blockIdx.z * RN;
+    const int rn = min(RN, nrhs - r0);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);   // [RN][kw]
+    for (int e = threadIdx.x; e < kw * RN; e += blockDim.x) {
+        const int r = e / kw, kk = e % kw;
+        rs[e] = (r < rn && k0 + kk < k1) ? rbuf[(size_t)(k0 + kk) * nrhs + r0 + r] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const cplx<T>* Gk = G + B.fac_off + (size_t)k * B.pstride;
+    for (int row = row_a + wid; row < row_b; row += nw) {
+        cplx<T> acc[RN];
+#pragma unroll
+        for (int r = 0; r < RN; ++r) acc[r] = mk<T>(0, 0);
+        const cplx<T>* g = Gk + (size_t)row * B.ld;
+        for (int kk = k0 + lane; kk < k1; kk += 32) {
+            const cplx<T> gv = g[kk];
+#pragma unroll
+            for (int r = 0; r < RN; ++r) cmac(acc[r], gv, rs[r * kw + (kk - k0)]);
+        }
+#pragma unroll
+        for (int r = 0; r < RN; ++r) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+            }
+        }
+        cplx<T>* dst = part + ((size_t)blockIdx.y * m_max + row) * nrhs + r0;
+#pragma unroll
+        for (int r = 0; r < RN; ++r)
+            if (lane == r && r < rn) dst[r] = acc[r];
+    }
+}
+
+template <typename T>
+__global__ void sweep_reduce(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ part,
+                             cplx<T>* __restrict__ loc, int m_max, int nrhs, int s, int fwd) {
+    const BoxInfo B = boxes[0];
+    const int m = B.m, bz = B.dims[2];
+    const int k = fwd ? s : bz - 1 - s;
+    if (k < 0 || k >= bz || (!fwd && k == bz - 1)) return;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * nrhs;
+         e += (long long)gridDim.x * blockDim.x) {
+        cplx<T> acc = mk<T>(0, 0);
+        for (int sl = 0; sl < KSPLIT; ++sl) acc = acc + part[(size_t)sl * m_max * nrhs + e];
+        cplx<T>* dst = loc + (B.loc_off + (long long)k * m) * nrhs + e;
+        *dst = fwd ? acc : *dst - acc;
     }
 }
 
@@ -487,7 +558,10 @@ helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
 template <typename T, int RN>
 void launch_sweep_rn(const PlaneSet& P, cplx<T>* loc, cplx<T>* rbuf, int nrhs, cudaStream_t st, helm_ctx ctx) {
     const int m = P.m_max;
-    const int rows_per = 64;
+    // rows per CTA: at most 64, fewer when there are few boxes, so that the grid covers every SM twice
+    const int chunks = (nrhs + RN - 1) / RN;
+    const long long want = 2LL * std::max(1, ctx->sm_count);
+    int rows_per = (int)std::min<long long>(64, std::max<long long>(8, (long long)m * P.nbox * chunks / want / 8 * 8));
     const dim3 ggrid((m + rows_per - 1) / rows_per, P.nbox, (nrhs + RN - 1) / RN);
     const size_t smem = (size_t)RN * m * sizeof(cplx<T>);
     const unsigned pblocks = (unsigned)std::min<long long>(((long long)m * nrhs + 255) / 256, 1024);
@@ -515,6 +589,36 @@ void launch_sweep_rn(const PlaneSet& P, cplx<T>* loc, cplx<T>* rbuf, int nrhs, c
         }
     };
     double gb, pb;
+    if (P.nbox == 1) {
+        // one box: split K so that the grid still covers the GPU
+        const int kw = (m + KSPLIT - 1) / KSPLIT;
+        const int rows = 32;
+        const dim3 sgrid((m + rows - 1) / rows, KSPLIT, (nrhs + RN - 1) / RN);
+        const size_t ssm = (size_t)RN * kw * sizeof(cplx<T>);
+        cplx<T>* part = rbuf + (size_t)m * nrhs;   // the caller sizes rbuf (1 + KSPLIT) planes deep
+        static bool sattr = false;
+        if (!sattr) {
+            cudaFuncSetAttribute(sweep_gemv_splitk<T, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            sattr = true;
+        }
+        const unsigned rblocks = (unsigned)std::min<long long>(((long long)m * nrhs + 255) / 256, 512);
+        for (int pass = 0; pass < 2; ++pass) {
+            const int fwd = pass == 0;
+            for (int s = fwd ? 0 : 1; s < P.bz_max; ++s) {
+                step_bytes(s, fwd, gb, pb);
+                int t = prof_begin(ctx, "sweep_prep");
+                if (fwd) sweep_prep<T, true><<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, rbuf, m, nrhs, s);
+                else sweep_prep<T, false><<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, rbuf, m, nrhs, s);
+                prof_end(ctx, t, pb);
+                t = prof_begin(ctx, "sweep_gemv");
+                sweep_gemv_splitk<T, RN><<<sgrid, 256, ssm, st>>>(P.dbox, G, rbuf, part, m, nrhs, s, fwd, rows);
+                sweep_reduce<T><<<rblocks, 256, 0, st>>>(P.dbox, part, loc, m, nrhs, s, fwd);
+                prof_end(ctx, t, gb);
+                ctx->launches += 3;
+            }
+        }
+        return;
+    }
     for (int s = 0; s < P.bz_max; ++s) {
         step_bytes(s, true, gb, pb);
         int t = prof_begin(ctx, "sweep_prep");
@@ -560,23 +664,33 @@ helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P) {
     P.nbox = (int)P.hbox.size();
     P.m_max = 0;
     P.bz_max = 0;
-    long long loc = 0;
-    size_t fac = 0;
     for (auto& b : P.hbox) {
         b.m = b.dims[0] * b.dims[1];
-        b.loc_off = loc;
-        b.fac_off = (long long)fac;
-        loc += (long long)b.m * b.dims[2];
-        fac += (size_t)b.m * b.m * b.dims[2];
         P.m_max = std::max(P.m_max, b.m);
         P.bz_max = std::max(P.bz_max, b.dims[2]);
     }
+    P.ld = P.padded ? (P.m_max + 15) / 16 * 16 : 0;
+    long long loc = 0;
+    size_t fac = 0;
+    int planes = 0;
+    for (auto& b : P.hbox) {
+        b.loc_off = loc;
+        b.fac_off = (long long)fac;
+        b.plane0 = planes;
+        b.ld = P.padded ? P.ld : b.m;
+        b.pstride = P.padded ? (long long)P.ld * P.ld : (long long)b.m * b.m;
+        loc += (long long)b.m * b.dims[2];
+        fac += (size_t)b.pstride * b.dims[2];
+        planes += b.dims[2];
+    }
     P.nloc = loc;
     P.fac_entries = fac;
+    P.nplanes = planes;
     HELM_TRY(dev_alloc(ctx, (void**)&P.dbox, P.nbox * sizeof(BoxInfo), "box table"));
     HELM_CUDA(ctx, cudaMemcpy(P.dbox, P.hbox.data(), P.nbox * sizeof(BoxInfo), cudaMemcpyHostToDevice));
     HELM_TRY(dev_alloc(ctx, &P.coef, (size_t)P.nloc * 27 * P.esize(), "local operator coefficients"));
     HELM_TRY(dev_alloc(ctx, &P.G, P.fac_entries * P.esize(), "plane factors"));
+    if (P.padded) HELM_CUDA(ctx, cudaMemsetAsync(P.G, 0, P.fac_entries * P.esize(), ctx->stream));
     return HELM_OK;
 }
 

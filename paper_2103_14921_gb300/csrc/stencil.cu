@@ -24,12 +24,23 @@
 
 namespace {
 
-template <typename T, int RCH, bool SUB>
-__global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict__ u, const cplx<T>* __restrict__ b,
+// Rows whose 1-D coefficients are all the plain (1, -2, 1) and whose 26 neighbours exist
+// (inside [lo, hi] on every axis) use the four class constants of the stencil: with
+// plain differences the Laplacian coefficient of a neighbour depends only on its class
+// (centre, face, edge, corner), Lc = {-6+12a2-8a3, 1-4a2+4a3, a2-2a3, a3}, and the mass
+// coefficient is Mc = {wm1, wm2, wm3, wm4}; the neighbour's coefficient is Lc/h^2 + Mc k^2_q,
+// real when k^2 is real (REALK).
+struct Interior {
+    int lo[3], hi[3];
+    double Lc[4], Mc[4];
+};
+
+template <typename T, int RCH, bool SUB, bool REALK>
+__global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict__ u, const cplx<T>* __restrict__ b,
                                                       cplx<T>* __restrict__ y,
                                                       const cplx<T>* __restrict__ k2,
                                                       const cplx<T>* __restrict__ tab, int nx, int ny, int nz,
-                                                      int nrhs, StencilW w) {
+                                                      int nrhs, StencilW w, Interior in) {
     const int nch = nrhs / RCH;
     const long long total = (long long)nx * ny * nz * nch;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,6 +52,44 @@ __global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict_
     const int j = (int)(tmp % ny);
     const int k = (int)(tmp / ny);
 
+    const T ih2 = (T)w.inv_h2;
+    const cplx<T> zero = mk<T>(0, 0);
+    cplx<T> acc[RCH];
+#pragma unroll
+    for (int r = 0; r < RCH; ++r) acc[r] = zero;
+
+    if (i >= in.lo[0] && i <= in.hi[0] && j >= in.lo[1] && j <= in.hi[1] && k >= in.lo[2] && k <= in.hi[2]) {
+        T L[4], M[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            L[c] = (T)(in.Lc[c] * w.inv_h2);
+            M[c] = (T)in.Mc[c];
+        }
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int cls = (dx != 0) + (dy != 0) + (dz != 0);
+                    const long long q = ((long long)(k + dz) * ny + (j + dy)) * nx + (i + dx);
+                    const cplx<T> kq = k2[q];
+                    const cplx<T>* uq = u + q * nrhs + (long long)ch * RCH;
+                    if (REALK) {
+                        const T cr = L[cls] + M[cls] * kq.x;
+#pragma unroll
+                        for (int r = 0; r < RCH; ++r) {
+                            const cplx<T> v = uq[r];
+                            acc[r].x = fma(cr, v.x, acc[r].x);
+                            acc[r].y = fma(cr, v.y, acc[r].y);
+                        }
+                    } else {
+                        const cplx<T> cc = mk<T>(L[cls] + M[cls] * kq.x, M[cls] * kq.y);
+#pragma unroll
+                        for (int r = 0; r < RCH; ++r) cmac(acc[r], cc, uq[r]);
+                    }
+                }
+    } else {
     const cplx<T>* tx = tab + 3 * i;
     const cplx<T>* ty = tab + 3 * (nx + j);
     const cplx<T>* tz = tab + 3 * (nx + ny + k);
@@ -49,11 +98,6 @@ __global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict_
     for (int d = 0; d < 3; ++d) { X[d] = tx[d]; Y[d] = ty[d]; Z[d] = tz[d]; }
 
     const T a2 = (T)w.a2, a3 = (T)w.a3, m0 = (T)w.m0, m1 = (T)w.m1, m2 = (T)w.m2, m3 = (T)w.m3;
-    const T ih2 = (T)w.inv_h2;
-    const cplx<T> zero = mk<T>(0, 0);
-    cplx<T> acc[RCH];
-#pragma unroll
-    for (int r = 0; r < RCH; ++r) acc[r] = zero;
 
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
@@ -93,6 +137,7 @@ __global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict_
             }
         }
     }
+    }
     cplx<T>* yp = y + p * nrhs + (long long)ch * RCH;
     if (SUB) {
         const cplx<T>* bp = b + p * nrhs + (long long)ch * RCH;
@@ -106,19 +151,48 @@ __global__ void __launch_bounds__(256) stencil_kernel(const cplx<T>* __restrict_
 
 template <typename T, int RCH, bool SUB>
 void launch_t(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab,
-              const helm_grid_desc& d, int nrhs, const StencilW& w, cudaStream_t s) {
+              const helm_grid_desc& d, int nrhs, const StencilW& w, const Interior& in, bool realk, cudaStream_t s) {
     const long long total = (long long)d.nx * d.ny * d.nz * (nrhs / RCH);
-    const int threads = 256;
+    const int threads = 128;
     const long long blocks = (total + threads - 1) / threads;
-    stencil_kernel<T, RCH, SUB><<<(unsigned)blocks, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w);
+    if (realk)
+        stencil_kernel<T, RCH, SUB, true><<<(unsigned)blocks, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz,
+                                                                              nrhs, w, in);
+    else
+        stencil_kernel<T, RCH, SUB, false><<<(unsigned)blocks, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz,
+                                                                               nrhs, w, in);
 }
 
 template <typename T, bool SUB>
 void dispatch(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab,
-              const helm_grid_desc& d, int nrhs, const StencilW& w, cudaStream_t s) {
-    if (nrhs % 4 == 0) launch_t<T, 4, SUB>(u, b, y, k2, tab, d, nrhs, w, s);
-    else if (nrhs % 2 == 0) launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, s);
-    else launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, s);
+              const helm_grid_desc& d, int nrhs, const StencilW& w, const Interior& in, bool realk, cudaStream_t s) {
+    // at most 4 columns per thread: consecutive threads then read consecutive 32-byte pieces of a
+    // node's [rhs] row, so every neighbour load of a warp is a contiguous run
+    if (nrhs % 4 == 0) launch_t<T, 4, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+    else if (nrhs % 2 == 0) launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+    else launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+}
+
+Interior interior_of(helm_grid g) {
+    const helm_grid_desc& d = g->d;
+    Interior in;
+    const int n[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a) {
+        const bool low = a < 2 || d.top_bc == HELM_TOP_PML;
+        in.lo[a] = std::max(1, low && d.npml > 0 ? d.npml + 1 : 1);
+        in.hi[a] = n[a] - 2 - (d.npml > 0 ? d.npml : 0);
+    }
+    const double a2 = g->w.a2, a3 = g->w.a3;
+    in.Lc[0] = -6.0 + 12.0 * a2 - 8.0 * a3;
+    in.Lc[1] = 1.0 - 4.0 * a2 + 4.0 * a3;
+    in.Lc[2] = a2 - 2.0 * a3;
+    in.Lc[3] = a3;
+    const double m0 = g->w.m0, m1 = g->w.m1, m2 = g->w.m2, m3 = g->w.m3;
+    in.Mc[0] = m0 - 6.0 * m1 + 12.0 * m2 - 8.0 * m3;
+    in.Mc[1] = m1 - 4.0 * m2 + 4.0 * m3;
+    in.Mc[2] = m2 - 2.0 * m3;
+    in.Mc[3] = m3;
+    return in;
 }
 
 template <bool SUB>
@@ -128,10 +202,13 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
     const double es = prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
     const double bytes = (double)g->n * es * ((SUB ? 3.0 : 2.0) * nrhs + 1.0);
     const int tok = prof_begin(g->ctx, "stencil");
+    const Interior in = interior_of(g);
     if (prec == HELM_PREC_FP64) {
-        dispatch<double, SUB>((const c128*)u, (const c128*)b, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, s);
+        dispatch<double, SUB>((const c128*)u, (const c128*)b, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, in,
+                              g->k2_real, s);
     } else {
-        dispatch<float, SUB>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, s);
+        dispatch<float, SUB>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, in,
+                             g->k2_real, s);
     }
     prof_end(g->ctx, tok, bytes);
     HELM_LAUNCH_CHECK(g->ctx, "stencil_kernel");

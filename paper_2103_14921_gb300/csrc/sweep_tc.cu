@@ -1,0 +1,307 @@
+// Plane sweeps of the ORAS local solves on the 5th-generation tensor cores
+// (tcgen05, kind::tf32, FP32 accumulation in TMEM, operands staged by TMA).
+//
+// Each sweep step multiplies, for every box, the dense plane inverse
+// G_k = S_k^{-1} (m x m complex, stored interleaved (re, im) with row pitch
+// ld) by the prepared m x nrhs complex block R.  The complex product is one
+// real GEMM: row i of G read as 2m floats (re, im, re, im, ...) is a K-major
+// A operand with K = 2m, and the B operand is the 2x2 real embedding of R,
+// stored transposed (N x K, K contiguous):
+//   B^T[2r][2p] = Re R[p][r],  B^T[2r][2p+1] = -Im R[p][r],
+//   B^T[2r+1][2p] = Im R[p][r], B^T[2r+1][2p+1] = Re R[p][r],
+// so D[i][2r] = Re (G R)[i][r] and D[i][2r+1] = Im (G R)[i][r].
+//
+// tc_prep builds B^T for the step (FWD: R = b_k - L_k y_{k-1}; BWD:
+// R = U_k x_{k+1}).  tc_sweep_gemm: one CTA per (128-row tile, box), four
+// warps; warp 0 lane 0 issues the TMA loads of 128 x 32-float A tiles and
+// N x 32-float B tiles (128-byte swizzle) into a 5-stage mbarrier ring, warp 1
+// lane 0 issues 4 MMAs (M = 128, N = NPAD, K = 8) per stage and commits each
+// stage back to the producer, and all four warps read the accumulator from
+// TMEM (thread t <-> row t) and write y_k (FWD) or x_k = y_k - D (BWD).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 32;     // fp32 per 128-byte swizzled row
+
+// Tiles of 32 plane nodes x nrhs: values formed with the rhs index fastest (coalesced reads of
+// the [node][rhs] local vectors), transposed through shared memory, written as B^T rows.
+constexpr int PREP_TP = 32;
+
+__global__ void __launch_bounds__(256) tc_prep(const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
+                                               const c64* __restrict__ loc, float* __restrict__ bt, int ld2, int npad,
+                                               int nrhs, int s, int fwd) {
+    __shared__ c64 tile[128 * (PREP_TP + 1)];
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m, bz = B.dims[2], bx = B.dims[0], by = B.dims[1];
+    const int k = fwd ? s : bz - 1 - s;
+    if (k < 0 || k >= bz) return;
+    if (!fwd && k == bz - 1) return;
+    const long long plane = B.loc_off + (long long)k * m;
+    const long long nbr = fwd ? plane - m : plane + m;
+    const int off = fwd ? 0 : 18;
+    float* bb = bt + (size_t)blockIdx.y * npad * ld2;
+    for (int p0 = blockIdx.x * PREP_TP; p0 < m; p0 += gridDim.x * PREP_TP) {
+        for (int e = threadIdx.x; e < PREP_TP * nrhs; e += blockDim.x) {
+            const int pl = e / nrhs, r = e % nrhs, p = p0 + pl;
+            c64 acc = mk<float>(0, 0);
+            if (p < m) {
+                if (fwd) acc = loc[(plane + p) * nrhs + r];
+                if (!(fwd && k == 0)) {
+                    const int px = p % bx, py = p / bx;
+                    const c64* cp = coef + (plane + p) * 27 + off;
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const int qy = py + dy;
+                        if (qy < 0 || qy >= by) continue;
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int qx = px + dx;
+                            if (qx < 0 || qx >= bx) continue;
+                            const c64 c = cp[(dy + 1) * 3 + (dx + 1)];
+                            const c64 v = loc[(nbr + qy * bx + qx) * nrhs + r];
+                            if (fwd) {
+                                acc.x -= c.x * v.x - c.y * v.y;
+                                acc.y -= c.x * v.y + c.y * v.x;
+                            } else {
+                                cmac(acc, c, v);
+                            }
+                        }
+                    }
+                }
+            }
+            tile[r * (PREP_TP + 1) + pl] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nrhs * PREP_TP; e += blockDim.x) {
+            const int r = e / PREP_TP, pl = e % PREP_TP, p = p0 + pl;
+            if (p < m) {
+                const c64 a = tile[r * (PREP_TP + 1) + pl];
+                reinterpret_cast<float2*>(bb + (size_t)(2 * r) * ld2)[p] = make_float2(a.x, -a.y);
+                reinterpret_cast<float2*>(bb + (size_t)(2 * r + 1) * ld2)[p] = make_float2(a.y, a.x);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int NPAD>
+struct TcCfg {
+    static constexpr int A_BYTES = TC_BM * TC_BK * 4;
+    static constexpr int B_BYTES = NPAD * TC_BK * 4;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = NPAD >= 256 ? 3 : (NPAD >= 128 ? 4 : 5);
+    static constexpr uint32_t TCOLS = NPAD <= 32 ? 32 : (NPAD <= 64 ? 64 : (NPAD <= 128 ? 128 : 256));
+    static constexpr int SMEM = STAGES * STAGE + (2 * STAGES + 1) * 8 + 16 + 1024;
+};
+
+template <int NPAD>
+__global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapB,
+                                                        const BoxInfo* __restrict__ boxes, c64* __restrict__ loc,
+                                                        int nrhs, int s, int fwd, int* __restrict__ err) {
+    using Cfg = TcCfg<NPAD>;
+    constexpr int TC_STAGES = Cfg::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~static_cast<uintptr_t>(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + TC_STAGES * Cfg::STAGE);
+    uint64_t* empty = full + TC_STAGES;
+    uint64_t* done = empty + TC_STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m, bz = B.dims[2];
+    const int k = fwd ? s : bz - 1 - s;
+    if (k < 0 || k >= bz) return;
+    if (!fwd && k == bz - 1) return;
+    const int row0 = blockIdx.x * TC_BM;
+    if (row0 >= m) return;
+    const int nK = (2 * m + TC_BK - 1) / TC_BK;
+    const int plane = B.plane0 + k;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+        tc::prefetch_tmap(&mapA);
+        tc::prefetch_tmap(&mapB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, Cfg::TCOLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kc = 0; kc < nK; ++kc) {
+            const int st = kc % TC_STAGES;
+            if (kc >= TC_STAGES && !tc::mbar_wait(&empty[st], ((kc / TC_STAGES) - 1) & 1, err, 1)) break;
+            unsigned char* sa = base + st * Cfg::STAGE;
+            tc::mbar_arrive_expect_tx(&full[st], Cfg::STAGE);
+            tc::tma_load_3d(sa, &mapA, kc * TC_BK, row0, plane, &full[st]);
+            tc::tma_load_3d(sa + Cfg::A_BYTES, &mapB, kc * TC_BK, 0, blockIdx.y, &full[st]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = tc::idesc_tf32(TC_BM, NPAD);
+        for (int kc = 0; kc < nK; ++kc) {
+            const int st = kc % TC_STAGES;
+            if (!tc::mbar_wait(&full[st], (kc / TC_STAGES) & 1, err, 2)) break;
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(base + st * Cfg::STAGE);
+            const uint32_t sb = sa + Cfg::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 8; ++kk)
+                tc::mma_tf32(tmem, tc::desc_k_sw128(sa + kk * 32), tc::desc_k_sw128(sb + kk * 32), idesc,
+                             (kc > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_commit(&empty[st]);
+        }
+        tc::mma_commit(done);
+    }
+    __syncwarp();
+
+    // epilogue: thread t of warp w owns TMEM lane 32 w + t = output row row0 + 32 w + t
+    const bool ok = tc::mbar_wait(done, 0, err, 3);
+    tc::fence_after_sync();
+    if (ok) {
+        const int row = row0 + warp * 32 + lane;
+        c64* dst = loc + (B.loc_off + (long long)k * m + row) * nrhs;
+#pragma unroll
+        for (int c0 = 0; c0 < NPAD; c0 += 32) {
+            uint32_t v[32];
+            tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld_wait();
+            if (row < m) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int r = c0 / 2 + q;
+                    if (r < nrhs) {
+                        const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
+                        if (fwd) {
+                            dst[r] = mk<float>(re, im);
+                        } else {
+                            const c64 o = dst[r];
+                            dst[r] = mk<float>(o.x - re, o.y - im);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, Cfg::TCOLS);
+    }
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime so that the
+// library itself does not link against libcuda (it still loads on machines without a driver).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool encode_3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1) {
+    PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = encode_fn();
+    if (!cuTensorMapEncodeTiled) return false;
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {d0 * 4, d0 * d1 * 4};
+    cuuint32_t box[3] = {b0, b1, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int NPAD>
+helm_status run_tc(helm_ctx ctx, const PlaneSet& P, c64* loc, float* bt, int nrhs, cudaStream_t st, int* err) {
+    using Cfg = TcCfg<NPAD>;
+    CUtensorMap mapA, mapB;
+    const int ld = P.ld;
+    if (!encode_3d(&mapA, P.G, 2ull * ld, (uint64_t)ld, (uint64_t)P.nplanes, TC_BK, TC_BM) ||
+        !encode_3d(&mapB, bt, 2ull * ld, (uint64_t)NPAD, (uint64_t)P.nbox, TC_BK, NPAD))
+        return set_error(ctx, HELM_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc_sweep_gemm<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        attr = true;
+    }
+    const int m = P.m_max;
+    const dim3 ggrid((m + TC_BM - 1) / TC_BM, P.nbox);
+    const dim3 pgrid((unsigned)((m + PREP_TP - 1) / PREP_TP), P.nbox);
+    const c64* coef = (const c64*)P.coef;
+    const double es = sizeof(c64);
+    auto bytes = [&](int s, bool fwd, double& gemm, double& prep) {
+        gemm = prep = 0;
+        for (const auto& b : P.hbox) {
+            const int bz = b.dims[2];
+            const bool act = fwd ? s < bz : (s >= 1 && s <= bz - 1);
+            if (!act) continue;
+            gemm += ((double)b.m * b.m + (double)b.m * NPAD / 2 + (fwd ? 1.0 : 2.0) * b.m * nrhs) * es;
+            prep += ((double)b.m * 9 + (fwd ? 3.0 : 2.0) * b.m * nrhs) * es;
+        }
+    };
+    double gb, pb;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int fwd = pass == 0;
+        for (int s = fwd ? 0 : 1; s < P.bz_max; ++s) {
+            bytes(s, fwd, gb, pb);
+            int t = prof_begin(ctx, "sweep_prep");
+            tc_prep<<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
+            prof_end(ctx, t, pb);
+            t = prof_begin(ctx, "sweep_gemm_tc");
+            tc_sweep_gemm<NPAD><<<ggrid, 128, Cfg::SMEM, st>>>(mapA, mapB, P.dbox, loc, nrhs, s, fwd, err);
+            prof_end(ctx, t, gb);
+            ctx->launches += 2;
+        }
+    }
+    return cuda_check(ctx, cudaGetLastError(), "tensor-core plane sweeps");
+}
+
+}  // namespace
+
+int tc_npad(int nrhs) {
+    const int n = 2 * nrhs;
+    if (n <= 16) return 16;
+    if (n <= 32) return 32;
+    if (n <= 64) return 64;
+    if (n <= 128) return 128;
+    return 256;
+}
+
+helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, void* loc, void* bt, int npad, int nrhs,
+                              cudaStream_t st, int* err) {
+    if (nrhs > 128 || tc_npad(nrhs) > npad) return set_error(ctx, HELM_EINVAL, "tensor-core sweep: too many rhs");
+    switch (npad) {
+        case 16: return run_tc<16>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 32: return run_tc<32>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 64: return run_tc<64>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 128: return run_tc<128>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        default: return run_tc<256>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+    }
+}

@@ -1,0 +1,88 @@
+"""Tensor-core (tcgen05 kind::tf32) plane sweeps, through the C ABI.
+
+Single-plane boxes make every local solve exactly one tensor-core GEMM
+y = G_0 (R_i v); the result must equal the same product computed in FP64
+from TF32-rounded operands up to FP32 accumulation (2e-5 relative), and the
+exact FP64 product up to TF32 input rounding (2e-3).  Multi-plane TF32 local
+solves are checked through converged FGMRES solutions.
+"""
+import numpy as np
+import pytest
+
+from oracle.discretization import Problem, apply_A
+from oracle.schwarz import direct_solve_planes
+from paper_2103_14921_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2103_14921_gb300 import build, helm
+    build.build()
+    return helm.Context(0)
+
+
+def _tf32(a, mode):
+    """Round float32 values to TF32 (10 explicit mantissa bits): truncation or nearest-even."""
+    import torch
+    x = a.contiguous().view(torch.int32)
+    if mode == "rn":
+        lsb = (x >> 13) & 1
+        x = x + 0x0FFF + lsb
+    return (x & ~0x1FFF).view(torch.float32)
+
+
+def _emulate(G, R, mode):
+    import torch
+    Gr = torch.complex(_tf32(G.real.float(), mode), _tf32(G.imag.float(), mode)).to(torch.complex128)
+    Rr = torch.complex(_tf32(R.real.float(), mode), _tf32(R.imag.float(), mode)).to(torch.complex128)
+    return Gr @ Rr
+
+
+@pytest.mark.parametrize("dims,nrhs", [((24, 20, 2), 16), ((37, 29, 2), 3), ((12, 40, 2), 40)])
+def test_single_plane_boxes_equal_emulated_tf32_gemm(ctx, dims, nrhs):
+    import torch
+    from paper_2103_14921_gb300 import helm
+    nx, ny, nz = dims
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 1.0)
+    grid = helm.Grid(ctx, nx, ny, nz, 25.0, 5.0, c, npml=1, weights=helm.fit_weights())
+    parts = (2, 2, 2)
+    o = helm.Oras(grid, parts, 0, factor_prec=helm.PREC_TF32)
+    v = torch.from_numpy(synth.random_complex((nz, ny, nx, nrhs), 61)).cuda()
+    got = o.apply(v)
+    nb = o.box_info(0)[0]
+    for b in range(nb):
+        _, lo, bd = o.box_info(b)
+        assert bd[2] == 1
+        G = o.plane_inverse(b, 0)                                 # stored complex64 values, widened
+        vb = v[lo[2], lo[1]:lo[1] + bd[1], lo[0]:lo[0] + bd[0], :].reshape(-1, nrhs)
+        vb32 = vb.to(torch.complex64).to(torch.complex128)
+        y = got[lo[2], lo[1]:lo[1] + bd[1], lo[0]:lo[0] + bd[0], :].reshape(-1, nrhs)
+        exact = G @ vb32
+        errs = [float(torch.linalg.norm(y - _emulate(G, vb32, mode)) / torch.linalg.norm(exact))
+                for mode in ("trunc", "rn")]
+        assert min(errs) <= 2e-5, (b, errs)
+        assert float(torch.linalg.norm(y - exact) / torch.linalg.norm(exact)) <= 2e-3
+
+
+def test_tf32_fgmres_converges_to_the_direct_solution(ctx):
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (30, 28, 26)
+    nx, ny, nz = dims
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 0.6)
+    w = helm.fit_weights()
+    grid = helm.Grid(ctx, nx, ny, nz, 25.0, 6.0, c, npml=4, weights=w)
+    prob = Problem(nx, ny, nz, 25.0, 6.0, c, npml=4, weights=w)
+    pos = synth.source_plane_positions(nx, ny, 4, 3, 6, 9)
+    b = synth.point_sources(nx, ny, nz, 25.0, pos)
+    xs = direct_solve_planes(prob, b.reshape(-1, 6)).reshape(b.shape)
+    o = helm.Oras(grid, (2, 2, 2), 2, coarse_ratio=4, factor_prec=helm.PREC_TF32)
+    x, stats = o.solve(torch.from_numpy(b).cuda(), tol=1e-6, restart=30, basis_prec=helm.PREC_FP32)
+    x = x.cpu().numpy()
+    for r in range(6):
+        assert stats[r]["converged"]
+        res = np.linalg.norm(apply_A(prob, x[..., r]) - b[..., r]) / np.linalg.norm(b[..., r])
+        assert res <= 1e-6
+        assert np.linalg.norm(x[..., r] - xs[..., r]) <= 1e-5 * np.linalg.norm(xs[..., r])
