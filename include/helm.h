@@ -211,6 +211,56 @@ typedef struct {
 helm_status gmres_solve(helm_oras o, const void* b, void* x, int nrhs, const helm_gmres_desc* desc,
                         helm_rhs_stats* stats);
 
+/* -------------------------------------------------------------- serving
+ *
+ * A request loop on one context (BASELINE serving pattern; the paper's
+ * forward problem with many right-hand sides per frequency arriving over
+ * time).  A worker thread owns the context's stream: factors are built on
+ * first use and kept resident in a cache keyed by (model_id, grid
+ * description, ORAS description, restart, flexible, basis precision), and
+ * evicted least-recently-used when idle and the HBM budget needs the room.
+ * Requests that share factors are batched: each right-hand side takes one
+ * column slot of the factor set's batch, new requests join at the next
+ * restart-cycle boundary while others are running, and every column keeps
+ * its own Krylov space, tolerance and iteration count, so a result does not
+ * depend on which other requests share the batch.  A request is admitted
+ * when its columns fit the free slots and its factors (if not cached) fit
+ * the budget; one that cannot fit even on an idle server fails with
+ * HELM_ENOMEM.  While serving is active no other call may use the context.
+ */
+typedef struct {
+    uint64_t        model_id;  /* caller's identifier of the wave-speed model (part of the cache key) */
+    helm_grid_desc  grid;
+    const void*     c;         /* complex128 [nz][ny][nx], host or device; read when the factors are built */
+    helm_oras_desc  oras;
+    helm_gmres_desc gmres;     /* tol and maxit per request; restart, flexible, basis_prec key the batch */
+    int             nrhs;      /* 1 .. slots_per_batch */
+    const void*     b;         /* complex128 [N][nrhs], host or device; read when the request is admitted */
+    void*           x;         /* complex128 [N][nrhs], host or device; written before poll reports done */
+} helm_request;
+
+typedef struct {
+    int    done;               /* 1 once x is written (or the request failed)                  */
+    int    status;             /* HELM_OK, HELM_ENOTCONV, or the error that ended the request   */
+    int    iterations_max;     /* largest iteration count over the request's columns            */
+    double true_relres_max;    /* largest FP64 true relative residual over its columns          */
+    double queue_ms;           /* submit -> admitted into a batch                               */
+    double latency_ms;         /* submit -> done                                                */
+    int    factors_reused;     /* 1 if the factors came from the cache                          */
+} helm_request_stats;
+
+/* Start the worker with `slots_per_batch` columns per factor set (1..256). */
+helm_status helm_serve_start(helm_ctx ctx, int slots_per_batch);
+/* Queue a request (non-blocking).  The buffers c, b and x must stay valid
+ * until helm_poll reports done.  Returns HELM_EINVAL for a malformed request. */
+helm_status helm_submit(helm_ctx ctx, const helm_request* req, uint64_t* ticket);
+/* Non-blocking status of a ticket; HELM_ENOTFOUND for an unknown ticket.
+ * Once done is reported the ticket is forgotten. */
+helm_status helm_poll(helm_ctx ctx, uint64_t ticket, int* done, helm_request_stats* stats);
+/* Finish every queued and running request, then stop the worker and free
+ * the cached factors. */
+helm_status helm_serve_stop(helm_ctx ctx);
+
 #ifdef __cplusplus
 }
 #endif

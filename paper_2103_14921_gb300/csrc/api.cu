@@ -74,6 +74,7 @@ extern "C" helm_status helm_create(helm_ctx* out, int device, void* stream, size
 
 extern "C" void helm_destroy(helm_ctx ctx) {
     if (!ctx) return;
+    if (ctx->server) helm_serve_stop(ctx);
     if (ctx->children > 0) {
         ctx->destroy_pending = true;   // freed when its last grid is destroyed
         return;

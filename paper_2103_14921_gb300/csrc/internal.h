@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <algorithm>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -53,6 +54,8 @@ struct Profiler {
     std::vector<double> ms, bytes;
 };
 
+struct Server;   // serve.cu
+
 struct helm_ctx_s {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -64,6 +67,7 @@ struct helm_ctx_s {
     int children = 0;          // live grids; helm_destroy defers the delete until they are gone
     bool destroy_pending = false;
     Profiler prof;
+    Server* server = nullptr;
 };
 
 // Bracket one launch of an instrumented family with events on the context's stream.
@@ -192,5 +196,39 @@ helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbu
 int tc_npad(int nrhs);
 helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, void* loc, void* bt, int npad, int nrhs,
                               cudaStream_t st, int* err);
+// Device bytes an ORAS handle with this description will hold (factors, local operators,
+// coarse level) plus its apply scratch for nrhs columns; an estimate for admission control.
+size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int nrhs);
 // HELM_ETIMEOUT if a bounded device wait of this handle's kernels gave up
 helm_status oras_check_device_error(helm_oras o);
+
+// Per-column state of a batched (F)GMRES (FP64 quantities).
+struct RhsState {
+    double bnorm;
+    int active;       // column still iterating this cycle
+    int steps;        // Krylov steps taken in this cycle
+    int iters;        // total iterations
+    int done;         // finished (converged, out of iterations, or an empty slot)
+    double est;       // last residual estimate (relative)
+    double tol;
+    int maxit;
+};
+
+// Batched (F)GMRES over a fixed number of columns (krylov.cu).  Columns are started with
+// begin_columns, advanced one restart cycle at a time, and retired; a column's arithmetic
+// does not depend on which other columns are active.
+struct KrylovEngine {
+    virtual ~KrylovEngine() {}
+    virtual c128* B() = 0;   // [N][S] right-hand sides
+    virtual c128* X() = 0;   // [N][S] solutions
+    virtual int slots() const = 0;
+    virtual const RhsState& state(int c) const = 0;
+    virtual double true_rel(int c) const = 0;
+    virtual size_t bytes() const = 0;
+    virtual helm_status begin_columns(const int* cols, int n, const double* tol, const int* maxit) = 0;
+    virtual void retire(int c) = 0;
+    virtual helm_status push_state() = 0;
+    virtual helm_status cycle(bool* any_left) = 0;
+};
+KrylovEngine* make_krylov_engine(helm_oras o, int S, int restart, bool flexible, int basis_prec, c128* B_ext,
+                                 c128* X_ext, helm_status* rc);

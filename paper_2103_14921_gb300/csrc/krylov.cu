@@ -162,15 +162,6 @@ __global__ void scale_copy(const cplx<TS>* __restrict__ src, cplx<TD>* __restric
     }
 }
 
-// Per-rhs solver state (FP64), one thread per rhs.
-struct RhsState {
-    double bnorm;
-    int active;       // column still iterating this cycle
-    int steps;        // Krylov steps taken in this cycle
-    int iters;        // total iterations
-    int done;         // finished (converged or out of iterations)
-    double est;       // last residual estimate (relative)
-};
 
 // Start of a cycle: inv[r] = 1/beta for active columns, g = beta e_0.
 __global__ void cycle_start(RhsState* __restrict__ S, const double* __restrict__ beta, double* __restrict__ inv,
@@ -189,8 +180,7 @@ __global__ void cycle_start(RhsState* __restrict__ S, const double* __restrict__
 // H[r][i][j] is (m+1) x m per rhs; hnorm[r] = ||w|| = H[j+1][j]; inv[r] <- 1/hnorm (or 0).
 __global__ void givens_step(RhsState* __restrict__ S, c128* __restrict__ H, double* __restrict__ cs,
                             c128* __restrict__ sn, c128* __restrict__ g, const double* __restrict__ hnorm,
-                            double* __restrict__ inv, int j, int m, int nrhs, double tol, int maxit,
-                            int* __restrict__ running) {
+                            double* __restrict__ inv, int j, int m, int nrhs, int* __restrict__ running) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrhs) return;
     RhsState& s = S[r];
@@ -241,7 +231,7 @@ __global__ void givens_step(RhsState* __restrict__ S, c128* __restrict__ H, doub
     s.steps = j + 1;
     s.iters += 1;
     s.est = hypot(gg[j + 1].x, gg[j + 1].y) / s.bnorm;
-    const bool stop = s.est <= tol || hn == 0.0 || s.iters >= maxit || j + 1 >= m;
+    const bool stop = s.est <= s.tol || hn == 0.0 || s.iters >= s.maxit || j + 1 >= m;
     inv[r] = (hn > 0.0 && !stop) ? 1.0 / hn : 0.0;
     if (stop) s.active = 0;
     else atomicAdd(running, 1);
@@ -293,142 +283,205 @@ __global__ void finite_check(const c128* __restrict__ v, long long n_el, int* __
         if (!isfinite(v[e].x) || !isfinite(v[e].y)) atomicOr(bad, 1);
 }
 
+// column-masked set-up of new columns: x = 0, r = b (mask[r] != 0)
+__global__ void start_columns_kernel(const c128* __restrict__ B, c128* __restrict__ X, c128* __restrict__ R,
+                                     const int* __restrict__ mask, long long n_el, int nrhs) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
+        if (!mask[e % nrhs]) continue;
+        X[e] = mk<double>(0, 0);
+        R[e] = B[e];
+    }
+}
+
+// bad |= 1 when a masked column of v has NaN/Inf
+__global__ void finite_check_cols(const c128* __restrict__ v, const int* __restrict__ mask, long long n_el, int nrhs,
+                                  int* __restrict__ bad) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x)
+        if (mask[e % nrhs] && (!isfinite(v[e].x) || !isfinite(v[e].y))) atomicOr(bad, 1);
+}
+
 // ------------------------------------------------------------------ host driver
 
-struct Work {
-    helm_ctx ctx;
+// Batched (F)GMRES over S columns: workspaces, per-column state and one restart cycle at a time.
+template <typename T>
+struct Krylov final : KrylovEngine {
+    helm_oras o = nullptr;
+    helm_ctx ctx = nullptr;
+    cudaStream_t st = nullptr;
+    int S = 0, m = 0, wp = 0;
+    bool flex = true;
+    long long N = 0, nel = 0;
+    int nblk = 0, ldp = 0;
+    unsigned eg = 0, rg = 0;
     std::vector<std::pair<void*, size_t>> allocs;
+    cplx<T>*V = nullptr, *Zb = nullptr, *w = nullptr, *u = nullptr;
+    c128 *Bd = nullptr, *Xd = nullptr, *r = nullptr, *H = nullptr, *sn = nullptr, *gv = nullptr, *y = nullptr;
+    c128 *part = nullptr, *hpass = nullptr;
+    double *cs = nullptr, *dpart = nullptr, *beta = nullptr, *inv = nullptr, *hn = nullptr;
+    RhsState* Sd = nullptr;
+    int *running = nullptr, *mask = nullptr;
+    std::vector<RhsState> hs;
+    std::vector<double> trel;
+
     helm_status alloc(void** p, size_t bytes, const char* what) {
         helm_status rc = dev_alloc(ctx, p, bytes, what);
         if (!rc && *p) allocs.push_back({*p, bytes});
         return rc;
     }
-    ~Work() {
-        cudaStreamSynchronize(ctx->stream);
-        for (auto& a : allocs) dev_free(ctx, a.first, a.second);
+    ~Krylov() override {
+        if (ctx) {
+            cudaStreamSynchronize(st);
+            for (auto& a : allocs) dev_free(ctx, a.first, a.second);
+        }
     }
-};
+    c128* B() override { return Bd; }
+    c128* X() override { return Xd; }
+    int slots() const override { return S; }
+    const RhsState& state(int c) const override { return hs[c]; }
+    double true_rel(int c) const override { return trel[c]; }
+    size_t bytes() const override {
+        size_t b = 0;
+        for (auto& a : allocs) b += a.second;
+        return b;
+    }
 
-template <typename T>
-helm_status solve_t(helm_oras o, const c128* b, c128* x, int nrhs, const helm_gmres_desc& D, helm_rhs_stats* stats) {
-    helm_grid g = o->g;
-    helm_ctx ctx = g->ctx;
-    cudaStream_t st = ctx->stream;
-    const int wp = sizeof(T) == 8 ? HELM_PREC_FP64 : HELM_PREC_FP32;
-    const int m = D.restart;
-    const long long N = g->n;
-    const long long nel = N * nrhs;
-    const bool flex = D.flexible != 0;
-    Work W{ctx};
-    cplx<T>*V = nullptr, *Zb = nullptr, *w = nullptr, *u = nullptr;
-    c128 *r = nullptr, *H = nullptr, *sn = nullptr, *gv = nullptr, *y = nullptr, *part = nullptr, *hpass = nullptr;
-    double *cs = nullptr, *dpart = nullptr, *beta = nullptr, *inv = nullptr, *hn = nullptr;
-    RhsState* S = nullptr;
-    int* running = nullptr;
-    const int nblk = red_blocks(ctx, nel, nrhs);
-    const int ldp = m + 1;
-    HELM_TRY(W.alloc((void**)&V, (size_t)(m + 1) * nel * sizeof(cplx<T>), "Krylov basis V"));
-    if (flex) HELM_TRY(W.alloc((void**)&Zb, (size_t)m * nel * sizeof(cplx<T>), "Krylov basis Z"));
-    HELM_TRY(W.alloc((void**)&w, nel * sizeof(cplx<T>), "Arnoldi vector"));
-    HELM_TRY(W.alloc((void**)&u, nel * sizeof(cplx<T>), "preconditioned vector"));
-    HELM_TRY(W.alloc((void**)&r, nel * sizeof(c128), "residual"));
-    HELM_TRY(W.alloc((void**)&H, (size_t)nrhs * (m + 1) * m * sizeof(c128), "Hessenberg"));
-    HELM_TRY(W.alloc((void**)&sn, (size_t)nrhs * m * sizeof(c128), "Givens sines"));
-    HELM_TRY(W.alloc((void**)&cs, (size_t)nrhs * m * sizeof(double), "Givens cosines"));
-    HELM_TRY(W.alloc((void**)&gv, (size_t)nrhs * (m + 1) * sizeof(c128), "Givens rhs"));
-    HELM_TRY(W.alloc((void**)&y, (size_t)nrhs * m * sizeof(c128), "least-squares solution"));
-    HELM_TRY(W.alloc((void**)&part, (size_t)nblk * ldp * nrhs * sizeof(c128), "dot partials"));
-    HELM_TRY(W.alloc((void**)&hpass, (size_t)ldp * nrhs * sizeof(c128), "dot pass"));
-    HELM_TRY(W.alloc((void**)&dpart, (size_t)nblk * nrhs * sizeof(double), "norm partials"));
-    HELM_TRY(W.alloc((void**)&beta, nrhs * sizeof(double), "norms"));
-    HELM_TRY(W.alloc((void**)&inv, nrhs * sizeof(double), "inverse norms"));
-    HELM_TRY(W.alloc((void**)&hn, nrhs * sizeof(double), "new norms"));
-    HELM_TRY(W.alloc((void**)&S, nrhs * sizeof(RhsState), "rhs state"));
-    HELM_TRY(W.alloc((void**)&running, 2 * sizeof(int), "running flag"));
-    const unsigned eg = (unsigned)std::min<long long>((nel + 255) / 256, (long long)ctx->sm_count * 16);
-    const unsigned rg = (unsigned)((nrhs + 127) / 128);
+    helm_status init(helm_oras o_, int S_, int restart, bool flexible, int basis_prec, c128* B_ext, c128* X_ext) {
+        o = o_;
+        ctx = o->g->ctx;
+        st = ctx->stream;
+        S = S_;
+        m = restart;
+        flex = flexible;
+        wp = basis_prec;
+        N = o->g->n;
+        nel = N * S;
+        nblk = red_blocks(ctx, nel, S);
+        ldp = m + 1;
+        eg = (unsigned)std::min<long long>((nel + 255) / 256, (long long)ctx->sm_count * 16);
+        rg = (unsigned)((S + 127) / 128);
+        if (B_ext) Bd = B_ext;
+        else HELM_TRY(alloc((void**)&Bd, nel * sizeof(c128), "batch right-hand sides"));
+        if (X_ext) Xd = X_ext;
+        else HELM_TRY(alloc((void**)&Xd, nel * sizeof(c128), "batch solutions"));
+        HELM_TRY(alloc((void**)&V, (size_t)(m + 1) * nel * sizeof(cplx<T>), "Krylov basis V"));
+        if (flex) HELM_TRY(alloc((void**)&Zb, (size_t)m * nel * sizeof(cplx<T>), "Krylov basis Z"));
+        HELM_TRY(alloc((void**)&w, nel * sizeof(cplx<T>), "Arnoldi vector"));
+        HELM_TRY(alloc((void**)&u, nel * sizeof(cplx<T>), "preconditioned vector"));
+        HELM_TRY(alloc((void**)&r, nel * sizeof(c128), "residual"));
+        HELM_TRY(alloc((void**)&H, (size_t)S * (m + 1) * m * sizeof(c128), "Hessenberg"));
+        HELM_TRY(alloc((void**)&sn, (size_t)S * m * sizeof(c128), "Givens sines"));
+        HELM_TRY(alloc((void**)&cs, (size_t)S * m * sizeof(double), "Givens cosines"));
+        HELM_TRY(alloc((void**)&gv, (size_t)S * (m + 1) * sizeof(c128), "Givens rhs"));
+        HELM_TRY(alloc((void**)&y, (size_t)S * m * sizeof(c128), "least-squares solution"));
+        HELM_TRY(alloc((void**)&part, (size_t)nblk * ldp * S * sizeof(c128), "dot partials"));
+        HELM_TRY(alloc((void**)&hpass, (size_t)ldp * S * sizeof(c128), "dot pass"));
+        HELM_TRY(alloc((void**)&dpart, (size_t)nblk * S * sizeof(double), "norm partials"));
+        HELM_TRY(alloc((void**)&beta, S * sizeof(double), "norms"));
+        HELM_TRY(alloc((void**)&inv, S * sizeof(double), "inverse norms"));
+        HELM_TRY(alloc((void**)&hn, S * sizeof(double), "new norms"));
+        HELM_TRY(alloc((void**)&Sd, S * sizeof(RhsState), "column state"));
+        HELM_TRY(alloc((void**)&running, 2 * sizeof(int), "running flag"));
+        HELM_TRY(alloc((void**)&mask, S * sizeof(int), "column mask"));
+        hs.assign(S, RhsState{0.0, 0, 0, 0, 1, 0.0, 0.0, 0});
+        trel.assign(S, 0.0);
+        HELM_CUDA(ctx, cudaMemcpyAsync(Sd, hs.data(), S * sizeof(RhsState), cudaMemcpyHostToDevice, st));
+        if (!X_ext) HELM_CUDA(ctx, cudaMemsetAsync(Xd, 0, nel * sizeof(c128), st));
+        if (!B_ext) HELM_CUDA(ctx, cudaMemsetAsync(Bd, 0, nel * sizeof(c128), st));
+        HELM_CUDA(ctx, cudaMemsetAsync(r, 0, nel * sizeof(c128), st));
+        return HELM_OK;
+    }
 
-    auto norms = [&](const auto* vec, double* out) {
+    template <typename V_t>
+    void norms(const V_t* vec, double* out) {
         const int tk = prof_begin(ctx, "krylov_misc");
-        norm2_kernel<<<nblk, RED_THREADS, 0, st>>>(vec, nel, nrhs, dpart);
-        finish_norm2<<<rg, 128, 0, st>>>(dpart, nblk, nrhs, out);
+        norm2_kernel<<<nblk, RED_THREADS, 0, st>>>(vec, nel, S, dpart);
+        finish_norm2<<<rg, 128, 0, st>>>(dpart, nblk, S, out);
         prof_end(ctx, tk, (double)nel * sizeof(*vec));
         ctx->launches += 2;
-    };
-    auto dots_into = [&](const cplx<T>* Vb, const cplx<T>* vec, int ni, c128* dst, int ldh_i, int ldh_r, int col,
-                         int accumulate) {
-        const int tk = prof_begin(ctx, "arnoldi");
-        dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, nrhs, 0, ni, part, ldp);
-        prof_end(ctx, tk, (double)(ni + 1) * nel * sizeof(cplx<T>));
-        finish_dots<<<(ni * nrhs + 127) / 128, 128, 0, st>>>(part, nblk, ldp, ni, nrhs, dst, ldh_i, ldh_r, col,
-                                                             accumulate);
-        ctx->launches += 2;
-    };
+    }
 
-    // ||b||, finite check
-    {
+    void dots_into(const cplx<T>* Vb, const cplx<T>* vec, int ni, c128* dst, int ldh_i, int ldh_r, int col,
+                   int accumulate) {
+        const int tk = prof_begin(ctx, "arnoldi");
+        dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, S, 0, ni, part, ldp);
+        prof_end(ctx, tk, (double)(ni + 1) * nel * sizeof(cplx<T>));
+        finish_dots<<<(ni * S + 127) / 128, 128, 0, st>>>(part, nblk, ldp, ni, S, dst, ldh_i, ldh_r, col, accumulate);
+        ctx->launches += 2;
+    }
+
+    // Start the listed columns (their b already in B()): x = 0, r = b, state reset.
+    helm_status begin_columns(const int* cols, int n, const double* tol, const int* maxit) override {
+        std::vector<int> hm(S, 0);
+        for (int i = 0; i < n; ++i) hm[cols[i]] = 1;
+        HELM_CUDA(ctx, cudaMemcpyAsync(mask, hm.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
         int* bad = running + 1;
-        cudaMemsetAsync(bad, 0, sizeof(int), st);
-        finite_check<<<eg, 256, 0, st>>>(b, nel, bad);
-        ctx->launches++;
+        HELM_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), st));
+        finite_check_cols<<<eg, 256, 0, st>>>(Bd, mask, nel, S, bad);
+        start_columns_kernel<<<eg, 256, 0, st>>>(Bd, Xd, r, mask, nel, S);
+        ctx->launches += 2;
+        norms(Bd, beta);
+        std::vector<double> hb(S);
         int hbad = 0;
-        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+        HELM_CUDA(ctx, cudaMemcpyAsync(hb.data(), beta, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA(ctx, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
         HELM_CUDA(ctx, cudaStreamSynchronize(st));
         if (hbad) return set_error(ctx, HELM_ENONFINITE, "gmres_solve: right-hand side has NaN/Inf");
+        for (int i = 0; i < n; ++i) {
+            const int c = cols[i];
+            hs[c] = RhsState{hb[c], 0, 0, 0, hb[c] == 0.0 ? 1 : 0, 0.0, tol[i], maxit[i]};
+            trel[c] = 0.0;
+        }
+        HELM_CUDA(ctx, cudaMemcpyAsync(Sd, hs.data(), S * sizeof(RhsState), cudaMemcpyHostToDevice, st));
+        return HELM_OK;
     }
-    norms(b, beta);
-    std::vector<double> hb(nrhs);
-    HELM_CUDA(ctx, cudaMemcpyAsync(hb.data(), beta, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
-    HELM_CUDA(ctx, cudaStreamSynchronize(st));
-    std::vector<RhsState> hs(nrhs);
-    for (int i = 0; i < nrhs; ++i) {
-        hs[i] = RhsState{hb[i], 0, 0, 0, hb[i] == 0.0 ? 1 : 0, 0.0};
-    }
-    HELM_CUDA(ctx, cudaMemcpyAsync(S, hs.data(), nrhs * sizeof(RhsState), cudaMemcpyHostToDevice, st));
-    HELM_CUDA(ctx, cudaMemsetAsync(x, 0, nel * sizeof(c128), st));
-    HELM_CUDA(ctx, cudaMemcpyAsync(r, b, nel * sizeof(c128), cudaMemcpyDeviceToDevice, st));
-    std::vector<double> true_rel(nrhs, 0.0);
 
-    for (int cycle = 0;; ++cycle) {
-        // beta = ||r||, v_0 = r / beta
+    // Leave column c out of the following cycles.
+    void retire(int c) override {
+        hs[c].done = 1;
+        hs[c].bnorm = 0.0;
+    }
+    helm_status push_state() override {
+        HELM_CUDA(ctx, cudaMemcpyAsync(Sd, hs.data(), S * sizeof(RhsState), cudaMemcpyHostToDevice, st));
+        return HELM_OK;
+    }
+
+    // One restart cycle for every column not done; then the FP64 true residual decides which are done.
+    helm_status cycle(bool* any_left) override {
         norms(r, beta);
-        cycle_start<<<rg, 128, 0, st>>>(S, beta, inv, gv, m, nrhs);
-        scale_copy<double, T><<<eg, 256, 0, st>>>(r, V, nel, nrhs, inv);
+        cycle_start<<<rg, 128, 0, st>>>(Sd, beta, inv, gv, m, S);
+        scale_copy<double, T><<<eg, 256, 0, st>>>(r, V, nel, S, inv);
         ctx->launches += 2;
         int jdone = 0;
         for (int j = 0; j < m; ++j) {
             cplx<T>* vj = V + (long long)j * nel;
             cplx<T>* zj = flex ? Zb + (long long)j * nel : u;
-            HELM_TRY(oras_apply_wp(o, wp, vj, zj, nrhs));
-            HELM_TRY(launch_stencil(g, wp, zj, w, nrhs, st));
-            // CGS2, column j of H for every rhs: H[r][i][j]
-            dots_into(V, w, j + 1, hpass, nrhs, 1, 0, 0);
+            HELM_TRY(oras_apply_wp(o, wp, vj, zj, S));
+            HELM_TRY(launch_stencil(o->g, wp, zj, w, S, st));
+            // CGS2 for column j of H: H[r][i][j]
+            dots_into(V, w, j + 1, hpass, S, 1, 0, 0);
             {
                 const int tk = prof_begin(ctx, "arnoldi");
-                update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, nrhs, j + 1, hpass);
+                update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, S, j + 1, hpass);
                 prof_end(ctx, tk, (double)(j + 3) * nel * sizeof(cplx<T>));
             }
-            ctx->launches++;
-            // pass-1 coefficients into H column j
-            finish_dots<<<((j + 1) * nrhs + 127) / 128, 128, 0, st>>>(part, nblk, ldp, j + 1, nrhs, H, m, (m + 1) * m,
-                                                                     j, 0);
-            ctx->launches++;
-            dots_into(V, w, j + 1, hpass, nrhs, 1, 0, 0);
+            finish_dots<<<((j + 1) * S + 127) / 128, 128, 0, st>>>(part, nblk, ldp, j + 1, S, H, m, (m + 1) * m, j, 0);
+            ctx->launches += 2;
+            dots_into(V, w, j + 1, hpass, S, 1, 0, 0);
             {
                 const int tk = prof_begin(ctx, "arnoldi");
-                update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, nrhs, j + 1, hpass);
+                update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, S, j + 1, hpass);
                 prof_end(ctx, tk, (double)(j + 3) * nel * sizeof(cplx<T>));
             }
-            ctx->launches++;
-            finish_dots<<<((j + 1) * nrhs + 127) / 128, 128, 0, st>>>(part, nblk, ldp, j + 1, nrhs, H, m, (m + 1) * m,
-                                                                     j, 1);
-            ctx->launches++;
+            finish_dots<<<((j + 1) * S + 127) / 128, 128, 0, st>>>(part, nblk, ldp, j + 1, S, H, m, (m + 1) * m, j, 1);
+            ctx->launches += 2;
             norms(w, hn);
             cudaMemsetAsync(running, 0, sizeof(int), st);
-            const int tk = prof_begin(ctx, "krylov_misc");
-            givens_step<<<rg, 128, 0, st>>>(S, H, cs, sn, gv, hn, inv, j, m, nrhs, D.tol, D.maxit, running);
-            scale_copy<T, T><<<eg, 256, 0, st>>>(w, V + (long long)(j + 1) * nel, nel, nrhs, inv);
-            prof_end(ctx, tk, 2.0 * nel * sizeof(cplx<T>));
+            {
+                const int tk = prof_begin(ctx, "krylov_misc");
+                givens_step<<<rg, 128, 0, st>>>(Sd, H, cs, sn, gv, hn, inv, j, m, S, running);
+                scale_copy<T, T><<<eg, 256, 0, st>>>(w, V + (long long)(j + 1) * nel, nel, S, inv);
+                prof_end(ctx, tk, 2.0 * nel * sizeof(cplx<T>));
+            }
             ctx->launches += 2;
             int hrun = 0;
             HELM_CUDA(ctx, cudaMemcpyAsync(&hrun, running, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -438,44 +491,82 @@ helm_status solve_t(helm_oras o, const c128* b, c128* x, int nrhs, const helm_gm
             if (hrun == 0) break;
         }
         // x update with the steps taken in this cycle
-        back_substitute<<<rg, 128, 0, st>>>(S, H, gv, y, m, nrhs);
+        back_substitute<<<rg, 128, 0, st>>>(Sd, H, gv, y, m, S);
         ctx->launches++;
         if (flex) {
-            combine_kernel<T, double, true><<<eg, 256, 0, st>>>(Zb, nel, y, x, nel, nrhs, jdone);
+            combine_kernel<T, double, true><<<eg, 256, 0, st>>>(Zb, nel, y, Xd, nel, S, jdone);
             ctx->launches++;
         } else {
-            combine_kernel<T, T, false><<<eg, 256, 0, st>>>(V, nel, y, w, nel, nrhs, jdone);
+            combine_kernel<T, T, false><<<eg, 256, 0, st>>>(V, nel, y, w, nel, S, jdone);
             ctx->launches++;
-            HELM_TRY(oras_apply_wp(o, wp, w, u, nrhs));
-            accum_widen<T><<<eg, 256, 0, st>>>(u, x, nel);
+            HELM_TRY(oras_apply_wp(o, wp, w, u, S));
+            accum_widen<T><<<eg, 256, 0, st>>>(u, Xd, nel);
             ctx->launches++;
         }
         // true residual r = b - A x (FP64)
-        HELM_TRY(launch_stencil_sub(g, HELM_PREC_FP64, x, b, r, nrhs, st));
+        HELM_TRY(launch_stencil_sub(o->g, HELM_PREC_FP64, Xd, Bd, r, S, st));
         norms(r, beta);
-        HELM_CUDA(ctx, cudaMemcpyAsync(hs.data(), S, nrhs * sizeof(RhsState), cudaMemcpyDeviceToHost, st));
-        std::vector<double> rn(nrhs);
-        HELM_CUDA(ctx, cudaMemcpyAsync(rn.data(), beta, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+        std::vector<double> rn(S);
+        HELM_CUDA(ctx, cudaMemcpyAsync(hs.data(), Sd, S * sizeof(RhsState), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA(ctx, cudaMemcpyAsync(rn.data(), beta, S * sizeof(double), cudaMemcpyDeviceToHost, st));
         HELM_CUDA(ctx, cudaStreamSynchronize(st));
         bool any = false;
-        for (int i = 0; i < nrhs; ++i) {
+        for (int i = 0; i < S; ++i) {
             if (hs[i].done) continue;
-            true_rel[i] = hs[i].bnorm > 0 ? rn[i] / hs[i].bnorm : 0.0;
-            if (!std::isfinite(true_rel[i])) return set_error(ctx, HELM_ENONFINITE, "gmres_solve: residual is NaN/Inf");
-            if (true_rel[i] <= D.tol || hs[i].iters >= D.maxit) hs[i].done = 1;
+            trel[i] = hs[i].bnorm > 0 ? rn[i] / hs[i].bnorm : 0.0;
+            if (!std::isfinite(trel[i])) return set_error(ctx, HELM_ENONFINITE, "gmres_solve: residual is NaN/Inf");
+            if (trel[i] <= hs[i].tol || hs[i].iters >= hs[i].maxit) hs[i].done = 1;
             else any = true;
         }
-        HELM_CUDA(ctx, cudaMemcpyAsync(S, hs.data(), nrhs * sizeof(RhsState), cudaMemcpyHostToDevice, st));
-        if (!any) break;
+        HELM_CUDA(ctx, cudaMemcpyAsync(Sd, hs.data(), S * sizeof(RhsState), cudaMemcpyHostToDevice, st));
+        HELM_TRY(oras_check_device_error(o));
+        *any_left = any;
+        return HELM_OK;
     }
-    HELM_CUDA(ctx, cudaStreamSynchronize(st));
+};
+
+}  // namespace
+
+KrylovEngine* make_krylov_engine(helm_oras o, int S, int restart, bool flexible, int basis_prec, c128* B_ext,
+                                 c128* X_ext, helm_status* rc) {
+    KrylovEngine* e = nullptr;
+    if (basis_prec == HELM_PREC_FP64) {
+        auto* k = new Krylov<double>();
+        *rc = k->init(o, S, restart, flexible, basis_prec, B_ext, X_ext);
+        e = k;
+    } else {
+        auto* k = new Krylov<float>();
+        *rc = k->init(o, S, restart, flexible, basis_prec, B_ext, X_ext);
+        e = k;
+    }
+    if (*rc) {
+        delete e;
+        return nullptr;
+    }
+    return e;
+}
+
+namespace {
+
+helm_status solve_all(helm_oras o, c128* b, c128* x, int nrhs, const helm_gmres_desc& D, helm_rhs_stats* stats) {
+    helm_ctx ctx = o->g->ctx;
+    helm_status rc = HELM_OK;
+    std::unique_ptr<KrylovEngine> K(make_krylov_engine(o, nrhs, D.restart, D.flexible != 0, D.basis_prec, b, x, &rc));
+    if (!K) return rc;
+    std::vector<int> cols(nrhs), maxit(nrhs, D.maxit);
+    std::vector<double> tol(nrhs, D.tol);
+    for (int i = 0; i < nrhs; ++i) cols[i] = i;
+    HELM_TRY(K->begin_columns(cols.data(), nrhs, tol.data(), maxit.data()));
+    bool any = true;
+    while (any) HELM_TRY(K->cycle(&any));
     bool all = true;
     for (int i = 0; i < nrhs; ++i) {
-        const bool conv = true_rel[i] <= D.tol;
+        const RhsState& s = K->state(i);
+        const double tr = K->true_rel(i);
+        const bool conv = tr <= D.tol;
         all = all && conv;
-        if (stats) stats[i] = helm_rhs_stats{hs[i].iters, conv ? 1 : 0, true_rel[i], hs[i].est};
+        if (stats) stats[i] = helm_rhs_stats{s.iters, conv ? 1 : 0, tr, s.est};
     }
-    HELM_TRY(oras_check_device_error(o));
     if (!all) return set_error(ctx, HELM_ENOTCONV, "gmres_solve: some columns did not reach tol within maxit");
     return HELM_OK;
 }
@@ -512,8 +603,7 @@ extern "C" helm_status gmres_solve(helm_oras o, const void* b, void* x, int nrhs
         }
         xd = (c128*)stage_x;
     }
-    helm_status rc = d->basis_prec == HELM_PREC_FP64 ? solve_t<double>(o, bd, xd, nrhs, *d, stats)
-                                                     : solve_t<float>(o, bd, xd, nrhs, *d, stats);
+    helm_status rc = solve_all(o, bd, xd, nrhs, *d, stats);
     if (!xdev && (rc == HELM_OK || rc == HELM_ENOTCONV)) {
         cudaError_t e = cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -709,3 +709,49 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     ctx->prof.on = prof_on;
     return rc;
 }
+
+size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int nrhs) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const int p[3] = {std::max(1, d.px), std::max(1, d.py), std::max(1, d.pz)};
+    const size_t fe = d.factor_prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+    const bool padded = d.factor_prec == HELM_PREC_TF32;
+    size_t m_max = 0, nloc = 0, planes = 0, fac = 0;
+    std::vector<std::pair<size_t, size_t>> boxes;   // (m, bz)
+    for (int tz = 0; tz < p[2]; ++tz)
+        for (int ty = 0; ty < p[1]; ++ty)
+            for (int tx = 0; tx < p[0]; ++tx) {
+                const int t[3] = {tx, ty, tz};
+                size_t dims[3];
+                for (int a = 0; a < 3; ++a) {
+                    const int c0 = (int)((long long)t[a] * n[a] / p[a]), c1 = (int)((long long)(t[a] + 1) * n[a] / p[a]);
+                    const int lo = c0 > 0 ? std::max(0, c0 - d.overlap) : 0;
+                    const int hi = c1 < n[a] ? std::min(n[a], c1 + d.overlap) : n[a];
+                    dims[a] = (size_t)(hi - lo);
+                }
+                const size_t m = dims[0] * dims[1];
+                boxes.push_back({m, dims[2]});
+                m_max = std::max(m_max, m);
+                nloc += m * dims[2];
+                planes += dims[2];
+            }
+    const size_t ld = padded ? (m_max + 15) / 16 * 16 : 0;
+    for (auto& b : boxes) fac += (padded ? ld * ld : b.first * b.first) * b.second;
+    size_t bytes = fac * fe + nloc * 27 * fe;
+    const size_t N = (size_t)g.nx * g.ny * g.nz;
+    const size_t R = (size_t)std::max(1, nrhs);
+    bytes += nloc * R * fe + std::max<size_t>(boxes.size(), 9) * m_max * R * fe;   // apply scratch
+    if (padded) bytes += boxes.size() * (size_t)tc_npad(nrhs) * 2 * ld * sizeof(float);
+    if (d.coarse_ratio > 0) {
+        size_t nc = 1, cm = 1;
+        for (int a = 0; a < 3; ++a) {
+            const size_t ca = (size_t)((n[a] - 1 + d.coarse_ratio - 1) / d.coarse_ratio + 1);
+            nc *= ca;
+            if (a < 2) cm *= ca;
+        }
+        const size_t cz = nc / cm;
+        bytes += (cm * cm * cz + nc * 27) * (sizeof(c128) + sizeof(c64));   // FP64 factors and the complex64 copy
+        bytes += 2 * N * 27 * sizeof(c128);                                  // probing vectors during set-up
+        bytes += nc * R * sizeof(c128) + 9 * cm * R * sizeof(c128) + 2 * N * R * sizeof(c128);
+    }
+    return bytes + bytes / 16;
+}

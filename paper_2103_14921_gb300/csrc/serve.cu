@@ -1,0 +1,431 @@
+// Request loop with continuous batching (helm_serve_start / helm_submit /
+// helm_poll / helm_serve_stop).
+//
+// One worker thread owns the context's stream.  Per factor set (a cached
+// grid + ORAS handle keyed by model id, grid, decomposition and solver
+// settings) it keeps one batched Krylov engine with a fixed number of column
+// slots.  Each right-hand side of a request occupies one slot.  The worker
+// repeats: admit queued requests whose factors exist or fit the HBM budget
+// (building them, evicting idle factor sets least-recently-used) and whose
+// columns fit the free slots; run one restart cycle of every batch that has
+// active columns; hand back the columns that finished (copying their
+// solutions out) and free their slots.  New requests therefore join running
+// batches at cycle boundaries and share every kernel launch with them.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct FactorSet;
+
+struct SRequest {
+    uint64_t ticket = 0;
+    helm_request req{};
+    int state = 0;   // 0 queued, 1 running, 2 done
+    helm_status status = HELM_OK;
+    Clock::time_point t_submit, t_admit, t_done;
+    std::vector<int> slots;
+    int cols_left = 0;
+    int iters_max = 0;
+    double rel_max = 0.0;
+    bool reused = false;
+    bool notconv = false;
+    FactorSet* fs = nullptr;
+};
+
+bool same_grid(const helm_grid_desc& a, const helm_grid_desc& b) {
+    if (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.h != b.h || a.freq_hz != b.freq_hz || a.npml != b.npml ||
+        a.pml_R != b.pml_R || a.top_bc != b.top_bc)
+        return false;
+    for (int i = 0; i < 7; ++i)
+        if (a.weights[i] != b.weights[i]) return false;
+    return true;
+}
+bool same_oras(const helm_oras_desc& a, const helm_oras_desc& b) {
+    return a.px == b.px && a.py == b.py && a.pz == b.pz && a.overlap == b.overlap && a.coarse_ratio == b.coarse_ratio &&
+           a.interface_bc == b.interface_bc && a.factor_prec == b.factor_prec;
+}
+
+struct FactorSet {
+    uint64_t model_id = 0;
+    helm_grid_desc gd{};
+    helm_oras_desc od{};
+    int restart = 0, flexible = 0, basis_prec = 0;
+    helm_grid g = nullptr;
+    helm_oras o = nullptr;
+    std::unique_ptr<KrylovEngine> K;
+    std::vector<SRequest*> owner;   // per slot
+    std::vector<int> col;           // per slot: column index within its request
+    int active = 0;
+    Clock::time_point last_used;
+
+    bool matches(const helm_request& r) const {
+        return model_id == r.model_id && same_grid(gd, r.grid) && same_oras(od, r.oras) &&
+               restart == r.gmres.restart && flexible == r.gmres.flexible && basis_prec == r.gmres.basis_prec;
+    }
+    int free_slots() const {
+        int n = 0;
+        for (auto* p : owner) n += p == nullptr;
+        return n;
+    }
+};
+
+// dst[p * S + slot[c]] = src[p * ns + c]   (request columns into batch slots)
+__global__ void pack_columns(const c128* __restrict__ src, c128* __restrict__ dst, const int* __restrict__ slot,
+                             long long N, int ns, int S) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N * ns; e += (long long)gridDim.x * blockDim.x) {
+        const long long p = e / ns;
+        const int c = (int)(e % ns);
+        dst[p * S + slot[c]] = src[e];
+    }
+}
+
+// dst[p * ns + c] = src[p * S + slot[c]]   (batch slots back into a request's layout)
+__global__ void unpack_columns(const c128* __restrict__ src, c128* __restrict__ dst, const int* __restrict__ slot,
+                               long long N, int ns, int S) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N * ns; e += (long long)gridDim.x * blockDim.x) {
+        const long long p = e / ns;
+        const int c = (int)(e % ns);
+        dst[e] = src[p * S + slot[c]];
+    }
+}
+
+}  // namespace
+
+struct Server {
+    helm_ctx ctx = nullptr;
+    int slots = 0;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    std::deque<SRequest*> incoming;                 // submitted, not yet seen by the worker
+    std::unordered_map<uint64_t, SRequest*> reqs;   // every live ticket
+    uint64_t next_ticket = 1;
+    // worker-only state
+    std::deque<SRequest*> waiting;
+    std::vector<FactorSet*> sets;
+    int* dslot = nullptr;                           // device slot map for (un)packing
+
+    void finish(SRequest* r, helm_status st) {
+        std::lock_guard<std::mutex> lk(mu);
+        r->status = st;
+        r->state = 2;
+        r->t_done = Clock::now();
+    }
+
+    void destroy_set(FactorSet* fs) {
+        fs->K.reset();
+        if (fs->o) oras_destroy(fs->o);
+        if (fs->g) helm_destroy_grid(fs->g);
+        delete fs;
+    }
+
+    size_t engine_estimate(const helm_request& r) const {
+        const size_t N = (size_t)r.grid.nx * r.grid.ny * r.grid.nz;
+        const size_t e = r.gmres.basis_prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+        const size_t m = (size_t)r.gmres.restart;
+        return N * slots * ((2 * m + 3) * e + 3 * sizeof(c128)) + N * 48;
+    }
+
+    // Try to place r: returns true if admitted (or failed), false if it must keep waiting.
+    bool try_admit(SRequest* r, bool idle) {
+        FactorSet* fs = nullptr;
+        for (auto* s : sets)
+            if (s->matches(r->req)) fs = s;
+        if (!fs) {
+            const size_t need = oras_estimate_bytes(r->req.grid, r->req.oras, slots) + engine_estimate(r->req);
+            auto room = [&]() { return ctx->budget == 0 || ctx->in_use + need <= ctx->budget; };
+            while (!room()) {
+                FactorSet* lru = nullptr;
+                for (auto* s : sets)
+                    if (s->active == 0 && (!lru || s->last_used < lru->last_used)) lru = s;
+                if (!lru) break;
+                sets.erase(std::find(sets.begin(), sets.end(), lru));
+                destroy_set(lru);
+            }
+            if (!room()) {
+                if (idle && sets.empty()) {
+                    set_error(ctx, HELM_ENOMEM, "request needs about %zu bytes, more than the HBM budget", need);
+                    finish(r, HELM_ENOMEM);
+                    return true;
+                }
+                return false;
+            }
+            fs = new FactorSet();
+            fs->model_id = r->req.model_id;
+            fs->gd = r->req.grid;
+            fs->od = r->req.oras;
+            fs->restart = r->req.gmres.restart;
+            fs->flexible = r->req.gmres.flexible;
+            fs->basis_prec = r->req.gmres.basis_prec;
+            helm_status st = helm_setup_grid(ctx, &fs->gd, r->req.c, &fs->g);
+            if (!st) st = oras_factor(fs->g, &fs->od, &fs->o);
+            if (!st) {
+                fs->K.reset(make_krylov_engine(fs->o, slots, fs->restart, fs->flexible != 0, fs->basis_prec, nullptr,
+                                               nullptr, &st));
+            }
+            if (st) {
+                destroy_set(fs);
+                finish(r, st);
+                return true;
+            }
+            fs->owner.assign(slots, nullptr);
+            fs->col.assign(slots, -1);
+            fs->last_used = Clock::now();
+            sets.push_back(fs);
+        } else {
+            r->reused = true;
+        }
+        if (fs->free_slots() < r->req.nrhs) return false;
+        // take slots, copy the request's columns into them and start them
+        const long long N = fs->g->n;
+        std::vector<int> sl;
+        for (int s = 0; s < slots && (int)sl.size() < r->req.nrhs; ++s)
+            if (!fs->owner[s]) sl.push_back(s);
+        cudaStream_t st = ctx->stream;
+        const size_t bytes = (size_t)N * r->req.nrhs * sizeof(c128);
+        void* stage = nullptr;
+        const c128* src = (const c128*)r->req.b;
+        helm_status rc = HELM_OK;
+        if (!is_device_pointer(r->req.b)) {
+            rc = dev_alloc(ctx, &stage, bytes, "request b staging");
+            if (!rc) rc = cuda_check(ctx, cudaMemcpyAsync(stage, r->req.b, bytes, cudaMemcpyHostToDevice, st), "b H2D");
+            src = (const c128*)stage;
+        }
+        if (!rc) rc = cuda_check(ctx, cudaMemcpyAsync(dslot, sl.data(), sl.size() * sizeof(int), cudaMemcpyHostToDevice, st),
+                                 "slot map");
+        if (!rc) {
+            pack_columns<<<(unsigned)std::min<long long>((N * r->req.nrhs + 255) / 256, 4096), 256, 0, st>>>(
+                src, fs->K->B(), dslot, N, r->req.nrhs, slots);
+            ctx->launches++;
+            std::vector<double> tol(sl.size(), r->req.gmres.tol);
+            std::vector<int> maxit(sl.size(), r->req.gmres.maxit);
+            rc = fs->K->begin_columns(sl.data(), (int)sl.size(), tol.data(), maxit.data());
+        }
+        cudaStreamSynchronize(st);
+        if (stage) dev_free(ctx, stage, bytes);
+        if (rc) {
+            for (int s : sl) fs->K->retire(s);
+            fs->K->push_state();
+            finish(r, rc);
+            return true;
+        }
+        for (size_t i = 0; i < sl.size(); ++i) {
+            fs->owner[sl[i]] = r;
+            fs->col[sl[i]] = (int)i;
+        }
+        fs->active += (int)sl.size();
+        fs->last_used = Clock::now();
+        r->fs = fs;
+        r->slots = sl;
+        r->cols_left = (int)sl.size();
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            r->state = 1;
+            r->t_admit = Clock::now();
+        }
+        return true;
+    }
+
+    // Copy a finished request's columns out and release its slots.
+    void complete(FactorSet* fs, SRequest* r) {
+        const long long N = fs->g->n;
+        cudaStream_t st = ctx->stream;
+        const size_t bytes = (size_t)N * r->req.nrhs * sizeof(c128);
+        helm_status rc = cuda_check(
+            ctx, cudaMemcpyAsync(dslot, r->slots.data(), r->slots.size() * sizeof(int), cudaMemcpyHostToDevice, st),
+            "slot map");
+        void* stage = nullptr;
+        c128* dst = (c128*)r->req.x;
+        const bool xdev = is_device_pointer(r->req.x);
+        if (!rc && !xdev) {
+            rc = dev_alloc(ctx, &stage, bytes, "request x staging");
+            dst = (c128*)stage;
+        }
+        if (!rc) {
+            unpack_columns<<<(unsigned)std::min<long long>((N * r->req.nrhs + 255) / 256, 4096), 256, 0, st>>>(
+                fs->K->X(), dst, dslot, N, r->req.nrhs, slots);
+            ctx->launches++;
+            if (!xdev) rc = cuda_check(ctx, cudaMemcpyAsync(r->req.x, stage, bytes, cudaMemcpyDeviceToHost, st), "x D2H");
+        }
+        if (!rc) rc = cuda_check(ctx, cudaStreamSynchronize(st), "request completion");
+        if (stage) dev_free(ctx, stage, bytes);
+        for (int s : r->slots) {
+            fs->K->retire(s);
+            fs->owner[s] = nullptr;
+            fs->col[s] = -1;
+        }
+        fs->K->push_state();
+        fs->active -= (int)r->slots.size();
+        fs->last_used = Clock::now();
+        finish(r, rc ? rc : (r->notconv ? HELM_ENOTCONV : HELM_OK));
+    }
+
+    void loop() {
+        cudaSetDevice(ctx->device);
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                bool busy = !waiting.empty();
+                for (auto* s : sets) busy = busy || s->active > 0;
+                if (!busy && incoming.empty()) {
+                    if (stop) break;
+                    cv.wait_for(lk, std::chrono::milliseconds(20));
+                }
+                while (!incoming.empty()) {
+                    waiting.push_back(incoming.front());
+                    incoming.pop_front();
+                }
+            }
+            bool idle = true;
+            for (auto* s : sets) idle = idle && s->active == 0;
+            for (auto it = waiting.begin(); it != waiting.end();) {
+                if (try_admit(*it, idle)) {
+                    it = waiting.erase(it);
+                    idle = false;
+                } else {
+                    ++it;
+                }
+            }
+            for (auto* fs : sets) {
+                if (fs->active == 0) continue;
+                bool any = false;
+                helm_status rc = fs->K->cycle(&any);
+                std::vector<SRequest*> done_reqs;
+                for (int s = 0; s < slots; ++s) {
+                    SRequest* r = fs->owner[s];
+                    if (!r) continue;
+                    const RhsState& cs = fs->K->state(s);
+                    if (rc || cs.done) {
+                        if (std::find(done_reqs.begin(), done_reqs.end(), r) == done_reqs.end()) done_reqs.push_back(r);
+                    }
+                }
+                for (auto* r : done_reqs) {
+                    bool all = true;
+                    for (int s : r->slots) all = all && (rc || fs->K->state(s).done);
+                    if (!all) continue;
+                    for (int s : r->slots) {
+                        const RhsState& cs = fs->K->state(s);
+                        const double tr = fs->K->true_rel(s);
+                        r->iters_max = std::max(r->iters_max, cs.iters);
+                        r->rel_max = std::max(r->rel_max, tr);
+                        if (!(tr <= cs.tol)) r->notconv = true;
+                    }
+                    if (rc) {
+                        for (int s : r->slots) {
+                            fs->K->retire(s);
+                            fs->owner[s] = nullptr;
+                        }
+                        fs->K->push_state();
+                        fs->active -= (int)r->slots.size();
+                        finish(r, rc);
+                    } else {
+                        complete(fs, r);
+                    }
+                }
+            }
+        }
+        for (auto* s : sets) destroy_set(s);
+        sets.clear();
+    }
+};
+
+extern "C" helm_status helm_serve_start(helm_ctx ctx, int slots) {
+    if (!ctx) return HELM_EINVAL;
+    if (ctx->server) return set_error(ctx, HELM_EBUSY, "helm_serve_start: already serving");
+    if (slots < 1 || slots > 256) return set_error(ctx, HELM_EINVAL, "helm_serve_start: slots must be 1..256");
+    HELM_CUDA(ctx, cudaSetDevice(ctx->device));
+    Server* sv = new Server();
+    sv->ctx = ctx;
+    sv->slots = slots;
+    helm_status rc = dev_alloc(ctx, (void**)&sv->dslot, 256 * sizeof(int), "slot map");
+    if (rc) {
+        delete sv;
+        return rc;
+    }
+    ctx->server = sv;
+    sv->th = std::thread([sv]() { sv->loop(); });
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_submit(helm_ctx ctx, const helm_request* req, uint64_t* ticket) {
+    if (!ctx || !req || !ticket) return HELM_EINVAL;
+    Server* sv = ctx->server;
+    if (!sv) return set_error(ctx, HELM_EINVAL, "helm_submit: serving not started");
+    if (req->nrhs < 1 || req->nrhs > sv->slots || !req->b || !req->x || !req->c || !(req->gmres.tol > 0) ||
+        req->gmres.restart < 1 || req->gmres.restart > 200 || req->gmres.maxit < 1 ||
+        (req->gmres.basis_prec != HELM_PREC_FP64 && req->gmres.basis_prec != HELM_PREC_FP32))
+        return set_error(ctx, HELM_EINVAL, "helm_submit: malformed request");
+    SRequest* r = new SRequest();
+    r->req = *req;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stop) {
+            delete r;
+            return set_error(ctx, HELM_EBUSY, "helm_submit: serving is stopping");
+        }
+        r->ticket = sv->next_ticket++;
+        sv->reqs[r->ticket] = r;
+        sv->incoming.push_back(r);
+    }
+    sv->cv.notify_one();
+    *ticket = r->ticket;
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_poll(helm_ctx ctx, uint64_t ticket, int* done, helm_request_stats* stats) {
+    if (!ctx || !done) return HELM_EINVAL;
+    Server* sv = ctx->server;
+    if (!sv) return set_error(ctx, HELM_EINVAL, "helm_poll: serving not started");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return HELM_ENOTFOUND;
+    SRequest* r = it->second;
+    *done = r->state == 2;
+    if (stats) {
+        const auto now = Clock::now();
+        stats->done = *done;
+        stats->status = r->status;
+        stats->iterations_max = r->iters_max;
+        stats->true_relres_max = r->rel_max;
+        stats->queue_ms = r->state >= 1 ? ms_since(r->t_submit, r->t_admit) : ms_since(r->t_submit, now);
+        stats->latency_ms = r->state == 2 ? ms_since(r->t_submit, r->t_done) : ms_since(r->t_submit, now);
+        stats->factors_reused = r->reused ? 1 : 0;
+    }
+    if (*done) {
+        sv->reqs.erase(it);
+        delete r;
+    }
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_serve_stop(helm_ctx ctx) {
+    if (!ctx) return HELM_EINVAL;
+    Server* sv = ctx->server;
+    if (!sv) return HELM_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_one();
+    sv->th.join();
+    for (auto& kv : sv->reqs) delete kv.second;
+    dev_free(ctx, sv->dslot, 256 * sizeof(int));
+    delete sv;
+    ctx->server = nullptr;
+    return HELM_OK;
+}

@@ -57,6 +57,16 @@ class RhsStats(C.Structure):
                 ("est_relres", C.c_double)]
 
 
+class Request(C.Structure):
+    _fields_ = [("model_id", C.c_uint64), ("grid", GridDesc), ("c", C.c_void_p), ("oras", OrasDesc),
+                ("gmres", GmresDesc), ("nrhs", C.c_int), ("b", C.c_void_p), ("x", C.c_void_p)]
+
+
+class RequestStats(C.Structure):
+    _fields_ = [("done", C.c_int), ("status", C.c_int), ("iterations_max", C.c_int), ("true_relres_max", C.c_double),
+                ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("factors_reused", C.c_int)]
+
+
 def lib():
     """Load the CUDA library (raises if it has not been built)."""
     global _lib
@@ -87,6 +97,10 @@ def lib():
         "oras_plane_inverse": (st, [vp, i32, i32, vp]),
         "oras_setup_seconds": (C.c_double, [vp]),
         "gmres_solve": (st, [vp, vp, vp, i32, C.POINTER(GmresDesc), C.POINTER(RhsStats)]),
+        "helm_serve_start": (st, [vp, i32]),
+        "helm_submit": (st, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        "helm_poll": (st, [vp, C.c_uint64, C.POINTER(i32), C.POINTER(RequestStats)]),
+        "helm_serve_stop": (st, [vp]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -270,5 +284,74 @@ class Oras:
             return
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """``helm_serve_start`` .. ``helm_serve_stop``: request loop with continuous batching on a context.
+
+    While serving, the context must not be used for other calls.  Buffers
+    passed to :meth:`submit` are kept referenced until the request is done.
+    """
+
+    def __init__(self, ctx: Context, slots_per_batch=16):
+        self.ctx = ctx
+        self._keep = {}
+        ctx.check(lib().helm_serve_start(ctx._h, slots_per_batch), "helm_serve_start")
+        self.running = True
+
+    def submit(self, model_id, grid_desc, c, oras_desc, b, x, tol=1e-6, restart=30, maxit=1000, flexible=True,
+               basis_prec=PREC_FP32):
+        """Queue a solve; c, b, x are contiguous complex128 tensors (CUDA or CPU); returns a ticket."""
+        nrhs = b.shape[-1]
+        req = Request(model_id, grid_desc, C.c_void_p(c.data_ptr()), oras_desc,
+                      GmresDesc(tol, restart, maxit, 1 if flexible else 0, basis_prec), nrhs,
+                      C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()))
+        t = C.c_uint64()
+        self.ctx.check(lib().helm_submit(self.ctx._h, C.byref(req), C.byref(t)), "helm_submit")
+        self._keep[t.value] = (c, b, x)
+        return t.value
+
+    def poll(self, ticket):
+        """``(done, stats dict)``."""
+        done = C.c_int()
+        s = RequestStats()
+        self.ctx.check(lib().helm_poll(self.ctx._h, ticket, C.byref(done), C.byref(s)), "helm_poll")
+        out = dict(done=bool(done.value), status=s.status, iterations_max=s.iterations_max,
+                   true_relres_max=s.true_relres_max, queue_ms=s.queue_ms, latency_ms=s.latency_ms,
+                   factors_reused=bool(s.factors_reused))
+        if done.value:
+            self._keep.pop(ticket, None)
+        return out["done"], out
+
+    def wait(self, ticket, timeout_s=600.0, interval_s=0.002):
+        import time
+        t0 = time.time()
+        while True:
+            d, s = self.poll(ticket)
+            if d:
+                return s
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError(f"ticket {ticket} not done after {timeout_s} s")
+            time.sleep(interval_s)
+
+    def stop(self):
+        if self.running:
+            self.ctx.check(lib().helm_serve_stop(self.ctx._h), "helm_serve_stop")
+            self.running = False
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.stop()
+
+    def __del__(self):
+        if _finalizing:
+            return
+        try:
+            self.stop()
         except Exception:
             pass
