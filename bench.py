@@ -41,6 +41,9 @@ WORKLOADS = {
     "lg112": dict(desc="linear-gradient 112^3, 5 Hz, 16 RHS, two-level ORAS 4x4x4 ov2 r4, FGMRES(30) tol 1e-6",
                   n=112, h=25.0, f=5.0, c0=1500.0, alpha=0.6, npml=8, parts=(4, 4, 4), overlap=2, coarse=4,
                   nrhs=16, src_k=3, seed=synth.workload_seed(2), restart=30, tol=1e-6),
+    "lg64": dict(desc="linear-gradient 64^3, 5 Hz, 16 RHS, two-level ORAS 2x2x2 ov2 r4, FGMRES(30) tol 1e-6",
+                 n=64, h=25.0, f=5.0, c0=1500.0, alpha=0.6, npml=8, parts=(2, 2, 2), overlap=2, coarse=4,
+                 nrhs=16, src_k=3, seed=synth.workload_seed(2), restart=30, tol=1e-6),
     "lg48": dict(desc="linear-gradient 48^3, 3 Hz, 1 RHS, one-level ORAS 2x2x2 ov2, GMRES(30) tol 1e-6",
                  n=48, h=25.0, f=3.0, c0=1500.0, alpha=0.6, npml=8, parts=(2, 2, 2), overlap=2, coarse=0,
                  nrhs=1, src_k=None, seed=synth.workload_seed(1), restart=30, tol=1e-6),
@@ -180,6 +183,62 @@ def oracle_sample(W, iters_per_rhs, weights, repeats=1):
     }
 
 
+def run_serving(helm, device, stream, weights, args):
+    """Request stream through helm_submit/helm_poll: Poisson arrivals, seeded layered models,
+    cubic grids from 48^3 to 96^3, 3 or 5 Hz, 1..16 RHS each, a 150 GB HBM budget, TF32
+    factors cached per (model, grid, frequency); returns RHS/s and p50/p99 latency."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(synth.workload_seed(5))
+    ctx = helm.Context(device, stream=stream.cuda_stream, budget_bytes=150 << 30)
+    sizes = [48, 64, 80, 96]
+    models = {}
+    reqs = []
+    t_arr = 0.0
+    for i in range(args.serve_requests):
+        n = int(rng.choice(sizes))
+        mid = int(rng.integers(0, 2))
+        f = float(rng.choice([3.0, 5.0]))
+        nrhs = int(rng.integers(1, 17))
+        t_arr += float(rng.exponential(1.0 / args.serve_rate))
+        key = (n, mid)
+        if key not in models:
+            models[key] = torch.from_numpy(synth.layered(n, n, n, 25.0, seed=synth.workload_seed(5) * 10 + n + mid,
+                                                         vmin=1500.0, vmax=4500.0))
+        pos = [tuple(int(v) for v in p) for p in rng.integers(8, n - 8, size=(nrhs, 3))]
+        pos = [(p[0], p[1], min(p[2], n - 9)) for p in pos]
+        b = torch.from_numpy(synth.point_sources(n, n, n, 25.0, pos)).cuda()
+        reqs.append(dict(t=t_arr, n=n, mid=mid, f=f, b=b))
+    import ctypes as C
+    lat, done_rhs, statuses = [], 0, []
+    with helm.Server(ctx, slots_per_batch=32) as sv:
+        t0 = time.perf_counter()
+        pending = []
+        for r in reqs:
+            while time.perf_counter() - t0 < r["t"]:
+                time.sleep(0.0005)
+            n = r["n"]
+            gd = helm.GridDesc(n, n, n, 25.0, r["f"], 8, 1e-3, helm.TOP_DIRICHLET, (C.c_double * 7)(*weights))
+            p = max(2, n // 24)                      # boxes of about 24 nodes plus overlap per axis
+            od = helm.OrasDesc(p, p, p, 2, 4, 0, helm.PREC_TF32)
+            x = torch.empty_like(r["b"])
+            tk = sv.submit(1000 * n + r["mid"], gd, models[(n, r["mid"])], od, r["b"], x, tol=1e-6, restart=30,
+                           basis_prec=helm.PREC_FP32)
+            pending.append((tk, r["b"].shape[-1]))
+        for tk, nr in pending:
+            s = sv.wait(tk, timeout_s=900)
+            statuses.append(s["status"])
+            lat.append(s["latency_ms"])
+            done_rhs += nr
+        wall = time.perf_counter() - t0
+    ok = sum(1 for s in statuses if s == helm.OK)
+    return {"requests": len(reqs), "ok": ok, "rhs": done_rhs, "wall_s": wall, "rhs_per_s": done_rhs / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "arrival_rate_per_s": args.serve_rate, "slots_per_batch": 32, "budget_gb": 150,
+            "mix": "cubic 48..96, 2 layered models per size, 3/5 Hz, 1..16 RHS, two-level ORAS with ~24-node boxes, "
+                   "TF32 factors"}
+
+
 def run_reference(args, W):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -269,12 +328,10 @@ def run_gpu(args, W):
     prof = {fam: ctx.profile_query(fam) for fam in ("sweep_gemm_tc", "sweep_gemv", "sweep_prep", "stencil", "arnoldi",
                                                      "oras_transfer", "coarse_transfer", "krylov_misc")}
     ctx.profile(False)
-    t_max = elapsed_ms
-    if ws > 1:
-        tt = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * nrhs * args.steps / (t_max / 1000.0)
+    from paper_2103_14921_gb300 import replicas
+    dev = torch.device("cuda", local)
+    value, t_max_s = replicas.job_throughput(nrhs * args.steps, elapsed_ms / 1000.0, dev)
+    t_max = 1000.0 * t_max_s
     iters = [s["iterations"] for s in stats_all[-1]]
     relres = max(s["true_relres"] for s in stats_all[-1])
     x_mixed = x.clone()
@@ -287,8 +344,7 @@ def run_gpu(args, W):
     t = time.perf_counter()
     for _ in range(e2e_steps):
         oras.solve(bh, xh, **solve_kw)
-    e2e_s = (time.perf_counter() - t) / e2e_steps
-    e2e_value = ws * nrhs / e2e_s
+    e2e_value, _ = replicas.job_throughput(nrhs * e2e_steps, time.perf_counter() - t, dev)
 
     # plain FP64 single-RHS path on the GPU (same preconditioner structure, FP64 everywhere)
     plain = None
@@ -332,6 +388,11 @@ def run_gpu(args, W):
             nl, ms, by = v
             kernels[fam] = {"launches": nl, "ms_total": ms, "share_of_step": ms / elapsed_ms,
                             "GBps": by / (ms / 1000.0) / 1e9}
+    serving = None
+    if not args.no_serve:
+        del grid
+        torch.cuda.synchronize()
+        serving = run_serving(helm, local, stream, weights, args)
     if rank != 0:
         return
     cpu = None
@@ -353,7 +414,7 @@ def run_gpu(args, W):
                 "d2h_bytes_per_step": int(b_host.nbytes)},
         "gpu_launches": int(launches),
         "roofline": roof, "kernels": kernels, "plain_fp64_gpu": plain,
-        "cpu_baseline": cpu, "clocks": clk,
+        "cpu_baseline": cpu, "clocks": clk, "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -371,6 +432,9 @@ def main():
                     help="fine local factors: tf32 = complex64 factors, tensor-core sweeps; fp32 = CUDA-core sweeps")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 single-RHS measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-stream (serving) measurement")
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-rate", type=float, default=8.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--ref-iters", type=float, default=20.0,
                     help="iterations per RHS used to scale the oracle's per-iteration time (reference arm)")
     args = ap.parse_args()
