@@ -98,6 +98,9 @@ uint64_t    helm_launch_count(helm_ctx ctx);
  * launch must move at least once, as stated in each kernel's description).
  * Returns HELM_ENOTFOUND for a family with no recorded launch. */
 helm_status helm_profile_enable(helm_ctx ctx, int on);
+/* Restrict recording to a comma-separated list of families (NULL or "" = all), so that
+ * the events bracket only the kernels of interest inside a timed region. */
+helm_status helm_profile_select(helm_ctx ctx, const char* families);
 helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launches, double* ms, double* bytes);
 
 /* ------------------------------------------------------------ grid / model */

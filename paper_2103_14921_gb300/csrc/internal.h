@@ -47,6 +47,7 @@ struct ProfRecord {
 };
 struct Profiler {
     bool on = false;
+    std::vector<std::string> only;   // when non-empty, only these families are recorded
     std::vector<std::string> names;
     std::vector<ProfRecord> pending;
     std::vector<cudaEvent_t> pool;

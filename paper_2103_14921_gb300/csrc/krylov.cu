@@ -90,16 +90,32 @@ __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const cplx<T>* __rest
     }
 }
 
-// out[i][r] (+)= sum_blk partial[blk][i][r], fixed order
-__global__ void finish_dots(const c128* __restrict__ partial, int nblk, int ldp, int ni, int nrhs,
-                            c128* __restrict__ H, int ldh_i, int ldh_r, int col, int accumulate) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ni * nrhs) return;
-    const int i = e / nrhs, r = e % nrhs;
+// out[i][r] (+)= sum_blk partial[blk][i][r]: one 128-thread block per (i, r); thread t sums the
+// partials t, t+128, ... in order, then a fixed shuffle and shared-memory tree (deterministic).
+__device__ __forceinline__ c128 block_sum128(c128 v) {
+    __shared__ c128 red[4];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    return (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+__global__ void __launch_bounds__(128) finish_dots(const c128* __restrict__ partial, int nblk, int ldp, int ni,
+                                                   int nrhs, c128* __restrict__ H, int ldh_i, int ldh_r, int col,
+                                                   int accumulate) {
+    const int i = blockIdx.x / nrhs, r = blockIdx.x % nrhs;
+    if (i >= ni) return;
     c128 sum = mk<double>(0, 0);
-    for (int b = 0; b < nblk; ++b) sum = sum + partial[((long long)b * ldp + i) * nrhs + r];
-    c128* dst = H + (long long)r * ldh_r + (long long)i * ldh_i + col;
-    *dst = accumulate ? *dst + sum : sum;
+    for (int b = threadIdx.x; b < nblk; b += 128) sum = sum + partial[((long long)b * ldp + i) * nrhs + r];
+    sum = block_sum128(sum);
+    if (threadIdx.x == 0) {
+        c128* dst = H + (long long)r * ldh_r + (long long)i * ldh_i + col;
+        *dst = accumulate ? *dst + sum : sum;
+    }
 }
 
 // w[e] -= sum_{i<ni} V_i[e] h_i[r]   (h from H column col, last pass's values only: hsrc)
@@ -143,12 +159,17 @@ __global__ void __launch_bounds__(RED_THREADS) norm2_kernel(const cplx<T>* __res
     }
 }
 
-__global__ void finish_norm2(const double* __restrict__ partial, int nblk, int nrhs, double* __restrict__ out) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrhs) return;
+__global__ void __launch_bounds__(128) finish_norm2(const double* __restrict__ partial, int nblk, int nrhs,
+                                                    double* __restrict__ out) {
+    __shared__ double red[4];
+    const int r = blockIdx.x;
     double sum = 0.0;
-    for (int b = 0; b < nblk; ++b) sum += partial[(long long)b * nrhs + r];
-    out[r] = sqrt(sum);
+    for (int b = threadIdx.x; b < nblk; b += 128) sum += partial[(long long)b * nrhs + r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) out[r] = sqrt((red[0] + red[1]) + (red[2] + red[3]));
 }
 
 // dst[e] = src[e] * scale[r]  (scale = 0 -> zero)
@@ -395,7 +416,7 @@ struct Krylov final : KrylovEngine {
     void norms(const V_t* vec, double* out) {
         const int tk = prof_begin(ctx, "krylov_misc");
         norm2_kernel<<<nblk, RED_THREADS, 0, st>>>(vec, nel, S, dpart);
-        finish_norm2<<<rg, 128, 0, st>>>(dpart, nblk, S, out);
+        finish_norm2<<<S, 128, 0, st>>>(dpart, nblk, S, out);
         prof_end(ctx, tk, (double)nel * sizeof(*vec));
         ctx->launches += 2;
     }
@@ -405,7 +426,7 @@ struct Krylov final : KrylovEngine {
         const int tk = prof_begin(ctx, "arnoldi");
         dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, S, 0, ni, part, ldp);
         prof_end(ctx, tk, (double)(ni + 1) * nel * sizeof(cplx<T>));
-        finish_dots<<<(ni * S + 127) / 128, 128, 0, st>>>(part, nblk, ldp, ni, S, dst, ldh_i, ldh_r, col, accumulate);
+        finish_dots<<<ni * S, 128, 0, st>>>(part, nblk, ldp, ni, S, dst, ldh_i, ldh_r, col, accumulate);
         ctx->launches += 2;
     }
 
@@ -464,7 +485,7 @@ struct Krylov final : KrylovEngine {
                 update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, S, j + 1, hpass);
                 prof_end(ctx, tk, (double)(j + 3) * nel * sizeof(cplx<T>));
             }
-            finish_dots<<<((j + 1) * S + 127) / 128, 128, 0, st>>>(part, nblk, ldp, j + 1, S, H, m, (m + 1) * m, j, 0);
+            finish_dots<<<(j + 1) * S, 128, 0, st>>>(part, nblk, ldp, j + 1, S, H, m, (m + 1) * m, j, 0);
             ctx->launches += 2;
             dots_into(V, w, j + 1, hpass, S, 1, 0, 0);
             {
@@ -472,7 +493,7 @@ struct Krylov final : KrylovEngine {
                 update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, S, j + 1, hpass);
                 prof_end(ctx, tk, (double)(j + 3) * nel * sizeof(cplx<T>));
             }
-            finish_dots<<<((j + 1) * S + 127) / 128, 128, 0, st>>>(part, nblk, ldp, j + 1, S, H, m, (m + 1) * m, j, 1);
+            finish_dots<<<(j + 1) * S, 128, 0, st>>>(part, nblk, ldp, j + 1, S, H, m, (m + 1) * m, j, 1);
             ctx->launches += 2;
             norms(w, hn);
             cudaMemsetAsync(running, 0, sizeof(int), st);

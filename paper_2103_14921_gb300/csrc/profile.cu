@@ -45,6 +45,7 @@ void prof_drain(helm_ctx ctx) {
 int prof_begin(helm_ctx ctx, const char* family) {
     Profiler& P = ctx->prof;
     if (!P.on) return -1;
+    if (!P.only.empty() && std::find(P.only.begin(), P.only.end(), family) == P.only.end()) return -1;
     if (P.pending.size() > 4096) prof_drain(ctx);
     ProfRecord r;
     r.family = family_index(P, family);
@@ -90,4 +91,22 @@ extern "C" helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64
             return HELM_OK;
         }
     return set_error(ctx, HELM_ENOTFOUND, "helm_profile_query: no launches recorded for %s", name);
+}
+
+extern "C" helm_status helm_profile_select(helm_ctx ctx, const char* families) {
+    if (!ctx) return HELM_EINVAL;
+    Profiler& P = ctx->prof;
+    P.only.clear();
+    if (!families) return HELM_OK;
+    std::string cur;
+    for (const char* c = families;; ++c) {
+        if (*c == ',' || *c == 0) {
+            if (!cur.empty()) P.only.push_back(cur);
+            cur.clear();
+            if (!*c) break;
+        } else if (*c != ' ') {
+            cur.push_back(*c);
+        }
+    }
+    return HELM_OK;
 }

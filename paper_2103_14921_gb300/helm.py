@@ -83,6 +83,7 @@ def lib():
         "helm_bytes_in_use": (C.c_size_t, [vp]),
         "helm_launch_count": (C.c_uint64, [vp]),
         "helm_profile_enable": (st, [vp, i32]),
+        "helm_profile_select": (st, [vp, C.c_char_p]),
         "helm_profile_query": (st, [vp, C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
         "helm_fit_weights": (st, [C.c_double, C.c_double, C.POINTER(C.c_double)]),
@@ -147,8 +148,10 @@ class Context:
     def launches(self):
         return lib().helm_launch_count(self._h)
 
-    def profile(self, on=True):
-        """Enable (and clear) or disable per-kernel-family event timing."""
+    def profile(self, on=True, only=None):
+        """Enable (and clear) or disable per-kernel-family event timing; ``only`` = list of families."""
+        self.check(lib().helm_profile_select(self._h, ",".join(only).encode() if only else None),
+                   "helm_profile_select")
         self.check(lib().helm_profile_enable(self._h, 1 if on else 0), "helm_profile_enable")
 
     def profile_query(self, family):
