@@ -309,7 +309,7 @@ def run_gpu(args, W):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    roof_fam = "sweep_gemm_tc" if args.factor_prec == "tf32" else "sweep_gemv"
+    roof_fam = "sweep_gemm_tc" if args.factor_prec in ("tf32", "bf16") else "sweep_gemv"
     ctx.profile(True, only=[roof_fam])          # events around the roofline kernel only
     l0 = ctx.launches
     e0 = torch.cuda.Event(enable_timing=True)
@@ -348,6 +348,29 @@ def run_gpu(args, W):
     iters = [s["iterations"] for s in stats_all[-1]]
     relres = max(s["true_relres"] for s in stats_all[-1])
     x_mixed = x.clone()
+
+    # variant: bfloat16-stored local factors (the same solve, reported beside the headline path)
+    variants = {}
+    if args.factor_prec == "tf32" and not args.no_variants:
+        ob = helm.Oras(grid, W["parts"], W["overlap"], coarse_ratio=W["coarse"], factor_prec=helm.PREC_BF16)
+        xb = torch.empty_like(b)
+        ob.solve(b, xb, **solve_kw)
+        torch.cuda.synchronize()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        kv = max(1, min(args.steps, 3))
+        for _ in range(kv):
+            _, stb = ob.solve(b, xb, **solve_kw)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vb, _ = replicas.job_throughput(nrhs * kv, v0.elapsed_time(v1) / 1000.0, dev)
+        err = float(torch.linalg.vector_norm(xb - x) / torch.linalg.vector_norm(x))
+        variants["bf16_factors"] = {"value": vb, "unit": "RHS/s", "steps": kv,
+                                    "iterations": [s_["iterations"] for s_ in stb],
+                                    "max_true_relres": max(s_["true_relres"] for s_ in stb),
+                                    "rel_l2_vs_tf32_solution": err}
+        del ob, xb
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     bh = torch.from_numpy(b_host).pin_memory()
@@ -388,7 +411,7 @@ def run_gpu(args, W):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     # DRAM traffic per launch relative to the algorithmic bytes, from the ncu capture summarised in
     # profiles/tc_sweep_gemm_lg64.md (dram__bytes_read.sum + dram__bytes_write.sum = 1.047 x algorithmic)
-    traffic_ratio = {"sweep_gemm_tc": 1.047}.get(roof_fam)
+    traffic_ratio = {"sweep_gemm_tc": 1.047}.get(roof_fam) if args.factor_prec == "tf32" else None
     roof = None
     fam = roof_fam
     g = roof_meas
@@ -432,7 +455,7 @@ def run_gpu(args, W):
                 "d2h_bytes_per_step": int(b_host.nbytes)},
         "gpu_launches": int(launches),
         "roofline": roof, "kernels": kernels, "plain_fp64_gpu": plain,
-        "cpu_baseline": cpu, "clocks": clk, "serving": serving,
+        "cpu_baseline": cpu, "clocks": clk, "serving": serving, "variants": variants,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -446,13 +469,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lg112")
-    ap.add_argument("--factor-prec", choices=["fp32", "tf32"], default="tf32",
-                    help="fine local factors: tf32 = complex64 factors, tensor-core sweeps; fp32 = CUDA-core sweeps")
+    ap.add_argument("--factor-prec", choices=["fp32", "tf32", "bf16"], default="tf32",
+                    help="fine local factors: tf32 = complex64 factors, tensor-core sweeps; bf16 = bfloat16-stored "
+                         "factors, tensor-core sweeps; fp32 = CUDA-core sweeps")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 single-RHS measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream (serving) measurement")
-    ap.add_argument("--serve-requests", type=int, default=40)
-    ap.add_argument("--serve-rate", type=float, default=8.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--no-variants", action="store_true", help="skip the bf16-factor variant measurement")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate, requests/s")
     ap.add_argument("--ref-iters", type=float, default=20.0,
                     help="iterations per RHS used to scale the oracle's per-iteration time (reference arm)")
     args = ap.parse_args()

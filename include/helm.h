@@ -72,6 +72,8 @@ typedef struct helm_oras_s* helm_oras;
 #define HELM_PREC_FP32   1
 #define HELM_PREC_TF32   2
 #define HELM_PREC_TF32X3 3
+#define HELM_PREC_BF16   4   /* local factors stored as bfloat16 pairs, sweeps on the tensor cores (kind::f16)
+                                with FP32 accumulation; factorised in FP32 first */
 
 /* ---------------------------------------------------------------- context */
 
@@ -142,8 +144,8 @@ typedef struct {
     int overlap;          /* nodes added on every interior side of each core (>= 1)         */
     int coarse_ratio;     /* 0 = one level (Eq. oras); r >= 2 = trilinear coarse grid (Eq. 2lvl) */
     int interface_bc;     /* 0 = absorbing (ORAS, rho = exp(i k_p h) folding); 1 = Dirichlet (RAS) */
-    int factor_prec;      /* HELM_PREC_FP64, _FP32 or _TF32 for the fine local factors (_TF32X3 is
-                             rejected: not available).  The coarse factors are always computed
+    int factor_prec;      /* HELM_PREC_FP64, _FP32, _TF32 or _BF16 for the fine local factors
+                             (_TF32X3 is rejected: not available).  The coarse factors are always computed
                              in FP64; with non-FP64 fine factors they are applied from a complex64
                              copy, with FP64 fine factors in FP64                                   */
 } helm_oras_desc;

@@ -126,7 +126,9 @@ struct PlaneSet {
     BoxInfo* dbox = nullptr;
     void* coef = nullptr;       // [nloc][27] in the set's precision
     void* G = nullptr;          // factors, per box: bz planes of m x m row-major
-    size_t esize() const { return prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64); }
+    // bytes of one stored factor entry, and of one coefficient / local-vector entry
+    size_t esize() const { return prec == HELM_PREC_FP64 ? sizeof(c128) : (prec == HELM_PREC_BF16 ? 4 : sizeof(c64)); }
+    size_t cesize() const { return prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64); }
 };
 
 struct helm_oras_s {
@@ -192,6 +194,7 @@ helm_status launch_max_real(helm_ctx ctx, const c128* v, long long n, double* ho
 helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P);
 void planeset_free(helm_ctx ctx, PlaneSet& P);
 helm_status planeset_factor(helm_ctx ctx, PlaneSet& P, int* singular);
+helm_status planeset_to_bf16(helm_ctx ctx, PlaneSet& P);
 helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st);
 // tensor-core sweeps (sweep_tc.cu), complex64 local vectors, padded factor layout
 int tc_npad(int nrhs);

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <cuda_bf16.h>
+
 #include "coef.cuh"
 #include "internal.h"
 
@@ -249,7 +251,7 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
     if (d->overlap < 0 || d->coarse_ratio < 0)
         return set_error(ctx, HELM_EINVAL, "oras_factor: bad overlap or coarse ratio");
     if (d->interface_bc != 0 && d->interface_bc != 1) return set_error(ctx, HELM_EINVAL, "oras_factor: bad interface_bc");
-    if (d->factor_prec < HELM_PREC_FP64 || d->factor_prec > HELM_PREC_TF32X3)
+    if (d->factor_prec < HELM_PREC_FP64 || d->factor_prec > HELM_PREC_BF16)
         return set_error(ctx, HELM_EINVAL, "oras_factor: bad factor_prec");
     HELM_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
@@ -285,7 +287,7 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
     if (d->factor_prec == HELM_PREC_TF32X3)
         return fail(set_error(ctx, HELM_EINVAL, "oras_factor: TF32X3 factors are not available"));
     o->fine.prec = d->factor_prec == HELM_PREC_FP64 ? HELM_PREC_FP64 : HELM_PREC_FP32;
-    o->fine.padded = d->factor_prec == HELM_PREC_TF32;
+    o->fine.padded = d->factor_prec == HELM_PREC_TF32 || d->factor_prec == HELM_PREC_BF16;
     if ((rc = dev_alloc(ctx, (void**)&o->dev_err, sizeof(int), "device error flag"))) return fail(rc);
     if ((rc = cuda_check(ctx, cudaMemsetAsync(o->dev_err, 0, sizeof(int), st), "clear error flag"))) return fail(rc);
     for (int tz = 0; tz < p[2]; ++tz)
@@ -327,6 +329,7 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
     int singular = 0;
     if ((rc = planeset_factor(ctx, o->fine, &singular))) return fail(rc);
     if (singular) return fail(set_error(ctx, HELM_ESINGULAR, "oras_factor: zero pivot in a local plane factor"));
+    if (d->factor_prec == HELM_PREC_BF16 && (rc = planeset_to_bf16(ctx, o->fine))) return fail(rc);
 
     // --- coarse level
     if (d->coarse_ratio > 0) {
@@ -399,10 +402,12 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
 // 8 split-K partial planes of its sweeps there.
 static int rbuf_planes(helm_oras o) { return o->fine.nbox == 1 ? 9 : o->fine.nbox; }
 
+static size_t tc_elem(helm_oras o) { return o->fine.prec == HELM_PREC_BF16 ? 2 : sizeof(float); }
+
 static void free_scratch(helm_oras o) {
     helm_ctx ctx = o->g->ctx;
     if (!o->cap_nrhs) return;
-    const size_t fe = o->fine.esize();
+    const size_t fe = o->fine.cesize();
     const size_t we = o->cap_wp == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
     const int R = o->cap_nrhs;
     dev_free(ctx, o->loc, (size_t)o->fine.nloc * R * fe);
@@ -411,7 +416,7 @@ static void free_scratch(helm_oras o) {
     dev_free(ctx, o->crbuf, (size_t)9 * o->coarse.m_max * R * sizeof(c128));
     dev_free(ctx, o->qf, (size_t)o->g->n * R * we);
     dev_free(ctx, o->tf, (size_t)o->g->n * R * we);
-    dev_free(ctx, o->tcb, (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * sizeof(float));
+    dev_free(ctx, o->tcb, (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * tc_elem(o));
     o->tcb = nullptr;
     o->tc_npad = 0;
     o->loc = o->rbuf = o->qf = o->tf = nullptr;
@@ -424,7 +429,7 @@ static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
     helm_ctx ctx = o->g->ctx;
     cudaStreamSynchronize(ctx->stream);
     free_scratch(o);
-    const size_t fe = o->fine.esize();
+    const size_t fe = o->fine.cesize();
     const size_t we = wp == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
     o->cap_nrhs = nrhs;
     o->cap_wp = wp;
@@ -433,7 +438,7 @@ static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
     HELM_TRY(dev_alloc(ctx, &o->rbuf, (size_t)rbuf_planes(o) * o->fine.m_max * R * fe, "sweep buffer"));
     if (o->fine.padded) {
         o->tc_npad = tc_npad(R);
-        const size_t bytes = (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * sizeof(float);
+        const size_t bytes = (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * tc_elem(o);
         HELM_TRY(dev_alloc(ctx, &o->tcb, bytes, "tensor-core sweep operand"));
         HELM_CUDA(ctx, cudaMemsetAsync(o->tcb, 0, bytes, ctx->stream));
     }
@@ -581,6 +586,14 @@ extern "C" helm_status oras_box_info(helm_oras o, int box, int* nboxes, int lo[3
 }
 
 namespace {
+__global__ void widen_bf16(const __nv_bfloat162* __restrict__ a, c128* __restrict__ b, int m, int ld) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)m * m) return;
+    const long long r = i / m, j = i % m;
+    const float2 v = __bfloat1622float2(a[r * ld + j]);
+    b[i] = mk<double>(v.x, v.y);
+}
+
 // b[r * m + j] = a[r * ld + j] widened, for an m x m plane stored with row pitch ld
 __global__ void widen_c64(const c64* __restrict__ a, c128* __restrict__ b, int m, int ld) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -608,6 +621,10 @@ extern "C" helm_status oras_plane_inverse(helm_oras o, int box, int plane, void*
     if (o->fine.prec == HELM_PREC_FP64) {
         cudaMemcpy2DAsync(dst, B.m * sizeof(c128), (c128*)o->fine.G + off, B.ld * sizeof(c128), B.m * sizeof(c128), B.m,
                           cudaMemcpyDeviceToDevice, ctx->stream);
+    } else if (o->fine.prec == HELM_PREC_BF16) {
+        widen_bf16<<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>((const __nv_bfloat162*)o->fine.G + off, dst,
+                                                                          B.m, B.ld);
+        ctx->launches++;
     } else {
         widen_c64<<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>((c64*)o->fine.G + off, dst, B.m, B.ld);
         ctx->launches++;
@@ -653,7 +670,7 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     if (ctx->device < 0 || ctx->device >= 64) return set_error(ctx, HELM_EINVAL, "oras_apply_noalloc: device id");
     HELM_CUDA(ctx, cudaSetDevice(ctx->device));
     // working vectors, carved from the static array (complex128 work precision)
-    const size_t fe = o->fine.esize();
+    const size_t fe = o->fine.cesize();
     const size_t R = (size_t)nrhs;
     const size_t s_loc = align256((size_t)o->fine.nloc * R * fe);
     const size_t s_rb = align256((size_t)rbuf_planes(o) * o->fine.m_max * R * fe);
@@ -661,7 +678,7 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     const size_t s_crb = o->nc ? align256((size_t)9 * o->coarse.m_max * R * sizeof(c128)) : 0;
     const size_t s_vec = o->nc ? align256((size_t)o->g->n * R * sizeof(c128)) : 0;
     const int npad = o->fine.padded ? tc_npad(nrhs) : 0;
-    const size_t s_tcb = o->fine.padded ? align256((size_t)o->fine.nbox * npad * 2 * o->fine.ld * sizeof(float)) : 0;
+    const size_t s_tcb = o->fine.padded ? align256((size_t)o->fine.nbox * npad * 2 * o->fine.ld * tc_elem(o)) : 0;
     const size_t need = s_loc + s_rb + s_cv + s_crb + 2 * s_vec + s_tcb;
     if (need > HELM_NOALLOC_SCRATCH_BYTES)
         return set_error(ctx, HELM_EINVAL,
@@ -713,8 +730,8 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
 size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int nrhs) {
     const int n[3] = {g.nx, g.ny, g.nz};
     const int p[3] = {std::max(1, d.px), std::max(1, d.py), std::max(1, d.pz)};
-    const size_t fe = d.factor_prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
-    const bool padded = d.factor_prec == HELM_PREC_TF32;
+    const size_t fe = d.factor_prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);   // as factorised
+    const bool padded = d.factor_prec == HELM_PREC_TF32 || d.factor_prec == HELM_PREC_BF16;
     size_t m_max = 0, nloc = 0, planes = 0, fac = 0;
     std::vector<std::pair<size_t, size_t>> boxes;   // (m, bz)
     for (int tz = 0; tz < p[2]; ++tz)

@@ -26,6 +26,8 @@
 // other columns B become W B = B + (W[:, j0:j1] - I[:, j0:j1]) B[j0:j1, :]
 // (rows j0..j1 of B are copied out first).  At the end the columns are
 // swapped back in reverse pivot order.
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace {
@@ -688,7 +690,7 @@ helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P) {
     P.nplanes = planes;
     HELM_TRY(dev_alloc(ctx, (void**)&P.dbox, P.nbox * sizeof(BoxInfo), "box table"));
     HELM_CUDA(ctx, cudaMemcpy(P.dbox, P.hbox.data(), P.nbox * sizeof(BoxInfo), cudaMemcpyHostToDevice));
-    HELM_TRY(dev_alloc(ctx, &P.coef, (size_t)P.nloc * 27 * P.esize(), "local operator coefficients"));
+    HELM_TRY(dev_alloc(ctx, &P.coef, (size_t)P.nloc * 27 * P.cesize(), "local operator coefficients"));
     HELM_TRY(dev_alloc(ctx, &P.G, P.fac_entries * P.esize(), "plane factors"));
     if (P.padded) HELM_CUDA(ctx, cudaMemsetAsync(P.G, 0, P.fac_entries * P.esize(), ctx->stream));
     return HELM_OK;
@@ -696,7 +698,7 @@ helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P) {
 
 void planeset_free(helm_ctx ctx, PlaneSet& P) {
     dev_free(ctx, P.dbox, P.nbox * sizeof(BoxInfo));
-    dev_free(ctx, P.coef, (size_t)P.nloc * 27 * P.esize());
+    dev_free(ctx, P.coef, (size_t)P.nloc * 27 * P.cesize());
     dev_free(ctx, P.G, P.fac_entries * P.esize());
     P.dbox = nullptr;
     P.coef = P.G = nullptr;
@@ -705,6 +707,28 @@ void planeset_free(helm_ctx ctx, PlaneSet& P) {
 helm_status planeset_factor(helm_ctx ctx, PlaneSet& P, int* singular) {
     if (P.prec == HELM_PREC_FP64) return factor_t<double>(ctx, P, singular);
     return factor_t<float>(ctx, P, singular);
+}
+
+namespace {
+__global__ void to_bf16_pairs(const c64* __restrict__ a, __nv_bfloat162* __restrict__ b, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = __floats2bfloat162_rn(a[i].x, a[i].y);
+}
+}  // namespace
+
+// Replace complex64 factors by bfloat16 pairs (same layout), freeing the complex64 copy.
+helm_status planeset_to_bf16(helm_ctx ctx, PlaneSet& P) {
+    if (P.prec != HELM_PREC_FP32) return set_error(ctx, HELM_EINVAL, "planeset_to_bf16: factors are not complex64");
+    void* g16 = nullptr;
+    HELM_TRY(dev_alloc(ctx, &g16, P.fac_entries * 4, "bf16 plane factors"));
+    to_bf16_pairs<<<(unsigned)std::min<size_t>((P.fac_entries + 255) / 256, 65535), 256, 0, ctx->stream>>>(
+        (const c64*)P.G, (__nv_bfloat162*)g16, P.fac_entries);
+    ctx->launches++;
+    HELM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx, P.G, P.fac_entries * sizeof(c64));
+    P.G = g16;
+    P.prec = HELM_PREC_BF16;
+    return HELM_OK;
 }
 
 helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st) {

@@ -11,6 +11,9 @@
 //   B^T[2r+1][2p] = Im R[p][r], B^T[2r+1][2p+1] = Re R[p][r],
 // so D[i][2r] = Re (G R)[i][r] and D[i][2r+1] = Im (G R)[i][r].
 //
+// Two operand types: TF32 (complex64 factors read as fp32, kind::tf32, K = 8 per MMA) and
+// BF16 (factors stored as bfloat16 pairs, kind::f16, K = 16 per MMA); both accumulate in FP32.
+//
 // tc_prep builds B^T for the step (FWD: R = b_k - L_k y_{k-1}; BWD:
 // R = U_k x_{k+1}).  tc_sweep_gemm: one CTA per (128-row tile, box), four
 // warps; warp 0 lane 0 issues the TMA loads of 128 x 32-float A tiles and
@@ -19,6 +22,7 @@
 // stage back to the producer, and all four warps read the accumulator from
 // TMEM (thread t <-> row t) and write y_k (FWD) or x_k = y_k - D (BWD).
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "internal.h"
@@ -27,14 +31,27 @@
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 32;     // fp32 per 128-byte swizzled row
+
+// element traits: operands per 128-byte swizzled row, MMA K, conversion from float
+template <typename E> struct Elem;
+template <> struct Elem<float> {
+    static constexpr int BK = 32;
+    static constexpr int MMA_K = 8;
+    static __device__ __forceinline__ float from(float v) { return v; }
+};
+template <> struct Elem<__nv_bfloat16> {
+    static constexpr int BK = 64;
+    static constexpr int MMA_K = 16;
+    static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
 
 // Tiles of 32 plane nodes x nrhs: values formed with the rhs index fastest (coalesced reads of
 // the [node][rhs] local vectors), transposed through shared memory, written as B^T rows.
 constexpr int PREP_TP = 32;
 
+template <typename E>
 __global__ void __launch_bounds__(256) tc_prep(const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
-                                               const c64* __restrict__ loc, float* __restrict__ bt, int ld2, int npad,
+                                               const c64* __restrict__ loc, E* __restrict__ bt, int ld2, int npad,
                                                int nrhs, int s, int fwd) {
     __shared__ c64 tile[128 * (PREP_TP + 1)];
     const BoxInfo B = boxes[blockIdx.y];
@@ -45,7 +62,7 @@ __global__ void __launch_bounds__(256) tc_prep(const BoxInfo* __restrict__ boxes
     const long long plane = B.loc_off + (long long)k * m;
     const long long nbr = fwd ? plane - m : plane + m;
     const int off = fwd ? 0 : 18;
-    float* bb = bt + (size_t)blockIdx.y * npad * ld2;
+    E* bb = bt + (size_t)blockIdx.y * npad * ld2;
     for (int p0 = blockIdx.x * PREP_TP; p0 < m; p0 += gridDim.x * PREP_TP) {
         for (int e = threadIdx.x; e < PREP_TP * nrhs; e += blockDim.x) {
             const int pl = e / nrhs, r = e % nrhs, p = p0 + pl;
@@ -82,31 +99,37 @@ __global__ void __launch_bounds__(256) tc_prep(const BoxInfo* __restrict__ boxes
             const int r = e / PREP_TP, pl = e % PREP_TP, p = p0 + pl;
             if (p < m) {
                 const c64 a = tile[r * (PREP_TP + 1) + pl];
-                reinterpret_cast<float2*>(bb + (size_t)(2 * r) * ld2)[p] = make_float2(a.x, -a.y);
-                reinterpret_cast<float2*>(bb + (size_t)(2 * r + 1) * ld2)[p] = make_float2(a.y, a.x);
+                E* re_row = bb + (size_t)(2 * r) * ld2 + 2 * p;
+                E* im_row = bb + (size_t)(2 * r + 1) * ld2 + 2 * p;
+                re_row[0] = Elem<E>::from(a.x);
+                re_row[1] = Elem<E>::from(-a.y);
+                im_row[0] = Elem<E>::from(a.y);
+                im_row[1] = Elem<E>::from(a.x);
             }
         }
         __syncthreads();
     }
 }
 
-template <int NPAD>
+template <typename E, int NPAD>
 struct TcCfg {
-    static constexpr int A_BYTES = TC_BM * TC_BK * 4;
-    static constexpr int B_BYTES = NPAD * TC_BK * 4;
+    static constexpr int BK = Elem<E>::BK;
+    static constexpr int A_BYTES = TC_BM * 128;
+    static constexpr int B_BYTES = NPAD * 128;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int STAGES = NPAD >= 256 ? 3 : (NPAD >= 128 ? 4 : 5);
     static constexpr uint32_t TCOLS = NPAD <= 32 ? 32 : (NPAD <= 64 ? 64 : (NPAD <= 128 ? 128 : 256));
     static constexpr int SMEM = STAGES * STAGE + (2 * STAGES + 1) * 8 + 16 + 1024;
 };
 
-template <int NPAD>
+template <typename E, int NPAD>
 __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ CUtensorMap mapA,
                                                         const __grid_constant__ CUtensorMap mapB,
                                                         const BoxInfo* __restrict__ boxes, c64* __restrict__ loc,
                                                         int nrhs, int s, int fwd, int* __restrict__ err) {
-    using Cfg = TcCfg<NPAD>;
+    using Cfg = TcCfg<E, NPAD>;
     constexpr int TC_STAGES = Cfg::STAGES;
+    constexpr int TC_BK = Cfg::BK;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
@@ -157,7 +180,8 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        constexpr uint32_t idesc = tc::idesc_tf32(TC_BM, NPAD);
+        constexpr bool BF = sizeof(E) == 2;
+        constexpr uint32_t idesc = BF ? tc::idesc_bf16(TC_BM, NPAD) : tc::idesc_tf32(TC_BM, NPAD);
         for (int kc = 0; kc < nK; ++kc) {
             const int st = kc % TC_STAGES;
             if (!tc::mbar_wait(&full[st], (kc / TC_STAGES) & 1, err, 2)) break;
@@ -165,9 +189,11 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
             const uint32_t sa = tc::smem_u32(base + st * Cfg::STAGE);
             const uint32_t sb = sa + Cfg::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 8; ++kk)
-                tc::mma_tf32(tmem, tc::desc_k_sw128(sa + kk * 32), tc::desc_k_sw128(sb + kk * 32), idesc,
-                             (kc > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < TC_BK / Elem<E>::MMA_K; ++kk) {
+                const uint64_t ad = tc::desc_k_sw128(sa + kk * 32), bd = tc::desc_k_sw128(sb + kk * 32);
+                if (BF) tc::mma_f16(tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                else tc::mma_tf32(tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+            }
             tc::mma_commit(&empty[st]);
         }
         tc::mma_commit(done);
@@ -225,30 +251,34 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool encode_3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1) {
+bool encode_3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
+               bool bf16) {
     PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = encode_fn();
     if (!cuTensorMapEncodeTiled) return false;
+    const uint64_t es_bytes = bf16 ? 2 : 4;
     cuuint64_t dims[3] = {d0, d1, d2};
-    cuuint64_t strides[2] = {d0 * 4, d0 * d1 * 4};
+    cuuint64_t strides[2] = {d0 * es_bytes, d0 * d1 * es_bytes};
     cuuint32_t box[3] = {b0, b1, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+    CUresult r = cuTensorMapEncodeTiled(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                                        base, dims, strides, box, es,
                                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-template <int NPAD>
-helm_status run_tc(helm_ctx ctx, const PlaneSet& P, c64* loc, float* bt, int nrhs, cudaStream_t st, int* err) {
-    using Cfg = TcCfg<NPAD>;
+template <typename E, int NPAD>
+helm_status run_tc(helm_ctx ctx, const PlaneSet& P, c64* loc, E* bt, int nrhs, cudaStream_t st, int* err) {
+    using Cfg = TcCfg<E, NPAD>;
+    constexpr bool BF = sizeof(E) == 2;
     CUtensorMap mapA, mapB;
     const int ld = P.ld;
-    if (!encode_3d(&mapA, P.G, 2ull * ld, (uint64_t)ld, (uint64_t)P.nplanes, TC_BK, TC_BM) ||
-        !encode_3d(&mapB, bt, 2ull * ld, (uint64_t)NPAD, (uint64_t)P.nbox, TC_BK, NPAD))
+    if (!encode_3d(&mapA, P.G, 2ull * ld, (uint64_t)ld, (uint64_t)P.nplanes, Cfg::BK, TC_BM, BF) ||
+        !encode_3d(&mapB, bt, 2ull * ld, (uint64_t)NPAD, (uint64_t)P.nbox, Cfg::BK, NPAD, BF))
         return set_error(ctx, HELM_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(tc_sweep_gemm<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        cudaFuncSetAttribute(tc_sweep_gemm<E, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         attr = true;
     }
     const int m = P.m_max;
@@ -256,13 +286,14 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, c64* loc, float* bt, int nrh
     const dim3 pgrid((unsigned)((m + PREP_TP - 1) / PREP_TP), P.nbox);
     const c64* coef = (const c64*)P.coef;
     const double es = sizeof(c64);
+    const double fs = 2.0 * sizeof(E);   // bytes of one stored complex factor entry
     auto bytes = [&](int s, bool fwd, double& gemm, double& prep) {
         gemm = prep = 0;
         for (const auto& b : P.hbox) {
             const int bz = b.dims[2];
             const bool act = fwd ? s < bz : (s >= 1 && s <= bz - 1);
             if (!act) continue;
-            gemm += ((double)b.m * b.m + (double)b.m * NPAD / 2 + (fwd ? 1.0 : 2.0) * b.m * nrhs) * es;
+            gemm += ((double)b.m * b.m + (double)b.m * NPAD / 2) * fs + (fwd ? 1.0 : 2.0) * b.m * nrhs * es;
             prep += ((double)b.m * 9 + (fwd ? 3.0 : 2.0) * b.m * nrhs) * es;
         }
     };
@@ -272,10 +303,10 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, c64* loc, float* bt, int nrh
         for (int s = fwd ? 0 : 1; s < P.bz_max; ++s) {
             bytes(s, fwd, gb, pb);
             int t = prof_begin(ctx, "sweep_prep");
-            tc_prep<<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
+            tc_prep<E><<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
             prof_end(ctx, t, pb);
             t = prof_begin(ctx, "sweep_gemm_tc");
-            tc_sweep_gemm<NPAD><<<ggrid, 128, Cfg::SMEM, st>>>(mapA, mapB, P.dbox, loc, nrhs, s, fwd, err);
+            tc_sweep_gemm<E, NPAD><<<ggrid, 128, Cfg::SMEM, st>>>(mapA, mapB, P.dbox, loc, nrhs, s, fwd, err);
             prof_end(ctx, t, gb);
             ctx->launches += 2;
         }
@@ -297,11 +328,21 @@ int tc_npad(int nrhs) {
 helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, void* loc, void* bt, int npad, int nrhs,
                               cudaStream_t st, int* err) {
     if (nrhs > 128 || tc_npad(nrhs) > npad) return set_error(ctx, HELM_EINVAL, "tensor-core sweep: too many rhs");
+    if (P.prec == HELM_PREC_BF16) {
+        typedef __nv_bfloat16 B;
+        switch (npad) {
+            case 16: return run_tc<B, 16>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
+            case 32: return run_tc<B, 32>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
+            case 64: return run_tc<B, 64>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
+            case 128: return run_tc<B, 128>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
+            default: return run_tc<B, 256>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
+        }
+    }
     switch (npad) {
-        case 16: return run_tc<16>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 32: return run_tc<32>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 64: return run_tc<64>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 128: return run_tc<128>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
-        default: return run_tc<256>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 16: return run_tc<float, 16>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 32: return run_tc<float, 32>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 64: return run_tc<float, 64>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 128: return run_tc<float, 128>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        default: return run_tc<float, 256>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
     }
 }

@@ -27,8 +27,8 @@ _atexit.register(_mark_finalizing)   # handles still alive at exit are left to p
 
 OK, EINVAL, ENOMEM, ENOTCONV, ESINGULAR, ENONFINITE, ETIMEOUT, EBUSY, ECUDA, ENOTFOUND = range(10)
 TOP_DIRICHLET, TOP_PML = 0, 1
-PREC_FP64, PREC_FP32, PREC_TF32, PREC_TF32X3 = 0, 1, 2, 3
-PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3}
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_TF32X3, PREC_BF16 = 0, 1, 2, 3, 4
+PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3, "bf16": PREC_BF16}
 
 
 class HelmError(RuntimeError):

@@ -66,6 +66,50 @@ def test_single_plane_boxes_equal_emulated_tf32_gemm(ctx, dims, nrhs):
         assert float(torch.linalg.norm(y - exact) / torch.linalg.norm(exact)) <= 2e-3
 
 
+@pytest.mark.parametrize("dims,nrhs", [((24, 20, 2), 16), ((37, 29, 2), 5)])
+def test_single_plane_boxes_bf16_factors(ctx, dims, nrhs):
+    """BF16-stored factors (kind::f16): equal to the FP64 product of the bf16-rounded operands (products of
+    bf16 values are exact in FP32, so only the FP32 accumulation differs: 2e-5), and within bf16 rounding
+    (2e-2) of the product with the complex64 operands."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    nx, ny, nz = dims
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 1.0)
+    grid = helm.Grid(ctx, nx, ny, nz, 25.0, 5.0, c, npml=1, weights=helm.fit_weights())
+    o = helm.Oras(grid, (2, 2, 2), 0, factor_prec=helm.PREC_BF16)
+    v = torch.from_numpy(synth.random_complex((nz, ny, nx, nrhs), 62)).cuda()
+    got = o.apply(v)
+    for b in range(o.box_info(0)[0]):
+        _, lo, bd = o.box_info(b)
+        G = o.plane_inverse(b, 0)                                  # the stored bf16 values, widened
+        vb = v[lo[2], lo[1]:lo[1] + bd[1], lo[0]:lo[0] + bd[0], :].reshape(-1, nrhs).to(torch.complex64)
+        vr = torch.complex(vb.real.to(torch.bfloat16).double(), vb.imag.to(torch.bfloat16).double())
+        y = got[lo[2], lo[1]:lo[1] + bd[1], lo[0]:lo[0] + bd[0], :].reshape(-1, nrhs)
+        want = G @ vr
+        assert float(torch.linalg.norm(y - want) / torch.linalg.norm(want)) <= 2e-5, b
+        exact = G @ vb.to(torch.complex128)
+        assert float(torch.linalg.norm(y - exact) / torch.linalg.norm(exact)) <= 2e-2
+
+
+def test_bf16_fgmres_converges(ctx):
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (30, 28, 26)
+    nx, ny, nz = dims
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 0.6)
+    w = helm.fit_weights()
+    grid = helm.Grid(ctx, nx, ny, nz, 25.0, 6.0, c, npml=4, weights=w)
+    prob = Problem(nx, ny, nz, 25.0, 6.0, c, npml=4, weights=w)
+    b = synth.point_sources(nx, ny, nz, 25.0, synth.source_plane_positions(nx, ny, 4, 3, 4, 10))
+    o = helm.Oras(grid, (2, 2, 2), 2, coarse_ratio=4, factor_prec=helm.PREC_BF16)
+    x, stats = o.solve(torch.from_numpy(b).cuda(), tol=1e-6, restart=30, basis_prec=helm.PREC_FP32)
+    x = x.cpu().numpy()
+    for r in range(4):
+        assert stats[r]["converged"]
+        res = np.linalg.norm(apply_A(prob, x[..., r]) - b[..., r]) / np.linalg.norm(b[..., r])
+        assert res <= 1e-6
+
+
 def test_tf32_fgmres_converges_to_the_direct_solution(ctx):
     import torch
     from paper_2103_14921_gb300 import helm
