@@ -159,6 +159,11 @@ typedef struct {
 helm_status oras_factor(helm_grid g, const helm_oras_desc* desc, helm_oras* out);
 void        oras_destroy(helm_oras o);
 
+/* Estimated device bytes an ORAS handle with this description holds (factors, local
+ * operators, coarse level, set-up probes) plus its apply scratch for nrhs columns -- the
+ * figure the serving loop admits against.  Host-only, no device work. */
+helm_status oras_estimate_bytes_c(const helm_grid_desc* grid, const helm_oras_desc* desc, int nrhs, size_t* bytes);
+
 /* out = M^{-1} v (Eq. 2lvl, or Eq. oras without a coarse level).
  * v, out: complex128, nrhs columns, device pointers. */
 helm_status oras_apply(helm_oras o, const void* v, void* out, int nrhs);

@@ -47,10 +47,30 @@ template <typename T> __device__ __forceinline__ c128 widen(cplx<T> a) { return 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
                                                            const cplx<T>* __restrict__ w, long long n_el, int nrhs,
-                                                           int i0, int ni, c128* __restrict__ partial, int ldp) {
+                                                           int i0, int ni, c128* __restrict__ partial, int ldp,
+                                                           double* __restrict__ npart, const int* __restrict__ any) {
     __shared__ c128 s[RED_THREADS];
+    if (any && *any == 0) return;
     const long long t = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
     const long long stride = (long long)gridDim.x * RED_THREADS;
+    if (npart) {
+        // |w|^2 per column (the norm before the projection, for the re-orthogonalisation test)
+        double nrm = 0.0;
+        for (long long e = t; e < n_el; e += stride) {
+            const c128 a = widen(w[e]);
+            nrm += a.x * a.x + a.y * a.y;
+        }
+        __shared__ double sn[RED_THREADS];
+        sn[threadIdx.x] = nrm;
+        __syncthreads();
+        if (threadIdx.x < min(nrhs, RED_THREADS)) {
+            double sum = 0.0;
+            for (int u = threadIdx.x; u < RED_THREADS; u += nrhs) sum += sn[u];
+            const int r = (int)(((long long)blockIdx.x * RED_THREADS + threadIdx.x) % nrhs);
+            npart[(long long)blockIdx.x * nrhs + r] = sum;
+        }
+        __syncthreads();
+    }
     for (int ib = 0; ib < ni; ib += IC) {
         c128 acc[IC];
         cplx<T> part[IC];
@@ -106,9 +126,12 @@ __device__ __forceinline__ c128 block_sum128(c128 v) {
 
 __global__ void __launch_bounds__(128) finish_dots(const c128* __restrict__ partial, int nblk, int ldp, int ni,
                                                    int nrhs, c128* __restrict__ H, int ldh_i, int ldh_r, int col,
-                                                   int accumulate) {
+                                                   int accumulate, const int* __restrict__ colmask,
+                                                   const int* __restrict__ any) {
     const int i = blockIdx.x / nrhs, r = blockIdx.x % nrhs;
     if (i >= ni) return;
+    if (any && *any == 0) return;
+    if (colmask && !colmask[r]) return;
     c128 sum = mk<double>(0, 0);
     for (int b = threadIdx.x; b < nblk; b += 128) sum = sum + partial[((long long)b * ldp + i) * nrhs + r];
     sum = block_sum128(sum);
@@ -135,6 +158,66 @@ __global__ void update_kernel(const cplx<T>* __restrict__ V, long long vstride, 
         }
         w[e] = acc;
     }
+}
+
+// w -= V h for the columns selected by colmask (all when colmask is null; none when *any == 0),
+// and npart[blk][r] = |w|^2 of the result over this block's elements.  Runs on the reduction grid
+// (grid stride a multiple of nrhs), so each thread keeps one column; the coefficients h are staged
+// in shared memory in the basis precision when they fit (ni * nrhs entries).
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(const cplx<T>* __restrict__ V, long long vstride,
+                                                                  cplx<T>* __restrict__ w, long long n_el, int nrhs,
+                                                                  int ni, const c128* __restrict__ hsrc,
+                                                                  const int* __restrict__ colmask,
+                                                                  const int* __restrict__ any,
+                                                                  double* __restrict__ npart, int hsmem) {
+    extern __shared__ __align__(16) unsigned char upd_smem[];
+    cplx<T>* hs = reinterpret_cast<cplx<T>*>(upd_smem);
+    __shared__ double sn[RED_THREADS];
+    const long long t = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
+    const long long stride = (long long)gridDim.x * RED_THREADS;
+    const int r = (int)(t % nrhs);
+    const bool project = (!any || *any != 0) && (!colmask || colmask[r]);
+    if (hsmem)
+        for (int e = threadIdx.x; e < ni * nrhs; e += RED_THREADS) hs[e] = mk<T>((T)hsrc[e].x, (T)hsrc[e].y);
+    __syncthreads();
+    double nrm = 0.0;
+    for (long long e = t; e < n_el; e += stride) {
+        cplx<T> acc = w[e];
+        if (project) {
+            for (int i = 0; i < ni; ++i) {
+                cplx<T> h;
+                if (hsmem) h = hs[i * nrhs + r];
+                else h = mk<T>((T)hsrc[(long long)i * nrhs + r].x, (T)hsrc[(long long)i * nrhs + r].y);
+                const cplx<T> v = V[(long long)i * vstride + e];
+                acc.x -= h.x * v.x - h.y * v.y;
+                acc.y -= h.x * v.y + h.y * v.x;
+            }
+            w[e] = acc;
+        }
+        nrm += (double)acc.x * (double)acc.x + (double)acc.y * (double)acc.y;
+    }
+    sn[threadIdx.x] = nrm;
+    __syncthreads();
+    if (threadIdx.x < min(nrhs, RED_THREADS)) {
+        double sum = 0.0;
+        for (int u = threadIdx.x; u < RED_THREADS; u += nrhs) sum += sn[u];
+        const int rr = (int)(((long long)blockIdx.x * RED_THREADS + threadIdx.x) % nrhs);
+        npart[(long long)blockIdx.x * nrhs + rr] = sum;
+    }
+}
+
+// Re-orthogonalisation test per column: a second projection when ||w'|| < ||w|| / sqrt(2).
+__global__ void reorth_flags(const double* __restrict__ before, const double* __restrict__ after, int* __restrict__ flag,
+                             int* __restrict__ any, int nrhs) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int a = 0;
+    for (int r = 0; r < nrhs; ++r) {
+        const int f = after[r] < 0.70710678118654752 * before[r];
+        flag[r] = f;
+        a |= f;
+    }
+    *any = a;
 }
 
 // partial[blk][r] = sum |v[e]|^2 over this block's elements
@@ -340,7 +423,9 @@ struct Krylov final : KrylovEngine {
     c128 *part = nullptr, *hpass = nullptr;
     double *cs = nullptr, *dpart = nullptr, *beta = nullptr, *inv = nullptr, *hn = nullptr;
     RhsState* Sd = nullptr;
-    int *running = nullptr, *mask = nullptr;
+    int *running = nullptr, *mask = nullptr, *rflag = nullptr, *rany = nullptr;
+    double *nb = nullptr, *na = nullptr;
+    int hsmem_cap = 0;
     std::vector<RhsState> hs;
     std::vector<double> trel;
 
@@ -403,6 +488,11 @@ struct Krylov final : KrylovEngine {
         HELM_TRY(alloc((void**)&Sd, S * sizeof(RhsState), "column state"));
         HELM_TRY(alloc((void**)&running, 2 * sizeof(int), "running flag"));
         HELM_TRY(alloc((void**)&mask, S * sizeof(int), "column mask"));
+        HELM_TRY(alloc((void**)&rflag, S * sizeof(int), "re-orthogonalisation flags"));
+        HELM_TRY(alloc((void**)&rany, sizeof(int), "re-orthogonalisation any"));
+        HELM_TRY(alloc((void**)&nb, S * sizeof(double), "norms before projection"));
+        HELM_TRY(alloc((void**)&na, S * sizeof(double), "norms after projection"));
+        hsmem_cap = 40 * 1024 / (int)sizeof(cplx<T>);   // coefficient entries kept in shared memory (<= 40 KB)
         hs.assign(S, RhsState{0.0, 0, 0, 0, 1, 0.0, 0.0, 0});
         trel.assign(S, 0.0);
         HELM_CUDA(ctx, cudaMemcpyAsync(Sd, hs.data(), S * sizeof(RhsState), cudaMemcpyHostToDevice, st));
@@ -421,12 +511,25 @@ struct Krylov final : KrylovEngine {
         ctx->launches += 2;
     }
 
-    void dots_into(const cplx<T>* Vb, const cplx<T>* vec, int ni, c128* dst, int ldh_i, int ldh_r, int col,
-                   int accumulate) {
+    // partials of V^H w (and, with npart, of |w|^2) into `part`; skipped on the device when *any == 0
+    void dots_pass(const cplx<T>* Vb, const cplx<T>* vec, int ni, double* npart, const int* anyp) {
         const int tk = prof_begin(ctx, "arnoldi");
-        dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, S, 0, ni, part, ldp);
-        prof_end(ctx, tk, (double)(ni + 1) * nel * sizeof(cplx<T>));
-        finish_dots<<<ni * S, 128, 0, st>>>(part, nblk, ldp, ni, S, dst, ldh_i, ldh_r, col, accumulate);
+        dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, S, 0, ni, part, ldp, npart, anyp);
+        prof_end(ctx, tk, (double)(ni + 1 + (npart ? 1 : 0)) * nel * sizeof(cplx<T>));
+        ctx->launches++;
+    }
+    void finish_into(int ni, c128* dst, int ldh_i, int ldh_r, int col, int accumulate, const int* cm, const int* anyp) {
+        finish_dots<<<ni * S, 128, 0, st>>>(part, nblk, ldp, ni, S, dst, ldh_i, ldh_r, col, accumulate, cm, anyp);
+        ctx->launches++;
+    }
+    // w -= V h (masked), |w|^2 partials into dpart, then the norms into out
+    void update_pass(int ni, const int* cm, const int* anyp, double* out) {
+        const int hs = ni * S <= hsmem_cap ? 1 : 0;
+        const size_t smem = hs ? (size_t)ni * S * sizeof(cplx<T>) : 0;
+        const int tk = prof_begin(ctx, "arnoldi");
+        update_norm_kernel<T><<<nblk, RED_THREADS, smem, st>>>(V, nel, w, nel, S, ni, hpass, cm, anyp, dpart, hs);
+        prof_end(ctx, tk, (double)(ni + 2) * nel * sizeof(cplx<T>));
+        finish_norm2<<<S, 128, 0, st>>>(dpart, nblk, S, out);
         ctx->launches += 2;
     }
 
@@ -478,24 +581,20 @@ struct Krylov final : KrylovEngine {
             cplx<T>* zj = flex ? Zb + (long long)j * nel : u;
             HELM_TRY(oras_apply_wp(o, wp, vj, zj, S));
             HELM_TRY(launch_stencil(o->g, wp, zj, w, S, st));
-            // CGS2 for column j of H: H[r][i][j]
-            dots_into(V, w, j + 1, hpass, S, 1, 0, 0);
-            {
-                const int tk = prof_begin(ctx, "arnoldi");
-                update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, S, j + 1, hpass);
-                prof_end(ctx, tk, (double)(j + 3) * nel * sizeof(cplx<T>));
-            }
-            finish_dots<<<(j + 1) * S, 128, 0, st>>>(part, nblk, ldp, j + 1, S, H, m, (m + 1) * m, j, 0);
-            ctx->launches += 2;
-            dots_into(V, w, j + 1, hpass, S, 1, 0, 0);
-            {
-                const int tk = prof_begin(ctx, "arnoldi");
-                update_kernel<T><<<eg, 256, 0, st>>>(V, nel, w, nel, S, j + 1, hpass);
-                prof_end(ctx, tk, (double)(j + 3) * nel * sizeof(cplx<T>));
-            }
-            finish_dots<<<(j + 1) * S, 128, 0, st>>>(part, nblk, ldp, j + 1, S, H, m, (m + 1) * m, j, 1);
-            ctx->launches += 2;
-            norms(w, hn);
+            // Classical Gram-Schmidt for column j of H (H[r][i][j]) with a second projection for the
+            // columns whose norm dropped below 1/sqrt(2) of its value (selective re-orthogonalisation)
+            dots_pass(V, w, j + 1, dpart, nullptr);
+            finish_into(j + 1, hpass, S, 1, 0, 0, nullptr, nullptr);
+            finish_into(j + 1, H, m, (m + 1) * m, j, 0, nullptr, nullptr);
+            finish_norm2<<<S, 128, 0, st>>>(dpart, nblk, S, nb);
+            ctx->launches++;
+            update_pass(j + 1, nullptr, nullptr, na);
+            reorth_flags<<<1, 32, 0, st>>>(nb, na, rflag, rany, S);
+            ctx->launches++;
+            dots_pass(V, w, j + 1, nullptr, rany);
+            finish_into(j + 1, hpass, S, 1, 0, 0, nullptr, rany);
+            finish_into(j + 1, H, m, (m + 1) * m, j, 1, rflag, rany);
+            update_pass(j + 1, rflag, rany, hn);
             cudaMemsetAsync(running, 0, sizeof(int), st);
             {
                 const int tk = prof_begin(ctx, "krylov_misc");

@@ -772,3 +772,10 @@ size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int
     }
     return bytes + bytes / 16;
 }
+
+extern "C" helm_status oras_estimate_bytes_c(const helm_grid_desc* g, const helm_oras_desc* d, int nrhs, size_t* bytes) {
+    if (!g || !d || !bytes || nrhs < 0 || g->nx < 2 || g->ny < 2 || g->nz < 2 || d->px < 1 || d->py < 1 || d->pz < 1)
+        return HELM_EINVAL;
+    *bytes = oras_estimate_bytes(*g, *d, nrhs);
+    return HELM_OK;
+}

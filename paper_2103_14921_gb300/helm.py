@@ -97,6 +97,7 @@ def lib():
         "oras_box_info": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
         "oras_plane_inverse": (st, [vp, i32, i32, vp]),
         "oras_setup_seconds": (C.c_double, [vp]),
+        "oras_estimate_bytes_c": (st, [C.POINTER(GridDesc), C.POINTER(OrasDesc), i32, C.POINTER(C.c_size_t)]),
         "gmres_solve": (st, [vp, vp, vp, i32, C.POINTER(GmresDesc), C.POINTER(RhsStats)]),
         "helm_serve_start": (st, [vp, i32]),
         "helm_submit": (st, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
@@ -119,6 +120,15 @@ def fit_weights(G_min=4.0, G_max=30.0):
     if st:
         raise HelmError(st, "helm_fit_weights")
     return tuple(out)
+
+
+def estimate_bytes(grid_desc, oras_desc, nrhs):
+    """Library estimate of the device bytes of an ORAS handle plus apply scratch (host computation)."""
+    out = C.c_size_t()
+    st = lib().oras_estimate_bytes_c(C.byref(grid_desc), C.byref(oras_desc), nrhs, C.byref(out))
+    if st:
+        raise HelmError(st, "oras_estimate_bytes_c")
+    return out.value
 
 
 def _ptr(t):
