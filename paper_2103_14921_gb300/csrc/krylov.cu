@@ -40,38 +40,25 @@ inline int red_blocks(helm_ctx ctx, long long elems, int nrhs) {
 
 template <typename T> __device__ __forceinline__ c128 widen(cplx<T> a) { return mk<double>((double)a.x, (double)a.y); }
 
-// partial[blk][i][r] = sum over this block's elements of conj(V_i[e]) w[e], i in [i0, i0+ni)
-// With a block of 256 consecutive thread ids every r = e % nrhs appears; each thread keeps one r.
-// Products are formed in the basis precision and summed in groups of up to 8 elements before they
-// are added to the FP64 accumulators.
+// partial[blk][i][r] = sum over this block's elements of conj(V_i[e]) w[e], i in [i0, i0+ni),
+// and with npart also |w|^2.  Runs on the reduction grid (grid stride a multiple of nrhs, so each
+// thread keeps one column).  Two elements per loop trip and IC basis vectors per pass keep 2 * (IC+1)
+// independent loads in flight; products in the basis precision are summed in groups of up to 8
+// before they are added to FP64 accumulators; one block-wide reduction per pass.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
-                                                           const cplx<T>* __restrict__ w, long long n_el, int nrhs,
-                                                           int i0, int ni, c128* __restrict__ partial, int ldp,
-                                                           double* __restrict__ npart, const int* __restrict__ any) {
-    __shared__ c128 s[RED_THREADS];
+__global__ void __launch_bounds__(RED_THREADS, 2) dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
+                                                              const cplx<T>* __restrict__ w, long long n_el, int nrhs,
+                                                              int i0, int ni, c128* __restrict__ partial, int ldp,
+                                                              double* __restrict__ npart,
+                                                              const int* __restrict__ any) {
+    __shared__ c128 s[IC][RED_THREADS];
+    __shared__ double sn[RED_THREADS];
     if (any && *any == 0) return;
     const long long t = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
     const long long stride = (long long)gridDim.x * RED_THREADS;
-    if (npart) {
-        // |w|^2 per column (the norm before the projection, for the re-orthogonalisation test)
-        double nrm = 0.0;
-        for (long long e = t; e < n_el; e += stride) {
-            const c128 a = widen(w[e]);
-            nrm += a.x * a.x + a.y * a.y;
-        }
-        __shared__ double sn[RED_THREADS];
-        sn[threadIdx.x] = nrm;
-        __syncthreads();
-        if (threadIdx.x < min(nrhs, RED_THREADS)) {
-            double sum = 0.0;
-            for (int u = threadIdx.x; u < RED_THREADS; u += nrhs) sum += sn[u];
-            const int r = (int)(((long long)blockIdx.x * RED_THREADS + threadIdx.x) % nrhs);
-            npart[(long long)blockIdx.x * nrhs + r] = sum;
-        }
-        __syncthreads();
-    }
     for (int ib = 0; ib < ni; ib += IC) {
+        const int nq = min(IC, ni - ib);
+        const bool with_norm = npart && ib == 0;
         c128 acc[IC];
         cplx<T> part[IC];
 #pragma unroll
@@ -79,34 +66,70 @@ __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const cplx<T>* __rest
             acc[q] = mk<double>(0, 0);
             part[q] = mk<T>(0, 0);
         }
+        double nrm = 0.0;
+        T pn = (T)0;
         int cnt = 0;
-        for (long long e = t; e < n_el; e += stride) {
-            const cplx<T> wv = w[e];
+        const cplx<T>* Vb = V + (long long)(i0 + ib) * vstride;
+        long long e = t;
+        for (; e + stride < n_el; e += 2 * stride) {
+            const cplx<T> w0 = w[e], w1 = w[e + stride];
+            cplx<T> a[IC], b[IC];
 #pragma unroll
-            for (int q = 0; q < IC; ++q)
-                if (ib + q < ni) cmac_conj(part[q], V[(long long)(i0 + ib + q) * vstride + e], wv);
-            if (++cnt == 8) {
+            for (int q = 0; q < IC; ++q) {
+                if (q < nq) {
+                    a[q] = Vb[(long long)q * vstride + e];
+                    b[q] = Vb[(long long)q * vstride + e + stride];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < IC; ++q) {
+                if (q < nq) {
+                    cmac_conj(part[q], a[q], w0);
+                    cmac_conj(part[q], b[q], w1);
+                }
+            }
+            if (with_norm) pn += w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y;
+            if ((cnt += 2) >= 8) {
 #pragma unroll
                 for (int q = 0; q < IC; ++q) {
                     acc[q] = acc[q] + widen(part[q]);
                     part[q] = mk<T>(0, 0);
                 }
+                nrm += (double)pn;
+                pn = (T)0;
                 cnt = 0;
             }
         }
+        if (e < n_el) {
+            const cplx<T> w0 = w[e];
 #pragma unroll
-        for (int q = 0; q < IC; ++q) acc[q] = acc[q] + widen(part[q]);
-        for (int q = 0; q < IC && ib + q < ni; ++q) {
-            s[threadIdx.x] = acc[q];
-            __syncthreads();
-            if (threadIdx.x < min(nrhs, RED_THREADS)) {
-                c128 sum = mk<double>(0, 0);
-                for (int u = threadIdx.x; u < RED_THREADS; u += nrhs) sum = sum + s[u];
-                const int r = (int)(((long long)blockIdx.x * RED_THREADS + threadIdx.x) % nrhs);
-                partial[((long long)blockIdx.x * ldp + (i0 + ib + q)) * nrhs + r] = sum;
-            }
-            __syncthreads();
+            for (int q = 0; q < IC; ++q)
+                if (q < nq) cmac_conj(part[q], Vb[(long long)q * vstride + e], w0);
+            if (with_norm) pn += w0.x * w0.x + w0.y * w0.y;
         }
+#pragma unroll
+        for (int q = 0; q < IC; ++q) {
+            acc[q] = acc[q] + widen(part[q]);
+            s[q][threadIdx.x] = acc[q];
+        }
+        nrm += (double)pn;
+        if (with_norm) sn[threadIdx.x] = nrm;
+        __syncthreads();
+        const int nr = min(nrhs, RED_THREADS);
+        for (int o = threadIdx.x; o < nq * nr; o += RED_THREADS) {
+            const int q = o / nr, u0 = o % nr;
+            c128 sum = mk<double>(0, 0);
+            for (int u = u0; u < RED_THREADS; u += nrhs) sum = sum + s[q][u];
+            const int r = (int)(((long long)blockIdx.x * RED_THREADS + u0) % nrhs);
+            partial[((long long)blockIdx.x * ldp + (i0 + ib + q)) * nrhs + r] = sum;
+        }
+        if (with_norm && threadIdx.x < nr) {
+            double sum = 0.0;
+            for (int u = threadIdx.x; u < RED_THREADS; u += nrhs) sum += sn[u];
+            const int r = (int)(((long long)blockIdx.x * RED_THREADS + threadIdx.x) % nrhs);
+            npart[(long long)blockIdx.x * nrhs + r] = sum;
+        }
+        __syncthreads();
     }
 }
 
@@ -185,13 +208,22 @@ __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(const cplx<T>*
     for (long long e = t; e < n_el; e += stride) {
         cplx<T> acc = w[e];
         if (project) {
-            for (int i = 0; i < ni; ++i) {
-                cplx<T> h;
-                if (hsmem) h = hs[i * nrhs + r];
-                else h = mk<T>((T)hsrc[(long long)i * nrhs + r].x, (T)hsrc[(long long)i * nrhs + r].y);
-                const cplx<T> v = V[(long long)i * vstride + e];
-                acc.x -= h.x * v.x - h.y * v.y;
-                acc.y -= h.x * v.y + h.y * v.x;
+            // batches of 8 independent basis loads, then the 8 multiply-subtracts
+            for (int i0 = 0; i0 < ni; i0 += 8) {
+                cplx<T> v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (i0 + q < ni) v[q] = V[(long long)(i0 + q) * vstride + e];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (i0 + q < ni) {
+                        cplx<T> h;
+                        if (hsmem) h = hs[(i0 + q) * nrhs + r];
+                        else h = mk<T>((T)hsrc[(long long)(i0 + q) * nrhs + r].x, (T)hsrc[(long long)(i0 + q) * nrhs + r].y);
+                        acc.x -= h.x * v[q].x - h.y * v[q].y;
+                        acc.y -= h.x * v[q].y + h.y * v[q].x;
+                    }
+                }
             }
             w[e] = acc;
         }
