@@ -478,7 +478,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the bf16-factor variant measurement")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate, requests/s")
-    ap.add_argument("--ref-iters", type=float, default=20.0,
+    ap.add_argument("--ref-iters", type=float, default=32.0,
                     help="iterations per RHS used to scale the oracle's per-iteration time (reference arm)")
     args = ap.parse_args()
     W = WORKLOADS[args.workload]

@@ -152,6 +152,7 @@ struct helm_oras_s {
     int cap_wp = -1;
     size_t scratch_bytes = 0;
     void* tcb = nullptr;        // tensor-core sweep operand B^T, [nbox][tc_npad][2 ld] fp32
+    void* lb = nullptr;         // restricted right-hand sides of the tensor-core sweeps (same layout as loc)
     int tc_npad = 0;
     int* dev_err = nullptr;     // device error code of bounded waits (0 = none)
 };
@@ -198,7 +199,8 @@ helm_status planeset_to_bf16(helm_ctx ctx, PlaneSet& P);
 helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st);
 // tensor-core sweeps (sweep_tc.cu), complex64 local vectors, padded factor layout
 int tc_npad(int nrhs);
-helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, void* loc, void* bt, int npad, int nrhs,
+// lb: the restricted right-hand sides b (read by the forward sweep); loc receives y, then x.
+helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb, void* loc, void* bt, int npad, int nrhs,
                               cudaStream_t st, int* err);
 // Device bytes an ORAS handle with this description will hold (factors, local operators,
 // coarse level) plus its apply scratch for nrhs columns; an estimate for admission control.

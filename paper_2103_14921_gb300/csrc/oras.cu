@@ -417,7 +417,9 @@ static void free_scratch(helm_oras o) {
     dev_free(ctx, o->qf, (size_t)o->g->n * R * we);
     dev_free(ctx, o->tf, (size_t)o->g->n * R * we);
     dev_free(ctx, o->tcb, (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * tc_elem(o));
+    if (o->fine.padded) dev_free(ctx, o->lb, (size_t)o->fine.nloc * R * fe);
     o->tcb = nullptr;
+    o->lb = nullptr;
     o->tc_npad = 0;
     o->loc = o->rbuf = o->qf = o->tf = nullptr;
     o->cvec = o->crbuf = nullptr;
@@ -441,6 +443,7 @@ static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
         const size_t bytes = (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * tc_elem(o);
         HELM_TRY(dev_alloc(ctx, &o->tcb, bytes, "tensor-core sweep operand"));
         HELM_CUDA(ctx, cudaMemsetAsync(o->tcb, 0, bytes, ctx->stream));
+        HELM_TRY(dev_alloc(ctx, &o->lb, (size_t)o->fine.nloc * R * fe, "restricted right-hand sides"));
     }
     if (o->nc) {
         HELM_TRY(dev_alloc(ctx, (void**)&o->cvec, (size_t)o->nc * R * sizeof(c128), "coarse vector"));
@@ -499,12 +502,14 @@ helm_status apply_t(helm_oras o, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
     for (auto& b : o->fine.hbox) mx = std::max(mx, (long long)b.m * b.dims[2] * nrhs);
     const double lb = (double)o->fine.nloc * nrhs * (sizeof(cplx<TV>) + sizeof(cplx<TL>));
     int tr = prof_begin(ctx, "oras_transfer");
-    restrict_boxes<TV, TL><<<dim3(grid_for(mx, 256, 4096), o->fine.nbox), 256, 0, st>>>(o->fine.dbox, src,
-                                                                                         (cplx<TL>*)o->loc, nx, ny, nrhs);
+    // the tensor-core sweeps keep b apart (o->lb): their forward step overwrites loc while others read b
+    cplx<TL>* rdst = (cplx<TL>*)(o->fine.padded ? o->lb : o->loc);
+    restrict_boxes<TV, TL><<<dim3(grid_for(mx, 256, 4096), o->fine.nbox), 256, 0, st>>>(o->fine.dbox, src, rdst, nx,
+                                                                                         ny, nrhs);
     prof_end(ctx, tr, lb);
     ctx->launches++;
     if (o->fine.padded)
-        HELM_TRY(planeset_solve_tc(ctx, o->fine, o->loc, o->tcb, o->tc_npad, nrhs, st, o->dev_err));
+        HELM_TRY(planeset_solve_tc(ctx, o->fine, o->lb, o->loc, o->tcb, o->tc_npad, nrhs, st, o->dev_err));
     else
         HELM_TRY(planeset_solve(ctx, o->fine, o->loc, o->rbuf, nrhs, st));
     tr = prof_begin(ctx, "oras_transfer");
@@ -679,7 +684,8 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     const size_t s_vec = o->nc ? align256((size_t)o->g->n * R * sizeof(c128)) : 0;
     const int npad = o->fine.padded ? tc_npad(nrhs) : 0;
     const size_t s_tcb = o->fine.padded ? align256((size_t)o->fine.nbox * npad * 2 * o->fine.ld * tc_elem(o)) : 0;
-    const size_t need = s_loc + s_rb + s_cv + s_crb + 2 * s_vec + s_tcb;
+    const size_t s_lb = o->fine.padded ? s_loc : 0;
+    const size_t need = s_loc + s_rb + s_cv + s_crb + 2 * s_vec + s_tcb + s_lb;
     if (need > HELM_NOALLOC_SCRATCH_BYTES)
         return set_error(ctx, HELM_EINVAL,
                          "oras_apply_noalloc: needs %zu bytes of scratch for this problem and nrhs = %d, more than "
@@ -694,7 +700,7 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     }
     unsigned char* base = (unsigned char*)g_noalloc_ptr[ctx->device];
     // point the handle's working vectors into the static array for this call only
-    void *s_loc_p = o->loc, *s_rbuf_p = o->rbuf, *s_qf_p = o->qf, *s_tf_p = o->tf, *s_tcb_p = o->tcb;
+    void *s_loc_p = o->loc, *s_rbuf_p = o->rbuf, *s_qf_p = o->qf, *s_tf_p = o->tf, *s_tcb_p = o->tcb, *s_lb_p = o->lb;
     const int s_npad = o->tc_npad;
     if (o->fine.padded) {
         // the tensor-core operand's padding must read as zero
@@ -702,6 +708,7 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
         HELM_CUDA(ctx, cudaMemsetAsync(t, 0, s_tcb, ctx->stream));
         o->tcb = t;
         o->tc_npad = npad;
+        o->lb = t + s_tcb;
     }
     c128 *s_cvec_p = o->cvec, *s_crbuf_p = o->crbuf;
     const bool prof_on = ctx->prof.on;
@@ -720,6 +727,7 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     o->qf = s_qf_p;
     o->tf = s_tf_p;
     o->tcb = s_tcb_p;
+    o->lb = s_lb_p;
     o->tc_npad = s_npad;
     o->cvec = s_cvec_p;
     o->crbuf = s_crbuf_p;
@@ -757,7 +765,7 @@ size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int
     const size_t N = (size_t)g.nx * g.ny * g.nz;
     const size_t R = (size_t)std::max(1, nrhs);
     bytes += nloc * R * fe + std::max<size_t>(boxes.size(), 9) * m_max * R * fe;   // apply scratch
-    if (padded) bytes += boxes.size() * (size_t)tc_npad(nrhs) * 2 * ld * sizeof(float);
+    if (padded) bytes += boxes.size() * (size_t)tc_npad(nrhs) * 2 * ld * sizeof(float) + nloc * R * fe;
     if (d.coarse_ratio > 0) {
         size_t nc = 1, cm = 1;
         for (int a = 0; a < 3; ++a) {

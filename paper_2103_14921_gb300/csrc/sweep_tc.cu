@@ -51,8 +51,8 @@ constexpr int PREP_TP = 32;
 
 template <typename E>
 __global__ void __launch_bounds__(256) tc_prep(const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
-                                               const c64* __restrict__ loc, E* __restrict__ bt, int ld2, int npad,
-                                               int nrhs, int s, int fwd) {
+                                               const c64* __restrict__ lb, const c64* __restrict__ loc,
+                                               E* __restrict__ bt, int ld2, int npad, int nrhs, int s, int fwd) {
     __shared__ c64 tile[128 * (PREP_TP + 1)];
     const BoxInfo B = boxes[blockIdx.y];
     const int m = B.m, bz = B.dims[2], bx = B.dims[0], by = B.dims[1];
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) tc_prep(const BoxInfo* __restrict__ boxes
             const int pl = e / nrhs, r = e % nrhs, p = p0 + pl;
             c64 acc = mk<float>(0, 0);
             if (p < m) {
-                if (fwd) acc = loc[(plane + p) * nrhs + r];
+                if (fwd) acc = lb[(plane + p) * nrhs + r];
                 if (!(fwd && k == 0)) {
                     const int px = p % bx, py = p / bx;
                     const c64* cp = coef + (plane + p) * 27 + off;
@@ -268,7 +268,8 @@ bool encode_3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t 
 }
 
 template <typename E, int NPAD>
-helm_status run_tc(helm_ctx ctx, const PlaneSet& P, c64* loc, E* bt, int nrhs, cudaStream_t st, int* err) {
+helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* bt, int nrhs, cudaStream_t st,
+                   int* err) {
     using Cfg = TcCfg<E, NPAD>;
     constexpr bool BF = sizeof(E) == 2;
     CUtensorMap mapA, mapB;
@@ -303,7 +304,7 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, c64* loc, E* bt, int nrhs, c
         for (int s = fwd ? 0 : 1; s < P.bz_max; ++s) {
             bytes(s, fwd, gb, pb);
             int t = prof_begin(ctx, "sweep_prep");
-            tc_prep<E><<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
+            tc_prep<E><<<pgrid, 256, 0, st>>>(P.dbox, coef, lb, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
             prof_end(ctx, t, pb);
             t = prof_begin(ctx, "sweep_gemm_tc");
             tc_sweep_gemm<E, NPAD><<<ggrid, 128, Cfg::SMEM, st>>>(mapA, mapB, P.dbox, loc, nrhs, s, fwd, err);
@@ -325,24 +326,25 @@ int tc_npad(int nrhs) {
     return 256;
 }
 
-helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, void* loc, void* bt, int npad, int nrhs,
-                              cudaStream_t st, int* err) {
+helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb_, void* loc, void* bt, int npad,
+                              int nrhs, cudaStream_t st, int* err) {
+    const c64* lb = (const c64*)lb_;
     if (nrhs > 128 || tc_npad(nrhs) > npad) return set_error(ctx, HELM_EINVAL, "tensor-core sweep: too many rhs");
     if (P.prec == HELM_PREC_BF16) {
         typedef __nv_bfloat16 B;
         switch (npad) {
-            case 16: return run_tc<B, 16>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
-            case 32: return run_tc<B, 32>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
-            case 64: return run_tc<B, 64>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
-            case 128: return run_tc<B, 128>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
-            default: return run_tc<B, 256>(ctx, P, (c64*)loc, (B*)bt, nrhs, st, err);
+            case 16: return run_tc<B, 16>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
+            case 32: return run_tc<B, 32>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
+            case 64: return run_tc<B, 64>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
+            case 128: return run_tc<B, 128>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
+            default: return run_tc<B, 256>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
         }
     }
     switch (npad) {
-        case 16: return run_tc<float, 16>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 32: return run_tc<float, 32>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 64: return run_tc<float, 64>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 128: return run_tc<float, 128>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
-        default: return run_tc<float, 256>(ctx, P, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 16: return run_tc<float, 16>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 32: return run_tc<float, 32>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 64: return run_tc<float, 64>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
+        case 128: return run_tc<float, 128>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
+        default: return run_tc<float, 256>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
     }
 }
