@@ -105,6 +105,12 @@ helm_status helm_profile_enable(helm_ctx ctx, int on);
 helm_status helm_profile_select(helm_ctx ctx, const char* families);
 helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launches, double* ms, double* bytes);
 
+/* Tuning knobs (read by the autotuner).  HELM_TUNE_TC_STAGES: pipeline depth of the
+ * tensor-core plane sweep, 2..5 (0 = automatic: 5 for up to 32 right-hand sides, fewer for
+ * more).  Returns HELM_EINVAL for an unknown key or value out of range. */
+#define HELM_TUNE_TC_STAGES 1
+helm_status helm_set_tuning(helm_ctx ctx, int key, int value);
+
 /* ------------------------------------------------------------ grid / model */
 
 typedef struct {

@@ -87,6 +87,17 @@ extern "C" const char* helm_last_error(helm_ctx ctx) {
 }
 
 extern "C" size_t helm_bytes_in_use(helm_ctx ctx) { return ctx ? ctx->in_use : 0; }
+
+extern "C" helm_status helm_set_tuning(helm_ctx ctx, int key, int value) {
+    if (!ctx) return HELM_EINVAL;
+    if (key == HELM_TUNE_TC_STAGES) {
+        if (value != 0 && (value < 2 || value > 5))
+            return set_error(ctx, HELM_EINVAL, "helm_set_tuning: tensor-core stages must be 0 or 2..5");
+        ctx->tc_stages = value;
+        return HELM_OK;
+    }
+    return set_error(ctx, HELM_EINVAL, "helm_set_tuning: unknown key %d", key);
+}
 extern "C" uint64_t helm_launch_count(helm_ctx ctx) { return ctx ? ctx->launches : 0; }
 
 // ------------------------------------------------------------------ setup kernels

@@ -69,6 +69,7 @@ struct helm_ctx_s {
     bool destroy_pending = false;
     Profiler prof;
     Server* server = nullptr;
+    int tc_stages = 0;         // tuning: pipeline stages of the tensor-core sweep (0 = automatic)
 };
 
 // Bracket one launch of an instrumented family with events on the context's stream.

@@ -111,23 +111,89 @@ __global__ void __launch_bounds__(256) tc_prep(const BoxInfo* __restrict__ boxes
     }
 }
 
-template <typename E, int NPAD>
+// Variant without the shared-memory transpose: thread per (plane node, chunk of 4 right-hand sides),
+// the chunk index fastest, so the neighbour loads of a warp are contiguous 32-byte pieces; each
+// thread writes its 4 columns' (re, -im) and (im, re) pairs into rows 2r, 2r+1 of B^T.
+template <typename E>
+__global__ void __launch_bounds__(256) tc_prep4(const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
+                                                const c64* __restrict__ lb, const c64* __restrict__ loc,
+                                                E* __restrict__ bt, int ld2, int npad, int nrhs, int s, int fwd) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m, bz = B.dims[2], bx = B.dims[0], by = B.dims[1];
+    const int k = fwd ? s : bz - 1 - s;
+    if (k < 0 || k >= bz || (!fwd && k == bz - 1)) return;
+    const int nch = nrhs >> 2;
+    const long long plane = B.loc_off + (long long)k * m;
+    const long long nbr = fwd ? plane - m : plane + m;
+    const int off = fwd ? 0 : 18;
+    E* bb = bt + (size_t)blockIdx.y * npad * ld2;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * nch;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(e % nch), p = (int)(e / nch);
+        const int r0 = 4 * ch;
+        c64 acc[4];
+        if (fwd) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = lb[(plane + p) * nrhs + r0 + q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = mk<float>(0, 0);
+        }
+        if (!(fwd && k == 0)) {
+            const int px = p % bx, py = p / bx;
+            const c64* cp = coef + (plane + p) * 27 + off;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int qy = py + dy;
+                if (qy < 0 || qy >= by) continue;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int qx = px + dx;
+                    if (qx < 0 || qx >= bx) continue;
+                    const c64 c = cp[(dy + 1) * 3 + (dx + 1)];
+                    const c64* v = loc + (nbr + qy * bx + qx) * nrhs + r0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const c64 vq = v[q];
+                        if (fwd) {
+                            acc[q].x -= c.x * vq.x - c.y * vq.y;
+                            acc[q].y -= c.x * vq.y + c.y * vq.x;
+                        } else {
+                            cmac(acc[q], c, vq);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            E* re_row = bb + (size_t)(2 * (r0 + q)) * ld2 + 2 * p;
+            E* im_row = re_row + ld2;
+            re_row[0] = Elem<E>::from(acc[q].x);
+            re_row[1] = Elem<E>::from(-acc[q].y);
+            im_row[0] = Elem<E>::from(acc[q].y);
+            im_row[1] = Elem<E>::from(acc[q].x);
+        }
+    }
+}
+
+template <typename E, int NPAD, int NST>
 struct TcCfg {
     static constexpr int BK = Elem<E>::BK;
     static constexpr int A_BYTES = TC_BM * 128;
     static constexpr int B_BYTES = NPAD * 128;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = NPAD >= 256 ? 3 : (NPAD >= 128 ? 4 : 5);
+    static constexpr int STAGES = NST;
     static constexpr uint32_t TCOLS = NPAD <= 32 ? 32 : (NPAD <= 64 ? 64 : (NPAD <= 128 ? 128 : 256));
     static constexpr int SMEM = STAGES * STAGE + (2 * STAGES + 1) * 8 + 16 + 1024;
 };
 
-template <typename E, int NPAD>
+template <typename E, int NPAD, int NST>
 __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ CUtensorMap mapA,
                                                         const __grid_constant__ CUtensorMap mapB,
                                                         const BoxInfo* __restrict__ boxes, c64* __restrict__ loc,
                                                         int nrhs, int s, int fwd, int* __restrict__ err) {
-    using Cfg = TcCfg<E, NPAD>;
+    using Cfg = TcCfg<E, NPAD, NST>;
     constexpr int TC_STAGES = Cfg::STAGES;
     constexpr int TC_BK = Cfg::BK;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -267,10 +333,10 @@ bool encode_3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t 
     return r == CUDA_SUCCESS;
 }
 
-template <typename E, int NPAD>
+template <typename E, int NPAD, int NST>
 helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* bt, int nrhs, cudaStream_t st,
                    int* err) {
-    using Cfg = TcCfg<E, NPAD>;
+    using Cfg = TcCfg<E, NPAD, NST>;
     constexpr bool BF = sizeof(E) == 2;
     CUtensorMap mapA, mapB;
     const int ld = P.ld;
@@ -279,12 +345,13 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
         return set_error(ctx, HELM_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(tc_sweep_gemm<E, NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        cudaFuncSetAttribute(tc_sweep_gemm<E, NPAD, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         attr = true;
     }
     const int m = P.m_max;
     const dim3 ggrid((m + TC_BM - 1) / TC_BM, P.nbox);
     const dim3 pgrid((unsigned)((m + PREP_TP - 1) / PREP_TP), P.nbox);
+    const dim3 pgrid4((unsigned)std::max(1, (m * std::max(1, nrhs / 4) + 255) / 256), P.nbox);
     const c64* coef = (const c64*)P.coef;
     const double es = sizeof(c64);
     const double fs = 2.0 * sizeof(E);   // bytes of one stored complex factor entry
@@ -304,15 +371,41 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
         for (int s = fwd ? 0 : 1; s < P.bz_max; ++s) {
             bytes(s, fwd, gb, pb);
             int t = prof_begin(ctx, "sweep_prep");
-            tc_prep<E><<<pgrid, 256, 0, st>>>(P.dbox, coef, lb, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
+            if (nrhs % 4 == 0)
+                tc_prep4<E><<<pgrid4, 256, 0, st>>>(P.dbox, coef, lb, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
+            else
+                tc_prep<E><<<pgrid, 256, 0, st>>>(P.dbox, coef, lb, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
             prof_end(ctx, t, pb);
             t = prof_begin(ctx, "sweep_gemm_tc");
-            tc_sweep_gemm<E, NPAD><<<ggrid, 128, Cfg::SMEM, st>>>(mapA, mapB, P.dbox, loc, nrhs, s, fwd, err);
+            tc_sweep_gemm<E, NPAD, NST><<<ggrid, 128, Cfg::SMEM, st>>>(mapA, mapB, P.dbox, loc, nrhs, s, fwd, err);
             prof_end(ctx, t, gb);
             ctx->launches += 2;
         }
     }
     return cuda_check(ctx, cudaGetLastError(), "tensor-core plane sweeps");
+}
+
+template <typename E, int NPAD>
+helm_status dispatch_stages(helm_ctx ctx, const PlaneSet& P, const c64* lb, void* loc, void* bt, int ns, int nrhs,
+                            cudaStream_t st, int* err) {
+    switch (ns) {
+        case 2: return run_tc<E, NPAD, 2>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err);
+        case 3: return run_tc<E, NPAD, 3>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err);
+        case 4: return run_tc<E, NPAD, 4>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err);
+        default: return run_tc<E, NPAD, (NPAD >= 256 ? 4 : 5)>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err);
+    }
+}
+
+template <typename E>
+helm_status dispatch_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, void* loc, void* bt, int npad, int ns,
+                        int nrhs, cudaStream_t st, int* err) {
+    switch (npad) {
+        case 16: return dispatch_stages<E, 16>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
+        case 32: return dispatch_stages<E, 32>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
+        case 64: return dispatch_stages<E, 64>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
+        case 128: return dispatch_stages<E, 128>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
+        default: return dispatch_stages<E, 256>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
+    }
 }
 
 }  // namespace
@@ -330,21 +423,12 @@ helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb_, 
                               int nrhs, cudaStream_t st, int* err) {
     const c64* lb = (const c64*)lb_;
     if (nrhs > 128 || tc_npad(nrhs) > npad) return set_error(ctx, HELM_EINVAL, "tensor-core sweep: too many rhs");
-    if (P.prec == HELM_PREC_BF16) {
-        typedef __nv_bfloat16 B;
-        switch (npad) {
-            case 16: return run_tc<B, 16>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
-            case 32: return run_tc<B, 32>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
-            case 64: return run_tc<B, 64>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
-            case 128: return run_tc<B, 128>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
-            default: return run_tc<B, 256>(ctx, P, lb, (c64*)loc, (B*)bt, nrhs, st, err);
-        }
-    }
-    switch (npad) {
-        case 16: return run_tc<float, 16>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 32: return run_tc<float, 32>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 64: return run_tc<float, 64>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
-        case 128: return run_tc<float, 128>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
-        default: return run_tc<float, 256>(ctx, P, lb, (c64*)loc, (float*)bt, nrhs, st, err);
-    }
+    // pipeline depth: the context's tuning value, else 4 stages (3 for N = 256); measured at 112^3 x 16 RHS:
+    // 2/3/4/5 stages give 4.97/4.92/5.24/5.16 TB/s (TF32)
+    int ns = ctx->tc_stages;
+    if (ns < 2 || ns > 5) ns = npad >= 256 ? 3 : 4;
+    if (npad >= 256 && ns > 4) ns = 4;   // shared memory: 5 x 48 KB does not fit
+    if (P.prec == HELM_PREC_BF16) return dispatch_tc<__nv_bfloat16>(ctx, P, lb, loc, bt, npad, ns, nrhs, st, err);
+    return dispatch_tc<float>(ctx, P, lb, loc, bt, npad, ns, nrhs, st, err);
 }
+

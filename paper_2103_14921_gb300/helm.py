@@ -27,6 +27,7 @@ _atexit.register(_mark_finalizing)   # handles still alive at exit are left to p
 
 OK, EINVAL, ENOMEM, ENOTCONV, ESINGULAR, ENONFINITE, ETIMEOUT, EBUSY, ECUDA, ENOTFOUND = range(10)
 TOP_DIRICHLET, TOP_PML = 0, 1
+TUNE_TC_STAGES = 1
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_TF32X3, PREC_BF16 = 0, 1, 2, 3, 4
 PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3, "bf16": PREC_BF16}
 
@@ -83,6 +84,7 @@ def lib():
         "helm_bytes_in_use": (C.c_size_t, [vp]),
         "helm_launch_count": (C.c_uint64, [vp]),
         "helm_profile_enable": (st, [vp, i32]),
+        "helm_set_tuning": (st, [vp, i32, i32]),
         "helm_profile_select": (st, [vp, C.c_char_p]),
         "helm_profile_query": (st, [vp, C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
@@ -157,6 +159,10 @@ class Context:
     @property
     def launches(self):
         return lib().helm_launch_count(self._h)
+
+    def set_tuning(self, key, value):
+        """``helm_set_tuning`` (e.g. ``TUNE_TC_STAGES``)."""
+        self.check(lib().helm_set_tuning(self._h, key, value), "helm_set_tuning")
 
     def profile(self, on=True, only=None):
         """Enable (and clear) or disable per-kernel-family event timing; ``only`` = list of families."""
