@@ -27,8 +27,9 @@ Readings taken where the paper is silent:
   drops those neighbours instead (Dirichlet).
 * Coarse space: nodes at fine indices ``r J_a``, ``J_a = 0..ceil((n_a-1)/r)``,
   trilinear hats ``Z[i, J] = prod_a max(0, 1 - |i_a - r J_a| / r)``; ``E`` is
-  solved exactly (the paper's 10 inner GMRES iterations on the coarse level
-  are not reproduced).
+  solved exactly (``coarse_solve="exact"``), or as in the paper by 10 GMRES
+  iterations preconditioned by one-level ORAS on the coarse grid over the same
+  spatial partition (``coarse_solve="gmres"``, :class:`CoarseGMRES`).
 
 Local solves have two independent routes: ``scipy.sparse.linalg.splu`` (the
 paper's sparse direct solver) and the plane-by-plane block-tridiagonal LU
@@ -111,10 +112,18 @@ def local_operator(prob: Problem, box: Box, mode: str = "oras", coef=None) -> sp
     """``A_i``: the rows of A for the box nodes with absorbing (or Dirichlet) interface folding."""
     if coef is None:
         coef = neighbour_coefficients(prob)
+    rho = np.exp(1j * (prob.omega / np.asarray(prob.c, dtype=np.complex128)) * prob.h)
+    return fold_operator(coef, rho, box, mode)
+
+
+def fold_operator(coef, rho, box: Box, mode: str = "oras") -> sp.csr_matrix:
+    """Rows of a 27-point grid operator (coefficients ``coef[3, 3, 3, nz, ny, nx]``) for the box nodes,
+    a neighbour outside the box folded onto the clamped in-box node times ``rho`` of the row node per
+    crossed face (``mode="oras"``) or dropped (``mode="ras"``).  ``rho`` is ``[nz, ny, nx]``."""
     bx, by, bz = box.dims
     k, j, i = np.meshgrid(np.arange(bz), np.arange(by), np.arange(bx), indexing="ij")
     gi, gj, gk = i + box.lo[0], j + box.lo[1], k + box.lo[2]
-    rho = np.exp(1j * (prob.omega / np.asarray(prob.c, dtype=np.complex128)[gk, gj, gi]) * prob.h)
+    rho = np.asarray(rho)[gk, gj, gi]
     row = ((k * by + j) * bx + i)
     rows, cols, vals = [], [], []
     for dz in (-1, 0, 1):
@@ -204,6 +213,94 @@ def coarse_basis(dims, r) -> sp.csr_matrix:
     return sp.kron(Zz, sp.kron(Zy, Zx, format="csr"), format="csr")
 
 
+def stencil_coefficients_of(M: sp.spmatrix, dims) -> np.ndarray:
+    """The 27 diagonals of a grid operator with a 27-point pattern, as ``coef[3, 3, 3, nz, ny, nx]``
+    (``coef[dz+1, dy+1, dx+1, k, j, i] = M[(k, j, i), (k+dz, j+dy, i+dx)]``, zero past the grid)."""
+    nx, ny, nz = dims
+    M = M.tocsr()
+    coef = np.zeros((3, 3, 3, nz, ny, nx), dtype=np.complex128)
+    rows, cols = M.nonzero()
+    vals = np.asarray(M[rows, cols]).ravel()
+    ri, rj, rk = rows % nx, (rows // nx) % ny, rows // (nx * ny)
+    ci, cj, ck = cols % nx, (cols // nx) % ny, cols // (nx * ny)
+    dx, dy, dz = ci - ri, cj - rj, ck - rk
+    if np.any(np.abs(dx) > 1) or np.any(np.abs(dy) > 1) or np.any(np.abs(dz) > 1):
+        raise ValueError("operator couples nodes more than one step apart")
+    coef[dz + 1, dy + 1, dx + 1, rk, rj, ri] = vals
+    return coef
+
+
+def coarse_decompose(dims, parts, r, overlap):
+    """The fine partition carried to the coarse grid: coarse node ``J`` (at fine index ``r J``) belongs
+    to the part whose fine core holds ``r J`` (the last coarse node, which may lie past the fine grid,
+    to the last part); boxes grow by ``overlap`` coarse layers on interior sides."""
+    cd = coarse_dims(dims, r)
+    cuts = []
+    for a in range(3):
+        fine = [(t * dims[a]) // parts[a] for t in range(parts[a] + 1)]
+        c = [0] + [-(-fine[t] // r) for t in range(1, parts[a])] + [cd[a]]
+        if any(c[t + 1] <= c[t] for t in range(parts[a])):
+            raise ValueError("the coarse grid is too small for this partition")
+        cuts.append(c)
+    boxes = []
+    for tz in range(parts[2]):
+        for ty in range(parts[1]):
+            for tx in range(parts[0]):
+                t = (tx, ty, tz)
+                clo = tuple(cuts[a][t[a]] for a in range(3))
+                chi = tuple(cuts[a][t[a] + 1] for a in range(3))
+                lo = tuple(max(0, clo[a] - overlap) if clo[a] > 0 else 0 for a in range(3))
+                hi = tuple(min(cd[a], chi[a] + overlap) if chi[a] < cd[a] else cd[a] for a in range(3))
+                boxes.append(Box(clo, chi, lo, hi))
+    return boxes
+
+
+class CoarseGMRES:
+    """The inexact coarse solve of the paper's two-level method: ``iters`` right-preconditioned GMRES
+    iterations on ``E y = c`` (``x0 = 0``, no restart) with the one-level ORAS preconditioner of the
+    coarse grid over the same spatial partition, local problems solved exactly.
+
+    Readings: the coarse boxes are the fine partition carried to the coarse nodes
+    (:func:`coarse_decompose`) with ``overlap`` coarse layers; the absorbing fold uses
+    ``rho = exp(i k H)``, ``H = r h`` the coarse spacing, ``k`` at the coarse node's fine position
+    (clamped to the grid); the partition of unity is the Boolean owner one."""
+
+    def __init__(self, prob: Problem, E, parts, r, overlap=1, iters=10, mode="oras"):
+        self.E = E.tocsr()
+        self.iters = iters
+        dims = (prob.nx, prob.ny, prob.nz)
+        self.cdims = coarse_dims(dims, r)
+        self.boxes = coarse_decompose(dims, parts, r, overlap)
+        coef = stencil_coefficients_of(self.E, self.cdims)
+        cx, cy, cz = self.cdims
+        K, J, I = np.meshgrid(np.arange(cz), np.arange(cy), np.arange(cx), indexing="ij")
+        c = np.asarray(prob.c, dtype=np.complex128)
+        cf = c[np.minimum(r * K, prob.nz - 1), np.minimum(r * J, prob.ny - 1), np.minimum(r * I, prob.nx - 1)]
+        rho = np.exp(1j * (prob.omega / cf) * (r * prob.h))
+        self.idx, self.pu, self.lu = [], [], []
+        for box in self.boxes:
+            self.idx.append(box_global_indices(box, self.cdims))
+            self.pu.append(partition_of_unity(box))
+            self.lu.append(spla.splu(fold_operator(coef, rho, box, mode).tocsc()))
+
+    def apply_M(self, v):
+        """One-level ORAS on the coarse grid: ``sum_i R_i^T D_i E_i^{-1} R_i v``."""
+        out = np.zeros(v.shape, dtype=np.complex128)
+        for i in range(len(self.boxes)):
+            out[self.idx[i]] += self.pu[i] * self.lu[i].solve(np.ascontiguousarray(v[self.idx[i]]))
+        return out
+
+    def solve(self, c):
+        """The inner GMRES approximation of ``E^{-1} c`` (``c`` is ``[nc]`` or ``[nc, nrhs]``)."""
+        from .krylov import gmres
+        c = np.asarray(c, dtype=np.complex128)
+        if c.ndim == 2:
+            return np.stack([self.solve(c[:, q]) for q in range(c.shape[1])], axis=1)
+        y, _ = gmres(lambda v: self.E @ v, c, self.apply_M, tol=0.0, restart=self.iters, maxit=self.iters,
+                     flexible=False)
+        return y
+
+
 # ---------------------------------------------------------------------------
 # The preconditioner
 # ---------------------------------------------------------------------------
@@ -211,7 +308,8 @@ def coarse_basis(dims, r) -> sp.csr_matrix:
 class ORAS:
     """``M^{-1}`` of Eq. (2lvl) (or Eq. (oras) alone when ``coarse_ratio == 0``)."""
 
-    def __init__(self, prob: Problem, parts, overlap, coarse_ratio=0, mode="oras", local="splu"):
+    def __init__(self, prob: Problem, parts, overlap, coarse_ratio=0, mode="oras", local="splu",
+                 coarse_solve="exact", coarse_iters=10, coarse_overlap=1):
         self.prob = prob
         self.dims = (prob.nx, prob.ny, prob.nz)
         self.boxes = decompose(self.dims, parts, overlap)
@@ -236,7 +334,13 @@ class ORAS:
         if coarse_ratio:
             self.Z = coarse_basis(self.dims, coarse_ratio)
             self.E = (self.Z.T @ self.A @ self.Z).tocsc()
-            self.E_lu = spla.splu(self.E)
+            if coarse_solve == "exact":
+                self.E_lu = spla.splu(self.E)
+                self.coarse = None
+            elif coarse_solve == "gmres":
+                self.coarse = CoarseGMRES(prob, self.E, parts, coarse_ratio, coarse_overlap, coarse_iters, mode)
+            else:
+                raise ValueError(coarse_solve)
 
     def local_solve(self, i, r):
         if self.local == "splu":
@@ -254,8 +358,12 @@ class ORAS:
         return out
 
     def coarse_correction(self, v):
-        """``Q v = Z E^{-1} Z^T v``."""
-        return self.Z @ self.E_lu.solve(np.asarray(self.Z.T @ v))
+        """``Q v = Z E^{-1} Z^T v`` (the inner GMRES approximation of ``E^{-1}`` with ``coarse_solve="gmres"``,
+        which makes the preconditioner depend on ``v`` nonlinearly: the outer method must be FGMRES)."""
+        c = np.asarray(self.Z.T @ v)
+        if self.coarse is not None:
+            return self.Z @ self.coarse.solve(c)
+        return self.Z @ self.E_lu.solve(c)
 
     def apply(self, v):
         v = np.asarray(v, dtype=np.complex128)

@@ -180,3 +180,82 @@ def test_plane_local_route_equals_splu_route():
     a = ORAS(prob, (2, 2, 1), 2, coarse_ratio=4, local="splu").apply(v)
     b = ORAS(prob, (2, 2, 1), 2, coarse_ratio=4, local="planes").apply(v)
     assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a)
+
+
+# --- the paper's inexact coarse solve (10 inner GMRES iterations, one-level ORAS on the coarse grid) ---
+
+def test_stencil_diagonals_reassemble_the_operator():
+    """The 27 diagonals read off the assembled matrix equal the oracle's own coefficient array."""
+    from oracle.discretization import neighbour_coefficients
+    from oracle.schwarz import stencil_coefficients_of
+    prob = _prob(9, 8, 7, npml=2)
+    got = stencil_coefficients_of(assemble_A(prob), (9, 8, 7))
+    assert np.array_equal(got, neighbour_coefficients(prob))
+
+
+def test_coarse_partition_follows_the_fine_cuts_and_sums_to_identity():
+    from oracle.schwarz import coarse_decompose
+    dims, parts, r = (21, 18, 17), (3, 2, 2), 4
+    cd = coarse_dims(dims, r)
+    boxes = coarse_decompose(dims, parts, r, 1)
+    fine = decompose(dims, parts, 0)
+    n = int(np.prod(cd))
+    S = np.zeros((n, n))
+    for b, fb in zip(boxes, fine):
+        R = restriction(b, cd).toarray()
+        S += R.T @ (partition_of_unity(b)[:, None] * R)
+        # every core node's fine position r J (clamped) lies in the matching fine core
+        for a in range(3):
+            for J in range(b.core_lo[a], b.core_hi[a]):
+                assert fb.core_lo[a] <= min(r * J, dims[a] - 1) < fb.core_hi[a]
+    assert np.array_equal(S, np.eye(n))
+    with pytest.raises(ValueError):
+        coarse_decompose((9, 9, 9), (4, 1, 1), 4, 1)          # 3 coarse nodes cannot hold 4 parts
+
+
+def test_coarse_gmres_with_one_box_is_the_exact_coarse_solve():
+    """One coarse box: the coarse ORAS is E^{-1} itself, one GMRES step solves exactly."""
+    from oracle.schwarz import CoarseGMRES
+    prob = _prob(17, 15, 13, npml=3)
+    Z = coarse_basis((17, 15, 13), 4)
+    E = (Z.T @ assemble_A(prob) @ Z).tocsc()
+    cg = CoarseGMRES(prob, E, (1, 1, 1), 4, overlap=1, iters=10)
+    c = synth.random_complex((E.shape[0], 2), 16)
+    want = spla.spsolve(E, c)
+    assert np.linalg.norm(cg.solve(c) - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_coarse_gmres_finite_termination_and_monotone_residual():
+    """GMRES on n coarse unknowns is exact after n steps whatever the preconditioner; with fewer
+    steps the residual of E y = c decreases with the number of steps."""
+    from oracle.schwarz import CoarseGMRES
+    dims = (9, 9, 9)                                          # 3 x 3 x 3 coarse nodes
+    prob = _prob(*dims, npml=2)
+    Z = coarse_basis(dims, 4)
+    E = (Z.T @ assemble_A(prob) @ Z).tocsc()
+    c = synth.random_complex((E.shape[0],), 17)
+    exact = CoarseGMRES(prob, E, (2, 2, 1), 4, overlap=1, iters=E.shape[0]).solve(c)
+    want = spla.spsolve(E, c)
+    assert np.linalg.norm(exact - want) <= 1e-9 * np.linalg.norm(want)
+    dims = (29, 25, 21)
+    prob = _prob(*dims, npml=4, f=5.0)
+    Z = coarse_basis(dims, 4)
+    E = (Z.T @ assemble_A(prob) @ Z).tocsc()
+    c = synth.random_complex((E.shape[0],), 18)
+    res = [np.linalg.norm(c - E @ CoarseGMRES(prob, E, (2, 2, 2), 4, overlap=1, iters=k).solve(c))
+           for k in (1, 3, 10)]
+    assert res[0] < np.linalg.norm(c) and res[1] < res[0] and res[2] < res[1]
+
+
+def test_inexact_two_level_fgmres_reaches_direct_solution():
+    """The paper's two-level method (coarse E by 10 ORAS-preconditioned GMRES steps) inside FGMRES
+    converges to the direct solution; the inner iteration makes the preconditioner nonlinear, which
+    FGMRES tolerates."""
+    prob = _prob(20, 20, 20, npml=4, f=5.0)
+    A = assemble_A(prob)
+    b = synth.point_sources(20, 20, 20, 25.0, [(10, 10, 3)])[..., 0].ravel()
+    xs = direct_solve_planes(prob, b)
+    M = ORAS(prob, (2, 2, 2), 2, coarse_ratio=4, coarse_solve="gmres", coarse_iters=10)
+    x, info = gmres(lambda v: A @ v, b, M.apply, tol=1e-8, restart=30, flexible=True)
+    assert info["converged"]
+    assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
