@@ -44,6 +44,11 @@ WORKLOADS = {
     "lg64": dict(desc="linear-gradient 64^3, 5 Hz, 16 RHS, two-level ORAS 2x2x2 ov2 r4, FGMRES(30) tol 1e-6",
                  n=64, h=25.0, f=5.0, c0=1500.0, alpha=0.6, npml=8, parts=(2, 2, 2), overlap=2, coarse=4,
                  nrhs=16, src_k=3, seed=synth.workload_seed(2), restart=30, tol=1e-6),
+    # same plane sizes as lg112 (1024-node fine planes, 841-node coarse planes) on a 24-plane slab: a few GB
+    # of factors, the size ncu full-section captures of single kernels are taken on
+    "slab112": dict(desc="linear-gradient 112x112x24 slab, 5 Hz, 16 RHS, two-level ORAS 4x4x1 ov2 r4, FGMRES(30)",
+                    n=112, nz=24, h=25.0, f=5.0, c0=1500.0, alpha=0.6, npml=8, parts=(4, 4, 1), overlap=2, coarse=4,
+                    nrhs=16, src_k=3, seed=synth.workload_seed(2), restart=30, tol=1e-6),
     "lg48": dict(desc="linear-gradient 48^3, 3 Hz, 1 RHS, one-level ORAS 2x2x2 ov2, GMRES(30) tol 1e-6",
                  n=48, h=25.0, f=3.0, c0=1500.0, alpha=0.6, npml=8, parts=(2, 2, 2), overlap=2, coarse=0,
                  nrhs=1, src_k=None, seed=synth.workload_seed(1), restart=30, tol=1e-6),
@@ -65,7 +70,7 @@ def sources(W):
 
 
 def velocity(W):
-    return synth.linear_gradient(W["n"], W["n"], W["n"], W["h"], W["c0"], W["alpha"])
+    return synth.linear_gradient(W["n"], W["n"], W.get("nz", W["n"]), W["h"], W["c0"], W["alpha"])
 
 
 def load_peaks():
@@ -144,16 +149,16 @@ def oracle_sample(W, iters_per_rhs, weights, repeats=1):
     from oracle.discretization import Problem, apply_A, neighbour_coefficients
     from oracle.schwarz import decompose, local_operator
 
-    n = W["n"]
-    prob = Problem(n, n, n, W["h"], W["f"], velocity(W), npml=W["npml"], weights=weights)
-    boxes = decompose((n, n, n), W["parts"], W["overlap"])
+    n, nz = W["n"], W.get("nz", W["n"])
+    prob = Problem(n, n, nz, W["h"], W["f"], velocity(W), npml=W["npml"], weights=weights)
+    boxes = decompose((n, n, nz), W["parts"], W["overlap"])
     big = max(boxes, key=lambda b: b.size)
     t0 = time.perf_counter()
     coef = neighbour_coefficients(prob)
     Ai = local_operator(prob, big, "oras", coef)
     lu = spla.splu(Ai.tocsc())
     setup_box = time.perf_counter() - t0
-    u = synth.random_complex((n, n, n), 1)
+    u = synth.random_complex((nz, n, n), 1)
     rb = synth.random_complex((big.size,), 2)
     out = []
     jbar = W["restart"] / 2.0
@@ -287,12 +292,12 @@ def run_gpu(args, W):
         torch.distributed.barrier()
     stream = torch.cuda.current_stream()
     ctx = helm.Context(local, stream=stream.cuda_stream)
-    n = W["n"]
+    n, nz = W["n"], W.get("nz", W["n"])
     weights = helm.fit_weights()
-    grid = helm.Grid(ctx, n, n, n, W["h"], W["f"], velocity(W), npml=W["npml"], weights=weights)
+    grid = helm.Grid(ctx, n, n, nz, W["h"], W["f"], velocity(W), npml=W["npml"], weights=weights)
     pos = sources(W)
     nrhs = len(pos)
-    b_host = synth.point_sources(n, n, n, W["h"], pos)
+    b_host = synth.point_sources(n, n, nz, W["h"], pos)
     b = torch.from_numpy(b_host).cuda()
     x = torch.empty_like(b)
     mixed_prec = helm.PREC_NAMES[args.factor_prec]
@@ -301,6 +306,10 @@ def run_gpu(args, W):
     setup_wall = time.perf_counter() - t
     solve_kw = dict(tol=W["tol"], restart=W["restart"], flexible=True, basis_prec=helm.PREC_FP32)
 
+    roof_fam = "sweep_gemm_tc" if args.factor_prec in ("tf32", "bf16") else "sweep_gemv"
+    # events around the roofline kernel only; enabled before the warm-up so that the iteration graphs
+    # captured there already carry the event nodes the timed region reads
+    ctx.profile(True, only=[roof_fam])
     for _ in range(args.warmup):
         oras.solve(b, x, **solve_kw)
     torch.cuda.synchronize()
@@ -309,8 +318,7 @@ def run_gpu(args, W):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    roof_fam = "sweep_gemm_tc" if args.factor_prec in ("tf32", "bf16") else "sweep_gemv"
-    ctx.profile(True, only=[roof_fam])          # events around the roofline kernel only
+    ctx.profile(True, only=[roof_fam])          # clears the totals; same selection, graphs stay valid
     l0 = ctx.launches
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -329,9 +337,11 @@ def run_gpu(args, W):
     roof_meas = ctx.profile_query(roof_fam)
     ctx.profile(False)
     # per-family breakdown from one more, fully instrumented solve (outside the timed region)
-    families = ("sweep_gemm_tc", "sweep_gemv", "sweep_prep", "stencil", "arnoldi", "oras_transfer",
-                "coarse_transfer", "krylov_misc")
+    families = ("sweep_gemm_tc", "sweep_gemv", "sweep_prep", "coarse_sweep", "coarse_prep", "stencil", "stencil64",
+                "arnoldi", "arnoldi_reorth", "oras_transfer", "coarse_restrict", "coarse_prolong", "krylov_misc")
     ctx.profile(True)
+    oras.solve(b, x, **solve_kw)                # captures the iteration graphs with every family's events
+    ctx.profile(True)                           # clears the totals
     b0 = torch.cuda.Event(enable_timing=True)
     b1 = torch.cuda.Event(enable_timing=True)
     b0.record(stream)
@@ -354,7 +364,8 @@ def run_gpu(args, W):
     if args.factor_prec == "tf32" and not args.no_variants:
         ob = helm.Oras(grid, W["parts"], W["overlap"], coarse_ratio=W["coarse"], factor_prec=helm.PREC_BF16)
         xb = torch.empty_like(b)
-        ob.solve(b, xb, **solve_kw)
+        for _ in range(2):                      # first use runs eagerly, the second captures the graphs
+            ob.solve(b, xb, **solve_kw)
         torch.cuda.synchronize()
         v0 = torch.cuda.Event(enable_timing=True)
         v1 = torch.cuda.Event(enable_timing=True)
@@ -371,6 +382,29 @@ def run_gpu(args, W):
                                     "max_true_relres": max(s_["true_relres"] for s_ in stb),
                                     "rel_l2_vs_tf32_solution": err}
         del ob, xb
+        if W["coarse"]:
+            # variant: the paper's own coarse solve (10 GMRES steps with one-level ORAS on the coarse grid)
+            oi = helm.Oras(grid, W["parts"], W["overlap"], coarse_ratio=W["coarse"], factor_prec=mixed_prec,
+                           coarse_iters=10, coarse_overlap=1)
+            xi = torch.empty_like(b)
+            for _ in range(2):
+                oi.solve(b, xi, **solve_kw)
+            torch.cuda.synchronize()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            kv = max(1, min(args.steps, 3))
+            for _ in range(kv):
+                _, sti = oi.solve(b, xi, **solve_kw)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vi, _ = replicas.job_throughput(nrhs * kv, v0.elapsed_time(v1) / 1000.0, dev)
+            err = float(torch.linalg.vector_norm(xi - x) / torch.linalg.vector_norm(x))
+            variants["coarse_gmres10"] = {"value": vi, "unit": "RHS/s", "steps": kv, "setup_s": oi.setup_seconds,
+                                          "iterations": [s_["iterations"] for s_ in sti],
+                                          "max_true_relres": max(s_["true_relres"] for s_ in sti),
+                                          "rel_l2_vs_exact_coarse_solution": err}
+            del oi, xi
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     bh = torch.from_numpy(b_host).pin_memory()
@@ -392,7 +426,8 @@ def run_gpu(args, W):
         setup64 = time.perf_counter() - t
         b1 = b[..., :1].contiguous()
         x1 = torch.empty_like(b1)
-        o64.solve(b1, x1, tol=W["tol"], restart=W["restart"], flexible=True, basis_prec=helm.PREC_FP64)
+        for _ in range(2):                      # eager first use, then graph capture
+            o64.solve(b1, x1, tol=W["tol"], restart=W["restart"], flexible=True, basis_prec=helm.PREC_FP64)
         torch.cuda.synchronize()
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
@@ -447,7 +482,7 @@ def run_gpu(args, W):
         "value": value, "unit": "RHS/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64", "data": "synthetic (seeded linear-gradient model, seeded point sources)",
-        "config": {"workload": W["desc"], "grid": [n, n, n], "nrhs": nrhs, "factor_prec": args.factor_prec,
+        "config": {"workload": W["desc"], "grid": [n, n, nz], "nrhs": nrhs, "factor_prec": args.factor_prec,
                    "basis_prec": "fp32", "parallelism": f"replicas x{ws}",
                    "l2": "factors (>10 GB) and Krylov basis exceed L2; no flush"},
         "setup_s": setup_wall, "setup_device_s": None, "iterations": iters, "max_true_relres": relres,

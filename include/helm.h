@@ -106,9 +106,18 @@ helm_status helm_profile_select(helm_ctx ctx, const char* families);
 helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launches, double* ms, double* bytes);
 
 /* Tuning knobs (read by the autotuner).  HELM_TUNE_TC_STAGES: pipeline depth of the
- * tensor-core plane sweep, 2..5 (0 = automatic: 5 for up to 32 right-hand sides, fewer for
- * more).  Returns HELM_EINVAL for an unknown key or value out of range. */
+ * tensor-core plane sweep, 2..5 (0 = automatic: 4, or 3 above 64 right-hand sides).
+ * HELM_TUNE_COARSE_COOP: 1 (default) runs both sweeps of a complex64 coarse problem in one
+ * cooperative launch when the device supports it and a coarse plane fits in shared memory;
+ * 0 uses three launches per plane.  HELM_TUNE_GRAPHS: 1 (default) keeps the Krylov workspace
+ * of the last gmres_solve on its ORAS handle (freed by oras_destroy, by a gmres_solve with
+ * another slot count, restart, method or basis precision, or by setting this knob to 0) and
+ * replays each Krylov iteration from a CUDA graph captured on its second use; 0 launches every
+ * kernel from the host and frees the workspace after each call.  Returns HELM_EINVAL for an
+ * unknown key or value out of range. */
 #define HELM_TUNE_TC_STAGES 1
+#define HELM_TUNE_COARSE_COOP 2
+#define HELM_TUNE_GRAPHS 3
 helm_status helm_set_tuning(helm_ctx ctx, int key, int value);
 
 /* ------------------------------------------------------------ grid / model */
@@ -154,6 +163,14 @@ typedef struct {
                              (_TF32X3 is rejected: not available).  The coarse factors are always computed
                              in FP64; with non-FP64 fine factors they are applied from a complex64
                              copy, with FP64 fine factors in FP64                                   */
+    int coarse_iters;     /* 0 = the coarse problem E solved exactly (plane LU of the whole coarse grid);
+                             k >= 1 = solved as in the paper by k GMRES iterations (x0 = 0, no restart)
+                             preconditioned by one-level ORAS on the coarse grid over the same
+                             spatial partition (the paper uses 10).  The preconditioner then depends
+                             on its input nonlinearly: solve with flexible GMRES.  Zero-initialise
+                             the struct to keep the exact coarse solve                              */
+    int coarse_overlap;   /* coarse layers added on every interior side of each coarse core
+                             (coarse_iters >= 1 only)                                              */
 } helm_oras_desc;
 
 /* Build the ORAS preconditioner: box decomposition, local operators A_i with

@@ -94,6 +94,19 @@ extern "C" helm_status helm_set_tuning(helm_ctx ctx, int key, int value) {
         if (value != 0 && (value < 2 || value > 5))
             return set_error(ctx, HELM_EINVAL, "helm_set_tuning: tensor-core stages must be 0 or 2..5");
         ctx->tc_stages = value;
+        ctx->graph_gen++;
+        return HELM_OK;
+    }
+    if (key == HELM_TUNE_COARSE_COOP) {
+        if (value != 0 && value != 1) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: coarse_coop must be 0 or 1");
+        ctx->coarse_coop = value;
+        ctx->graph_gen++;
+        return HELM_OK;
+    }
+    if (key == HELM_TUNE_GRAPHS) {
+        if (value != 0 && value != 1) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: graphs must be 0 or 1");
+        ctx->use_graphs = value;
+        ctx->graph_gen++;
         return HELM_OK;
     }
     return set_error(ctx, HELM_EINVAL, "helm_set_tuning: unknown key %d", key);

@@ -47,6 +47,7 @@ struct ProfRecord {
 };
 struct Profiler {
     bool on = false;
+    std::vector<ProfRecord>* capture = nullptr;   // set while a CUDA graph is captured: records go here
     std::vector<std::string> only;   // when non-empty, only these families are recorded
     std::vector<std::string> names;
     std::vector<ProfRecord> pending;
@@ -70,12 +71,25 @@ struct helm_ctx_s {
     Profiler prof;
     Server* server = nullptr;
     int tc_stages = 0;         // tuning: pipeline stages of the tensor-core sweep (0 = automatic)
+    int coarse_coop = 1;       // tuning: one cooperative launch for the complex64 coarse sweeps
+    int use_graphs = 1;        // tuning: Krylov iterations replayed from captured CUDA graphs
+    uint64_t graph_gen = 1;    // bumped when a setting that captured graphs depend on changes
+    cudaStream_t cap_stream = nullptr;   // private stream graphs are captured on (the context's may be
+                                         // the legacy default stream, which cannot be captured)
+    ~helm_ctx_s() {
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 };
 
 // Bracket one launch of an instrumented family with events on the context's stream.
 int prof_begin(helm_ctx ctx, const char* family);   // returns a token (-1 when profiling is off)
 void prof_end(helm_ctx ctx, int token, double bytes);
 void prof_drain(helm_ctx ctx);                       // fold completed records into the totals
+// Records captured into a CUDA graph (external event nodes): after each replay has completed,
+// prof_harvest adds their times to the totals; prof_release returns their events.
+void prof_harvest(helm_ctx ctx, const std::vector<ProfRecord>& recs);
+void prof_reserve(helm_ctx ctx, size_t n);   // pool at least n events (none are created during a capture)
+void prof_release(helm_ctx ctx, std::vector<ProfRecord>& recs);
 
 // Stencil weights in product form (see stencil.cu).
 struct StencilW {
@@ -119,6 +133,13 @@ struct PlaneSet {
     int prec = HELM_PREC_FP64;  // FP64 -> complex128 storage, otherwise complex64
     bool padded = false;        // every plane stored as ld x ld with ld = m_max rounded up (tensor-core layout)
     int ld = 0;                 // padded row pitch
+    // tensor-core tile layout (planeset_pack_tc): plane = [row tile t][chunk c][row i < 128][128 bytes],
+    // the bytes [128 c, 128 c + 128) of row 128 t + i, so each 128-row x 128-byte operand tile is
+    // one contiguous 16 KB block
+    bool packed = false;
+    int pk_tiles = 0, pk_chunks = 0;
+    bool coef_only = false;     // local operator coefficients without factor storage (the coarse E of the
+                                // inexact coarse solve, which is applied, not factorised)
     int nplanes = 0;            // total planes over all boxes
     int nbox = 0, m_max = 0, bz_max = 0;
     long long nloc = 0;         // total local nodes
@@ -131,6 +152,8 @@ struct PlaneSet {
     size_t esize() const { return prec == HELM_PREC_FP64 ? sizeof(c128) : (prec == HELM_PREC_BF16 ? 4 : sizeof(c64)); }
     size_t cesize() const { return prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64); }
 };
+
+struct KrylovEngine;
 
 struct helm_oras_s {
     helm_grid g = nullptr;
@@ -156,6 +179,18 @@ struct helm_oras_s {
     void* lb = nullptr;         // restricted right-hand sides of the tensor-core sweeps (same layout as loc)
     int tc_npad = 0;
     int* dev_err = nullptr;     // device error code of bounded waits (0 = none)
+    uint64_t scratch_gen = 0;   // bumped whenever the apply scratch is reallocated
+    // inexact coarse solve (coarse_iters > 0): one-level ORAS on the coarse grid and inner GMRES
+    PlaneSet cdd, cdd32;        // coarse local factors over the coarse boxes (FP64; complex64 copy when mixed)
+    int* cowner = nullptr;      // device: coarse owner part per axis, [cx + cy + cz]
+    void* Ecoef32 = nullptr;    // complex64 copy of E's 27 coefficients per coarse node (mixed precision)
+    void* cy = nullptr;         // inner solution, coarse vector (work precision)
+    void* cloc = nullptr;       // coarse local vectors (coarse factor precision)
+    void* crb = nullptr;        // coarse sweep buffer
+    struct InnerKrylov* inner = nullptr;   // inner GMRES workspace (krylov.cu)
+    // Krylov workspace of the last gmres_solve, kept with its captured iteration graphs
+    KrylovEngine* kcache = nullptr;
+    int kc_slots = 0, kc_restart = 0, kc_flex = 0, kc_prec = -1;
 };
 
 // ----------------------------------------------------------------- helpers
@@ -197,7 +232,15 @@ helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P);
 void planeset_free(helm_ctx ctx, PlaneSet& P);
 helm_status planeset_factor(helm_ctx ctx, PlaneSet& P, int* singular);
 helm_status planeset_to_bf16(helm_ctx ctx, PlaneSet& P);
-helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st);
+helm_status planeset_pack_tc(helm_ctx ctx, PlaneSet& P);   // row-major padded planes -> tile layout
+// plane slot of a padded set, in stored entries: room for ld x ld row-major or the tile layout
+inline long long padded_pstride(int ld) { return (long long)((ld + 127) / 128) * 128 * ((ld + 31) / 32 * 32); }
+// err: device error flag of bounded waits; with it a one-box complex64 set may use the
+// cooperative single-launch sweeps (sweep_coop.cu), whose rbuf needs m * nrhs + 1 entries
+helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st,
+                           int* err = nullptr);
+helm_status planeset_solve_coop(helm_ctx ctx, const PlaneSet& P, c64* loc, c64* rbuf, int nrhs, cudaStream_t st,
+                                int* err, bool* done);
 // tensor-core sweeps (sweep_tc.cu), complex64 local vectors, padded factor layout
 int tc_npad(int nrhs);
 // lb: the restricted right-hand sides b (read by the forward sweep); loc receives y, then x.
@@ -236,6 +279,19 @@ struct KrylovEngine {
     virtual void retire(int c) = 0;
     virtual helm_status push_state() = 0;
     virtual helm_status cycle(bool* any_left) = 0;
+    // point the engine at other caller-owned b / x buffers (engines made with external buffers)
+    virtual void rebind(c128* B_ext, c128* X_ext) = 0;
+    // replay each iteration j from a CUDA graph captured on its second use
+    virtual void enable_graphs(bool on) = 0;
 };
 KrylovEngine* make_krylov_engine(helm_oras o, int S, int restart, bool flexible, int basis_prec, c128* B_ext,
                                  c128* X_ext, helm_status* rc);
+
+// Inexact coarse solve (oras.cu, krylov.cu): y ~ E^{-1} c by o->d.coarse_iters right-preconditioned GMRES
+// iterations with one-level ORAS on the coarse grid, all on the device (no host synchronisation), vectors
+// [nc][nrhs] in the work precision wp.
+helm_status coarse_dd_apply(helm_oras o, int wp, const void* v, void* out, int nrhs);   // M_c^{-1} v
+helm_status coarse_E_apply(helm_oras o, int wp, const void* x, void* y, int nrhs);      // y = E x
+helm_status inner_alloc(helm_oras o, int wp, int nrhs);
+void inner_free(helm_oras o);
+helm_status inner_solve(helm_oras o, int wp, const void* c, void* y, int nrhs);

@@ -27,24 +27,63 @@ constexpr int RED_THREADS = 256;
 constexpr int IC = 8;   // basis vectors handled per pass of a dot-product kernel
 
 // Number of reduction blocks: the grid stride (blocks x 256) must be a multiple
-// of nrhs so that every thread only ever touches one right-hand side.
+// of nrhs so that every thread only ever touches one right-hand side.  At most two
+// blocks per SM (the reduction kernels run two resident blocks each): one wave, so
+// each block's closing block-wide reduction is amortised over as many elements as
+// possible and no partial wave trails.
 inline int red_blocks(helm_ctx ctx, long long elems, int nrhs) {
     int a = RED_THREADS, b = nrhs;
     while (b) { const int t = a % b; a = b; b = t; }
     const long long q = nrhs / a;   // nrhs / gcd(256, nrhs)
     long long nb = (elems + RED_THREADS - 1) / RED_THREADS;
-    const long long cap = std::max(q, ((long long)std::max(1, ctx->sm_count) * 8 / q) * q);
+    const long long cap = std::max(q, ((long long)std::max(1, ctx->sm_count) * 2 / q) * q);
     nb = ((nb + q - 1) / q) * q;
     return (int)std::min(nb, cap);
 }
 
 template <typename T> __device__ __forceinline__ c128 widen(cplx<T> a) { return mk<double>((double)a.x, (double)a.y); }
 
+// Per-thread accumulators of the reductions.  complex64 data: compensated (Kahan) FP32 sums, which
+// keep the error of a thread's sum near one rounding of the FP32 inputs without FP64 arithmetic in the
+// element loops (FP64 issues far slower than FP32 on this part); the thread totals are then reduced
+// in FP64.  complex128 data: plain FP64 sums.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+template <typename T> struct CAcc;
+template <> struct CAcc<float> {
+    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
+    __device__ __forceinline__ void add(c64 v) {
+        kahan_add(sx, cx, v.x);
+        kahan_add(sy, cy, v.y);
+    }
+    __device__ __forceinline__ c128 value() const { return mk<double>((double)sx - (double)cx, (double)sy - (double)cy); }
+};
+template <> struct CAcc<double> {
+    c128 s = {0.0, 0.0};
+    __device__ __forceinline__ void add(c128 v) { s = s + v; }
+    __device__ __forceinline__ c128 value() const { return s; }
+};
+template <typename T> struct RAcc;
+template <> struct RAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) { kahan_add(s, c, v); }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <> struct RAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 // partial[blk][i][r] = sum over this block's elements of conj(V_i[e]) w[e], i in [i0, i0+ni),
 // and with npart also |w|^2.  Runs on the reduction grid (grid stride a multiple of nrhs, so each
 // thread keeps one column).  Two elements per loop trip and IC basis vectors per pass keep 2 * (IC+1)
 // independent loads in flight; products in the basis precision are summed in groups of up to 8
-// before they are added to FP64 accumulators; one block-wide reduction per pass.
+// before they are added to the thread's accumulator (CAcc); one FP64 block-wide reduction per pass.
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS, 2) dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
                                                               const cplx<T>* __restrict__ w, long long n_el, int nrhs,
@@ -59,14 +98,11 @@ __global__ void __launch_bounds__(RED_THREADS, 2) dots_kernel(const cplx<T>* __r
     for (int ib = 0; ib < ni; ib += IC) {
         const int nq = min(IC, ni - ib);
         const bool with_norm = npart && ib == 0;
-        c128 acc[IC];
+        CAcc<T> acc[IC];
         cplx<T> part[IC];
 #pragma unroll
-        for (int q = 0; q < IC; ++q) {
-            acc[q] = mk<double>(0, 0);
-            part[q] = mk<T>(0, 0);
-        }
-        double nrm = 0.0;
+        for (int q = 0; q < IC; ++q) part[q] = mk<T>(0, 0);
+        RAcc<T> nrm;
         T pn = (T)0;
         int cnt = 0;
         const cplx<T>* Vb = V + (long long)(i0 + ib) * vstride;
@@ -92,10 +128,10 @@ __global__ void __launch_bounds__(RED_THREADS, 2) dots_kernel(const cplx<T>* __r
             if ((cnt += 2) >= 8) {
 #pragma unroll
                 for (int q = 0; q < IC; ++q) {
-                    acc[q] = acc[q] + widen(part[q]);
+                    if (q < nq) acc[q].add(part[q]);
                     part[q] = mk<T>(0, 0);
                 }
-                nrm += (double)pn;
+                nrm.add(pn);
                 pn = (T)0;
                 cnt = 0;
             }
@@ -109,11 +145,11 @@ __global__ void __launch_bounds__(RED_THREADS, 2) dots_kernel(const cplx<T>* __r
         }
 #pragma unroll
         for (int q = 0; q < IC; ++q) {
-            acc[q] = acc[q] + widen(part[q]);
-            s[q][threadIdx.x] = acc[q];
+            acc[q].add(part[q]);
+            s[q][threadIdx.x] = acc[q].value();
         }
-        nrm += (double)pn;
-        if (with_norm) sn[threadIdx.x] = nrm;
+        nrm.add(pn);
+        if (with_norm) sn[threadIdx.x] = nrm.value();
         __syncthreads();
         const int nr = min(nrhs, RED_THREADS);
         for (int o = threadIdx.x; o < nq * nr; o += RED_THREADS) {
@@ -164,31 +200,12 @@ __global__ void __launch_bounds__(128) finish_dots(const c128* __restrict__ part
     }
 }
 
-// w[e] -= sum_{i<ni} V_i[e] h_i[r]   (h from H column col, last pass's values only: hsrc)
-template <typename T>
-__global__ void update_kernel(const cplx<T>* __restrict__ V, long long vstride, cplx<T>* __restrict__ w, long long n_el,
-                              int nrhs, int ni, const c128* __restrict__ hsrc) {
-    // arithmetic in the basis precision (the result is stored in it anyway)
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(e % nrhs);
-        cplx<T> acc = w[e];
-        for (int i = 0; i < ni; ++i) {
-            const c128 hd = hsrc[(long long)i * nrhs + r];
-            const cplx<T> h = mk<T>((T)hd.x, (T)hd.y);
-            const cplx<T> v = V[(long long)i * vstride + e];
-            acc.x -= h.x * v.x - h.y * v.y;
-            acc.y -= h.x * v.y + h.y * v.x;
-        }
-        w[e] = acc;
-    }
-}
-
 // w -= V h for the columns selected by colmask (all when colmask is null; none when *any == 0),
 // and npart[blk][r] = |w|^2 of the result over this block's elements.  Runs on the reduction grid
 // (grid stride a multiple of nrhs), so each thread keeps one column; the coefficients h are staged
 // in shared memory in the basis precision when they fit (ni * nrhs entries).
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(const cplx<T>* __restrict__ V, long long vstride,
+__global__ void __launch_bounds__(RED_THREADS, 2) update_norm_kernel(const cplx<T>* __restrict__ V, long long vstride,
                                                                   cplx<T>* __restrict__ w, long long n_el, int nrhs,
                                                                   int ni, const c128* __restrict__ hsrc,
                                                                   const int* __restrict__ colmask,
@@ -204,32 +221,42 @@ __global__ void __launch_bounds__(RED_THREADS) update_norm_kernel(const cplx<T>*
     if (hsmem)
         for (int e = threadIdx.x; e < ni * nrhs; e += RED_THREADS) hs[e] = mk<T>((T)hsrc[e].x, (T)hsrc[e].y);
     __syncthreads();
-    double nrm = 0.0;
-    for (long long e = t; e < n_el; e += stride) {
-        cplx<T> acc = w[e];
+    RAcc<T> nrm;
+    // two elements per trip (e and e + stride, the same column): batches of 2 x 8 independent basis
+    // loads, then the multiply-subtracts
+    for (long long e = t; e < n_el; e += 2 * stride) {
+        const bool two = e + stride < n_el;
+        const long long e1 = two ? e + stride : e;
+        cplx<T> acc0 = w[e], acc1 = w[e1];
         if (project) {
-            // batches of 8 independent basis loads, then the 8 multiply-subtracts
             for (int i0 = 0; i0 < ni; i0 += 8) {
-                cplx<T> v[8];
+                cplx<T> v0[8], v1[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    if (i0 + q < ni) v[q] = V[(long long)(i0 + q) * vstride + e];
+                    if (i0 + q < ni) {
+                        v0[q] = V[(long long)(i0 + q) * vstride + e];
+                        v1[q] = V[(long long)(i0 + q) * vstride + e1];
+                    }
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     if (i0 + q < ni) {
                         cplx<T> h;
                         if (hsmem) h = hs[(i0 + q) * nrhs + r];
                         else h = mk<T>((T)hsrc[(long long)(i0 + q) * nrhs + r].x, (T)hsrc[(long long)(i0 + q) * nrhs + r].y);
-                        acc.x -= h.x * v[q].x - h.y * v[q].y;
-                        acc.y -= h.x * v[q].y + h.y * v[q].x;
+                        acc0.x -= h.x * v0[q].x - h.y * v0[q].y;
+                        acc0.y -= h.x * v0[q].y + h.y * v0[q].x;
+                        acc1.x -= h.x * v1[q].x - h.y * v1[q].y;
+                        acc1.y -= h.x * v1[q].y + h.y * v1[q].x;
                     }
                 }
             }
-            w[e] = acc;
+            w[e] = acc0;
+            if (two) w[e1] = acc1;
         }
-        nrm += (double)acc.x * (double)acc.x + (double)acc.y * (double)acc.y;
+        nrm.add(acc0.x * acc0.x + acc0.y * acc0.y);
+        if (two) nrm.add(acc1.x * acc1.x + acc1.y * acc1.y);
     }
-    sn[threadIdx.x] = nrm;
+    sn[threadIdx.x] = nrm.value();
     __syncthreads();
     if (threadIdx.x < min(nrhs, RED_THREADS)) {
         double sum = 0.0;
@@ -287,14 +314,34 @@ __global__ void __launch_bounds__(128) finish_norm2(const double* __restrict__ p
     if (threadIdx.x == 0) out[r] = sqrt((red[0] + red[1]) + (red[2] + red[3]));
 }
 
+// Column index of a grid-stride loop over [N][nrhs] entries without a 64-bit division per entry:
+// one at the start, then the stride's remainder is added each trip.
+struct ColumnWalk {
+    int r, step, n;
+    __device__ ColumnWalk(long long e0, long long stride, int nrhs)
+        : r((int)(e0 % nrhs)), step((int)(stride % nrhs)), n(nrhs) {}
+    __device__ __forceinline__ void next() {
+        r += step;
+        if (r >= n) r -= n;
+    }
+};
+
 // dst[e] = src[e] * scale[r]  (scale = 0 -> zero)
 template <typename TS, typename TD>
 __global__ void scale_copy(const cplx<TS>* __restrict__ src, cplx<TD>* __restrict__ dst, long long n_el, int nrhs,
                            const double* __restrict__ scale) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
-        const double s = scale[e % nrhs];
+    const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    ColumnWalk cw(e0, stride, nrhs);
+    for (long long e = e0; e < n_el; e += stride, cw.next()) {
+        const int r = cw.r;
         const cplx<TS> a = src[e];
-        dst[e] = mk<TD>((TD)(s * (double)a.x), (TD)(s * (double)a.y));
+        if (sizeof(TS) == 4 && sizeof(TD) == 4) {   // complex64 -> complex64: FP32 arithmetic
+            const float s = (float)scale[r];
+            dst[e] = mk<TD>((TD)(s * (float)a.x), (TD)(s * (float)a.y));
+        } else {
+            const double s = scale[r];
+            dst[e] = mk<TD>((TD)(s * (double)a.x), (TD)(s * (double)a.y));
+        }
     }
 }
 
@@ -374,8 +421,9 @@ __global__ void givens_step(RhsState* __restrict__ S, c128* __restrict__ H, doub
 }
 
 // y = R^{-1} g for the steps taken this cycle (upper-triangular back substitution).
+// y32 (when not null) receives y rounded to complex64 for the FP32 combination kernel.
 __global__ void back_substitute(const RhsState* __restrict__ S, const c128* __restrict__ H, const c128* __restrict__ g,
-                                c128* __restrict__ y, int m, int nrhs) {
+                                c128* __restrict__ y, c64* __restrict__ y32, int m, int nrhs) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrhs) return;
     const int nsteps = S[r].steps;
@@ -393,17 +441,44 @@ __global__ void back_substitute(const RhsState* __restrict__ S, const c128* __re
         y[(long long)i * nrhs + r] =
             den > 0 ? mk<double>((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den) : mk<double>(0, 0);
     }
+    if (y32)
+        for (int i = 0; i < m; ++i) {
+            const c128 v = y[(long long)i * nrhs + r];
+            y32[(long long)i * nrhs + r] = mk<float>((float)v.x, (float)v.y);
+        }
 }
 
 // x[e] += sum_i Zb_i[e] y_i[r]  (FP64 accumulation into complex128 x)   -- or u = sum_i Zb_i y_i (into TU)
 template <typename T, typename TO, bool ACC>
 __global__ void combine_kernel(const cplx<T>* __restrict__ Zb, long long zstride, const c128* __restrict__ y,
                                cplx<TO>* __restrict__ x, long long n_el, int nrhs, int ni) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(e % nrhs);
+    const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    ColumnWalk cw(e0, stride, nrhs);
+    for (long long e = e0; e < n_el; e += stride, cw.next()) {
+        const int r = cw.r;
         c128 acc = ACC ? widen(x[e]) : mk<double>(0, 0);
         for (int i = 0; i < ni; ++i) cmac(acc, widen(Zb[(long long)i * zstride + e]), y[(long long)i * nrhs + r]);
         x[e] = mk<TO>((TO)acc.x, (TO)acc.y);
+    }
+}
+
+// The same for a complex64 basis: products and their compensated sum in FP32, then x[e] += sum in
+// FP64 (TO = double, FGMRES) or u[e] = sum (TO = float, GMRES).
+template <typename TO>
+__global__ void combine32(const c64* __restrict__ Zb, long long zstride, const c64* __restrict__ y32,
+                          cplx<TO>* __restrict__ x, long long n_el, int nrhs, int ni) {
+    const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    ColumnWalk cw(e0, stride, nrhs);
+    for (long long e = e0; e < n_el; e += stride, cw.next()) {
+        const int r = cw.r;
+        CAcc<float> acc;
+        for (int i = 0; i < ni; ++i) acc.add(Zb[(long long)i * zstride + e] * y32[(long long)i * nrhs + r]);
+        if (sizeof(TO) == 8) {
+            const c128 v = widen(x[e]) + acc.value();
+            x[e] = mk<TO>((TO)v.x, (TO)v.y);
+        } else {
+            x[e] = mk<TO>((TO)(acc.sx - acc.cx), (TO)(acc.sy - acc.cy));
+        }
     }
 }
 
@@ -453,6 +528,7 @@ struct Krylov final : KrylovEngine {
     cplx<T>*V = nullptr, *Zb = nullptr, *w = nullptr, *u = nullptr;
     c128 *Bd = nullptr, *Xd = nullptr, *r = nullptr, *H = nullptr, *sn = nullptr, *gv = nullptr, *y = nullptr;
     c128 *part = nullptr, *hpass = nullptr;
+    c64* y32 = nullptr;
     double *cs = nullptr, *dpart = nullptr, *beta = nullptr, *inv = nullptr, *hn = nullptr;
     RhsState* Sd = nullptr;
     int *running = nullptr, *mask = nullptr, *rflag = nullptr, *rany = nullptr;
@@ -460,6 +536,17 @@ struct Krylov final : KrylovEngine {
     int hsmem_cap = 0;
     std::vector<RhsState> hs;
     std::vector<double> trel;
+    // one captured CUDA graph per iteration index j (its kernels depend on j through the basis offsets)
+    struct IterGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<ProfRecord> recs;   // external event nodes of profiled families
+        uint64_t launches = 0;          // kernels in the graph
+        uint64_t ctx_gen = 0, scratch_gen = 0;
+        int uses = 0;
+        bool failed = false;
+    };
+    bool graphs = false;
+    std::vector<IterGraph> ig;
 
     helm_status alloc(void** p, size_t bytes, const char* what) {
         helm_status rc = dev_alloc(ctx, p, bytes, what);
@@ -469,8 +556,23 @@ struct Krylov final : KrylovEngine {
     ~Krylov() override {
         if (ctx) {
             cudaStreamSynchronize(st);
+            for (auto& g : ig) drop(g);
             for (auto& a : allocs) dev_free(ctx, a.first, a.second);
         }
+    }
+    void drop(IterGraph& g) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        prof_release(ctx, g.recs);
+    }
+    void rebind(c128* B_ext, c128* X_ext) override {
+        Bd = B_ext;
+        Xd = X_ext;
+    }
+    void enable_graphs(bool on) override {
+        graphs = on;
+        if (!on)
+            for (auto& g : ig) drop(g);
     }
     c128* B() override { return Bd; }
     c128* X() override { return Xd; }
@@ -511,6 +613,8 @@ struct Krylov final : KrylovEngine {
         HELM_TRY(alloc((void**)&cs, (size_t)S * m * sizeof(double), "Givens cosines"));
         HELM_TRY(alloc((void**)&gv, (size_t)S * (m + 1) * sizeof(c128), "Givens rhs"));
         HELM_TRY(alloc((void**)&y, (size_t)S * m * sizeof(c128), "least-squares solution"));
+        if (sizeof(T) == 4)
+            HELM_TRY(alloc((void**)&y32, (size_t)S * m * sizeof(c64), "least-squares solution (complex64)"));
         HELM_TRY(alloc((void**)&part, (size_t)nblk * ldp * S * sizeof(c128), "dot partials"));
         HELM_TRY(alloc((void**)&hpass, (size_t)ldp * S * sizeof(c128), "dot pass"));
         HELM_TRY(alloc((void**)&dpart, (size_t)nblk * S * sizeof(double), "norm partials"));
@@ -525,6 +629,7 @@ struct Krylov final : KrylovEngine {
         HELM_TRY(alloc((void**)&nb, S * sizeof(double), "norms before projection"));
         HELM_TRY(alloc((void**)&na, S * sizeof(double), "norms after projection"));
         hsmem_cap = 40 * 1024 / (int)sizeof(cplx<T>);   // coefficient entries kept in shared memory (<= 40 KB)
+        ig.resize(m);
         hs.assign(S, RhsState{0.0, 0, 0, 0, 1, 0.0, 0.0, 0});
         trel.assign(S, 0.0);
         HELM_CUDA(ctx, cudaMemcpyAsync(Sd, hs.data(), S * sizeof(RhsState), cudaMemcpyHostToDevice, st));
@@ -544,8 +649,10 @@ struct Krylov final : KrylovEngine {
     }
 
     // partials of V^H w (and, with npart, of |w|^2) into `part`; skipped on the device when *any == 0
+    // (profiled as "arnoldi", or "arnoldi_reorth" for the conditional second projection, whose
+    // kernels return at once when no column needs it, so that the first family's bandwidth is exact)
     void dots_pass(const cplx<T>* Vb, const cplx<T>* vec, int ni, double* npart, const int* anyp) {
-        const int tk = prof_begin(ctx, "arnoldi");
+        const int tk = prof_begin(ctx, anyp ? "arnoldi_reorth" : "arnoldi");
         dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, S, 0, ni, part, ldp, npart, anyp);
         prof_end(ctx, tk, (double)(ni + 1 + (npart ? 1 : 0)) * nel * sizeof(cplx<T>));
         ctx->launches++;
@@ -558,7 +665,7 @@ struct Krylov final : KrylovEngine {
     void update_pass(int ni, const int* cm, const int* anyp, double* out) {
         const int hs = ni * S <= hsmem_cap ? 1 : 0;
         const size_t smem = hs ? (size_t)ni * S * sizeof(cplx<T>) : 0;
-        const int tk = prof_begin(ctx, "arnoldi");
+        const int tk = prof_begin(ctx, anyp ? "arnoldi_reorth" : "arnoldi");
         update_norm_kernel<T><<<nblk, RED_THREADS, smem, st>>>(V, nel, w, nel, S, ni, hpass, cm, anyp, dpart, hs);
         prof_end(ctx, tk, (double)(ni + 2) * nel * sizeof(cplx<T>));
         finish_norm2<<<S, 128, 0, st>>>(dpart, nblk, S, out);
@@ -601,6 +708,95 @@ struct Krylov final : KrylovEngine {
         return HELM_OK;
     }
 
+    // Iteration j of a cycle: z_j = M^{-1} v_j, w = A z_j, CGS with selective re-orthogonalisation,
+    // the Givens step and v_{j+1}; no host synchronisation inside, so it can be captured as a graph.
+    helm_status iteration_body(int j) {
+        cplx<T>* vj = V + (long long)j * nel;
+        cplx<T>* zj = flex ? Zb + (long long)j * nel : u;
+        HELM_TRY(oras_apply_wp(o, wp, vj, zj, S));
+        HELM_TRY(launch_stencil(o->g, wp, zj, w, S, st));
+        // Classical Gram-Schmidt for column j of H (H[r][i][j]) with a second projection for the
+        // columns whose norm dropped below 1/sqrt(2) of its value (selective re-orthogonalisation)
+        dots_pass(V, w, j + 1, dpart, nullptr);
+        finish_into(j + 1, hpass, S, 1, 0, 0, nullptr, nullptr);
+        finish_into(j + 1, H, m, (m + 1) * m, j, 0, nullptr, nullptr);
+        finish_norm2<<<S, 128, 0, st>>>(dpart, nblk, S, nb);
+        ctx->launches++;
+        update_pass(j + 1, nullptr, nullptr, na);
+        reorth_flags<<<1, 32, 0, st>>>(nb, na, rflag, rany, S);
+        ctx->launches++;
+        dots_pass(V, w, j + 1, nullptr, rany);
+        finish_into(j + 1, hpass, S, 1, 0, 0, nullptr, rany);
+        finish_into(j + 1, H, m, (m + 1) * m, j, 1, rflag, rany);
+        update_pass(j + 1, rflag, rany, hn);
+        HELM_CUDA(ctx, cudaMemsetAsync(running, 0, sizeof(int), st));
+        {
+            const int tk = prof_begin(ctx, "krylov_misc");
+            givens_step<<<rg, 128, 0, st>>>(Sd, H, cs, sn, gv, hn, inv, j, m, S, running);
+            scale_copy<T, T><<<eg, 256, 0, st>>>(w, V + (long long)(j + 1) * nel, nel, S, inv);
+            prof_end(ctx, tk, 2.0 * nel * sizeof(cplx<T>));
+        }
+        ctx->launches += 2;
+        return cuda_check(ctx, cudaGetLastError(), "Krylov iteration");
+    }
+
+    // Run iteration j: eagerly on its first use, captured into a CUDA graph on the second, replayed
+    // from the graph afterwards.  A graph is dropped when the ORAS scratch is reallocated or a
+    // setting it depends on (tuning, profiling) changes; if capture fails the iteration stays eager.
+    helm_status run_iteration(int j, IterGraph** replayed) {
+        *replayed = nullptr;
+        if (!graphs || !ctx->use_graphs) return iteration_body(j);
+        IterGraph& G = ig[j];
+        if (G.exec && (G.ctx_gen != ctx->graph_gen || G.scratch_gen != o->scratch_gen)) drop(G);
+        if (!G.exec) {
+            const bool ready = o->cap_nrhs >= S && o->cap_wp == wp;   // no allocation inside the capture
+            if (G.failed || G.uses < 1 || !ready) {
+                G.uses++;
+                return iteration_body(j);
+            }
+            std::vector<ProfRecord> recs;
+            cudaGraph_t g = nullptr;
+            if (ctx->prof.on) prof_reserve(ctx, 1024);
+            if (!ctx->cap_stream) HELM_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            // capture on the private stream (nothing runs during a capture, so the swap orders nothing);
+            // the graph is launched on the context's stream
+            cudaStream_t user = st;
+            st = ctx->stream = ctx->cap_stream;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                st = ctx->stream = user;
+                cudaGetLastError();
+                G.failed = true;
+                return iteration_body(j);
+            }
+            ctx->prof.capture = &recs;
+            const uint64_t l0 = ctx->launches;
+            const helm_status rc = iteration_body(j);
+            ctx->prof.capture = nullptr;
+            cudaError_t e = cudaStreamEndCapture(st, &g);
+            st = ctx->stream = user;
+            const uint64_t nl = ctx->launches - l0;
+            ctx->launches = l0;
+            if (rc == HELM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&G.exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (rc != HELM_OK || e != cudaSuccess || !G.exec) {
+                cudaGetLastError();
+                if (G.exec) cudaGraphExecDestroy(G.exec);
+                G.exec = nullptr;
+                prof_release(ctx, recs);
+                G.failed = true;
+                return iteration_body(j);
+            }
+            G.recs = std::move(recs);
+            G.launches = nl;
+            G.ctx_gen = ctx->graph_gen;
+            G.scratch_gen = o->scratch_gen;
+        }
+        HELM_CUDA(ctx, cudaGraphLaunch(G.exec, st));
+        ctx->launches += G.launches;
+        *replayed = &G;
+        return HELM_OK;
+    }
+
     // One restart cycle for every column not done; then the FP64 true residual decides which are done.
     helm_status cycle(bool* any_left) override {
         norms(r, beta);
@@ -609,47 +805,32 @@ struct Krylov final : KrylovEngine {
         ctx->launches += 2;
         int jdone = 0;
         for (int j = 0; j < m; ++j) {
-            cplx<T>* vj = V + (long long)j * nel;
-            cplx<T>* zj = flex ? Zb + (long long)j * nel : u;
-            HELM_TRY(oras_apply_wp(o, wp, vj, zj, S));
-            HELM_TRY(launch_stencil(o->g, wp, zj, w, S, st));
-            // Classical Gram-Schmidt for column j of H (H[r][i][j]) with a second projection for the
-            // columns whose norm dropped below 1/sqrt(2) of its value (selective re-orthogonalisation)
-            dots_pass(V, w, j + 1, dpart, nullptr);
-            finish_into(j + 1, hpass, S, 1, 0, 0, nullptr, nullptr);
-            finish_into(j + 1, H, m, (m + 1) * m, j, 0, nullptr, nullptr);
-            finish_norm2<<<S, 128, 0, st>>>(dpart, nblk, S, nb);
-            ctx->launches++;
-            update_pass(j + 1, nullptr, nullptr, na);
-            reorth_flags<<<1, 32, 0, st>>>(nb, na, rflag, rany, S);
-            ctx->launches++;
-            dots_pass(V, w, j + 1, nullptr, rany);
-            finish_into(j + 1, hpass, S, 1, 0, 0, nullptr, rany);
-            finish_into(j + 1, H, m, (m + 1) * m, j, 1, rflag, rany);
-            update_pass(j + 1, rflag, rany, hn);
-            cudaMemsetAsync(running, 0, sizeof(int), st);
-            {
-                const int tk = prof_begin(ctx, "krylov_misc");
-                givens_step<<<rg, 128, 0, st>>>(Sd, H, cs, sn, gv, hn, inv, j, m, S, running);
-                scale_copy<T, T><<<eg, 256, 0, st>>>(w, V + (long long)(j + 1) * nel, nel, S, inv);
-                prof_end(ctx, tk, 2.0 * nel * sizeof(cplx<T>));
-            }
-            ctx->launches += 2;
+            IterGraph* replayed = nullptr;
+            HELM_TRY(run_iteration(j, &replayed));
             int hrun = 0;
             HELM_CUDA(ctx, cudaMemcpyAsync(&hrun, running, sizeof(int), cudaMemcpyDeviceToHost, st));
             HELM_CUDA(ctx, cudaStreamSynchronize(st));
             HELM_CUDA(ctx, cudaGetLastError());
+            if (replayed && ctx->prof.on && !replayed->recs.empty()) prof_harvest(ctx, replayed->recs);
             jdone = j + 1;
             if (hrun == 0) break;
         }
         // x update with the steps taken in this cycle
-        back_substitute<<<rg, 128, 0, st>>>(Sd, H, gv, y, m, S);
+        back_substitute<<<rg, 128, 0, st>>>(Sd, H, gv, y, y32, m, S);
         ctx->launches++;
         if (flex) {
-            combine_kernel<T, double, true><<<eg, 256, 0, st>>>(Zb, nel, y, Xd, nel, S, jdone);
+            const int tk = prof_begin(ctx, "krylov_misc");
+            if (y32)
+                combine32<double><<<eg, 256, 0, st>>>((const c64*)Zb, nel, y32, Xd, nel, S, jdone);
+            else
+                combine_kernel<T, double, true><<<eg, 256, 0, st>>>(Zb, nel, y, Xd, nel, S, jdone);
+            prof_end(ctx, tk, (double)(jdone * sizeof(cplx<T>) + 2 * sizeof(c128)) * nel);
             ctx->launches++;
         } else {
-            combine_kernel<T, T, false><<<eg, 256, 0, st>>>(V, nel, y, w, nel, S, jdone);
+            if (y32)
+                combine32<float><<<eg, 256, 0, st>>>((const c64*)V, nel, y32, (c64*)w, nel, S, jdone);
+            else
+                combine_kernel<T, T, false><<<eg, 256, 0, st>>>(V, nel, y, w, nel, S, jdone);
             ctx->launches++;
             HELM_TRY(oras_apply_wp(o, wp, w, u, S));
             accum_widen<T><<<eg, 256, 0, st>>>(u, Xd, nel);
@@ -698,13 +879,189 @@ KrylovEngine* make_krylov_engine(helm_oras o, int S, int restart, bool flexible,
     return e;
 }
 
+// ------------------------------------------------------------------ inexact coarse solve (inner GMRES)
+
+namespace {
+
+// Column state of the inner solve: tolerance 0 (only an exact zero residual stops a column early),
+// iteration cap = the inner iteration count.
+__global__ void inner_init(RhsState* __restrict__ S, const double* __restrict__ beta, int nrhs, int iters) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    S[r] = RhsState{beta[r], 0, 0, 0, beta[r] == 0.0 ? 1 : 0, 0.0, 0.0, iters};
+}
+
+}  // namespace
+
+// Workspace of the inner GMRES over coarse vectors [nc][S].
+struct InnerKrylov {
+    int wp = 0, S = 0, m = 0, nblk = 0;
+    long long nel = 0;
+    std::vector<std::pair<void*, size_t>> allocs;
+    void *V = nullptr, *w = nullptr, *u = nullptr;
+    c128 *H = nullptr, *sn = nullptr, *gv = nullptr, *y = nullptr, *part = nullptr, *hpass = nullptr;
+    c64* y32 = nullptr;
+    double *cs = nullptr, *dpart = nullptr, *beta = nullptr, *inv = nullptr, *hn = nullptr, *nb = nullptr, *na = nullptr;
+    RhsState* Sd = nullptr;
+    int *running = nullptr, *rflag = nullptr, *rany = nullptr;
+};
+
+helm_status inner_alloc(helm_oras o, int wp, int nrhs) {
+    helm_ctx ctx = o->g->ctx;
+    inner_free(o);
+    InnerKrylov* K = new InnerKrylov();
+    o->inner = K;
+    K->wp = wp;
+    K->S = nrhs;
+    K->m = o->d.coarse_iters;
+    K->nel = o->nc * nrhs;
+    K->nblk = red_blocks(ctx, K->nel, nrhs);
+    const size_t te = wp == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
+    const int S = nrhs, m = K->m, ldp = m + 1;
+    auto al = [&](void** p, size_t bytes, const char* what) {
+        helm_status rc = dev_alloc(ctx, p, bytes, what);
+        if (!rc) K->allocs.push_back({*p, bytes});
+        return rc;
+    };
+    HELM_TRY(al(&K->V, (size_t)(m + 1) * K->nel * te, "inner Krylov basis"));
+    HELM_TRY(al(&K->w, K->nel * te, "inner Arnoldi vector"));
+    HELM_TRY(al(&K->u, K->nel * te, "inner preconditioned vector"));
+    HELM_TRY(al((void**)&K->H, (size_t)S * (m + 1) * m * sizeof(c128), "inner Hessenberg"));
+    HELM_TRY(al((void**)&K->sn, (size_t)S * m * sizeof(c128), "inner Givens sines"));
+    HELM_TRY(al((void**)&K->cs, (size_t)S * m * sizeof(double), "inner Givens cosines"));
+    HELM_TRY(al((void**)&K->gv, (size_t)S * (m + 1) * sizeof(c128), "inner Givens rhs"));
+    HELM_TRY(al((void**)&K->y, (size_t)S * m * sizeof(c128), "inner least-squares solution"));
+    HELM_TRY(al((void**)&K->y32, (size_t)S * m * sizeof(c64), "inner least-squares solution (complex64)"));
+    HELM_TRY(al((void**)&K->part, (size_t)K->nblk * ldp * S * sizeof(c128), "inner dot partials"));
+    HELM_TRY(al((void**)&K->hpass, (size_t)ldp * S * sizeof(c128), "inner dot pass"));
+    HELM_TRY(al((void**)&K->dpart, (size_t)K->nblk * S * sizeof(double), "inner norm partials"));
+    for (double** q : {&K->beta, &K->inv, &K->hn, &K->nb, &K->na})
+        HELM_TRY(al((void**)q, S * sizeof(double), "inner norms"));
+    HELM_TRY(al((void**)&K->Sd, S * sizeof(RhsState), "inner column state"));
+    HELM_TRY(al((void**)&K->running, sizeof(int), "inner running flag"));
+    HELM_TRY(al((void**)&K->rflag, S * sizeof(int), "inner re-orthogonalisation flags"));
+    HELM_TRY(al((void**)&K->rany, sizeof(int), "inner re-orthogonalisation any"));
+    return HELM_OK;
+}
+
+void inner_free(helm_oras o) {
+    if (!o->inner) return;
+    helm_ctx ctx = o->g->ctx;
+    for (auto& a : o->inner->allocs) dev_free(ctx, a.first, a.second);
+    delete o->inner;
+    o->inner = nullptr;
+}
+
+namespace {
+
+template <typename T>
+helm_status inner_solve_t(helm_oras o, InnerKrylov& K, const cplx<T>* c, cplx<T>* yout) {
+    helm_ctx ctx = o->g->ctx;
+    cudaStream_t st = ctx->stream;
+    const int S = K.S, m = K.m, ldp = m + 1, nblk = K.nblk;
+    const long long nel = K.nel;
+    const unsigned eg = (unsigned)std::min<long long>((nel + 255) / 256, (long long)ctx->sm_count * 16);
+    const unsigned rg = (unsigned)((S + 127) / 128);
+    cplx<T>* V = (cplx<T>*)K.V;
+    cplx<T>* w = (cplx<T>*)K.w;
+    cplx<T>* u = (cplx<T>*)K.u;
+    const int hsmem_cap = 40 * 1024 / (int)sizeof(cplx<T>);
+    // beta = ||c||, state, v_0 = c / beta
+    norm2_kernel<T><<<nblk, RED_THREADS, 0, st>>>(c, nel, S, K.dpart);
+    finish_norm2<<<S, 128, 0, st>>>(K.dpart, nblk, S, K.beta);
+    inner_init<<<rg, 128, 0, st>>>(K.Sd, K.beta, S, m);
+    cycle_start<<<rg, 128, 0, st>>>(K.Sd, K.beta, K.inv, K.gv, m, S);
+    scale_copy<T, T><<<eg, 256, 0, st>>>(c, V, nel, S, K.inv);
+    ctx->launches += 5;
+    auto dots = [&](int ni, double* npart, const int* anyp) {
+        dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(V, nel, w, nel, S, 0, ni, K.part, ldp, npart, anyp);
+        finish_dots<<<ni * S, 128, 0, st>>>(K.part, nblk, ldp, ni, S, K.hpass, S, 1, 0, 0, nullptr, anyp);
+        ctx->launches += 2;
+    };
+    auto update = [&](int ni, const int* cm, const int* anyp, double* out) {
+        const int hs = ni * S <= hsmem_cap ? 1 : 0;
+        const size_t smem = hs ? (size_t)ni * S * sizeof(cplx<T>) : 0;
+        update_norm_kernel<T><<<nblk, RED_THREADS, smem, st>>>(V, nel, w, nel, S, ni, K.hpass, cm, anyp, K.dpart, hs);
+        finish_norm2<<<S, 128, 0, st>>>(K.dpart, nblk, S, out);
+        ctx->launches += 2;
+    };
+    for (int j = 0; j < m; ++j) {
+        HELM_TRY(coarse_dd_apply(o, K.wp, V + (long long)j * nel, u, S));
+        HELM_TRY(coarse_E_apply(o, K.wp, u, w, S));
+        // classical Gram-Schmidt with selective re-orthogonalisation, as in the outer iteration
+        dots(j + 1, K.dpart, nullptr);
+        finish_dots<<<(j + 1) * S, 128, 0, st>>>(K.part, nblk, ldp, j + 1, S, K.H, m, (m + 1) * m, j, 0, nullptr,
+                                                 nullptr);
+        finish_norm2<<<S, 128, 0, st>>>(K.dpart, nblk, S, K.nb);
+        ctx->launches += 2;
+        update(j + 1, nullptr, nullptr, K.na);
+        reorth_flags<<<1, 32, 0, st>>>(K.nb, K.na, K.rflag, K.rany, S);
+        ctx->launches++;
+        dots(j + 1, nullptr, K.rany);
+        finish_dots<<<(j + 1) * S, 128, 0, st>>>(K.part, nblk, ldp, j + 1, S, K.H, m, (m + 1) * m, j, 1, K.rflag,
+                                                 K.rany);
+        ctx->launches++;
+        update(j + 1, K.rflag, K.rany, K.hn);
+        HELM_CUDA(ctx, cudaMemsetAsync(K.running, 0, sizeof(int), st));
+        givens_step<<<rg, 128, 0, st>>>(K.Sd, K.H, K.cs, K.sn, K.gv, K.hn, K.inv, j, m, S, K.running);
+        scale_copy<T, T><<<eg, 256, 0, st>>>(w, V + (long long)(j + 1) * nel, nel, S, K.inv);
+        ctx->launches += 2;
+    }
+    // y = M_c^{-1} (V y_ls): standard right-preconditioned GMRES keeps only V
+    back_substitute<<<rg, 128, 0, st>>>(K.Sd, K.H, K.gv, K.y, sizeof(T) == 4 ? K.y32 : nullptr, m, S);
+    if (sizeof(T) == 4)
+        combine32<float><<<eg, 256, 0, st>>>((const c64*)V, nel, K.y32, (c64*)u, nel, S, m);
+    else
+        combine_kernel<T, T, false><<<eg, 256, 0, st>>>(V, nel, K.y, u, nel, S, m);
+    ctx->launches += 2;
+    HELM_TRY(coarse_dd_apply(o, K.wp, u, yout, S));
+    return cuda_check(ctx, cudaGetLastError(), "inner coarse GMRES");
+}
+
+}  // namespace
+
+helm_status inner_solve(helm_oras o, int wp, const void* c, void* y, int nrhs) {
+    helm_ctx ctx = o->g->ctx;
+    if (!o->inner || o->inner->wp != wp || o->inner->S != nrhs)
+        return set_error(ctx, HELM_EINVAL, "inner coarse solve: workspace not sized for this call");
+    const int tk = prof_begin(ctx, "coarse_inner");
+    helm_status rc = wp == HELM_PREC_FP64
+                         ? inner_solve_t<double>(o, *o->inner, (const c128*)c, (c128*)y)
+                         : inner_solve_t<float>(o, *o->inner, (const c64*)c, (c64*)y);
+    prof_end(ctx, tk, 0.0);
+    return rc;
+}
+
 namespace {
 
 helm_status solve_all(helm_oras o, c128* b, c128* x, int nrhs, const helm_gmres_desc& D, helm_rhs_stats* stats) {
     helm_ctx ctx = o->g->ctx;
     helm_status rc = HELM_OK;
-    std::unique_ptr<KrylovEngine> K(make_krylov_engine(o, nrhs, D.restart, D.flexible != 0, D.basis_prec, b, x, &rc));
-    if (!K) return rc;
+    // with graphs on, the workspace (and its captured iteration graphs) stays on the handle
+    const bool keep = ctx->use_graphs != 0;
+    const int flex = D.flexible != 0;
+    KrylovEngine* K = nullptr;
+    std::unique_ptr<KrylovEngine> owned;
+    if (keep && o->kcache && o->kc_slots == nrhs && o->kc_restart == D.restart && o->kc_flex == flex &&
+        o->kc_prec == D.basis_prec) {
+        K = o->kcache;
+        K->rebind(b, x);
+    } else {
+        delete o->kcache;
+        o->kcache = nullptr;
+        K = make_krylov_engine(o, nrhs, D.restart, flex != 0, D.basis_prec, b, x, &rc);
+        if (!K) return rc;
+        if (keep) {
+            o->kcache = K;
+            o->kc_slots = nrhs;
+            o->kc_restart = D.restart;
+            o->kc_flex = flex;
+            o->kc_prec = D.basis_prec;
+            K->enable_graphs(true);
+        } else {
+            owned.reset(K);
+        }
+    }
     std::vector<int> cols(nrhs), maxit(nrhs, D.maxit);
     std::vector<double> tol(nrhs, D.tol);
     for (int i = 0; i < nrhs; ++i) cols[i] = i;

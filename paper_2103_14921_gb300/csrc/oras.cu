@@ -74,21 +74,93 @@ __global__ void build_local_coef(const BoxInfo* __restrict__ boxes, const c128* 
     }
 }
 
+// Local coefficients of the coarse boxes (inexact coarse solve): rows of E (27 per coarse node, E27) with
+// the same folding as the fine boxes, rho = exp(i k H) with H = r h the coarse spacing and k = omega / c at
+// the coarse node's fine position r J (clamped to the grid).
+template <typename TO>
+__global__ void build_local_coef27(const BoxInfo* __restrict__ boxes, const c128* __restrict__ E27,
+                                   const c128* __restrict__ c, int nx, int ny, int nz, int cx, int cy, int r,
+                                   double omega, double H, int dirichlet, cplx<TO>* __restrict__ out) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const long long nl = (long long)B.m * B.dims[2];
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (long long)gridDim.x * blockDim.x) {
+        const int li = (int)(l % B.dims[0]);
+        const int lj = (int)((l / B.dims[0]) % B.dims[1]);
+        const int lk = (int)(l / B.m);
+        const int gi = B.lo[0] + li, gj = B.lo[1] + lj, gk = B.lo[2] + lk;
+        const c128* a = E27 + (((long long)gk * cy + gj) * cx + gi) * 27;
+        c128 loc[27];
+        for (int q = 0; q < 27; ++q) loc[q] = mk<double>(0, 0);
+        const int fi = min(r * gi, nx - 1), fj = min(r * gj, ny - 1), fk = min(r * gk, nz - 1);
+        const c128 cv = c[((long long)fk * ny + fj) * nx + fi];
+        const double den = cv.x * cv.x + cv.y * cv.y;
+        const double kr = omega * cv.x / den, ki = -omega * cv.y / den;   // k = omega / c
+        const double mag = exp(-ki * H);
+        const c128 rho = mk<double>(mag * cos(kr * H), mag * sin(kr * H));
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const c128 v = a[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+                    if (v.x == 0.0 && v.y == 0.0) continue;
+                    const int qi = li + dx, qj = lj + dy, qk = lk + dz;
+                    int crossed = 0;
+                    int ex = dx, ey = dy, ez = dz;
+                    if (qi < 0 || qi >= B.dims[0]) { crossed++; ex = 0; }
+                    if (qj < 0 || qj >= B.dims[1]) { crossed++; ey = 0; }
+                    if (qk < 0 || qk >= B.dims[2]) { crossed++; ez = 0; }
+                    c128 val = v;
+                    if (crossed) {
+                        if (dirichlet) continue;
+                        for (int t = 0; t < crossed; ++t) val = val * rho;
+                    }
+                    const int dd = (ez + 1) * 9 + (ey + 1) * 3 + (ex + 1);
+                    loc[dd] = loc[dd] + val;
+                }
+        cplx<TO>* o = out + (B.loc_off + l) * 27;
+        for (int q = 0; q < 27; ++q) o[q] = mk<TO>((TO)loc[q].x, (TO)loc[q].y);
+    }
+}
+
+// y = E x on the coarse grid from E's 27 coefficients per node; grid (x-line chunks, y, z)
+template <typename T>
+__global__ void e27_apply(const cplx<T>* __restrict__ E27, const cplx<T>* __restrict__ x, cplx<T>* __restrict__ y,
+                          int cx, int cy, int cz, int nrhs) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cx * nrhs) return;
+    const int i = t / nrhs, r = t % nrhs;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long p = ((long long)k * cy + j) * cx + i;
+    const cplx<T>* a = E27 + p * 27;
+    cplx<T> acc = mk<T>(0, 0);
+    for (int dz = -1; dz <= 1; ++dz) {
+        if (k + dz < 0 || k + dz >= cz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            if (j + dy < 0 || j + dy >= cy) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (i + dx < 0 || i + dx >= cx) continue;
+                const long long q = p + ((long long)dz * cy + dy) * cx + dx;
+                cmac(acc, a[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)], x[q * nrhs + r]);
+            }
+        }
+    }
+    y[p * nrhs + r] = acc;
+}
+
 // ------------------------------------------------------------------ restriction / prolongation
 
 // loc[(loc_off + l) * nrhs + r] = v[g(l) * nrhs + r]   (R_i v for every box)
 template <typename TV, typename TL>
 __global__ void restrict_boxes(const BoxInfo* __restrict__ boxes, const cplx<TV>* __restrict__ v,
                                cplx<TL>* __restrict__ loc, int nx, int ny, int nrhs) {
-    const BoxInfo B = boxes[blockIdx.y];
-    const long long total = (long long)B.m * B.dims[2] * nrhs;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const long long l = e / nrhs;
-        const int r = (int)(e % nrhs);
-        const int li = (int)(l % B.dims[0]);
-        const int lj = (int)((l / B.dims[0]) % B.dims[1]);
-        const int lk = (int)(l / B.m);
+    // grid: (x-line chunks, box rows (y, z) strided, box); 32-bit index arithmetic inside a row
+    const BoxInfo B = boxes[blockIdx.z];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B.dims[0] * nrhs) return;
+    const int li = t / nrhs, r = t % nrhs;
+    for (int row = blockIdx.y; row < B.dims[1] * B.dims[2]; row += gridDim.y) {
+        const int lj = row % B.dims[1], lk = row / B.dims[1];
         const long long g = ((long long)(B.lo[2] + lk) * ny + (B.lo[1] + lj)) * nx + (B.lo[0] + li);
+        const long long l = (long long)row * B.dims[0] + li;
         const cplx<TV> x = v[g * nrhs + r];
         loc[(B.loc_off + l) * nrhs + r] = mk<TL>((TL)x.x, (TL)x.y);
     }
@@ -99,21 +171,19 @@ template <typename TL, typename TV, bool ADDQ>
 __global__ void prolong_owner(const BoxInfo* __restrict__ boxes, const int* __restrict__ owner,
                               const cplx<TL>* __restrict__ loc, const cplx<TV>* __restrict__ q, cplx<TV>* __restrict__ out,
                               int nx, int ny, int nz, int px, int py, int nrhs) {
-    const long long total = (long long)nx * ny * nz * nrhs;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const long long g = e / nrhs;
-        const int r = (int)(e % nrhs);
-        const int i = (int)(g % nx);
-        const int j = (int)((g / nx) % ny);
-        const int k = (int)(g / ((long long)nx * ny));
-        const int b = (owner[nx + ny + k] * py + owner[nx + j]) * px + owner[i];
-        const BoxInfo& B = boxes[b];
-        const long long l = ((long long)(k - B.lo[2]) * B.dims[1] + (j - B.lo[1])) * B.dims[0] + (i - B.lo[0]);
-        const cplx<TL> x = loc[(B.loc_off + l) * nrhs + r];
-        cplx<TV> y = mk<TV>((TV)x.x, (TV)x.y);
-        if (ADDQ) y = y + q[e];
-        out[e] = y;
-    }
+    // grid: (x-line chunks, y, z)
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nx * nrhs) return;
+    const int i = t / nrhs, r = t % nrhs;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long e = (((long long)k * ny + j) * nx + i) * nrhs + r;
+    const int b = (owner[nx + ny + k] * py + owner[nx + j]) * px + owner[i];
+    const BoxInfo& B = boxes[b];
+    const long long l = ((long long)(k - B.lo[2]) * B.dims[1] + (j - B.lo[1])) * B.dims[0] + (i - B.lo[0]);
+    const cplx<TL> x = loc[(B.loc_off + l) * nrhs + r];
+    cplx<TV> y = mk<TV>((TV)x.x, (TV)x.y);
+    if (ADDQ) y = y + q[e];
+    out[e] = y;
 }
 
 // ------------------------------------------------------------------ coarse space
@@ -156,32 +226,81 @@ __global__ void coarse_restrict(const cplx<TV>* __restrict__ v, cplx<TC>* __rest
     }
 }
 
+inline unsigned grid_for(long long n, int threads = 256, long long cap = 152LL * 16) {
+    long long b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+// One axis of the separable restriction Z^T = Z_z^T (x) Z_y^T (x) Z_x^T on [n2][n1][n0][R] arrays:
+// along axis ax (0 = x, 1 = y, 2 = z) the n nodes are replaced by nc coarse nodes,
+// out[.., J, ..] = scale * sum_i (r - |i - r J|) in[.., i, ..] over the hat's support.  Three
+// passes read each fine value once (the direct 3-D sum reads it (2r - 1)^3 / r^3 times).
+template <typename TI, typename TO>
+__global__ void restrict_axis(const cplx<TI>* __restrict__ in, cplx<TO>* __restrict__ out, int n0, int n1, int n2,
+                              int ax, int nc, int r, int R, TI scale) {
+    const int d0 = ax == 0 ? nc : n0, d1 = ax == 1 ? nc : n1, d2 = ax == 2 ? nc : n2;
+    const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
+    const long long sa = (ax == 0 ? 1LL : (ax == 1 ? (long long)n0 : (long long)n0 * n1)) * R;
+    const long long total = (long long)d0 * d1 * d2 * R;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int rr = (int)(e % R);
+        long long t = e / R;
+        const int o0 = (int)(t % d0);
+        t /= d0;
+        const int o1 = (int)(t % d1);
+        const int o2 = (int)(t / d1);
+        const int J = ax == 0 ? o0 : (ax == 1 ? o1 : o2);
+        const long long base = ((((long long)(ax == 2 ? 0 : o2) * n1 + (ax == 1 ? 0 : o1)) * n0) + (ax == 0 ? 0 : o0)) * R + rr;
+        const int i0 = max(0, r * J - r + 1), i1 = min(n - 1, r * J + r - 1);
+        cplx<TI> acc = mk<TI>(0, 0);
+        for (int i = i0; i <= i1; ++i) {
+            const TI wt = (TI)(r - abs(i - r * J));
+            const cplx<TI> x = in[base + (long long)i * sa];
+            acc.x += wt * x.x;
+            acc.y += wt * x.y;
+        }
+        out[e] = mk<TO>((TO)(acc.x * scale), (TO)(acc.y * scale));
+    }
+}
+
+// cv = Z^T v / r^3 by three axis passes (x into t1, y into t2, z into cv)
+template <typename TV, typename TC>
+void restrict_separable(const cplx<TV>* v, cplx<TV>* t1, cplx<TV>* t2, cplx<TC>* cv, int nx, int ny, int nz, int cx,
+                        int cy, int cz, int r, int R, cudaStream_t st) {
+    const TV one = (TV)1, s3 = (TV)1 / (TV)(r * r * r);
+    restrict_axis<TV, TV><<<grid_for((long long)nz * ny * cx * R), 256, 0, st>>>(v, t1, nx, ny, nz, 0, cx, r, R, one);
+    restrict_axis<TV, TV><<<grid_for((long long)nz * cy * cx * R), 256, 0, st>>>(t1, t2, cx, ny, nz, 1, cy, r, R, one);
+    restrict_axis<TV, TC><<<grid_for((long long)cz * cy * cx * R), 256, 0, st>>>(t2, cv, cx, cy, nz, 2, cz, r, R, s3);
+}
+
 // q[i * nrhs + rr] = sum_J Z[i, J] cv[J * nrhs + rr]   (trilinear interpolation, weights (i mod r)/r,
 // exact in binary for r a power of two; accumulated in the output precision)
 template <typename TC, typename TV>
 __global__ void coarse_prolong(const cplx<TC>* __restrict__ cv, cplx<TV>* __restrict__ q, int nx, int ny, int nz,
                                int cx, int cy, int cz, int r, int nrhs) {
-    const long long total = (long long)nx * ny * nz * nrhs;
+    // grid: (x-line chunks, y, z)
     const TV inv_r = (TV)1 / (TV)r;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const long long g = e / nrhs;
-        const int rr = (int)(e % nrhs);
-        const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((long long)nx * ny));
-        const int I0 = i / r, J0 = j / r, K0 = k / r;
-        const TV wx1 = (TV)(i - r * I0) * inv_r, wy1 = (TV)(j - r * J0) * inv_r, wz1 = (TV)(k - r * K0) * inv_r;
-        const TV wx[2] = {(TV)1 - wx1, wx1}, wy[2] = {(TV)1 - wy1, wy1}, wz[2] = {(TV)1 - wz1, wz1};
-        cplx<TV> acc = mk<TV>(0, 0);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nx * nrhs) return;
+    const int i = t / nrhs, rr = t % nrhs;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long e = (((long long)k * ny + j) * nx + i) * nrhs + rr;
+    const int I0 = i / r, J0 = j / r, K0 = k / r;
+    const TV wx1 = (TV)(i - r * I0) * inv_r, wy1 = (TV)(j - r * J0) * inv_r, wz1 = (TV)(k - r * K0) * inv_r;
+    const TV wx[2] = {(TV)1 - wx1, wx1}, wy[2] = {(TV)1 - wy1, wy1}, wz[2] = {(TV)1 - wz1, wz1};
+    cplx<TV> acc = mk<TV>(0, 0);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
-            const TV wt = wx[a] * wy[b] * wz[d];
-            if (wt == (TV)0 || I0 + a >= cx || J0 + b >= cy || K0 + d >= cz) continue;
-            const cplx<TC> x = cv[(((long long)(K0 + d) * cy + (J0 + b)) * cx + (I0 + a)) * nrhs + rr];
-            acc.x += wt * (TV)x.x;
-            acc.y += wt * (TV)x.y;
-        }
-        q[e] = acc;
+    for (int c = 0; c < 8; ++c) {
+        const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+        const TV wt = wx[a] * wy[b] * wz[d];
+        if (wt == (TV)0 || I0 + a >= cx || J0 + b >= cy || K0 + d >= cz) continue;
+        const cplx<TC> x = cv[(((long long)(K0 + d) * cy + (J0 + b)) * cx + (I0 + a)) * nrhs + rr];
+        acc.x += wt * (TV)x.x;
+        acc.y += wt * (TV)x.y;
     }
+    q[e] = acc;
 }
 
 // Probe vectors: zc[i * 27 + c] = (Z e_c)_i, e_c = indicator of the coarse nodes of colour c = (J mod 3).
@@ -229,16 +348,84 @@ __global__ void narrow_c128(const c128* __restrict__ a, c64* __restrict__ b, lon
         b[i] = mk<float>((float)a[i].x, (float)a[i].y);
 }
 
-inline unsigned grid_for(long long n, int threads = 256, long long cap = 152LL * 16) {
-    long long b = (n + threads - 1) / threads;
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------ factor
+
+// The inexact coarse solve's one-level ORAS on the coarse grid: the fine partition carried to the coarse
+// nodes (coarse node J goes to the part whose fine core holds r J; the last coarse node, which may lie
+// past the fine grid, to the last part), coarse_overlap layers on interior sides, local operators from
+// E's rows with the absorbing fold, FP64 plane factors (and complex64 copies with mixed fine factors).
+static helm_status setup_coarse_dd(helm_oras o, const std::vector<int>& cuts) {
+    helm_grid g = o->g;
+    helm_ctx ctx = g->ctx;
+    cudaStream_t st = ctx->stream;
+    const helm_oras_desc& d = o->d;
+    const int n[3] = {g->d.nx, g->d.ny, g->d.nz};
+    const int p[3] = {d.px, d.py, d.pz};
+    const int r = d.coarse_ratio;
+    std::vector<int> cc[3];
+    std::vector<int> cowner(o->cdims[0] + o->cdims[1] + o->cdims[2]);
+    int base = 0, fb = 0;
+    for (int a = 0; a < 3; ++a) {
+        cc[a].push_back(0);
+        for (int t = 1; t < p[a]; ++t) cc[a].push_back((cuts[fb + t] + r - 1) / r);
+        cc[a].push_back(o->cdims[a]);
+        for (int t = 0; t < p[a]; ++t) {
+            if (cc[a][t + 1] <= cc[a][t])
+                return set_error(ctx, HELM_EINVAL, "oras_factor: the coarse grid is too small for the partition");
+            for (int J = cc[a][t]; J < cc[a][t + 1]; ++J) cowner[base + J] = t;
+        }
+        base += o->cdims[a];
+        fb += p[a] + 1;
+        (void)n;
+    }
+    const int ov = d.coarse_overlap;
+    for (int tz = 0; tz < p[2]; ++tz)
+        for (int ty = 0; ty < p[1]; ++ty)
+            for (int tx = 0; tx < p[0]; ++tx) {
+                BoxInfo b{};
+                const int t[3] = {tx, ty, tz};
+                for (int a = 0; a < 3; ++a) {
+                    const int c0 = cc[a][t[a]], c1 = cc[a][t[a] + 1];
+                    b.core_lo[a] = c0;
+                    b.core_hi[a] = c1;
+                    b.lo[a] = c0 > 0 ? std::max(0, c0 - ov) : 0;
+                    const int hi = c1 < o->cdims[a] ? std::min(o->cdims[a], c1 + ov) : o->cdims[a];
+                    b.dims[a] = hi - b.lo[a];
+                }
+                o->cdd.hbox.push_back(b);
+            }
+    o->cdd.prec = HELM_PREC_FP64;
+    HELM_TRY(planeset_alloc(ctx, o->cdd));
+    HELM_TRY(dev_alloc(ctx, (void**)&o->cowner, cowner.size() * sizeof(int), "coarse owner table"));
+    HELM_CUDA(ctx, cudaMemcpy(o->cowner, cowner.data(), cowner.size() * sizeof(int), cudaMemcpyHostToDevice));
+    long long mx = 0;
+    for (auto& b : o->cdd.hbox) mx = std::max(mx, (long long)b.m * b.dims[2]);
+    build_local_coef27<double><<<dim3(grid_for(mx, 128, 4096), o->cdd.nbox), 128, 0, st>>>(
+        o->cdd.dbox, (const c128*)o->coarse.coef, g->c, n[0], n[1], n[2], o->cdims[0], o->cdims[1], r, g->omega,
+        r * g->d.h, d.interface_bc, (c128*)o->cdd.coef);
+    ctx->launches++;
+    HELM_CUDA(ctx, cudaGetLastError());
+    int singular = 0;
+    HELM_TRY(planeset_factor(ctx, o->cdd, &singular));
+    if (singular) return set_error(ctx, HELM_ESINGULAR, "oras_factor: zero pivot in a coarse local factor");
+    // complex64 copies: E for FP32 work vectors, and the local factors with mixed fine factors
+    HELM_TRY(dev_alloc(ctx, &o->Ecoef32, (size_t)o->nc * 27 * sizeof(c64), "coarse operator (complex64)"));
+    narrow_c128<<<grid_for(o->nc * 27), 256, 0, st>>>((const c128*)o->coarse.coef, (c64*)o->Ecoef32, o->nc * 27);
+    ctx->launches++;
+    if (o->fine.prec != HELM_PREC_FP64) {
+        o->cdd32.prec = HELM_PREC_FP32;
+        o->cdd32.hbox = o->cdd.hbox;
+        HELM_TRY(planeset_alloc(ctx, o->cdd32));
+        narrow_c128<<<grid_for((long long)o->cdd.nloc * 27), 256, 0, st>>>(
+            (const c128*)o->cdd.coef, (c64*)o->cdd32.coef, (long long)o->cdd.nloc * 27);
+        narrow_c128<<<grid_for((long long)o->cdd.fac_entries), 256, 0, st>>>(
+            (const c128*)o->cdd.G, (c64*)o->cdd32.G, (long long)o->cdd.fac_entries);
+        ctx->launches += 2;
+    }
+    return cuda_check(ctx, cudaGetLastError(), "coarse subdomain set-up");
+}
 
 extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_oras* out) {
     if (!g || !d || !out) return set_error(g ? g->ctx : nullptr, HELM_EINVAL, "oras_factor: NULL argument");
@@ -251,6 +438,8 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
     if (d->overlap < 0 || d->coarse_ratio < 0)
         return set_error(ctx, HELM_EINVAL, "oras_factor: bad overlap or coarse ratio");
     if (d->interface_bc != 0 && d->interface_bc != 1) return set_error(ctx, HELM_EINVAL, "oras_factor: bad interface_bc");
+    if (d->coarse_iters < 0 || d->coarse_iters > 200 || (d->coarse_iters > 0 && (d->coarse_ratio < 1 || d->coarse_overlap < 0)))
+        return set_error(ctx, HELM_EINVAL, "oras_factor: coarse_iters needs 0..200 with a coarse grid and coarse_overlap >= 0");
     if (d->factor_prec < HELM_PREC_FP64 || d->factor_prec > HELM_PREC_BF16)
         return set_error(ctx, HELM_EINVAL, "oras_factor: bad factor_prec");
     HELM_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -330,6 +519,7 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
     if ((rc = planeset_factor(ctx, o->fine, &singular))) return fail(rc);
     if (singular) return fail(set_error(ctx, HELM_ESINGULAR, "oras_factor: zero pivot in a local plane factor"));
     if (d->factor_prec == HELM_PREC_BF16 && (rc = planeset_to_bf16(ctx, o->fine))) return fail(rc);
+    if (o->fine.padded && (rc = planeset_pack_tc(ctx, o->fine))) return fail(rc);
 
     // --- coarse level
     if (d->coarse_ratio > 0) {
@@ -365,6 +555,7 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
         }
         o->coarse.prec = HELM_PREC_FP64;
         o->coarse.hbox.push_back(cb);
+        o->coarse.coef_only = d->coarse_iters > 0;   // the inexact solve applies E, it does not factor it
         if ((rc = planeset_alloc(ctx, o->coarse))) { cfree(); return fail(rc); }
         coarse_gather_E<<<grid_for(o->nc), 256, 0, st>>>(probe, (c128*)o->coarse.coef, o->cdims[0], o->cdims[1],
                                                          o->cdims[2]);
@@ -372,6 +563,18 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
         rc = cuda_check(ctx, cudaStreamSynchronize(st), "coarse operator");
         cfree();
         if (rc) return fail(rc);
+        if (d->coarse_iters > 0) {
+            if ((rc = setup_coarse_dd(o, cuts))) return fail(rc);
+            cudaEventRecord(e1, st);
+            if ((rc = cuda_check(ctx, cudaEventSynchronize(e1), "oras_factor"))) return fail(rc);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            o->setup_s = ms * 1e-3;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            *out = o;
+            return HELM_OK;
+        }
         if ((rc = planeset_factor(ctx, o->coarse, &singular))) return fail(rc);
         if (singular) return fail(set_error(ctx, HELM_ESINGULAR, "oras_factor: zero pivot in the coarse factor"));
         if (o->fine.prec != HELM_PREC_FP64) {
@@ -413,7 +616,7 @@ static void free_scratch(helm_oras o) {
     dev_free(ctx, o->loc, (size_t)o->fine.nloc * R * fe);
     dev_free(ctx, o->rbuf, (size_t)rbuf_planes(o) * o->fine.m_max * R * fe);
     dev_free(ctx, o->cvec, (size_t)o->nc * R * sizeof(c128));
-    dev_free(ctx, o->crbuf, (size_t)9 * o->coarse.m_max * R * sizeof(c128));
+    if (o->d.coarse_iters == 0) dev_free(ctx, o->crbuf, (size_t)9 * o->coarse.m_max * R * sizeof(c128));
     dev_free(ctx, o->qf, (size_t)o->g->n * R * we);
     dev_free(ctx, o->tf, (size_t)o->g->n * R * we);
     dev_free(ctx, o->tcb, (size_t)o->fine.nbox * o->tc_npad * 2 * o->fine.ld * tc_elem(o));
@@ -423,6 +626,11 @@ static void free_scratch(helm_oras o) {
     o->tc_npad = 0;
     o->loc = o->rbuf = o->qf = o->tf = nullptr;
     o->cvec = o->crbuf = nullptr;
+    dev_free(ctx, o->cy, (size_t)o->nc * R * sizeof(c128));
+    dev_free(ctx, o->cloc, (size_t)o->cdd.nloc * R * sizeof(c128));
+    dev_free(ctx, o->crb, (size_t)o->cdd.nbox * o->cdd.m_max * R * sizeof(c128));
+    o->cy = o->cloc = o->crb = nullptr;
+    inner_free(o);
     o->cap_nrhs = 0;
 }
 
@@ -431,6 +639,7 @@ static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
     helm_ctx ctx = o->g->ctx;
     cudaStreamSynchronize(ctx->stream);
     free_scratch(o);
+    o->scratch_gen++;   // graphs captured over the old buffers are stale
     const size_t fe = o->fine.cesize();
     const size_t we = wp == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
     o->cap_nrhs = nrhs;
@@ -448,10 +657,18 @@ static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
     if (o->nc) {
         HELM_TRY(dev_alloc(ctx, (void**)&o->cvec, (size_t)o->nc * R * sizeof(c128), "coarse vector"));
         // coarse sweep buffer: the prepared plane plus 8 split-K partial planes
-        HELM_TRY(dev_alloc(ctx, (void**)&o->crbuf, (size_t)9 * o->coarse.m_max * R * sizeof(c128),
-                           "coarse sweep buffer"));
+        if (o->d.coarse_iters == 0)
+            HELM_TRY(dev_alloc(ctx, (void**)&o->crbuf, (size_t)9 * o->coarse.m_max * R * sizeof(c128),
+                               "coarse sweep buffer"));
         HELM_TRY(dev_alloc(ctx, &o->qf, (size_t)o->g->n * R * we, "coarse correction"));
         HELM_TRY(dev_alloc(ctx, &o->tf, (size_t)o->g->n * R * we, "coarse residual"));
+    }
+    if (o->d.coarse_iters > 0) {
+        HELM_TRY(dev_alloc(ctx, &o->cy, (size_t)o->nc * R * sizeof(c128), "inner coarse solution"));
+        HELM_TRY(dev_alloc(ctx, &o->cloc, (size_t)o->cdd.nloc * R * sizeof(c128), "coarse local vectors"));
+        HELM_TRY(dev_alloc(ctx, &o->crb, (size_t)o->cdd.nbox * o->cdd.m_max * R * sizeof(c128),
+                           "coarse sweep buffer (subdomains)"));
+        HELM_TRY(inner_alloc(o, wp, R));
     }
     return HELM_OK;
 }
@@ -474,26 +691,35 @@ helm_status apply_t(helm_oras o, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
         const int r = o->d.coarse_ratio;
         const int cx = o->cdims[0], cy = o->cdims[1], cz = o->cdims[2];
         const double vb = (double)N * nrhs * sizeof(cplx<TV>);
-        int tk = prof_begin(ctx, "coarse_transfer");
-        if (o->coarse32.G) {
-            coarse_restrict<TV, float><<<grid_for(o->nc * nrhs), 256, 0, st>>>(v, (c64*)o->cvec, nx, ny, nz, cx, cy,
-                                                                                cz, r, nrhs);
+        // the restriction's intermediates live in tf and qf, free until the prolongation and t = v - A q
+        cplx<TV>* t1 = (cplx<TV>*)o->tf;
+        cplx<TV>* t2 = (cplx<TV>*)o->qf;
+        int tk = prof_begin(ctx, "coarse_restrict");
+        if (o->d.coarse_iters > 0) {
+            // the paper's inexact coarse solve: coarse_iters GMRES steps with one-level ORAS on the coarse grid
+            restrict_separable<TV, TV>(v, t1, t2, (cplx<TV>*)o->cvec, nx, ny, nz, cx, cy, cz, r, nrhs, st);
             prof_end(ctx, tk, vb);
-            HELM_TRY(planeset_solve(ctx, o->coarse32, o->cvec, o->crbuf, nrhs, st));
-            tk = prof_begin(ctx, "coarse_transfer");
-            coarse_prolong<float, TV><<<grid_for(N * nrhs), 256, 0, st>>>((const c64*)o->cvec, (cplx<TV>*)o->qf, nx,
-                                                                           ny, nz, cx, cy, cz, r, nrhs);
+            HELM_TRY(inner_solve(o, wp, o->cvec, o->cy, nrhs));
+            tk = prof_begin(ctx, "coarse_prolong");
+            coarse_prolong<TV, TV><<<dim3((unsigned)((nx * nrhs + 255) / 256), (unsigned)ny, (unsigned)nz), 256, 0,
+                                     st>>>((const cplx<TV>*)o->cy, (cplx<TV>*)o->qf, nx, ny, nz, cx, cy, cz, r, nrhs);
+        } else if (o->coarse32.G) {
+            restrict_separable<TV, float>(v, t1, t2, (c64*)o->cvec, nx, ny, nz, cx, cy, cz, r, nrhs, st);
+            prof_end(ctx, tk, vb);
+            HELM_TRY(planeset_solve(ctx, o->coarse32, o->cvec, o->crbuf, nrhs, st, o->dev_err));
+            tk = prof_begin(ctx, "coarse_prolong");
+            coarse_prolong<float, TV><<<dim3((unsigned)((nx * nrhs + 255) / 256), (unsigned)ny, (unsigned)nz), 256, 0,
+                                        st>>>((const c64*)o->cvec, (cplx<TV>*)o->qf, nx, ny, nz, cx, cy, cz, r, nrhs);
         } else {
-            coarse_restrict<TV, double><<<grid_for(o->nc * nrhs), 256, 0, st>>>(v, o->cvec, nx, ny, nz, cx, cy, cz, r,
-                                                                                 nrhs);
+            restrict_separable<TV, double>(v, t1, t2, o->cvec, nx, ny, nz, cx, cy, cz, r, nrhs, st);
             prof_end(ctx, tk, vb);
             HELM_TRY(planeset_solve(ctx, o->coarse, o->cvec, o->crbuf, nrhs, st));
-            tk = prof_begin(ctx, "coarse_transfer");
-            coarse_prolong<double, TV><<<grid_for(N * nrhs), 256, 0, st>>>(o->cvec, (cplx<TV>*)o->qf, nx, ny, nz, cx,
-                                                                            cy, cz, r, nrhs);
+            tk = prof_begin(ctx, "coarse_prolong");
+            coarse_prolong<double, TV><<<dim3((unsigned)((nx * nrhs + 255) / 256), (unsigned)ny, (unsigned)nz), 256, 0,
+                                         st>>>(o->cvec, (cplx<TV>*)o->qf, nx, ny, nz, cx, cy, cz, r, nrhs);
         }
         prof_end(ctx, tk, vb);
-        ctx->launches += 2;
+        ctx->launches += 4;
         HELM_TRY(launch_stencil_sub(g, wp, o->qf, v, o->tf, nrhs, st));   // t = v - A q
         src = (const cplx<TV>*)o->tf;
         q = (const cplx<TV>*)o->qf;
@@ -504,8 +730,13 @@ helm_status apply_t(helm_oras o, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
     int tr = prof_begin(ctx, "oras_transfer");
     // the tensor-core sweeps keep b apart (o->lb): their forward step overwrites loc while others read b
     cplx<TL>* rdst = (cplx<TL>*)(o->fine.padded ? o->lb : o->loc);
-    restrict_boxes<TV, TL><<<dim3(grid_for(mx, 256, 4096), o->fine.nbox), 256, 0, st>>>(o->fine.dbox, src, rdst, nx,
-                                                                                         ny, nrhs);
+    int bxm = 0, rows = 0;
+    for (auto& b : o->fine.hbox) {
+        bxm = std::max(bxm, b.dims[0]);
+        rows = std::max(rows, b.dims[1] * b.dims[2]);
+    }
+    restrict_boxes<TV, TL><<<dim3((unsigned)((bxm * nrhs + 255) / 256), (unsigned)std::min(rows, 65535), o->fine.nbox),
+                             256, 0, st>>>(o->fine.dbox, src, rdst, nx, ny, nrhs);
     prof_end(ctx, tr, lb);
     ctx->launches++;
     if (o->fine.padded)
@@ -513,12 +744,13 @@ helm_status apply_t(helm_oras o, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
     else
         HELM_TRY(planeset_solve(ctx, o->fine, o->loc, o->rbuf, nrhs, st));
     tr = prof_begin(ctx, "oras_transfer");
+    const dim3 lgrid((unsigned)((nx * nrhs + 255) / 256), (unsigned)ny, (unsigned)nz);   // (x-line chunks, y, z)
     if (q)
-        prolong_owner<TL, TV, true><<<grid_for(N * nrhs), 256, 0, st>>>(
-            o->fine.dbox, o->owner, (const cplx<TL>*)o->loc, q, out, nx, ny, nz, o->d.px, o->d.py, nrhs);
+        prolong_owner<TL, TV, true><<<lgrid, 256, 0, st>>>(o->fine.dbox, o->owner, (const cplx<TL>*)o->loc, q, out,
+                                                           nx, ny, nz, o->d.px, o->d.py, nrhs);
     else
-        prolong_owner<TL, TV, false><<<grid_for(N * nrhs), 256, 0, st>>>(
-            o->fine.dbox, o->owner, (const cplx<TL>*)o->loc, nullptr, out, nx, ny, nz, o->d.px, o->d.py, nrhs);
+        prolong_owner<TL, TV, false><<<lgrid, 256, 0, st>>>(o->fine.dbox, o->owner, (const cplx<TL>*)o->loc, nullptr,
+                                                            out, nx, ny, nz, o->d.px, o->d.py, nrhs);
     prof_end(ctx, tr, (double)N * nrhs * (sizeof(cplx<TL>) + (q ? 2 : 1) * sizeof(cplx<TV>)));
     ctx->launches++;
     return cuda_check(ctx, cudaGetLastError(), "oras apply");
@@ -535,6 +767,54 @@ helm_status oras_apply_wp(helm_oras o, int wp, const void* v, void* out, int nrh
     }
     if (f64) return apply_t<float, double>(o, (const c64*)v, (c64*)out, nrhs);
     return apply_t<float, float>(o, (const c64*)v, (c64*)out, nrhs);
+}
+
+namespace {
+
+template <typename TV, typename TL>
+helm_status coarse_dd_t(helm_oras o, const PlaneSet& P, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
+    helm_ctx ctx = o->g->ctx;
+    cudaStream_t st = ctx->stream;
+    const int cx = o->cdims[0], cy = o->cdims[1], cz = o->cdims[2];
+    int bxm = 0, rows = 0;
+    for (auto& b : P.hbox) {
+        bxm = std::max(bxm, b.dims[0]);
+        rows = std::max(rows, b.dims[1] * b.dims[2]);
+    }
+    restrict_boxes<TV, TL><<<dim3((unsigned)((bxm * nrhs + 255) / 256), (unsigned)std::min(rows, 65535), P.nbox), 256, 0,
+                             st>>>(P.dbox, v, (cplx<TL>*)o->cloc, cx, cy, nrhs);
+    ctx->launches++;
+    HELM_TRY(planeset_solve(ctx, P, o->cloc, o->crb, nrhs, st));
+    prolong_owner<TL, TV, false><<<dim3((unsigned)((cx * nrhs + 255) / 256), (unsigned)cy, (unsigned)cz), 256, 0, st>>>(
+        P.dbox, o->cowner, (const cplx<TL>*)o->cloc, nullptr, out, cx, cy, cz, o->d.px, o->d.py, nrhs);
+    ctx->launches++;
+    return cuda_check(ctx, cudaGetLastError(), "coarse subdomain solve");
+}
+
+}  // namespace
+
+helm_status coarse_dd_apply(helm_oras o, int wp, const void* v, void* out, int nrhs) {
+    const PlaneSet& P = o->cdd32.G ? o->cdd32 : o->cdd;
+    const bool l64 = P.prec == HELM_PREC_FP64;
+    if (wp == HELM_PREC_FP64)
+        return l64 ? coarse_dd_t<double, double>(o, P, (const c128*)v, (c128*)out, nrhs)
+                   : coarse_dd_t<double, float>(o, P, (const c128*)v, (c128*)out, nrhs);
+    return l64 ? coarse_dd_t<float, double>(o, P, (const c64*)v, (c64*)out, nrhs)
+               : coarse_dd_t<float, float>(o, P, (const c64*)v, (c64*)out, nrhs);
+}
+
+helm_status coarse_E_apply(helm_oras o, int wp, const void* x, void* y, int nrhs) {
+    helm_ctx ctx = o->g->ctx;
+    const int cx = o->cdims[0], cy = o->cdims[1], cz = o->cdims[2];
+    const dim3 grid((unsigned)((cx * nrhs + 255) / 256), (unsigned)cy, (unsigned)cz);
+    if (wp == HELM_PREC_FP64)
+        e27_apply<double><<<grid, 256, 0, ctx->stream>>>((const c128*)o->coarse.coef, (const c128*)x, (c128*)y, cx, cy,
+                                                         cz, nrhs);
+    else
+        e27_apply<float><<<grid, 256, 0, ctx->stream>>>((const c64*)o->Ecoef32, (const c64*)x, (c64*)y, cx, cy, cz,
+                                                        nrhs);
+    ctx->launches++;
+    return cuda_check(ctx, cudaGetLastError(), "coarse operator apply");
 }
 
 extern "C" helm_status oras_apply(helm_oras o, const void* v, void* out, int nrhs) {
@@ -566,10 +846,16 @@ extern "C" void oras_destroy(helm_oras o) {
     if (!o) return;
     helm_ctx ctx = o->g->ctx;
     cudaStreamSynchronize(ctx->stream);
+    delete o->kcache;
+    o->kcache = nullptr;
     free_scratch(o);
     planeset_free(ctx, o->fine);
     planeset_free(ctx, o->coarse);
     planeset_free(ctx, o->coarse32);
+    planeset_free(ctx, o->cdd);
+    planeset_free(ctx, o->cdd32);
+    dev_free(ctx, o->cowner, (size_t)(o->cdims[0] + o->cdims[1] + o->cdims[2]) * sizeof(int));
+    dev_free(ctx, o->Ecoef32, (size_t)o->nc * 27 * sizeof(c64));
     const int n = o->g->d.nx + o->g->d.ny + o->g->d.nz;
     dev_free(ctx, o->owner, n * sizeof(int));
     dev_free(ctx, o->dev_err, sizeof(int));
@@ -600,6 +886,25 @@ __global__ void widen_bf16(const __nv_bfloat162* __restrict__ a, c128* __restric
 }
 
 // b[r * m + j] = a[r * ld + j] widened, for an m x m plane stored with row pitch ld
+// entry (r, j) of a plane in the tensor-core tile layout (esz-byte entries, pk_chunks chunks per row)
+template <typename T>
+__device__ __forceinline__ const T* packed_at(const T* plane, int r, int j, int chunks) {
+    const long long off = (long long)j * sizeof(T);
+    const long long line = ((long long)(r / 128) * chunks + off / 128) * 128 + (r % 128);
+    return reinterpret_cast<const T*>(reinterpret_cast<const unsigned char*>(plane) + line * 128 + off % 128);
+}
+__global__ void widen_packed_c64(const c64* __restrict__ a, c128* __restrict__ b, int m, int chunks) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)m * m) return;
+    const c64 v = *packed_at(a, (int)(i / m), (int)(i % m), chunks);
+    b[i] = mk<double>(v.x, v.y);
+}
+__global__ void widen_packed_bf16(const __nv_bfloat162* __restrict__ a, c128* __restrict__ b, int m, int chunks) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)m * m) return;
+    const float2 v = __bfloat1622float2(*packed_at(a, (int)(i / m), (int)(i % m), chunks));
+    b[i] = mk<double>(v.x, v.y);
+}
 __global__ void widen_c64(const c64* __restrict__ a, c128* __restrict__ b, int m, int ld) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)m * m) return;
@@ -626,6 +931,14 @@ extern "C" helm_status oras_plane_inverse(helm_oras o, int box, int plane, void*
     if (o->fine.prec == HELM_PREC_FP64) {
         cudaMemcpy2DAsync(dst, B.m * sizeof(c128), (c128*)o->fine.G + off, B.ld * sizeof(c128), B.m * sizeof(c128), B.m,
                           cudaMemcpyDeviceToDevice, ctx->stream);
+    } else if (o->fine.packed && o->fine.prec == HELM_PREC_BF16) {
+        widen_packed_bf16<<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>(
+            (const __nv_bfloat162*)o->fine.G + off, dst, B.m, o->fine.pk_chunks);
+        ctx->launches++;
+    } else if (o->fine.packed) {
+        widen_packed_c64<<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>((c64*)o->fine.G + off, dst, B.m,
+                                                                                o->fine.pk_chunks);
+        ctx->launches++;
     } else if (o->fine.prec == HELM_PREC_BF16) {
         widen_bf16<<<(unsigned)((mm + 255) / 256), 256, 0, ctx->stream>>>((const __nv_bfloat162*)o->fine.G + off, dst,
                                                                           B.m, B.ld);
@@ -673,6 +986,8 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     if (nrhs == 0) return HELM_OK;
     if (v == out) return set_error(ctx, HELM_EINVAL, "oras_apply_noalloc: v and out must differ");
     if (ctx->device < 0 || ctx->device >= 64) return set_error(ctx, HELM_EINVAL, "oras_apply_noalloc: device id");
+    if (o->d.coarse_iters > 0)
+        return set_error(ctx, HELM_EINVAL, "oras_apply_noalloc: not available with the inexact coarse solve");
     HELM_CUDA(ctx, cudaSetDevice(ctx->device));
     // working vectors, carved from the static array (complex128 work precision)
     const size_t fe = o->fine.cesize();
@@ -760,7 +1075,7 @@ size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int
                 planes += dims[2];
             }
     const size_t ld = padded ? (m_max + 15) / 16 * 16 : 0;
-    for (auto& b : boxes) fac += (padded ? ld * ld : b.first * b.first) * b.second;
+    for (auto& b : boxes) fac += (padded ? (size_t)padded_pstride((int)ld) : b.first * b.first) * b.second;
     size_t bytes = fac * fe + nloc * 27 * fe;
     const size_t N = (size_t)g.nx * g.ny * g.nz;
     const size_t R = (size_t)std::max(1, nrhs);
@@ -774,9 +1089,39 @@ size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int
             if (a < 2) cm *= ca;
         }
         const size_t cz = nc / cm;
-        bytes += (cm * cm * cz + nc * 27) * (sizeof(c128) + sizeof(c64));   // FP64 factors and the complex64 copy
         bytes += 2 * N * 27 * sizeof(c128);                                  // probing vectors during set-up
-        bytes += nc * R * sizeof(c128) + 9 * cm * R * sizeof(c128) + 2 * N * R * sizeof(c128);
+        bytes += nc * R * sizeof(c128) + 2 * N * R * sizeof(c128);
+        if (d.coarse_iters == 0) {
+            bytes += (cm * cm * cz + nc * 27) * (sizeof(c128) + sizeof(c64));   // FP64 factors and the complex64 copy
+            bytes += 9 * cm * R * sizeof(c128);
+        } else {
+            // E (FP64 and complex64), the coarse subdomain factors (FP64 and copy), their scratch, the inner basis
+            size_t cfac = 0, cloc = 0, cmx = 0;
+            const int r = d.coarse_ratio;
+            for (int tz = 0; tz < p[2]; ++tz)
+                for (int ty = 0; ty < p[1]; ++ty)
+                    for (int tx = 0; tx < p[0]; ++tx) {
+                        const int t[3] = {tx, ty, tz};
+                        size_t dims[3];
+                        for (int a = 0; a < 3; ++a) {
+                            const int ca = (n[a] - 1 + r - 1) / r + 1;
+                            auto cut = [&](int q) {
+                                return q == 0 ? 0 : (q == p[a] ? ca : (int)(((long long)q * n[a] / p[a] + r - 1) / r));
+                            };
+                            const int c0 = cut(t[a]), c1 = cut(t[a] + 1);
+                            const int lo = c0 > 0 ? std::max(0, c0 - d.coarse_overlap) : 0;
+                            const int hi = c1 < ca ? std::min(ca, c1 + d.coarse_overlap) : ca;
+                            dims[a] = (size_t)std::max(0, hi - lo);
+                        }
+                        const size_t m = dims[0] * dims[1];
+                        cfac += m * m * dims[2];
+                        cloc += m * dims[2];
+                        cmx = std::max(cmx, m);
+                    }
+            bytes += nc * 27 * (sizeof(c128) + sizeof(c64)) + (cfac + cloc * 27) * (sizeof(c128) + sizeof(c64));
+            bytes += (nc + cloc + boxes.size() * cmx) * R * sizeof(c128);
+            bytes += ((size_t)d.coarse_iters + 3) * nc * R * sizeof(c128);
+        }
     }
     return bytes + bytes / 16;
 }

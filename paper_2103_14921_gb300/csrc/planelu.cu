@@ -335,24 +335,24 @@ __global__ void sweep_prep(const BoxInfo* __restrict__ boxes, const cplx<T>* __r
             rb[e] = acc;
             continue;
         }
+        // all 18 loads first: a coupling that points out of the box has a zero coefficient (the fold moved
+        // it), so its neighbour index is clamped into the box
         const int px = p % bx, py = p / bx;
         const cplx<T>* cp = coef + (plane + p) * 27 + off;
+        cplx<T> c[9], v[9];
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int qy = py + dy;
-            if (qy < 0 || qy >= by) continue;
+        for (int d = 0; d < 9; ++d) {
+            const int qx = min(max(px + d % 3 - 1, 0), bx - 1), qy = min(max(py + d / 3 - 1, 0), by - 1);
+            c[d] = cp[d];
+            v[d] = loc[(nbr + qy * bx + qx) * nrhs + r];
+        }
 #pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int qx = px + dx;
-                if (qx < 0 || qx >= bx) continue;
-                const cplx<T> c = cp[(dy + 1) * 3 + (dx + 1)];
-                const cplx<T> v = loc[(nbr + qy * bx + qx) * nrhs + r];
-                if (FWD) {
-                    acc.x -= c.x * v.x - c.y * v.y;
-                    acc.y -= c.x * v.y + c.y * v.x;
-                } else {
-                    cmac(acc, c, v);
-                }
+        for (int d = 0; d < 9; ++d) {
+            if (FWD) {
+                acc.x -= c[d].x * v[d].x - c[d].y * v[d].y;
+                acc.y -= c[d].x * v[d].y + c[d].y * v[d].x;
+            } else {
+                cmac(acc, c[d], v[d]);
             }
         }
         rb[e] = acc;
@@ -608,11 +608,11 @@ void launch_sweep_rn(const PlaneSet& P, cplx<T>* loc, cplx<T>* rbuf, int nrhs, c
             const int fwd = pass == 0;
             for (int s = fwd ? 0 : 1; s < P.bz_max; ++s) {
                 step_bytes(s, fwd, gb, pb);
-                int t = prof_begin(ctx, "sweep_prep");
+                int t = prof_begin(ctx, "coarse_prep");
                 if (fwd) sweep_prep<T, true><<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, rbuf, m, nrhs, s);
                 else sweep_prep<T, false><<<pgrid, 256, 0, st>>>(P.dbox, coef, loc, rbuf, m, nrhs, s);
                 prof_end(ctx, t, pb);
-                t = prof_begin(ctx, "sweep_gemv");
+                t = prof_begin(ctx, "coarse_sweep");
                 sweep_gemv_splitk<T, RN><<<sgrid, 256, ssm, st>>>(P.dbox, G, rbuf, part, m, nrhs, s, fwd, rows);
                 sweep_reduce<T><<<rblocks, 256, 0, st>>>(P.dbox, part, loc, m, nrhs, s, fwd);
                 prof_end(ctx, t, gb);
@@ -680,7 +680,7 @@ helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P) {
         b.fac_off = (long long)fac;
         b.plane0 = planes;
         b.ld = P.padded ? P.ld : b.m;
-        b.pstride = P.padded ? (long long)P.ld * P.ld : (long long)b.m * b.m;
+        b.pstride = P.padded ? padded_pstride(P.ld) : (long long)b.m * b.m;
         loc += (long long)b.m * b.dims[2];
         fac += (size_t)b.pstride * b.dims[2];
         planes += b.dims[2];
@@ -691,6 +691,7 @@ helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P) {
     HELM_TRY(dev_alloc(ctx, (void**)&P.dbox, P.nbox * sizeof(BoxInfo), "box table"));
     HELM_CUDA(ctx, cudaMemcpy(P.dbox, P.hbox.data(), P.nbox * sizeof(BoxInfo), cudaMemcpyHostToDevice));
     HELM_TRY(dev_alloc(ctx, &P.coef, (size_t)P.nloc * 27 * P.cesize(), "local operator coefficients"));
+    if (P.coef_only) return HELM_OK;
     HELM_TRY(dev_alloc(ctx, &P.G, P.fac_entries * P.esize(), "plane factors"));
     if (P.padded) HELM_CUDA(ctx, cudaMemsetAsync(P.G, 0, P.fac_entries * P.esize(), ctx->stream));
     return HELM_OK;
@@ -731,7 +732,13 @@ helm_status planeset_to_bf16(helm_ctx ctx, PlaneSet& P) {
     return HELM_OK;
 }
 
-helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st) {
+helm_status planeset_solve(helm_ctx ctx, const PlaneSet& P, void* loc, void* rbuf, int nrhs, cudaStream_t st,
+                           int* err) {
     if (P.prec == HELM_PREC_FP64) return solve_t<double>(ctx, P, (c128*)loc, (c128*)rbuf, nrhs, st);
+    if (err && ctx->coarse_coop) {
+        bool done = false;
+        HELM_TRY(planeset_solve_coop(ctx, P, (c64*)loc, (c64*)rbuf, nrhs, st, err, &done));
+        if (done) return HELM_OK;
+    }
     return solve_t<float>(ctx, P, (c64*)loc, (c64*)rbuf, nrhs, st);
 }

@@ -42,10 +42,22 @@ void prof_drain(helm_ctx ctx) {
     P.pending.clear();
 }
 
+constexpr int CAPTURED = 1 << 30;   // token flag: the record lives in P.capture
+
 int prof_begin(helm_ctx ctx, const char* family) {
     Profiler& P = ctx->prof;
     if (!P.on) return -1;
     if (!P.only.empty() && std::find(P.only.begin(), P.only.end(), family) == P.only.end()) return -1;
+    if (P.capture) {
+        ProfRecord r;
+        r.family = family_index(P, family);
+        r.a = take_event(P);
+        r.b = take_event(P);
+        r.bytes = 0;
+        cudaEventRecordWithFlags(r.a, ctx->stream, cudaEventRecordExternal);
+        P.capture->push_back(r);
+        return CAPTURED | (int)(P.capture->size() - 1);
+    }
     if (P.pending.size() > 4096) prof_drain(ctx);
     ProfRecord r;
     r.family = family_index(P, family);
@@ -60,14 +72,53 @@ int prof_begin(helm_ctx ctx, const char* family) {
 void prof_end(helm_ctx ctx, int token, double bytes) {
     if (token < 0) return;
     Profiler& P = ctx->prof;
+    if (token & CAPTURED) {
+        ProfRecord& r = (*P.capture)[token & ~CAPTURED];
+        r.bytes = bytes;
+        cudaEventRecordWithFlags(r.b, ctx->stream, cudaEventRecordExternal);
+        return;
+    }
     P.pending[token].bytes = bytes;
     cudaEventRecord(P.pending[token].b, ctx->stream);
+}
+
+void prof_reserve(helm_ctx ctx, size_t n) {
+    Profiler& P = ctx->prof;
+    while (P.pool.size() < n) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) break;
+        P.pool.push_back(e);
+    }
+}
+
+void prof_harvest(helm_ctx ctx, const std::vector<ProfRecord>& recs) {
+    Profiler& P = ctx->prof;
+    for (const auto& r : recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            P.launches[r.family] += 1;
+            P.ms[r.family] += ms;
+            P.bytes[r.family] += r.bytes;
+        }
+    }
+}
+
+void prof_release(helm_ctx ctx, std::vector<ProfRecord>& recs) {
+    Profiler& P = ctx->prof;
+    for (auto& r : recs) {
+        P.pool.push_back(r.a);
+        P.pool.push_back(r.b);
+    }
+    recs.clear();
 }
 
 extern "C" helm_status helm_profile_enable(helm_ctx ctx, int on) {
     if (!ctx) return HELM_EINVAL;
     prof_drain(ctx);
     Profiler& P = ctx->prof;
+    // graphs captured while profiling was off lack the event nodes; graphs that have them keep
+    // recording while profiling is off, harmlessly (nothing harvests them)
+    if (on && !P.on) ctx->graph_gen++;
     P.on = on != 0;
     if (P.on)
         for (size_t i = 0; i < P.names.size(); ++i) {
@@ -96,17 +147,18 @@ extern "C" helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64
 extern "C" helm_status helm_profile_select(helm_ctx ctx, const char* families) {
     if (!ctx) return HELM_EINVAL;
     Profiler& P = ctx->prof;
-    P.only.clear();
-    if (!families) return HELM_OK;
+    std::vector<std::string> only;
     std::string cur;
-    for (const char* c = families;; ++c) {
+    for (const char* c = families ? families : "";; ++c) {
         if (*c == ',' || *c == 0) {
-            if (!cur.empty()) P.only.push_back(cur);
+            if (!cur.empty()) only.push_back(cur);
             cur.clear();
             if (!*c) break;
         } else if (*c != ' ') {
             cur.push_back(*c);
         }
     }
+    if (only != P.only) ctx->graph_gen++;   // captured graphs hold event nodes for the old selection
+    P.only = only;
     return HELM_OK;
 }

@@ -55,7 +55,8 @@ bool same_grid(const helm_grid_desc& a, const helm_grid_desc& b) {
 }
 bool same_oras(const helm_oras_desc& a, const helm_oras_desc& b) {
     return a.px == b.px && a.py == b.py && a.pz == b.pz && a.overlap == b.overlap && a.coarse_ratio == b.coarse_ratio &&
-           a.interface_bc == b.interface_bc && a.factor_prec == b.factor_prec;
+           a.interface_bc == b.interface_bc && a.factor_prec == b.factor_prec && a.coarse_iters == b.coarse_iters &&
+           (a.coarse_iters == 0 || a.coarse_overlap == b.coarse_overlap);
 }
 
 struct FactorSet {

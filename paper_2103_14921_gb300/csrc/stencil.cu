@@ -17,9 +17,12 @@
 //   A = e_y e_z + a2 (Y e_z + e_y Z) + a3 Y Z,  B = Y e_z + e_y Z + a2 Y Z
 // give the Laplacian coefficient X_dx A + [dx == 0] B, and likewise for the
 // real mass coefficient.  Each thread owns one node and RCH consecutive
-// right-hand sides (rhs fastest across threads, so warps read contiguous
-// memory); the coefficient is formed once per neighbour and reused for the
-// RCH columns.
+// right-hand sides, rhs fastest across threads (complex64: RCH = 2, one
+// 16-byte vector per thread, so every neighbour load of a warp covers 512
+// contiguous bytes; complex128: RCH up to 4, as the FP64 arithmetic and not
+// the loads bounds it).  The coefficient is formed once per neighbour and
+// reused for the RCH columns.  The grid is (x-line chunks, y, z), so no
+// thread divides 64-bit indices.
 #include "internal.h"
 
 namespace {
@@ -35,22 +38,31 @@ struct Interior {
     double Lc[4], Mc[4];
 };
 
-template <typename T, int RCH, bool SUB, bool REALK>
+// RCH consecutive complex values loaded or stored as one aligned vector
+template <typename T, int RCH>
+struct __align__(2 * sizeof(T) * RCH) CPack {
+    cplx<T> v[RCH];
+};
+
+// NR > 0: the column count as a compile-time constant (neighbour addresses become immediate offsets)
+template <typename T, int RCH, bool SUB, bool REALK, int NR>
 __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict__ u, const cplx<T>* __restrict__ b,
                                                       cplx<T>* __restrict__ y,
                                                       const cplx<T>* __restrict__ k2,
                                                       const cplx<T>* __restrict__ tab, int nx, int ny, int nz,
-                                                      int nrhs, StencilW w, Interior in) {
+                                                      int nrhs_rt, StencilW w, Interior in) {
+    // grid: (x-line chunks, y, z); a thread owns node (i, j, k) and columns [ch RCH, ch RCH + RCH)
+    const int nrhs = NR > 0 ? NR : nrhs_rt;
     const int nch = nrhs / RCH;
-    const long long total = (long long)nx * ny * nz * nch;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const int ch = (int)(t % nch);
-    const long long p = t / nch;
-    const int i = (int)(p % nx);
-    const long long tmp = p / nx;
-    const int j = (int)(tmp % ny);
-    const int k = (int)(tmp / ny);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nx * nch) return;
+    const int ch = t % nch, i = t / nch;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long p = ((long long)k * ny + j) * nx + i;
+    // neighbour offsets: nodes for k^2, entries for the vectors
+    const long long nxy = (long long)nx * ny;
+    const cplx<T>* up = u + p * nrhs + (long long)ch * RCH;
+    const cplx<T>* kp = k2 + p;
 
     const T ih2 = (T)w.inv_h2;
     const cplx<T> zero = mk<T>(0, 0);
@@ -65,30 +77,34 @@ __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict_
             L[c] = (T)(in.Lc[c] * w.inv_h2);
             M[c] = (T)in.Mc[c];
         }
+        // one z-plane of 9 neighbours at a time: its 18 loads are issued together, then the FMAs
 #pragma unroll
-        for (int dz = -1; dz <= 1; ++dz)
+        for (int dz = -1; dz <= 1; ++dz) {
+            cplx<T> kq[9];
+            CPack<T, RCH> uq[9];
 #pragma unroll
-            for (int dy = -1; dy <= 1; ++dy)
+            for (int d = 0; d < 9; ++d) {
+                const long long dq = dz * nxy + (d / 3 - 1) * nx + (d % 3 - 1);
+                kq[d] = kp[dq];
+                uq[d] = *reinterpret_cast<const CPack<T, RCH>*>(up + dq * nrhs);
+            }
 #pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int cls = (dx != 0) + (dy != 0) + (dz != 0);
-                    const long long q = ((long long)(k + dz) * ny + (j + dy)) * nx + (i + dx);
-                    const cplx<T> kq = k2[q];
-                    const cplx<T>* uq = u + q * nrhs + (long long)ch * RCH;
-                    if (REALK) {
-                        const T cr = L[cls] + M[cls] * kq.x;
+            for (int d = 0; d < 9; ++d) {
+                const int cls = (d % 3 != 1) + (d / 3 != 1) + (dz != 0);
+                if (REALK) {
+                    const T cr = L[cls] + M[cls] * kq[d].x;
 #pragma unroll
-                        for (int r = 0; r < RCH; ++r) {
-                            const cplx<T> v = uq[r];
-                            acc[r].x = fma(cr, v.x, acc[r].x);
-                            acc[r].y = fma(cr, v.y, acc[r].y);
-                        }
-                    } else {
-                        const cplx<T> cc = mk<T>(L[cls] + M[cls] * kq.x, M[cls] * kq.y);
-#pragma unroll
-                        for (int r = 0; r < RCH; ++r) cmac(acc[r], cc, uq[r]);
+                    for (int r = 0; r < RCH; ++r) {
+                        acc[r].x = fma(cr, uq[d].v[r].x, acc[r].x);
+                        acc[r].y = fma(cr, uq[d].v[r].y, acc[r].y);
                     }
+                } else {
+                    const cplx<T> cc = mk<T>(L[cls] + M[cls] * kq[d].x, M[cls] * kq[d].y);
+#pragma unroll
+                    for (int r = 0; r < RCH; ++r) cmac(acc[r], cc, uq[d].v[r]);
                 }
+            }
+        }
     } else {
     const cplx<T>* tx = tab + 3 * i;
     const cplx<T>* ty = tab + 3 * (nx + j);
@@ -128,49 +144,62 @@ __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict_
                 cplx<T> lap = X[dx + 1] * Ac;
                 T mass = ((dx == 0) ? (T)-2 : (T)1) * Am;
                 if (dx == 0) { lap = lap + Bc; mass += Bm; }
-                const long long q = ((long long)kk * ny + jj) * nx + ii;
-                const cplx<T> kq = k2[q];
+                const long long dq = dz * nxy + dy * nx + dx;
+                const cplx<T> kq = kp[dq];
                 cplx<T> coef = mk<T>(lap.x * ih2 + mass * kq.x, lap.y * ih2 + mass * kq.y);
-                const cplx<T>* uq = u + q * nrhs + (long long)ch * RCH;
+                const CPack<T, RCH> uq = *reinterpret_cast<const CPack<T, RCH>*>(up + dq * nrhs);
 #pragma unroll
-                for (int r = 0; r < RCH; ++r) cmac(acc[r], coef, uq[r]);
+                for (int r = 0; r < RCH; ++r) cmac(acc[r], coef, uq.v[r]);
             }
         }
     }
     }
-    cplx<T>* yp = y + p * nrhs + (long long)ch * RCH;
+    CPack<T, RCH> out;
     if (SUB) {
-        const cplx<T>* bp = b + p * nrhs + (long long)ch * RCH;
+        const CPack<T, RCH> bp = *reinterpret_cast<const CPack<T, RCH>*>(b + p * nrhs + (long long)ch * RCH);
 #pragma unroll
-        for (int r = 0; r < RCH; ++r) yp[r] = bp[r] - acc[r];
+        for (int r = 0; r < RCH; ++r) out.v[r] = bp.v[r] - acc[r];
     } else {
 #pragma unroll
-        for (int r = 0; r < RCH; ++r) yp[r] = acc[r];
+        for (int r = 0; r < RCH; ++r) out.v[r] = acc[r];
     }
+    *reinterpret_cast<CPack<T, RCH>*>(y + p * nrhs + (long long)ch * RCH) = out;
 }
 
-template <typename T, int RCH, bool SUB>
+template <typename T, int RCH, bool SUB, int NR = 0>
 void launch_t(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab,
               const helm_grid_desc& d, int nrhs, const StencilW& w, const Interior& in, bool realk, cudaStream_t s) {
-    const long long total = (long long)d.nx * d.ny * d.nz * (nrhs / RCH);
     const int threads = 128;
-    const long long blocks = (total + threads - 1) / threads;
+    const dim3 grid((unsigned)((d.nx * (nrhs / RCH) + threads - 1) / threads), (unsigned)d.ny, (unsigned)d.nz);
     if (realk)
-        stencil_kernel<T, RCH, SUB, true><<<(unsigned)blocks, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz,
-                                                                              nrhs, w, in);
+        stencil_kernel<T, RCH, SUB, true, NR><<<grid, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w, in);
     else
-        stencil_kernel<T, RCH, SUB, false><<<(unsigned)blocks, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz,
-                                                                               nrhs, w, in);
+        stencil_kernel<T, RCH, SUB, false, NR><<<grid, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w,
+                                                                        in);
 }
 
 template <typename T, bool SUB>
 void dispatch(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab,
               const helm_grid_desc& d, int nrhs, const StencilW& w, const Interior& in, bool realk, cudaStream_t s) {
-    // at most 4 columns per thread: consecutive threads then read consecutive 32-byte pieces of a
-    // node's [rhs] row, so every neighbour load of a warp is a contiguous run
-    if (nrhs % 4 == 0) launch_t<T, 4, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
-    else if (nrhs % 2 == 0) launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
-    else launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+    // complex64: one 16-byte vector per thread and neighbour, two columns when the column count is
+    // even and every base address is 16-byte aligned, else one.  complex128 (FP64-pipe bound on this
+    // part): up to four columns per thread, so each neighbour's coefficient is formed once for four
+    // (a pack of RCH values is loaded as one aligned object: every base address must be aligned to it)
+    const auto al = [&](uintptr_t a) {
+        return ((uintptr_t)u & (a - 1)) == 0 && ((uintptr_t)y & (a - 1)) == 0 && (!SUB || ((uintptr_t)b & (a - 1)) == 0);
+    };
+    if constexpr (sizeof(T) == 4) {
+        if (nrhs == 16 && al(16))
+            launch_t<T, 2, SUB, 16>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+        else if (nrhs % 2 == 0 && al(16))
+            launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+        else
+            launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+    } else {
+        if (nrhs % 4 == 0 && al(64)) launch_t<T, 4, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+        else if (nrhs % 2 == 0 && al(32)) launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+        else launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+    }
 }
 
 Interior interior_of(helm_grid g) {
@@ -201,7 +230,7 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
     // algorithmic bytes: read u (and b), write y, read k^2 once
     const double es = prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
     const double bytes = (double)g->n * es * ((SUB ? 3.0 : 2.0) * nrhs + 1.0);
-    const int tok = prof_begin(g->ctx, "stencil");
+    const int tok = prof_begin(g->ctx, prec == HELM_PREC_FP64 ? "stencil64" : "stencil");
     const Interior in = interior_of(g);
     if (prec == HELM_PREC_FP64) {
         dispatch<double, SUB>((const c128*)u, (const c128*)b, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, in,

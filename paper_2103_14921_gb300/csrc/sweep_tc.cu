@@ -111,69 +111,81 @@ __global__ void __launch_bounds__(256) tc_prep(const BoxInfo* __restrict__ boxes
     }
 }
 
-// Variant without the shared-memory transpose: thread per (plane node, chunk of 4 right-hand sides),
-// the chunk index fastest, so the neighbour loads of a warp are contiguous 32-byte pieces; each
-// thread writes its 4 columns' (re, -im) and (im, re) pairs into rows 2r, 2r+1 of B^T.
+// Vectorised variant for an even column count: thread per (plane node, column pair), the pair
+// fastest, so each neighbour load of a warp is one 16-byte vector per thread over contiguous memory
+// (512 threads: one item each at 16 columns, so every thread waits on one round of loads);
+// the values of a tile of PREP2_TP nodes are transposed through shared memory ([nrhs][PREP2_TP + 1])
+// and written as (re, -im) and (im, re) pairs along rows 2r and 2r+1 of B^T.
+constexpr int PREP2_TP = 64;
+
+template <typename E> struct Pair2;
+template <> struct Pair2<float> {
+    typedef float2 type;
+    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Pair2<__nv_bfloat16> {
+    typedef __nv_bfloat162 type;
+    static __device__ __forceinline__ __nv_bfloat162 make(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
 template <typename E>
-__global__ void __launch_bounds__(256) tc_prep4(const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
+__global__ void __launch_bounds__(512) tc_prep2(const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
                                                 const c64* __restrict__ lb, const c64* __restrict__ loc,
                                                 E* __restrict__ bt, int ld2, int npad, int nrhs, int s, int fwd) {
+    extern __shared__ __align__(16) unsigned char prep_smem[];
+    c64* tile = reinterpret_cast<c64*>(prep_smem);   // [nrhs][PREP2_TP + 1]
     const BoxInfo B = boxes[blockIdx.y];
     const int m = B.m, bz = B.dims[2], bx = B.dims[0], by = B.dims[1];
     const int k = fwd ? s : bz - 1 - s;
     if (k < 0 || k >= bz || (!fwd && k == bz - 1)) return;
-    const int nch = nrhs >> 2;
+    const int p0 = blockIdx.x * PREP2_TP;
+    if (p0 >= m) return;
+    const int npair = nrhs >> 1;
     const long long plane = B.loc_off + (long long)k * m;
     const long long nbr = fwd ? plane - m : plane + m;
     const int off = fwd ? 0 : 18;
-    E* bb = bt + (size_t)blockIdx.y * npad * ld2;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * nch;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int ch = (int)(e % nch), p = (int)(e / nch);
-        const int r0 = 4 * ch;
-        c64 acc[4];
-        if (fwd) {
+    const bool couple = !(fwd && k == 0);
+    for (int e = threadIdx.x; e < PREP2_TP * npair; e += blockDim.x) {
+        const int pr = e % npair, pl = e / npair, p = p0 + pl;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);   // columns 2 pr and 2 pr + 1: (re, im, re, im)
+        if (p < m) {
+            if (fwd) acc = *reinterpret_cast<const float4*>(lb + (plane + p) * nrhs + 2 * pr);
+            if (couple) {
+                // all 18 loads first (one memory latency, not nine): a coupling that points out of the box
+                // has a zero coefficient (the fold moved it), so its neighbour index is clamped into the box
+                const int px = p % bx, py = p / bx;
+                const c64* cp = coef + (plane + p) * 27 + off;
+                c64 c[9];
+                float4 v[9];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = lb[(plane + p) * nrhs + r0 + q];
-        } else {
+                for (int d = 0; d < 9; ++d) {
+                    const int qx = min(max(px + d % 3 - 1, 0), bx - 1), qy = min(max(py + d / 3 - 1, 0), by - 1);
+                    c[d] = cp[d];
+                    v[d] = *reinterpret_cast<const float4*>(loc + (nbr + qy * bx + qx) * nrhs + 2 * pr);
+                }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = mk<float>(0, 0);
-        }
-        if (!(fwd && k == 0)) {
-            const int px = p % bx, py = p / bx;
-            const c64* cp = coef + (plane + p) * 27 + off;
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int qy = py + dy;
-                if (qy < 0 || qy >= by) continue;
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int qx = px + dx;
-                    if (qx < 0 || qx >= bx) continue;
-                    const c64 c = cp[(dy + 1) * 3 + (dx + 1)];
-                    const c64* v = loc + (nbr + qy * bx + qx) * nrhs + r0;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const c64 vq = v[q];
-                        if (fwd) {
-                            acc[q].x -= c.x * vq.x - c.y * vq.y;
-                            acc[q].y -= c.x * vq.y + c.y * vq.x;
-                        } else {
-                            cmac(acc[q], c, vq);
-                        }
-                    }
+                for (int d = 0; d < 9; ++d) {
+                    // forward: acc -= c v; backward: acc += c v
+                    const float sr = fwd ? -c[d].x : c[d].x, si = fwd ? -c[d].y : c[d].y;
+                    acc.x = fmaf(sr, v[d].x, fmaf(-si, v[d].y, acc.x));
+                    acc.y = fmaf(sr, v[d].y, fmaf(si, v[d].x, acc.y));
+                    acc.z = fmaf(sr, v[d].z, fmaf(-si, v[d].w, acc.z));
+                    acc.w = fmaf(sr, v[d].w, fmaf(si, v[d].z, acc.w));
                 }
             }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            E* re_row = bb + (size_t)(2 * (r0 + q)) * ld2 + 2 * p;
-            E* im_row = re_row + ld2;
-            re_row[0] = Elem<E>::from(acc[q].x);
-            re_row[1] = Elem<E>::from(-acc[q].y);
-            im_row[0] = Elem<E>::from(acc[q].y);
-            im_row[1] = Elem<E>::from(acc[q].x);
-        }
+        tile[(2 * pr) * (PREP2_TP + 1) + pl] = mk<float>(acc.x, acc.y);
+        tile[(2 * pr + 1) * (PREP2_TP + 1) + pl] = mk<float>(acc.z, acc.w);
+    }
+    __syncthreads();
+    E* bb = bt + (size_t)blockIdx.y * npad * ld2;
+    typedef typename Pair2<E>::type P2;
+    for (int e = threadIdx.x; e < nrhs * PREP2_TP; e += blockDim.x) {
+        const int r = e / PREP2_TP, pl = e % PREP2_TP, p = p0 + pl;
+        if (p >= m) continue;
+        const c64 a = tile[r * (PREP2_TP + 1) + pl];
+        *reinterpret_cast<P2*>(bb + (size_t)(2 * r) * ld2 + 2 * p) = Pair2<E>::make(a.x, -a.y);
+        *reinterpret_cast<P2*>(bb + (size_t)(2 * r + 1) * ld2 + 2 * p) = Pair2<E>::make(a.y, a.x);
     }
 }
 
@@ -190,9 +202,10 @@ struct TcCfg {
 
 template <typename E, int NPAD, int NST>
 __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapA32,
                                                         const __grid_constant__ CUtensorMap mapB,
                                                         const BoxInfo* __restrict__ boxes, c64* __restrict__ loc,
-                                                        int nrhs, int s, int fwd, int* __restrict__ err) {
+                                                        int nrhs, int s, int fwd, int nkc, int* __restrict__ err) {
     using Cfg = TcCfg<E, NPAD, NST>;
     constexpr int TC_STAGES = Cfg::STAGES;
     constexpr int TC_BK = Cfg::BK;
@@ -223,6 +236,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
         tc::mbar_init(done, 1);
         tc::fence_barrier_init();
         tc::prefetch_tmap(&mapA);
+        tc::prefetch_tmap(&mapA32);
         tc::prefetch_tmap(&mapB);
     }
     if (warp == 1) {
@@ -235,13 +249,22 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
+        // TMA producer.  A tile (rows row0.., chunk kc): 16 KB contiguous in the tile layout; the last,
+        // partial row tile of a box loads only its 32-row groups that hold rows < m (the rest of the
+        // shared tile keeps stale values, which only reach accumulator rows that are never stored)
+        const int rows = min(TC_BM, m - row0);
+        const int nsub = rows >= TC_BM ? 0 : (rows + 31) / 32;
+        const uint32_t a_bytes = nsub ? (uint32_t)nsub * 32 * 128 : (uint32_t)Cfg::A_BYTES;
         for (int kc = 0; kc < nK; ++kc) {
             const int st = kc % TC_STAGES;
             if (kc >= TC_STAGES && !tc::mbar_wait(&empty[st], ((kc / TC_STAGES) - 1) & 1, err, 1)) break;
             unsigned char* sa = base + st * Cfg::STAGE;
-            tc::mbar_arrive_expect_tx(&full[st], Cfg::STAGE);
-            tc::tma_load_3d(sa, &mapA, kc * TC_BK, row0, plane, &full[st]);
+            tc::mbar_arrive_expect_tx(&full[st], a_bytes + Cfg::B_BYTES);
+            const int line = (blockIdx.x * nkc + kc) * TC_BM;
+            if (nsub == 0)
+                tc::tma_load_3d(sa, &mapA, 0, line, plane, &full[st]);
+            else
+                for (int q = 0; q < nsub; ++q) tc::tma_load_3d(sa + q * 4096, &mapA32, 0, line + 32 * q, plane, &full[st]);
             tc::tma_load_3d(sa + Cfg::A_BYTES, &mapB, kc * TC_BK, 0, blockIdx.y, &full[st]);
         }
     } else if (warp == 1 && lane == 0) {
@@ -317,13 +340,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool encode_3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
-               bool bf16) {
+bool encode_3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1, uint64_t s2,
+               uint32_t b0, uint32_t b1, bool bf16) {
     PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = encode_fn();
     if (!cuTensorMapEncodeTiled) return false;
-    const uint64_t es_bytes = bf16 ? 2 : 4;
     cuuint64_t dims[3] = {d0, d1, d2};
-    cuuint64_t strides[2] = {d0 * es_bytes, d0 * d1 * es_bytes};
+    cuuint64_t strides[2] = {s1, s2};   // bytes
     cuuint32_t box[3] = {b0, b1, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = cuTensorMapEncodeTiled(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
@@ -338,20 +360,31 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
                    int* err) {
     using Cfg = TcCfg<E, NPAD, NST>;
     constexpr bool BF = sizeof(E) == 2;
-    CUtensorMap mapA, mapB;
+    CUtensorMap mapA, mapA32, mapB;
     const int ld = P.ld;
-    if (!encode_3d(&mapA, P.G, 2ull * ld, (uint64_t)ld, (uint64_t)P.nplanes, Cfg::BK, TC_BM, BF) ||
-        !encode_3d(&mapB, bt, 2ull * ld, (uint64_t)NPAD, (uint64_t)P.nbox, Cfg::BK, NPAD, BF))
+    const uint64_t eb = BF ? 2 : 4;
+    if (!P.packed) return set_error(ctx, HELM_EINVAL, "tensor-core sweep: factors are not in the tile layout");
+    // A: the tile layout, one 128-byte line per (tile, chunk, row): lines of 128 bytes, planes pstride apart
+    const uint64_t lines = (uint64_t)P.pk_tiles * P.pk_chunks * TC_BM;
+    const uint64_t pbytes = (uint64_t)P.hbox[0].pstride * P.esize();
+    if (!encode_3d(&mapA, P.G, Cfg::BK, lines, (uint64_t)P.nplanes, 128, pbytes, Cfg::BK, TC_BM, BF) ||
+        !encode_3d(&mapA32, P.G, Cfg::BK, lines, (uint64_t)P.nplanes, 128, pbytes, Cfg::BK, 32, BF) ||
+        !encode_3d(&mapB, bt, 2ull * ld, (uint64_t)NPAD, (uint64_t)P.nbox, 2ull * ld * eb, 2ull * ld * NPAD * eb,
+                   Cfg::BK, NPAD, BF))
         return set_error(ctx, HELM_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tc_sweep_gemm<E, NPAD, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        cudaFuncSetAttribute(tc_prep2<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(128 * (PREP2_TP + 1) * sizeof(c64)));
         attr = true;
     }
     const int m = P.m_max;
     const dim3 ggrid((m + TC_BM - 1) / TC_BM, P.nbox);
     const dim3 pgrid((unsigned)((m + PREP_TP - 1) / PREP_TP), P.nbox);
-    const dim3 pgrid4((unsigned)std::max(1, (m * std::max(1, nrhs / 4) + 255) / 256), P.nbox);
+    const dim3 pgrid2((unsigned)((m + PREP2_TP - 1) / PREP2_TP), P.nbox);
+    const size_t psmem2 = (size_t)nrhs * (PREP2_TP + 1) * sizeof(c64);
+    const bool vec2 = nrhs % 2 == 0 && (((uintptr_t)lb | (uintptr_t)loc) & 15) == 0;
     const c64* coef = (const c64*)P.coef;
     const double es = sizeof(c64);
     const double fs = 2.0 * sizeof(E);   // bytes of one stored complex factor entry
@@ -371,13 +404,14 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
         for (int s = fwd ? 0 : 1; s < P.bz_max; ++s) {
             bytes(s, fwd, gb, pb);
             int t = prof_begin(ctx, "sweep_prep");
-            if (nrhs % 4 == 0)
-                tc_prep4<E><<<pgrid4, 256, 0, st>>>(P.dbox, coef, lb, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
+            if (vec2)
+                tc_prep2<E><<<pgrid2, 512, psmem2, st>>>(P.dbox, coef, lb, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
             else
                 tc_prep<E><<<pgrid, 256, 0, st>>>(P.dbox, coef, lb, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
             prof_end(ctx, t, pb);
             t = prof_begin(ctx, "sweep_gemm_tc");
-            tc_sweep_gemm<E, NPAD, NST><<<ggrid, 128, Cfg::SMEM, st>>>(mapA, mapB, P.dbox, loc, nrhs, s, fwd, err);
+            tc_sweep_gemm<E, NPAD, NST><<<ggrid, 128, Cfg::SMEM, st>>>(mapA, mapA32, mapB, P.dbox, loc, nrhs, s,
+                                                                        fwd, P.pk_chunks, err);
             prof_end(ctx, t, gb);
             ctx->launches += 2;
         }
@@ -409,6 +443,70 @@ helm_status dispatch_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, void* lo
 }
 
 }  // namespace
+
+namespace {
+
+// packed[((t * chunks + c) * 128 + i) * 128 + b] = row (128 t + i), byte 128 c + b of the row-major
+// plane (zero past the row or the plane), in 16-byte pieces
+__global__ void pack_tiles(const unsigned char* __restrict__ src, unsigned char* __restrict__ dst, int nplanes,
+                           long long pbytes, int rows, long long row_bytes, int tiles, int chunks) {
+    const long long lines = (long long)tiles * chunks * 128;
+    const long long total = (long long)nplanes * lines * 8;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(e % 8);
+        const long long L = (e / 8) % lines;
+        const int pl = (int)(e / 8 / lines);
+        const int t = (int)(L / ((long long)chunks * 128));
+        const int c = (int)((L / 128) % chunks);
+        const int i = (int)(L % 128);
+        const int r = t * 128 + i;
+        const long long boff = (long long)c * 128 + q * 16;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (r < rows && boff < row_bytes)
+            v = *reinterpret_cast<const uint4*>(src + pl * pbytes + (long long)r * row_bytes + boff);
+        *reinterpret_cast<uint4*>(dst + pl * pbytes + L * 128 + q * 16) = v;
+    }
+}
+
+}  // namespace
+
+// Rearrange the padded row-major plane inverses of a tensor-core set into the tile layout, in place,
+// a batch of planes at a time through a scratch copy.
+helm_status planeset_pack_tc(helm_ctx ctx, PlaneSet& P) {
+    if (!P.padded || P.packed) return HELM_OK;
+    const long long esz = (long long)P.esize();
+    const long long row_bytes = (long long)P.ld * esz;
+    const int tiles = (P.ld + TC_BM - 1) / TC_BM;
+    const int chunks = (int)((row_bytes + 127) / 128);
+    const long long pbytes = P.hbox[0].pstride * esz;
+    if ((long long)tiles * chunks * 128 * 128 > pbytes)
+        return set_error(ctx, HELM_EINVAL, "planeset_pack_tc: plane slot too small for the tile layout");
+    const int batch = (int)std::max<long long>(1, std::min<long long>(P.nplanes, (256ll << 20) / pbytes));
+    void* tmp = nullptr;
+    HELM_TRY(dev_alloc(ctx, &tmp, (size_t)batch * pbytes, "factor packing scratch"));
+    cudaStream_t st = ctx->stream;
+    helm_status rc = HELM_OK;
+    for (int p0 = 0; p0 < P.nplanes && rc == HELM_OK; p0 += batch) {
+        const int nb = std::min(batch, P.nplanes - p0);
+        unsigned char* slot = (unsigned char*)P.G + (size_t)p0 * pbytes;
+        rc = cuda_check(ctx, cudaMemcpyAsync(tmp, slot, (size_t)nb * pbytes, cudaMemcpyDeviceToDevice, st),
+                        "factor packing copy");
+        if (rc) break;
+        const long long work = (long long)nb * tiles * chunks * 128 * 8;
+        const unsigned grid = (unsigned)std::min<long long>((work + 255) / 256, (long long)ctx->sm_count * 32);
+        pack_tiles<<<std::max(1u, grid), 256, 0, st>>>((const unsigned char*)tmp, slot, nb, pbytes, P.ld, row_bytes,
+                                                       tiles, chunks);
+        ctx->launches++;
+        rc = cuda_check(ctx, cudaGetLastError(), "pack_tiles");
+    }
+    if (rc == HELM_OK) rc = cuda_check(ctx, cudaStreamSynchronize(st), "factor packing");
+    dev_free(ctx, tmp, (size_t)batch * pbytes);
+    if (rc) return rc;
+    P.packed = true;
+    P.pk_tiles = tiles;
+    P.pk_chunks = chunks;
+    return HELM_OK;
+}
 
 int tc_npad(int nrhs) {
     const int n = 2 * nrhs;

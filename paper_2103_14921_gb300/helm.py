@@ -28,6 +28,8 @@ _atexit.register(_mark_finalizing)   # handles still alive at exit are left to p
 OK, EINVAL, ENOMEM, ENOTCONV, ESINGULAR, ENONFINITE, ETIMEOUT, EBUSY, ECUDA, ENOTFOUND = range(10)
 TOP_DIRICHLET, TOP_PML = 0, 1
 TUNE_TC_STAGES = 1
+TUNE_COARSE_COOP = 2
+TUNE_GRAPHS = 3
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_TF32X3, PREC_BF16 = 0, 1, 2, 3, 4
 PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3, "bf16": PREC_BF16}
 
@@ -45,7 +47,8 @@ class GridDesc(C.Structure):
 
 class OrasDesc(C.Structure):
     _fields_ = [("px", C.c_int), ("py", C.c_int), ("pz", C.c_int), ("overlap", C.c_int), ("coarse_ratio", C.c_int),
-                ("interface_bc", C.c_int), ("factor_prec", C.c_int)]
+                ("interface_bc", C.c_int), ("factor_prec", C.c_int), ("coarse_iters", C.c_int),
+                ("coarse_overlap", C.c_int)]
 
 
 class GmresDesc(C.Structure):
@@ -241,8 +244,12 @@ class Grid:
 class Oras:
     """``oras_factor``: the two-level ORAS preconditioner with resident plane factors."""
 
-    def __init__(self, grid: Grid, parts, overlap, coarse_ratio=0, interface_bc=0, factor_prec=PREC_FP64):
-        d = OrasDesc(parts[0], parts[1], parts[2], overlap, coarse_ratio, interface_bc, factor_prec)
+    def __init__(self, grid: Grid, parts, overlap, coarse_ratio=0, interface_bc=0, factor_prec=PREC_FP64,
+                 coarse_iters=0, coarse_overlap=1):
+        """``coarse_iters = k >= 1`` solves the coarse problem as the paper does (k GMRES iterations with
+        one-level ORAS on the coarse grid, ``coarse_overlap`` coarse layers); 0 solves it exactly."""
+        d = OrasDesc(parts[0], parts[1], parts[2], overlap, coarse_ratio, interface_bc, factor_prec, coarse_iters,
+                     coarse_overlap)
         self.grid = grid
         self.ctx = grid.ctx
         self.desc = d

@@ -135,3 +135,66 @@ def test_linear_gradient_one_level_matches_closed_form(ctx):
     G = green_linear_gradient(X, Y, Z, (s[0] * h, s[1] * h, (s[2] + 1) * h), 2 * np.pi * f, 1500.0, 0.6)
     mask = comparison_mask(n, n, n, 8, True, s, 4)
     assert relative_l2_misfit(u, -G, mask) <= 0.05
+
+
+def test_graph_replayed_iterations_equal_eager_launches(ctx):
+    """Krylov iterations replayed from captured CUDA graphs run the same kernels with the same
+    arguments as host launches, and every reduction has a fixed order, so the solutions are
+    bit-identical; the launch count and the profiler's per-family records agree too (the profiled
+    kernels are timed through event nodes inside the graphs).  Restart 8 with about twice as many
+    iterations makes the second cycle and the next solves replay graphs captured earlier."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (28, 26, 24)
+    grid, prob = _problem(ctx, dims, f=6.0, Q=100.0)
+    pos = synth.source_plane_positions(28, 26, 4, 3, 6, 11)
+    b = torch.from_numpy(synth.point_sources(*dims, 25.0, pos)).cuda()
+    o = helm.Oras(grid, (2, 2, 2), 2, coarse_ratio=4, factor_prec=helm.PREC_TF32)
+    kw = dict(tol=1e-6, restart=8, basis_prec=helm.PREC_FP32)
+
+    def run():
+        ctx.profile(True, only=["sweep_gemm_tc", "coarse_sweep"])
+        l0 = ctx.launches
+        x, st = o.solve(b, **kw)
+        n = ctx.launches - l0
+        prof = {f: ctx.profile_query(f) for f in ("sweep_gemm_tc", "coarse_sweep")}
+        ctx.profile(False)
+        return x, [s["iterations"] for s in st], n, prof
+
+    ctx.set_tuning(helm.TUNE_GRAPHS, 0)
+    x0, it0, n0, p0 = run()
+    assert max(it0) > 8
+    ctx.set_tuning(helm.TUNE_GRAPHS, 1)
+    for _ in range(3):                       # capture on second use, then replays
+        x1, it1, n1, p1 = run()
+        assert it1 == it0
+        assert torch.equal(x1, x0)
+        assert n1 == n0
+        for f in p0:
+            assert p1[f][0] == p0[f][0] and p1[f][1] > 0
+    assert _residual(prob, x1.cpu().numpy()[..., 0], b.cpu().numpy()[..., 0]) <= 1e-6
+
+
+def test_inexact_coarse_fgmres_mixed_precision(ctx):
+    """FGMRES with the paper's inexact coarse solve (10 inner GMRES steps, coarse ORAS) and TF32 local
+    factors converges; the oracle's FP64 residual of the result is <= tol and the solution is within
+    10 x tol of the direct solution.  A second solve replays the captured iteration graphs (the inner
+    solve runs without host synchronisation inside them) and gives the same iterate."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (28, 26, 24)
+    grid, prob = _problem(ctx, dims, f=6.0, Q=100.0)
+    pos = synth.source_plane_positions(28, 26, 4, 3, 4, 9)
+    b = synth.point_sources(*dims, 25.0, pos)
+    xs = direct_solve_planes(prob, b.reshape(-1, 4)).reshape(b.shape)
+    tol = 1e-6
+    o = helm.Oras(grid, (2, 2, 2), 2, coarse_ratio=4, factor_prec=helm.PREC_TF32, coarse_iters=10)
+    bt = torch.from_numpy(b).cuda()
+    x1, st1 = o.solve(bt, tol=tol, restart=30, flexible=True, basis_prec=helm.PREC_FP32)
+    x2, st2 = o.solve(bt, tol=tol, restart=30, flexible=True, basis_prec=helm.PREC_FP32)
+    assert torch.equal(x1, x2) and [s["iterations"] for s in st1] == [s["iterations"] for s in st2]
+    x = x1.cpu().numpy()
+    for r in range(4):
+        assert st1[r]["converged"], st1[r]
+        assert _residual(prob, x[..., r], b[..., r]) <= tol
+        assert _rel(x[..., r], xs[..., r]) <= 10 * tol

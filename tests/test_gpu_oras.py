@@ -88,6 +88,67 @@ def test_oras_apply_fp32_factors(ctx):
     assert _rel(got, want) <= 1e-3
 
 
+@pytest.mark.parametrize("nrhs", [4, 20, 3])
+def test_cooperative_coarse_sweeps_match_per_plane_launches(ctx, nrhs):
+    """The complex64 coarse solve in one cooperative launch against the per-plane launches (the
+    tuning switch selects the path): the same arithmetic in FP32 summed in another order, so the two
+    agree to FP32 rounding (1e-5), and both match the FP64 oracle to the FP32-factor bar (1e-3).
+    20 columns take two passes of the 16-column product; the ragged grid gives a ragged coarse plane;
+    an odd column count keeps the per-plane launches (the cooperative copies move column pairs)."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (23, 21, 18)
+    grid, prob = _setup(ctx, dims, npml=3, Q=90.0)
+    o = helm.Oras(grid, (2, 2, 2), 2, coarse_ratio=3, factor_prec=helm.PREC_FP32)
+    M = ORAS(prob, (2, 2, 2), 2, coarse_ratio=3)
+    v = synth.random_complex((dims[2], dims[1], dims[0], nrhs), 35)
+    want = M.apply(v.reshape(-1, nrhs)).reshape(v.shape)
+    vt = torch.from_numpy(v).cuda()
+    got = {}
+    for coop in (1, 0):
+        ctx.set_tuning(helm.TUNE_COARSE_COOP, coop)
+        ctx.profile(True, only=["coarse_sweep"])
+        got[coop] = o.apply(vt).cpu().numpy()
+        launches = ctx.profile_query("coarse_sweep")[0]
+        ctx.profile(False)
+        cz = -(-(dims[2] - 1) // 3) + 1
+        assert launches == (1 if coop and nrhs % 2 == 0 else 2 * cz - 1), (coop, launches)
+    ctx.set_tuning(helm.TUNE_COARSE_COOP, 1)
+    assert _rel(got[1], got[0]) <= 1e-5
+    for coop in (1, 0):
+        assert _rel(got[coop], want) <= 1e-3
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_inexact_coarse_apply_matches_oracle(ctx, mode):
+    """The paper's coarse solve (10 GMRES steps with one-level ORAS on the coarse grid, same partition):
+    the FP64 preconditioner against the oracle's, on a ragged grid whose coarse partition is ragged too.
+    Ten GMRES steps are a smooth function of the data away from breakdown; CGS with re-orthogonalisation
+    (GPU) and MGS (oracle) differ by rounding only, so the bar is 1e-8."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (21, 18, 17)
+    grid, prob = _setup(ctx, dims, npml=3)
+    parts, ov = (3, 2, 2), 2
+    o = helm.Oras(grid, parts, ov, coarse_ratio=4, interface_bc=mode, coarse_iters=10, coarse_overlap=1)
+    M = ORAS(prob, parts, ov, coarse_ratio=4, mode="oras" if mode == 0 else "ras", coarse_solve="gmres",
+             coarse_iters=10, coarse_overlap=1)
+    v = synth.random_complex((dims[2], dims[1], dims[0], 3), 36)
+    want = M.apply(v.reshape(-1, 3)).reshape(v.shape)
+    got = o.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert _rel(got, want) <= 1e-8
+
+
+def test_inexact_coarse_rejects_too_small_coarse_grid(ctx):
+    from paper_2103_14921_gb300 import helm
+    grid, _ = _setup(ctx, (9, 9, 9), npml=2)
+    with pytest.raises(helm.HelmError) as e:
+        helm.Oras(grid, (4, 1, 1), 1, coarse_ratio=4, coarse_iters=10)   # 3 coarse nodes, 4 parts
+    assert e.value.status == helm.EINVAL
+    with pytest.raises(helm.HelmError):
+        helm.Oras(grid, (2, 1, 1), 1, coarse_ratio=0, coarse_iters=10)   # no coarse grid
+
+
 def test_one_box_is_the_exact_inverse(ctx):
     """One box: M^{-1} = A^{-1}, so A M^{-1} v = v (GPU stencil times GPU preconditioner)."""
     import torch
@@ -134,7 +195,7 @@ def test_destroy_order_and_profiler(ctx):
     v = torch.from_numpy(synth.random_complex((10, 12, 12, 2), 40)).cuda()
     o.apply(v)
     g = ctx.profile_query("sweep_gemv")
-    s = ctx.profile_query("stencil")
+    s = ctx.profile_query("stencil64")            # the FP64 apply: t = v - A q in FP64
     ctx.profile(False)
     assert g is not None and g[0] > 0 and g[1] > 0 and g[2] > 0
     assert s is not None and s[0] == 1

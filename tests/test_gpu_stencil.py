@@ -53,6 +53,35 @@ def test_stencil_matches_oracle(ctx, case):
     assert _rel(y32.astype(np.complex128), want) <= 1e-5
 
 
+def test_stencil_fp32_vector_and_scalar_paths_agree(ctx):
+    """complex64 with an even column count runs two columns per 16-byte load; the same data at an
+    8-byte offset (not 16-byte aligned) takes the one-column path.  The per-element operations are the
+    same up to the compiler's choice of fused multiply-adds, so the two agree to FP32 rounding (1e-6)
+    and both match the oracle (1e-5)."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    nx, ny, nz, nrhs = 23, 21, 19, 16
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 2.0, Q=70.0)
+    w = synth.random_weights(3)
+    grid = helm.Grid(ctx, nx, ny, nz, 25.0, 5.0, c, npml=4, weights=w)
+    prob = Problem(nx, ny, nz, 25.0, 5.0, c, npml=4, weights=w)
+    u = synth.random_complex((nz, ny, nx, nrhs), 91)
+    want = apply_A(prob, u)
+    u32 = torch.from_numpy(u.astype(np.complex64)).cuda()
+    y_vec = grid.apply(u32, prec=helm.PREC_FP32)
+    n = u32.numel()
+    ubuf = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+    ybuf = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")
+    u_off = ubuf[1:].view(u32.shape)
+    u_off.copy_(u32)
+    y_off = ybuf[1:].view(u32.shape)
+    assert u_off.data_ptr() % 16 == 8
+    grid.apply(u_off, y_off, prec=helm.PREC_FP32)
+    a, b = y_off.cpu().numpy().astype(np.complex128), y_vec.cpu().numpy().astype(np.complex128)
+    assert _rel(a, b) <= 1e-6
+    assert _rel(a, want) <= 1e-5 and _rel(b, want) <= 1e-5
+
+
 def test_stencil_fitted_weights_full_size_sampled(ctx):
     """112^3 x 16 (the two-level workload's size): sampled rows against the oracle's assembled rows."""
     import torch
