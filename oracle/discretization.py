@@ -66,6 +66,7 @@ class Problem:
     top_pml: bool = False             # False: Dirichlet top (paper); True: PML top
     pml_R: float = 1e-3
     weights: tuple = WEIGHTS_7PT      # (w1, w2, w3, wm1, wm2, wm3, wm4)
+    row_weights: np.ndarray = None    # optional [nz, ny, nx, 7]: weights of each row (adaptive stencil)
     _cache: dict = field(default_factory=dict, repr=False, compare=False)
 
     @property
@@ -100,6 +101,18 @@ def stencil_coefficients(weights):
     m2 = wm3 + 2.0 * wm4
     m3 = wm4
     return a2, a3, m0, m1, m2, m3
+
+
+def row_coefficients(prob: Problem):
+    """``(a2, a3, m0, m1, m2, m3)`` of every row: scalars for constant weights, ``[nz, ny, nx]`` arrays
+    when ``prob.row_weights`` gives each row its own weights (the adaptive stencil, whose row ``p`` is
+    the constant-weight row built with the weights of ``p``)."""
+    if prob.row_weights is None:
+        return stencil_coefficients(prob.weights)
+    w = np.asarray(prob.row_weights, dtype=np.float64)
+    w1, w2, w3, wm1, wm2, wm3, wm4 = (w[..., q] for q in range(7))
+    return (w2 / 6.0 + w3 / 2.0, w3 / 4.0, wm1 + 6.0 * wm2 + 12.0 * wm3 + 8.0 * wm4, wm2 + 4.0 * wm3 + 4.0 * wm4,
+            wm3 + 2.0 * wm4, wm4)
 
 
 def pml_xi(n: int, h: float, npml: int, low: bool, high: bool, omega: float, c_ref: float, R: float):
@@ -193,7 +206,7 @@ def apply_A(prob: Problem, u: np.ndarray) -> np.ndarray:
     """
     u = np.asarray(u, dtype=np.complex128)
     extra = u.ndim - 3
-    a2, a3, m0, m1, m2, m3 = stencil_coefficients(prob.weights)
+    a2, a3, m0, m1, m2, m3 = (np.reshape(q, np.shape(q) + (1,) * extra) for q in row_coefficients(prob))
     tx, ty, tz = axis_tables(prob)
     # axis 0 = z, axis 1 = y, axis 2 = x
     Dx = lambda v: _d2_along(v, 2, tx)
@@ -226,7 +239,7 @@ def neighbour_coefficients(prob: Problem) -> np.ndarray:
     product form as :func:`apply_A` but one matrix entry at a time, as the
     tensor product of the 1-D coefficient tables.
     """
-    a2, a3, m0, m1, m2, m3 = stencil_coefficients(prob.weights)
+    a2, a3, m0, m1, m2, m3 = row_coefficients(prob)
     tx, ty, tz = axis_tables(prob)
     nz, ny, nx = prob.shape
     k2 = prob.k2()

@@ -147,3 +147,81 @@ def test_stencil_coefficient_identities():
     a2, a3, m0, m1, m2, m3 = stencil_coefficients(w)
     assert abs(m0 - 1) < 1e-12
     assert a2 >= 0 and a3 >= 0
+
+
+# --- adaptive stencil weights (each row with the weights matched to its own points per wavelength) ---
+
+def test_row_weights_rows_equal_their_constant_weight_rows():
+    """Row p of the adaptive operator is row p of the constant-weight operator built with p's weights
+    (so per-row weights act on the right rows and nothing mixes across rows); matrix-free = assembled."""
+    nx, ny, nz = 9, 8, 7
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 3.0, Q=80.0)
+    sets = [synth.random_weights(s) for s in (31, 32, 33)]
+    rng = np.random.default_rng(4)
+    pick = rng.integers(0, 3, size=(nz, ny, nx))
+    rw = np.array(sets)[pick]
+    prob = Problem(nx, ny, nz, 25.0, 5.0, c, npml=2, weights=sets[0], row_weights=rw)
+    A = assemble_A(prob).toarray()
+    for q in range(3):
+        Aq = assemble_A(Problem(nx, ny, nz, 25.0, 5.0, c, npml=2, weights=sets[q])).toarray()
+        rows = np.flatnonzero(pick.ravel() == q)
+        assert np.allclose(A[rows], Aq[rows], rtol=0, atol=1e-12 * np.abs(Aq).max())
+    u = synth.random_complex((nz, ny, nx, 2), 5)
+    Au = apply_A(prob, u)
+    want = (A @ u.reshape(-1, 2)).reshape(u.shape)
+    assert np.linalg.norm(Au - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_one_bin_of_row_weights_is_the_constant_stencil():
+    nx, ny, nz = 8, 7, 6
+    c = synth.linear_gradient(nx, ny, nz, 25.0)
+    w = synth.random_weights(34)
+    rw = np.broadcast_to(np.array(w), (nz, ny, nx, 7))
+    u = synth.random_complex((nz, ny, nx), 6)
+    a = apply_A(Problem(nx, ny, nz, 25.0, 5.0, c, npml=2, weights=w, row_weights=rw), u)
+    b = apply_A(Problem(nx, ny, nz, 25.0, 5.0, c, npml=2, weights=w), u)
+    assert np.array_equal(a, b)
+
+
+def test_adaptive_bins_cover_the_model_and_beat_the_broadband_fit_in_their_range():
+    from oracle.weights import adaptive_bin_edges, row_weight_bins, adaptive_row_weights
+    c = synth.linear_gradient(10, 9, 24, 25.0, 1000.0, 2.0)
+    f, h = 8.0, 25.0
+    G = np.real(c) / (f * h)
+    edges = adaptive_bin_edges(G.min(), G.max(), 4)
+    assert np.isclose(edges[0], G.min()) and np.isclose(edges[-1], G.max())
+    bins = row_weight_bins(c, f, h, edges)
+    assert bins.min() == 0 and bins.max() == 3
+    for b in range(4):                           # every node lies in its bin's interval
+        g = G[bins == b]
+        assert g.min() >= edges[b] * (1 - 1e-12) and g.max() <= edges[b + 1] * (1 + 1e-12)
+    table, bins2, rw = adaptive_row_weights(c, f, h, 4)
+    assert np.array_equal(bins, bins2) and np.array_equal(rw, table[bins])
+    broad = fit_weights()
+    for b in range(4):
+        Gs = 1.0 / np.linspace(1.0 / edges[b + 1], 1.0 / edges[b], 8)
+        err_bin = np.abs(dispersion_residuals(tuple(table[b]), Gs)).max()
+        err_broad = np.abs(dispersion_residuals(broad, Gs)).max()
+        assert err_bin < err_broad
+
+
+def test_adaptive_weights_are_closer_to_the_linear_gradient_closed_form():
+    """In the paper's validation medium the row-adapted stencil is more accurate than the broadband one
+    against the closed-form solution (the purpose the paper gives for adaptive coefficients)."""
+    from oracle.analytic import green_linear_gradient, node_coordinates, relative_l2_misfit, comparison_mask
+    from oracle.schwarz import direct_solve_planes
+    from oracle.weights import adaptive_row_weights
+    n, h, f, c0, alpha = 32, 25.0, 5.0, 1500.0, 0.6
+    c = synth.linear_gradient(n, n, n, h, c0, alpha)
+    s = (16, 16, 16)
+    X, Y, Z = node_coordinates(n, n, n, h)
+    G = green_linear_gradient(X, Y, Z, (s[0] * h, s[1] * h, (s[2] + 1) * h), 2 * np.pi * f, c0, alpha)
+    mask = comparison_mask(n, n, n, 8, True, s, 4)
+    b = synth.point_sources(n, n, n, h, [s])[..., 0].ravel()
+    w = fit_weights()
+    _, _, rw = adaptive_row_weights(c, f, h, 4)
+    mis = []
+    for row_weights in (None, rw):
+        prob = Problem(n, n, n, h, f, c, npml=8, top_pml=True, weights=w, row_weights=row_weights)
+        mis.append(relative_l2_misfit(direct_solve_planes(prob, b).reshape(prob.shape), -G, mask))
+    assert mis[1] < mis[0] < 0.05
