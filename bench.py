@@ -445,8 +445,8 @@ def run_gpu(args, W):
     peaks, src = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     # DRAM traffic per launch relative to the algorithmic bytes, from the ncu capture summarised in
-    # profiles/tc_sweep_gemm_lg64.md (dram__bytes_read.sum + dram__bytes_write.sum = 1.047 x algorithmic)
-    traffic_ratio = {"sweep_gemm_tc": 1.047}.get(roof_fam) if args.factor_prec == "tf32" else None
+    # profiles/tc_sweep_gemm_slab112.md (dram__bytes_read.sum + dram__bytes_write.sum = 1.037 x algorithmic)
+    traffic_ratio = {"sweep_gemm_tc": 1.037}.get(roof_fam) if args.factor_prec == "tf32" else None
     roof = None
     fam = roof_fam
     g = roof_meas
@@ -455,7 +455,7 @@ def run_gpu(args, W):
         ach = by / (ms / 1000.0) / 1e9
         roof = {"kernel": fam, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": (traffic_ratio * by / nl) if traffic_ratio else None,
-                "traffic_source": "ncu 64^3 capture scaled by algorithmic bytes" if traffic_ratio else None,
+                "traffic_source": "ncu 112x112x24 slab capture scaled by algorithmic bytes" if traffic_ratio else None,
                 "peak_source": src, "launches": nl,
                 "avg_launch_us": 1000.0 * ms / nl, "algorithmic_bytes_per_launch": by / nl}
     kernels = {}
@@ -489,6 +489,7 @@ def run_gpu(args, W):
         "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": int(b_host.nbytes),
                 "d2h_bytes_per_step": int(b_host.nbytes)},
         "gpu_launches": int(launches),
+        "launches_before_timed": int(l0),   # the library's launches up to the timed region (ncu -s for a launch list)
         "roofline": roof, "kernels": kernels, "plain_fp64_gpu": plain,
         "cpu_baseline": cpu, "clocks": clk, "serving": serving, "variants": variants,
     }

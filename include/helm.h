@@ -131,13 +131,19 @@ typedef struct {
     int    top_bc;        /* HELM_TOP_DIRICHLET or HELM_TOP_PML                               */
     double weights[7];    /* w1, w2, w3, wm1, wm2, wm3, wm4 of the mixed-grid stencil;
                              w1+w2+w3 = 1 and wm1+6wm2+12wm3+8wm4 = 1 (checked, 1e-9)       */
+    int    weight_bins;   /* 0: every row uses weights[] (zero-initialise to keep this);
+                             1..64: adaptive weights matched to the local wave speed (the paper's
+                             adaptive coefficients): the points-per-wavelength range of the model,
+                             G = Re c / (f h) from its minimum to its maximum, is cut into this many
+                             geometric bins, each fitted as helm_fit_weights does over its own G
+                             interval, and each row uses the bin holding its own G (needs G >= 2) */
 } helm_grid_desc;
 
 /* Fit the stencil weights by least squares on the normalised phase-velocity
  * error 1 - sqrt(-L(kappa)/M(kappa))/|kappa| of plane waves over G_min..G_max
  * grid points per wavelength and directions in one octant, all weights kept
- * non-negative (the paper: "least-squares minimisation of the numerical
- * dispersion and anisotropy").  Host-only; writes weights_out[7]. */
+ * non-negative (the paper fits the weights by least squares against the
+ * stencil's phase and direction errors, section 2).  Host-only; writes weights_out[7]. */
 helm_status helm_fit_weights(double G_min, double G_max, double weights_out[7]);
 
 /* Set up one problem: copies the wave speed c (complex128 [nz][ny][nx],
@@ -146,6 +152,11 @@ helm_status helm_fit_weights(double G_min, double G_max, double weights_out[7]);
  * gamma(d)/omega, gamma = gamma0 (d/L)^2, c_ref = max Re c).  Eq. (eqh). */
 helm_status helm_setup_grid(helm_ctx ctx, const helm_grid_desc* desc, const void* c, helm_grid* out);
 void        helm_destroy_grid(helm_grid g);
+
+/* The adaptive weights of a grid built with weight_bins > 0: *nbins, and when the arrays are not
+ * NULL the bin edges in points per wavelength (edges[nbins + 1]: edge b = G_min ratio^b) and each
+ * bin's weights (table[nbins * 7], w1..wm4).  *nbins = 0 for constant weights.  Host memory. */
+helm_status helm_grid_row_weights(helm_grid g, int* nbins, double* edges, double* table);
 
 /* y = A u (Eq. eq1), matrix-free 27-point stencil, nrhs columns.
  * prec = HELM_PREC_FP64: u, y complex128; prec = HELM_PREC_FP32: complex64.

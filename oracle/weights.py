@@ -2,9 +2,9 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-The paper states that the stiffness and consistent-mass weights are computed
-by least-squares minimisation of the numerical dispersion and anisotropy
-(section "Tetrahedral finite elements versus 27-point finite-differences"),
+The paper fits the stiffness and consistent-mass weights by least squares against
+the stencil's phase-velocity and direction errors (section on finite elements versus
+the 27-point stencil),
 but prints no values.  Reading taken: minimise the normalised phase-velocity
 error ``1 - sqrt(-L_hat(kappa)/M_hat(kappa)) / |kappa|`` of plane waves over
 ``G`` = 4..30 grid points per wavelength and propagation directions in one

@@ -144,6 +144,31 @@ __global__ void max_real_kernel(const c128* __restrict__ v, long long n, double*
     if (threadIdx.x == 0) out[blockIdx.x] = s[0];
 }
 
+__global__ void min_real_kernel(const c128* __restrict__ v, long long n, double* out) {
+    __shared__ double s[256];
+    double m = 1e300;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmin(m, v[i].x);
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] = fmin(s[threadIdx.x], s[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = s[0];
+}
+
+// Bin of every node for the adaptive weights: the number of interior edges at or below G = Re c / (f h).
+__global__ void weight_bin_kernel(const c128* __restrict__ c, long long n, double fh, const double* __restrict__ edges,
+                                  int nbins, unsigned char* __restrict__ bin) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double G = c[i].x / fh;
+        int b = 0;
+        for (int e = 1; e < nbins; ++e) b += G >= edges[e];
+        bin[i] = (unsigned char)b;
+    }
+}
+
 // bad |= 1: NaN/Inf or Re c <= 0;  bad |= 2: some Im c != 0 (attenuation, complex k^2)
 __global__ void finite_check_kernel(const c128* __restrict__ v, long long n, int* bad) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -169,6 +194,82 @@ helm_status launch_max_real(helm_ctx ctx, const c128* v, long long n, double* ho
     double m = -1e300;
     for (int i = 0; i < blocks; ++i) m = fmax(m, h[i]);
     *host_out = m;
+    return HELM_OK;
+}
+
+static helm_status launch_min_real(helm_ctx ctx, const c128* v, long long n, double* host_out) {
+    const int blocks = 256;
+    double* part = nullptr;
+    HELM_TRY(dev_alloc(ctx, (void**)&part, blocks * sizeof(double), "min_real partials"));
+    min_real_kernel<<<blocks, 256, 0, ctx->stream>>>(v, n, part);
+    ctx->launches++;
+    double h[blocks];
+    cudaError_t e = cudaMemcpyAsync(h, part, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, part, blocks * sizeof(double));
+    HELM_CUDA(ctx, e);
+    double m = 1e300;
+    for (int i = 0; i < blocks; ++i) m = fmin(m, h[i]);
+    *host_out = m;
+    return HELM_OK;
+}
+
+static StencilW product_form(const double* w, double h) {
+    StencilW s;
+    s.a2 = w[1] / 6.0 + w[2] / 2.0;
+    s.a3 = w[2] / 4.0;
+    s.m0 = w[3] + 6 * w[4] + 12 * w[5] + 8 * w[6];
+    s.m1 = w[4] + 4 * w[5] + 4 * w[6];
+    s.m2 = w[5] + 2 * w[6];
+    s.m3 = w[6];
+    s.inv_h2 = 1.0 / (h * h);
+    return s;
+}
+
+// Adaptive weights: geometric bins over the model's points-per-wavelength range, one least-squares fit per
+// bin over its own interval, and each node's bin.
+static helm_status setup_row_weights(helm_grid g) {
+    helm_ctx ctx = g->ctx;
+    const int nb = g->d.weight_bins;
+    const double fh = g->d.freq_hz * g->d.h;
+    double cmin = 0;
+    HELM_TRY(launch_min_real(ctx, g->c, g->n, &cmin));
+    const double G_lo = cmin / fh, G_hi = g->c_ref / fh;
+    if (!(G_lo >= 2.0))
+        return set_error(ctx, HELM_EINVAL, "helm_setup_grid: adaptive weights need >= 2 points per wavelength "
+                                           "(minimum here %.3g)", G_lo);
+    const double ratio = pow(G_hi / G_lo, 1.0 / nb);
+    g->hedges.resize(nb + 1);
+    for (int b = 0; b <= nb; ++b) g->hedges[b] = G_lo * pow(ratio, (double)b);
+    g->hweights.resize((size_t)nb * 7);
+    std::vector<StencilW> tab(nb);
+    for (int b = 0; b < nb; ++b) {
+        double lo = g->hedges[b], hi = g->hedges[b + 1];
+        if (!(hi > lo)) hi = lo * (1.0 + 1e-6);   // a homogeneous model: one G, fitted on a sliver around it
+        if (helm_fit_weights(lo, hi, &g->hweights[(size_t)b * 7]) != HELM_OK)
+            return set_error(ctx, HELM_EINVAL, "helm_setup_grid: weight fit failed for bin %d", b);
+        tab[b] = product_form(&g->hweights[(size_t)b * 7], g->d.h);
+    }
+    g->nbins = nb;
+    double* dedges = nullptr;
+    HELM_TRY(dev_alloc(ctx, (void**)&g->wtab, nb * sizeof(StencilW), "adaptive weight table"));
+    HELM_TRY(dev_alloc(ctx, (void**)&g->wbin, (size_t)g->n, "adaptive weight bins"));
+    HELM_TRY(dev_alloc(ctx, (void**)&dedges, (nb + 1) * sizeof(double), "bin edges"));
+    HELM_CUDA(ctx, cudaMemcpy(g->wtab, tab.data(), nb * sizeof(StencilW), cudaMemcpyHostToDevice));
+    HELM_CUDA(ctx, cudaMemcpy(dedges, g->hedges.data(), (nb + 1) * sizeof(double), cudaMemcpyHostToDevice));
+    weight_bin_kernel<<<(unsigned)std::min<long long>((g->n + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        g->c, g->n, fh, dedges, nb, g->wbin);
+    ctx->launches++;
+    helm_status st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "weight bins");
+    dev_free(ctx, dedges, (nb + 1) * sizeof(double));
+    return st;
+}
+
+extern "C" helm_status helm_grid_row_weights(helm_grid g, int* nbins, double* edges, double* table) {
+    if (!g || !nbins) return HELM_EINVAL;
+    *nbins = g->nbins;
+    if (g->nbins && edges) memcpy(edges, g->hedges.data(), (g->nbins + 1) * sizeof(double));
+    if (g->nbins && table) memcpy(table, g->hweights.data(), (size_t)g->nbins * 7 * sizeof(double));
     return HELM_OK;
 }
 
@@ -217,6 +318,8 @@ extern "C" helm_status helm_setup_grid(helm_ctx ctx, const helm_grid_desc* d, co
     const double* w = d->weights;
     if (fabs(w[0] + w[1] + w[2] - 1.0) > 1e-9 || fabs(w[3] + 6 * w[4] + 12 * w[5] + 8 * w[6] - 1.0) > 1e-9)
         return set_error(ctx, HELM_EINVAL, "helm_setup_grid: stencil weights do not sum to one");
+    if (d->weight_bins < 0 || d->weight_bins > 64)
+        return set_error(ctx, HELM_EINVAL, "helm_setup_grid: weight_bins must be 0..64");
     HELM_CUDA(ctx, cudaSetDevice(ctx->device));
 
     helm_grid g = new helm_grid_s();
@@ -225,13 +328,7 @@ extern "C" helm_status helm_setup_grid(helm_ctx ctx, const helm_grid_desc* d, co
     g->d = *d;
     g->n = (long long)d->nx * d->ny * d->nz;
     g->omega = 2.0 * M_PI * d->freq_hz;
-    g->w.a2 = w[1] / 6.0 + w[2] / 2.0;
-    g->w.a3 = w[2] / 4.0;
-    g->w.m0 = w[3] + 6 * w[4] + 12 * w[5] + 8 * w[6];
-    g->w.m1 = w[4] + 4 * w[5] + 4 * w[6];
-    g->w.m2 = w[5] + 2 * w[6];
-    g->w.m3 = w[6];
-    g->w.inv_h2 = 1.0 / (d->h * d->h);
+    g->w = product_form(w, d->h);
     const long long n = g->n;
     const int ntab = d->nx + d->ny + d->nz;
     helm_status st = HELM_OK;
@@ -263,6 +360,7 @@ extern "C" helm_status helm_setup_grid(helm_ctx ctx, const helm_grid_desc* d, co
     ctx->launches++;
     if ((st = cuda_check(ctx, cudaGetLastError(), "k2_kernel"))) return fail(st);
     if ((st = launch_max_real(ctx, g->c, n, &g->c_ref))) return fail(st);
+    if (d->weight_bins > 0 && (st = setup_row_weights(g))) return fail(st);
 
     g->htab.resize(3 * ntab);
     const bool top = d->top_bc == HELM_TOP_PML;
@@ -297,6 +395,8 @@ extern "C" void helm_destroy_grid(helm_grid g) {
     dev_free(ctx, g->k2f, n * sizeof(c64));
     dev_free(ctx, g->tab, 3 * ntab * sizeof(c128));
     dev_free(ctx, g->tabf, 3 * ntab * sizeof(c64));
+    dev_free(ctx, g->wtab, g->nbins * sizeof(StencilW));
+    dev_free(ctx, g->wbin, g->nbins ? (size_t)n : 0);
     delete g;
     if (--ctx->children == 0 && ctx->destroy_pending) delete ctx;
 }

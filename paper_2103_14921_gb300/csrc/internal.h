@@ -110,6 +110,11 @@ struct helm_grid_s {
     c64* tabf = nullptr;
     std::vector<c128> htab;    // host copy of the tables
     bool k2_real = false;      // wave speed real everywhere (no attenuation)
+    // adaptive weights (weight_bins > 0): per-bin product-form weights and each node's bin
+    int nbins = 0;
+    StencilW* wtab = nullptr;  // device [nbins]
+    unsigned char* wbin = nullptr;   // device [N]
+    std::vector<double> hedges, hweights;   // host copies: edges [nbins + 1], weights [nbins][7]
     int refs = 0;              // ORAS handles built on this grid
     bool destroy_pending = false;   // helm_destroy_grid called while ORAS handles were alive
 };

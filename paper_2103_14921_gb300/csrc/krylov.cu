@@ -266,6 +266,155 @@ __global__ void __launch_bounds__(RED_THREADS, 2) update_norm_kernel(const cplx<
     }
 }
 
+// Fused first update and second projection of CGS2 (IM >= ni basis vectors): every element's ni basis
+// values are loaded once into registers, w' = w - V h1 is written, and the partials of V^H w' (the second
+// projection's coefficients, plain FP32 sums per thread: they only correct rounding-level remainders) and of
+// |w'|^2 (compensated) are reduced per block.  Runs on the reduction grid (one column per thread), one
+// resident block per SM.
+template <typename T, int IM>
+__global__ void __launch_bounds__(RED_THREADS, 1) update_dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
+                                                                    cplx<T>* __restrict__ w, long long n_el, int nrhs,
+                                                                    int ni, const c128* __restrict__ hsrc,
+                                                                    c128* __restrict__ partial, int ldp,
+                                                                    double* __restrict__ npart) {
+    __shared__ cplx<T> hs[IM * 16];
+    __shared__ c128 s[8][RED_THREADS];
+    __shared__ double sn[RED_THREADS];
+    const long long t = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
+    const long long stride = (long long)gridDim.x * RED_THREADS;
+    const int r = (int)(t % nrhs);
+    const bool hsm = ni * nrhs <= IM * 16;
+    if (hsm)
+        for (int e = threadIdx.x; e < ni * nrhs; e += RED_THREADS) hs[e] = mk<T>((T)hsrc[e].x, (T)hsrc[e].y);
+    __syncthreads();
+    cplx<T> h[IM];
+#pragma unroll
+    for (int q = 0; q < IM; ++q)
+        if (q < ni) {
+            if (hsm) h[q] = hs[q * nrhs + r];
+            else h[q] = mk<T>((T)hsrc[(long long)q * nrhs + r].x, (T)hsrc[(long long)q * nrhs + r].y);
+        }
+    cplx<T> acc[IM];
+#pragma unroll
+    for (int q = 0; q < IM; ++q) acc[q] = mk<T>(0, 0);
+    RAcc<T> nrm;
+    // EPT elements per trip (e, e + stride, ...: the same column), so that every trip keeps the same number
+    // of basis loads in flight whatever IM is
+    constexpr int EPT = (sizeof(T) == 4 ? 32 : 16) / IM > 0 ? (sizeof(T) == 4 ? 32 : 16) / IM : 1;
+    for (long long e0 = t; e0 < n_el; e0 += EPT * stride) {
+        cplx<T> v[EPT][IM];
+        cplx<T> x[EPT];
+#pragma unroll
+        for (int u = 0; u < EPT; ++u) {
+            const long long e = e0 + u * stride;
+            const long long ec = e < n_el ? e : e0;
+#pragma unroll
+            for (int q = 0; q < IM; ++q)
+                if (q < ni) v[u][q] = V[(long long)q * vstride + ec];
+            x[u] = w[ec];
+        }
+#pragma unroll
+        for (int u = 0; u < EPT; ++u) {
+            const long long e = e0 + u * stride;
+            if (e >= n_el) break;
+#pragma unroll
+            for (int q = 0; q < IM; ++q)
+                if (q < ni) {
+                    x[u].x -= h[q].x * v[u][q].x - h[q].y * v[u][q].y;
+                    x[u].y -= h[q].x * v[u][q].y + h[q].y * v[u][q].x;
+                }
+            w[e] = x[u];
+            nrm.add(x[u].x * x[u].x + x[u].y * x[u].y);
+#pragma unroll
+            for (int q = 0; q < IM; ++q)
+                if (q < ni) cmac_conj(acc[q], v[u][q], x[u]);
+        }
+    }
+    sn[threadIdx.x] = nrm.value();
+    const int nr = min(nrhs, RED_THREADS);
+    // block reduction of the ni coefficients in groups of 8 (fixed order)
+#pragma unroll
+    for (int q0 = 0; q0 < IM; q0 += 8) {
+        if (q0 >= ni) break;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s[q][threadIdx.x] = widen(acc[q0 + q]);
+        __syncthreads();
+        const int nq = min(8, ni - q0);
+        for (int o = threadIdx.x; o < nq * nr; o += RED_THREADS) {
+            const int q = o / nr, u0 = o % nr;
+            c128 sum = mk<double>(0, 0);
+            for (int u = u0; u < RED_THREADS; u += nrhs) sum = sum + s[q][u];
+            const int rr = (int)(((long long)blockIdx.x * RED_THREADS + u0) % nrhs);
+            partial[((long long)blockIdx.x * ldp + q0 + q) * nrhs + rr] = sum;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+        double sum = 0.0;
+        for (int u = threadIdx.x; u < RED_THREADS; u += nrhs) sum += sn[u];
+        const int rr = (int)(((long long)blockIdx.x * RED_THREADS + threadIdx.x) % nrhs);
+        npart[(long long)blockIdx.x * nrhs + rr] = sum;
+    }
+}
+
+// Second update of CGS2 fused with the normalisation: out = (w' - V h2) * inv[r] (inv = 0 writes zeros, for
+// the columns whose cycle has stopped).  Two elements per trip, batches of 8 basis loads.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS, 2) update_scale_kernel(const cplx<T>* __restrict__ V, long long vstride,
+                                                                     const cplx<T>* __restrict__ w,
+                                                                     cplx<T>* __restrict__ out, long long n_el,
+                                                                     int nrhs, int ni, const c128* __restrict__ hsrc,
+                                                                     const double* __restrict__ inv) {
+    extern __shared__ __align__(16) unsigned char us_smem[];
+    cplx<T>* hs = reinterpret_cast<cplx<T>*>(us_smem);
+    const long long t = (long long)blockIdx.x * RED_THREADS + threadIdx.x;
+    const long long stride = (long long)gridDim.x * RED_THREADS;
+    const int r = (int)(t % nrhs);
+    for (int e = threadIdx.x; e < ni * nrhs; e += RED_THREADS) hs[e] = mk<T>((T)hsrc[e].x, (T)hsrc[e].y);
+    __syncthreads();
+    const T sc = (T)inv[r];
+    for (long long e = t; e < n_el; e += 2 * stride) {
+        const bool two = e + stride < n_el;
+        const long long e1 = two ? e + stride : e;
+        cplx<T> acc0 = w[e], acc1 = w[e1];
+        for (int i0 = 0; i0 < ni; i0 += 8) {
+            cplx<T> v0[8], v1[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (i0 + q < ni) {
+                    v0[q] = V[(long long)(i0 + q) * vstride + e];
+                    v1[q] = V[(long long)(i0 + q) * vstride + e1];
+                }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (i0 + q < ni) {
+                    const cplx<T> h = hs[(i0 + q) * nrhs + r];
+                    acc0.x -= h.x * v0[q].x - h.y * v0[q].y;
+                    acc0.y -= h.x * v0[q].y + h.y * v0[q].x;
+                    acc1.x -= h.x * v1[q].x - h.y * v1[q].y;
+                    acc1.y -= h.x * v1[q].y + h.y * v1[q].x;
+                }
+        }
+        out[e] = mk<T>(acc0.x * sc, acc0.y * sc);
+        if (two) out[e1] = mk<T>(acc1.x * sc, acc1.y * sc);
+    }
+}
+
+// ||w''|| = sqrt(||w'||^2 - ||h2||^2) per column (V orthonormal; h2 is a rounding-level correction, so there
+// is no cancellation), as the subdiagonal entry H[j+1][j].
+__global__ void second_norm(const double* __restrict__ nw, const c128* __restrict__ h2, int ni, int nrhs,
+                            double* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    double s = nw[r] * nw[r];
+    for (int i = 0; i < ni; ++i) {
+        const c128 a = h2[(long long)i * nrhs + r];
+        s -= a.x * a.x + a.y * a.y;
+    }
+    out[r] = sqrt(fmax(s, 0.0));
+}
+
 // Re-orthogonalisation test per column: a second projection when ||w'|| < ||w|| / sqrt(2).
 __global__ void reorth_flags(const double* __restrict__ before, const double* __restrict__ after, int* __restrict__ flag,
                              int* __restrict__ any, int nrhs) {
@@ -708,6 +857,47 @@ struct Krylov final : KrylovEngine {
         return HELM_OK;
     }
 
+    // CGS2 in three passes over the basis (up to 32 basis vectors): h1 = V^H w; w' = w - V h1 fused with
+    // h2 = V^H w' and ||w'||; H[.][j] = h1 + h2, H[j+1][j] = sqrt(||w'||^2 - ||h2||^2); the Givens step; then
+    // v_{j+1} = (w' - V h2) / H[j+1][j] fused with the second update.
+    helm_status cgs2_fused(int j) {
+        const int ni = j + 1;
+        // one resident block per SM for the fused kernel: the largest multiple of q <= the SM count
+        int a = RED_THREADS, bq = S;
+        while (bq) { const int t = a % bq; a = bq; bq = t; }
+        const int q = S / a;
+        const int nb1 = std::min(nblk, std::max(q, (std::max(1, ctx->sm_count) / q) * q));
+        dots_pass(V, w, ni, nullptr, nullptr);
+        finish_into(ni, hpass, S, 1, 0, 0, nullptr, nullptr);
+        finish_into(ni, H, m, (m + 1) * m, j, 0, nullptr, nullptr);
+        {
+            const int tk = prof_begin(ctx, "arnoldi");
+            if (ni <= 8)
+                update_dots_kernel<T, 8><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
+            else if (ni <= 16 || sizeof(T) == 8)
+                update_dots_kernel<T, 16><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
+            else
+                update_dots_kernel<T, (sizeof(T) == 4 ? 32 : 16)><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni,
+                                                                                           hpass, part, ldp, dpart);
+            prof_end(ctx, tk, (double)(ni + 2) * nel * sizeof(cplx<T>));
+        }
+        finish_dots<<<ni * S, 128, 0, st>>>(part, nb1, ldp, ni, S, hpass, S, 1, 0, 0, nullptr, nullptr);
+        finish_dots<<<ni * S, 128, 0, st>>>(part, nb1, ldp, ni, S, H, m, (m + 1) * m, j, 1, nullptr, nullptr);
+        finish_norm2<<<S, 128, 0, st>>>(dpart, nb1, S, na);
+        second_norm<<<rg, 128, 0, st>>>(na, hpass, ni, S, hn);
+        ctx->launches += 5;
+        HELM_CUDA(ctx, cudaMemsetAsync(running, 0, sizeof(int), st));
+        givens_step<<<rg, 128, 0, st>>>(Sd, H, cs, sn, gv, hn, inv, j, m, S, running);
+        {
+            const int tk = prof_begin(ctx, "arnoldi");
+            update_scale_kernel<T><<<nblk, RED_THREADS, (size_t)ni * S * sizeof(cplx<T>), st>>>(
+                V, nel, w, V + (long long)(j + 1) * nel, nel, S, ni, hpass, inv);
+            prof_end(ctx, tk, (double)(ni + 2) * nel * sizeof(cplx<T>));
+        }
+        ctx->launches += 2;
+        return cuda_check(ctx, cudaGetLastError(), "Krylov iteration");
+    }
+
     // Iteration j of a cycle: z_j = M^{-1} v_j, w = A z_j, CGS with selective re-orthogonalisation,
     // the Givens step and v_{j+1}; no host synchronisation inside, so it can be captured as a graph.
     helm_status iteration_body(int j) {
@@ -715,6 +905,9 @@ struct Krylov final : KrylovEngine {
         cplx<T>* zj = flex ? Zb + (long long)j * nel : u;
         HELM_TRY(oras_apply_wp(o, wp, vj, zj, S));
         HELM_TRY(launch_stencil(o->g, wp, zj, w, S, st));
+        // (complex128 bases: up to 16 vectors, the register budget of the fused kernel)
+        if (j + 1 <= (sizeof(T) == 4 ? 32 : 16) && (size_t)(j + 1) * S * sizeof(cplx<T>) <= 40 * 1024)
+            return cgs2_fused(j);
         // Classical Gram-Schmidt for column j of H (H[r][i][j]) with a second projection for the
         // columns whose norm dropped below 1/sqrt(2) of its value (selective re-orthogonalisation)
         dots_pass(V, w, j + 1, dpart, nullptr);

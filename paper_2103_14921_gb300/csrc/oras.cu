@@ -34,7 +34,8 @@ namespace {
 template <typename TO>
 __global__ void build_local_coef(const BoxInfo* __restrict__ boxes, const c128* __restrict__ tab,
                                  const c128* __restrict__ k2, const c128* __restrict__ c, int nx, int ny, int nz,
-                                 StencilW w, double omega, double h, int dirichlet, cplx<TO>* __restrict__ out) {
+                                 StencilW w, const StencilW* __restrict__ wtab, const unsigned char* __restrict__ wbin,
+                                 double omega, double h, int dirichlet, cplx<TO>* __restrict__ out) {
     const BoxInfo B = boxes[blockIdx.y];
     const long long nl = (long long)B.m * B.dims[2];
     for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (long long)gridDim.x * blockDim.x) {
@@ -43,7 +44,8 @@ __global__ void build_local_coef(const BoxInfo* __restrict__ boxes, const c128* 
         const int lk = (int)(l / B.m);
         const int gi = B.lo[0] + li, gj = B.lo[1] + lj, gk = B.lo[2] + lk;
         c128 a[27], loc[27];
-        global_row_coef27(tab, k2, nx, ny, nz, w, gi, gj, gk, a);
+        const long long gidx = ((long long)gk * ny + gj) * nx + gi;
+        global_row_coef27(tab, k2, nx, ny, nz, wtab ? wtab[wbin[gidx]] : w, gi, gj, gk, a);
         for (int d = 0; d < 27; ++d) loc[d] = mk<double>(0, 0);
         const c128 cv = c[((long long)gk * ny + gj) * nx + gi];
         const double den = cv.x * cv.x + cv.y * cv.y;
@@ -303,6 +305,44 @@ __global__ void coarse_prolong(const cplx<TC>* __restrict__ cv, cplx<TV>* __rest
     q[e] = acc;
 }
 
+// The same for complex64 with an even column count: a thread per fine node forms the 8 trilinear weights
+// and corner indices once and sweeps the columns in 16-byte pairs (the per-column kernel repeats that
+// integer work for every column).  grid: (x-line chunks of 128 nodes, y, z).
+__global__ void coarse_prolong_pairs(const c64* __restrict__ cv, c64* __restrict__ q, int nx, int ny, int nz, int cx,
+                                     int cy, int cz, int r, int nrhs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const float inv_r = 1.0f / (float)r;
+    const int I0 = i / r, J0 = j / r, K0 = k / r;
+    const float wx1 = (float)(i - r * I0) * inv_r, wy1 = (float)(j - r * J0) * inv_r, wz1 = (float)(k - r * K0) * inv_r;
+    const float wx[2] = {1.0f - wx1, wx1}, wy[2] = {1.0f - wy1, wy1}, wz[2] = {1.0f - wz1, wz1};
+    float wt[8];
+    long long base[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+        const bool in = I0 + a < cx && J0 + b < cy && K0 + d < cz;
+        wt[c] = in ? wx[a] * wy[b] * wz[d] : 0.0f;
+        // a corner past the coarse grid has weight 0: point it at the base corner
+        base[c] = in ? (((long long)(K0 + d) * cy + (J0 + b)) * cx + (I0 + a)) * nrhs
+                     : (((long long)K0 * cy + J0) * cx + I0) * nrhs;
+    }
+    float4* out = reinterpret_cast<float4*>(q + (((long long)k * ny + j) * nx + i) * nrhs);
+    for (int p = 0; p < nrhs / 2; ++p) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float4 x = *reinterpret_cast<const float4*>(cv + base[c] + 2 * p);
+            acc.x += wt[c] * x.x;
+            acc.y += wt[c] * x.y;
+            acc.z += wt[c] * x.z;
+            acc.w += wt[c] * x.w;
+        }
+        out[p] = acc;
+    }
+}
+
 // Probe vectors: zc[i * 27 + c] = (Z e_c)_i, e_c = indicator of the coarse nodes of colour c = (J mod 3).
 __global__ void coarse_probe_vectors(c128* __restrict__ zc, int nx, int ny, int nz, int cx, int cy, int cz, int r) {
     const long long n = (long long)nx * ny * nz;
@@ -508,10 +548,12 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
         const dim3 grid(grid_for(mx, 128, 4096), o->fine.nbox);
         if (o->fine.prec == HELM_PREC_FP64)
             build_local_coef<double><<<grid, 128, 0, st>>>(o->fine.dbox, g->tab, g->k2, g->c, n[0], n[1], n[2], g->w,
-                                                           g->omega, g->d.h, d->interface_bc, (c128*)o->fine.coef);
+                                                           g->wtab, g->wbin, g->omega, g->d.h, d->interface_bc,
+                                                           (c128*)o->fine.coef);
         else
             build_local_coef<float><<<grid, 128, 0, st>>>(o->fine.dbox, g->tab, g->k2, g->c, n[0], n[1], n[2], g->w,
-                                                          g->omega, g->d.h, d->interface_bc, (c64*)o->fine.coef);
+                                                          g->wtab, g->wbin, g->omega, g->d.h, d->interface_bc,
+                                                          (c64*)o->fine.coef);
         ctx->launches++;
         if ((rc = cuda_check(ctx, cudaGetLastError(), "build_local_coef"))) return fail(rc);
     }
@@ -708,8 +750,13 @@ helm_status apply_t(helm_oras o, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
             prof_end(ctx, tk, vb);
             HELM_TRY(planeset_solve(ctx, o->coarse32, o->cvec, o->crbuf, nrhs, st, o->dev_err));
             tk = prof_begin(ctx, "coarse_prolong");
-            coarse_prolong<float, TV><<<dim3((unsigned)((nx * nrhs + 255) / 256), (unsigned)ny, (unsigned)nz), 256, 0,
-                                        st>>>((const c64*)o->cvec, (cplx<TV>*)o->qf, nx, ny, nz, cx, cy, cz, r, nrhs);
+            if (sizeof(TV) == 4 && nrhs % 2 == 0 && (((uintptr_t)o->cvec | (uintptr_t)o->qf) & 15) == 0)
+                coarse_prolong_pairs<<<dim3((unsigned)((nx + 127) / 128), (unsigned)ny, (unsigned)nz), 128, 0, st>>>(
+                    (const c64*)o->cvec, (c64*)o->qf, nx, ny, nz, cx, cy, cz, r, nrhs);
+            else
+                coarse_prolong<float, TV><<<dim3((unsigned)((nx * nrhs + 255) / 256), (unsigned)ny, (unsigned)nz), 256,
+                                            0, st>>>((const c64*)o->cvec, (cplx<TV>*)o->qf, nx, ny, nz, cx, cy, cz, r,
+                                                     nrhs);
         } else {
             restrict_separable<TV, double>(v, t1, t2, o->cvec, nx, ny, nz, cx, cy, cz, r, nrhs, st);
             prof_end(ctx, tk, vb);

@@ -47,7 +47,7 @@ struct SRequest {
 
 bool same_grid(const helm_grid_desc& a, const helm_grid_desc& b) {
     if (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.h != b.h || a.freq_hz != b.freq_hz || a.npml != b.npml ||
-        a.pml_R != b.pml_R || a.top_bc != b.top_bc)
+        a.pml_R != b.pml_R || a.top_bc != b.top_bc || a.weight_bins != b.weight_bins)
         return false;
     for (int i = 0; i < 7; ++i)
         if (a.weights[i] != b.weights[i]) return false;

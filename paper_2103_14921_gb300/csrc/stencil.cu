@@ -50,7 +50,9 @@ __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict_
                                                       cplx<T>* __restrict__ y,
                                                       const cplx<T>* __restrict__ k2,
                                                       const cplx<T>* __restrict__ tab, int nx, int ny, int nz,
-                                                      int nrhs_rt, StencilW w, Interior in) {
+                                                      int nrhs_rt, StencilW w, Interior in,
+                                                      const StencilW* __restrict__ wtab,
+                                                      const unsigned char* __restrict__ wbin) {
     // grid: (x-line chunks, y, z); a thread owns node (i, j, k) and columns [ch RCH, ch RCH + RCH)
     const int nrhs = NR > 0 ? NR : nrhs_rt;
     const int nch = nrhs / RCH;
@@ -64,6 +66,7 @@ __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict_
     const cplx<T>* up = u + p * nrhs + (long long)ch * RCH;
     const cplx<T>* kp = k2 + p;
 
+    if (wtab) w = wtab[wbin[p]];   // adaptive weights: this row's bin
     const T ih2 = (T)w.inv_h2;
     const cplx<T> zero = mk<T>(0, 0);
     cplx<T> acc[RCH];
@@ -72,10 +75,22 @@ __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict_
 
     if (i >= in.lo[0] && i <= in.hi[0] && j >= in.lo[1] && j <= in.hi[1] && k >= in.lo[2] && k <= in.hi[2]) {
         T L[4], M[4];
+        if (wtab) {
+            // class constants of this row's weights (the same identities as for the grid's constant weights)
+            const double Lr[4] = {-6.0 + 12.0 * w.a2 - 8.0 * w.a3, 1.0 - 4.0 * w.a2 + 4.0 * w.a3, w.a2 - 2.0 * w.a3, w.a3};
+            const double Mr[4] = {w.m0 - 6.0 * w.m1 + 12.0 * w.m2 - 8.0 * w.m3, w.m1 - 4.0 * w.m2 + 4.0 * w.m3,
+                                  w.m2 - 2.0 * w.m3, w.m3};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            L[c] = (T)(in.Lc[c] * w.inv_h2);
-            M[c] = (T)in.Mc[c];
+            for (int c = 0; c < 4; ++c) {
+                L[c] = (T)(Lr[c] * w.inv_h2);
+                M[c] = (T)Mr[c];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                L[c] = (T)(in.Lc[c] * w.inv_h2);
+                M[c] = (T)in.Mc[c];
+            }
         }
         // one z-plane of 9 neighbours at a time: its 18 loads are issued together, then the FMAs
 #pragma unroll
@@ -166,21 +181,29 @@ __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict_
     *reinterpret_cast<CPack<T, RCH>*>(y + p * nrhs + (long long)ch * RCH) = out;
 }
 
+struct RowW {
+    const StencilW* wtab;
+    const unsigned char* wbin;
+};
+
 template <typename T, int RCH, bool SUB, int NR = 0>
 void launch_t(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab,
-              const helm_grid_desc& d, int nrhs, const StencilW& w, const Interior& in, bool realk, cudaStream_t s) {
+              const helm_grid_desc& d, int nrhs, const StencilW& w, const Interior& in, bool realk, RowW rw,
+              cudaStream_t s) {
     const int threads = 128;
     const dim3 grid((unsigned)((d.nx * (nrhs / RCH) + threads - 1) / threads), (unsigned)d.ny, (unsigned)d.nz);
     if (realk)
-        stencil_kernel<T, RCH, SUB, true, NR><<<grid, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w, in);
+        stencil_kernel<T, RCH, SUB, true, NR><<<grid, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w, in,
+                                                                       rw.wtab, rw.wbin);
     else
         stencil_kernel<T, RCH, SUB, false, NR><<<grid, threads, 0, s>>>(u, b, y, k2, tab, d.nx, d.ny, d.nz, nrhs, w,
-                                                                        in);
+                                                                        in, rw.wtab, rw.wbin);
 }
 
 template <typename T, bool SUB>
 void dispatch(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2, const cplx<T>* tab,
-              const helm_grid_desc& d, int nrhs, const StencilW& w, const Interior& in, bool realk, cudaStream_t s) {
+              const helm_grid_desc& d, int nrhs, const StencilW& w, const Interior& in, bool realk, RowW rw,
+              cudaStream_t s) {
     // complex64: one 16-byte vector per thread and neighbour, two columns when the column count is
     // even and every base address is 16-byte aligned, else one.  complex128 (FP64-pipe bound on this
     // part): up to four columns per thread, so each neighbour's coefficient is formed once for four
@@ -190,15 +213,15 @@ void dispatch(const cplx<T>* u, const cplx<T>* b, cplx<T>* y, const cplx<T>* k2,
     };
     if constexpr (sizeof(T) == 4) {
         if (nrhs == 16 && al(16))
-            launch_t<T, 2, SUB, 16>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+            launch_t<T, 2, SUB, 16>(u, b, y, k2, tab, d, nrhs, w, in, realk, rw, s);
         else if (nrhs % 2 == 0 && al(16))
-            launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+            launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, rw, s);
         else
-            launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+            launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, rw, s);
     } else {
-        if (nrhs % 4 == 0 && al(64)) launch_t<T, 4, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
-        else if (nrhs % 2 == 0 && al(32)) launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
-        else launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, s);
+        if (nrhs % 4 == 0 && al(64)) launch_t<T, 4, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, rw, s);
+        else if (nrhs % 2 == 0 && al(32)) launch_t<T, 2, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, rw, s);
+        else launch_t<T, 1, SUB>(u, b, y, k2, tab, d, nrhs, w, in, realk, rw, s);
     }
 }
 
@@ -232,12 +255,13 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
     const double bytes = (double)g->n * es * ((SUB ? 3.0 : 2.0) * nrhs + 1.0);
     const int tok = prof_begin(g->ctx, prec == HELM_PREC_FP64 ? "stencil64" : "stencil");
     const Interior in = interior_of(g);
+    const RowW rw{g->wtab, g->wbin};
     if (prec == HELM_PREC_FP64) {
         dispatch<double, SUB>((const c128*)u, (const c128*)b, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, in,
-                              g->k2_real, s);
+                              g->k2_real, rw, s);
     } else {
         dispatch<float, SUB>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, in,
-                             g->k2_real, s);
+                             g->k2_real, rw, s);
     }
     prof_end(g->ctx, tok, bytes);
     HELM_LAUNCH_CHECK(g->ctx, "stencil_kernel");

@@ -42,7 +42,8 @@ class HelmError(RuntimeError):
 
 class GridDesc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double), ("freq_hz", C.c_double),
-                ("npml", C.c_int), ("pml_R", C.c_double), ("top_bc", C.c_int), ("weights", C.c_double * 7)]
+                ("npml", C.c_int), ("pml_R", C.c_double), ("top_bc", C.c_int), ("weights", C.c_double * 7),
+                ("weight_bins", C.c_int)]
 
 
 class OrasDesc(C.Structure):
@@ -94,6 +95,7 @@ def lib():
         "helm_fit_weights": (st, [C.c_double, C.c_double, C.POINTER(C.c_double)]),
         "helm_setup_grid": (st, [vp, C.POINTER(GridDesc), vp, C.POINTER(vp)]),
         "helm_destroy_grid": (None, [vp]),
+        "helm_grid_row_weights": (st, [vp, C.POINTER(C.c_int), vp, vp]),
         "helm_apply": (st, [vp, i32, vp, vp, i32]),
         "oras_factor": (st, [vp, C.POINTER(OrasDesc), C.POINTER(vp)]),
         "oras_destroy": (None, [vp]),
@@ -200,11 +202,12 @@ class Grid:
     """``helm_setup_grid``: one problem (grid, medium, frequency)."""
 
     def __init__(self, ctx: Context, nx, ny, nz, h, freq_hz, c, npml=8, top_bc=TOP_DIRICHLET, pml_R=1e-3,
-                 weights=None):
+                 weights=None, weight_bins=0):
+        """``weight_bins > 0``: adaptive weights matched to the local wave speed (``row_weights()``)."""
         import torch
         if weights is None:
             weights = fit_weights()
-        d = GridDesc(nx, ny, nz, h, freq_hz, npml, pml_R, top_bc, (C.c_double * 7)(*weights))
+        d = GridDesc(nx, ny, nz, h, freq_hz, npml, pml_R, top_bc, (C.c_double * 7)(*weights), weight_bins)
         self.ctx = ctx
         self.desc = d
         self.shape = (nz, ny, nx)
@@ -226,6 +229,17 @@ class Grid:
             y = torch.empty_like(u)
         self.ctx.check(lib().helm_apply(self._h, prec, _ptr(u), _ptr(y), nrhs), "helm_apply")
         return y
+
+    def row_weights(self):
+        """``(edges[nbins + 1], table[nbins, 7])`` of the adaptive weights (``None`` for constant weights)."""
+        nb = C.c_int()
+        self.ctx.check(lib().helm_grid_row_weights(self._h, C.byref(nb), None, None), "helm_grid_row_weights")
+        if nb.value == 0:
+            return None
+        edges = (C.c_double * (nb.value + 1))()
+        table = (C.c_double * (nb.value * 7))()
+        self.ctx.check(lib().helm_grid_row_weights(self._h, C.byref(nb), edges, table), "helm_grid_row_weights")
+        return np.array(edges[:]), np.array(table[:]).reshape(nb.value, 7)
 
     def close(self):
         if self._h:

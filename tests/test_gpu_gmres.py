@@ -198,3 +198,29 @@ def test_inexact_coarse_fgmres_mixed_precision(ctx):
         assert st1[r]["converged"], st1[r]
         assert _residual(prob, x[..., r], b[..., r]) <= tol
         assert _rel(x[..., r], xs[..., r]) <= 10 * tol
+
+
+def test_adaptive_weights_two_level_solve(ctx):
+    """The two-level FGMRES solve with adaptive stencil weights (TF32 local factors): converged, the oracle's
+    FP64 residual of its own row-weighted operator <= tol, and within 10 x tol of its direct solution."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    from oracle.weights import row_weight_bins
+    nx, ny, nz = 26, 24, 28
+    h, f = 25.0, 7.0
+    c = synth.linear_gradient(nx, ny, nz, h, 1000.0, 2.0)
+    w = helm.fit_weights()
+    grid = helm.Grid(ctx, nx, ny, nz, h, f, c, npml=4, weights=w, weight_bins=4)
+    edges, table = grid.row_weights()
+    prob = Problem(nx, ny, nz, h, f, c, npml=4, weights=w, row_weights=table[row_weight_bins(c, f, h, edges)])
+    pos = synth.source_plane_positions(nx, ny, 4, 3, 3, 13)
+    b = synth.point_sources(nx, ny, nz, h, pos)
+    xs = direct_solve_planes(prob, b.reshape(-1, 3)).reshape(b.shape)
+    tol = 1e-6
+    o = helm.Oras(grid, (2, 2, 2), 2, coarse_ratio=4, factor_prec=helm.PREC_TF32)
+    x, st = o.solve(torch.from_numpy(b).cuda(), tol=tol, restart=30, basis_prec=helm.PREC_FP32)
+    x = x.cpu().numpy()
+    for r in range(3):
+        assert st[r]["converged"]
+        assert _residual(prob, x[..., r], b[..., r]) <= tol
+        assert _rel(x[..., r], xs[..., r]) <= 10 * tol

@@ -82,6 +82,34 @@ def test_stencil_fp32_vector_and_scalar_paths_agree(ctx):
     assert _rel(a, want) <= 1e-5 and _rel(b, want) <= 1e-5
 
 
+@pytest.mark.parametrize("top,Q", [(False, None), (True, 60.0)])
+def test_adaptive_weights_stencil_matches_oracle(ctx, top, Q):
+    """Adaptive weights (each row with the least-squares weights of its points-per-wavelength bin): the
+    library's bin edges agree with the oracle's formula, and with the library's per-bin weights the oracle's
+    row-weighted operator equals the GPU stencil (FP64 1e-12, FP32 1e-5)."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    from oracle.weights import adaptive_bin_edges, row_weight_bins
+    nx, ny, nz, h, f = 21, 19, 30, 25.0, 8.0
+    c = synth.linear_gradient(nx, ny, nz, h, 1000.0, 2.0, Q=Q)          # 5.2 .. 8.9 points per wavelength
+    w = helm.fit_weights()
+    grid = helm.Grid(ctx, nx, ny, nz, h, f, c, npml=4, top_bc=helm.TOP_PML if top else helm.TOP_DIRICHLET,
+                     weights=w, weight_bins=4)
+    edges, table = grid.row_weights()
+    G = np.real(c) / (f * h)
+    assert np.allclose(edges, adaptive_bin_edges(G.min(), G.max(), 4), rtol=1e-13, atol=0)
+    bins = row_weight_bins(c, f, h, edges)
+    assert len(np.unique(bins)) == 4
+    prob = Problem(nx, ny, nz, h, f, c, npml=4, top_pml=top, weights=w, row_weights=table[bins])
+    u = synth.random_complex((nz, ny, nx, 3), 92)
+    want = apply_A(prob, u)
+    assert _rel(grid.apply(torch.from_numpy(u).cuda()).cpu().numpy(), want) <= 1e-12
+    u16 = synth.random_complex((nz, ny, nx, 16), 93)
+    want16 = apply_A(prob, u16)
+    got16 = grid.apply(torch.from_numpy(u16.astype(np.complex64)).cuda(), prec=helm.PREC_FP32).cpu().numpy()
+    assert _rel(got16.astype(np.complex128), want16) <= 1e-5
+
+
 def test_stencil_fitted_weights_full_size_sampled(ctx):
     """112^3 x 16 (the two-level workload's size): sampled rows against the oracle's assembled rows."""
     import torch
