@@ -237,6 +237,12 @@ typedef struct {
     int    maxit;         /* total iteration cap per column                                   */
     int    flexible;      /* 1 = FGMRES (keeps Z_j = M^{-1} v_j), 0 = right-preconditioned GMRES */
     int    basis_prec;    /* HELM_PREC_FP64 (complex128 basis) or HELM_PREC_FP32 (complex64)  */
+    int    use_x0;        /* 0: x0 = 0; 1: x holds the initial guess on entry (a warm start, e.g.
+                             the solution at a neighbouring frequency of a sweep); columns whose
+                             b is zero still return x = 0, and a column whose guess already has an
+                             FP64 relative residual <= tol returns it unchanged with 0 iterations.
+                             A NaN/Inf in x gives HELM_ENONFINITE.  gmres_solve only (helm_submit
+                             rejects it with HELM_EINVAL)                                        */
 } helm_gmres_desc;
 
 typedef struct {
@@ -247,7 +253,7 @@ typedef struct {
 } helm_rhs_stats;
 
 /* Solve A x = b for nrhs columns with right-preconditioned (F)GMRES(m),
- * x0 = 0, independent Krylov spaces per column, CGS2 Arnoldi with FP64
+ * x0 = 0 (or the caller's x with use_x0), independent Krylov spaces per column, CGS2 Arnoldi with FP64
  * accumulation, complex Givens rotations, FP64 true residual at every cycle
  * end (restart if above tol).  b, x complex128 [N][nrhs]; device or host.
  * stats (host array of nrhs, may be NULL) receives per-column results.

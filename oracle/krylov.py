@@ -36,8 +36,9 @@ def givens(a: complex, b: complex):
     return abs(a) / t, (a / abs(a)) * np.conj(b) / t
 
 
-def gmres(apply_A, b, apply_M=None, tol=1e-6, restart=30, maxit=1000, flexible=True, record=None):
-    """Solve ``A x = b`` for one right-hand side ``b`` (complex vector).
+def gmres(apply_A, b, apply_M=None, tol=1e-6, restart=30, maxit=1000, flexible=True, record=None, x0=None):
+    """Solve ``A x = b`` for one right-hand side ``b`` (complex vector), from ``x0`` (zero by default;
+    ``b = 0`` gives ``x = 0`` whatever ``x0``).
 
     Returns ``(x, info)``; ``info`` holds ``iterations``, ``converged``,
     ``estimates`` (relative residual estimate after each iteration) and
@@ -55,6 +56,13 @@ def gmres(apply_A, b, apply_M=None, tol=1e-6, restart=30, maxit=1000, flexible=T
         return x, info
     total = 0
     r = b.copy()
+    if x0 is not None:
+        x = np.array(x0, dtype=np.complex128)
+        r = b - apply_A(x)
+        rel = np.linalg.norm(r) / bnorm
+        if rel <= tol:
+            info.update(true_residual=float(rel))
+            return x, info
     while True:
         info["cycles"] += 1
         beta = np.linalg.norm(r)

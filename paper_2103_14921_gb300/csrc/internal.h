@@ -280,7 +280,9 @@ struct KrylovEngine {
     virtual const RhsState& state(int c) const = 0;
     virtual double true_rel(int c) const = 0;
     virtual size_t bytes() const = 0;
-    virtual helm_status begin_columns(const int* cols, int n, const double* tol, const int* maxit) = 0;
+    // warm: X() holds the initial guess of every column (all S columns must be listed): r = b - A x
+    virtual helm_status begin_columns(const int* cols, int n, const double* tol, const int* maxit,
+                                      bool warm = false) = 0;
     virtual void retire(int c) = 0;
     virtual helm_status push_state() = 0;
     virtual helm_status cycle(bool* any_left) = 0;

@@ -822,26 +822,53 @@ struct Krylov final : KrylovEngine {
     }
 
     // Start the listed columns (their b already in B()): x = 0, r = b, state reset.
-    helm_status begin_columns(const int* cols, int n, const double* tol, const int* maxit) override {
+    helm_status begin_columns(const int* cols, int n, const double* tol, const int* maxit, bool warm) override {
+        if (warm && n != S) return set_error(ctx, HELM_EINVAL, "gmres_solve: a warm start lists every column");
         std::vector<int> hm(S, 0);
         for (int i = 0; i < n; ++i) hm[cols[i]] = 1;
         HELM_CUDA(ctx, cudaMemcpyAsync(mask, hm.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
         int* bad = running + 1;
         HELM_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), st));
         finite_check_cols<<<eg, 256, 0, st>>>(Bd, mask, nel, S, bad);
-        start_columns_kernel<<<eg, 256, 0, st>>>(Bd, Xd, r, mask, nel, S);
-        ctx->launches += 2;
+        ctx->launches++;
+        if (warm) {
+            finite_check_cols<<<eg, 256, 0, st>>>(Xd, mask, nel, S, bad);
+            ctx->launches++;
+        } else {
+            start_columns_kernel<<<eg, 256, 0, st>>>(Bd, Xd, r, mask, nel, S);
+            ctx->launches++;
+        }
         norms(Bd, beta);
         std::vector<double> hb(S);
         int hbad = 0;
         HELM_CUDA(ctx, cudaMemcpyAsync(hb.data(), beta, S * sizeof(double), cudaMemcpyDeviceToHost, st));
         HELM_CUDA(ctx, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
         HELM_CUDA(ctx, cudaStreamSynchronize(st));
-        if (hbad) return set_error(ctx, HELM_ENONFINITE, "gmres_solve: right-hand side has NaN/Inf");
+        if (hbad) return set_error(ctx, HELM_ENONFINITE, "gmres_solve: right-hand side or initial guess has NaN/Inf");
+        if (warm) {
+            // columns with b = 0 return x = 0; the others start from r = b - A x0 (FP64)
+            std::vector<int> hz(S, 0);
+            for (int c = 0; c < S; ++c) hz[c] = hb[c] == 0.0 ? 1 : 0;
+            HELM_CUDA(ctx, cudaMemcpyAsync(mask, hz.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+            start_columns_kernel<<<eg, 256, 0, st>>>(Bd, Xd, r, mask, nel, S);
+            ctx->launches++;
+            HELM_TRY(launch_stencil_sub(o->g, HELM_PREC_FP64, Xd, Bd, r, S, st));
+        }
+        std::vector<double> hr(S, 0.0);
+        if (warm) {
+            norms(r, beta);
+            HELM_CUDA(ctx, cudaMemcpyAsync(hr.data(), beta, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+            HELM_CUDA(ctx, cudaStreamSynchronize(st));
+        }
         for (int i = 0; i < n; ++i) {
             const int c = cols[i];
-            hs[c] = RhsState{hb[c], 0, 0, 0, hb[c] == 0.0 ? 1 : 0, 0.0, tol[i], maxit[i]};
-            trel[c] = 0.0;
+            // a warm start that already meets its tolerance returns x0 with no iterations
+            const double rel = hb[c] > 0.0 ? hr[c] / hb[c] : 0.0;
+            if (warm && !std::isfinite(rel))
+                return set_error(ctx, HELM_ENONFINITE, "gmres_solve: residual of the initial guess is NaN/Inf");
+            const int done = hb[c] == 0.0 || (warm && rel <= tol[i]);
+            hs[c] = RhsState{hb[c], 0, 0, 0, done, 0.0, tol[i], maxit[i]};
+            trel[c] = warm ? rel : 0.0;
         }
         HELM_CUDA(ctx, cudaMemcpyAsync(Sd, hs.data(), S * sizeof(RhsState), cudaMemcpyHostToDevice, st));
         return HELM_OK;
@@ -1258,8 +1285,9 @@ helm_status solve_all(helm_oras o, c128* b, c128* x, int nrhs, const helm_gmres_
     std::vector<int> cols(nrhs), maxit(nrhs, D.maxit);
     std::vector<double> tol(nrhs, D.tol);
     for (int i = 0; i < nrhs; ++i) cols[i] = i;
-    HELM_TRY(K->begin_columns(cols.data(), nrhs, tol.data(), maxit.data()));
-    bool any = true;
+    HELM_TRY(K->begin_columns(cols.data(), nrhs, tol.data(), maxit.data(), D.use_x0 != 0));
+    bool any = false;
+    for (int i = 0; i < nrhs; ++i) any = any || !K->state(i).done;
     while (any) HELM_TRY(K->cycle(&any));
     bool all = true;
     for (int i = 0; i < nrhs; ++i) {
@@ -1281,7 +1309,7 @@ extern "C" helm_status gmres_solve(helm_oras o, const void* b, void* x, int nrhs
     helm_ctx ctx = o->g->ctx;
     if (!b || !x || !d || nrhs < 0) return set_error(ctx, HELM_EINVAL, "gmres_solve: invalid argument");
     if (!(d->tol > 0) || d->restart < 1 || d->restart > 200 || d->maxit < 1 ||
-        (d->basis_prec != HELM_PREC_FP64 && d->basis_prec != HELM_PREC_FP32))
+        (d->basis_prec != HELM_PREC_FP64 && d->basis_prec != HELM_PREC_FP32) || (d->use_x0 != 0 && d->use_x0 != 1))
         return set_error(ctx, HELM_EINVAL, "gmres_solve: invalid solver description");
     if (nrhs == 0) return HELM_OK;
     if (nrhs > 256) return set_error(ctx, HELM_EINVAL, "gmres_solve: at most 256 right-hand sides per call");
@@ -1304,6 +1332,13 @@ extern "C" helm_status gmres_solve(helm_oras o, const void* b, void* x, int nrhs
             return rc;
         }
         xd = (c128*)stage_x;
+        if (d->use_x0 && (rc = cuda_check(ctx, cudaMemcpyAsync(stage_x, x, bytes, cudaMemcpyHostToDevice, st),
+                                          "copy x0"))) {
+            cudaStreamSynchronize(st);
+            dev_free(ctx, stage_b, bytes);
+            dev_free(ctx, stage_x, bytes);
+            return rc;
+        }
     }
     helm_status rc = solve_all(o, bd, xd, nrhs, *d, stats);
     if (!xdev && (rc == HELM_OK || rc == HELM_ENOTCONV)) {

@@ -370,6 +370,7 @@ extern "C" helm_status helm_submit(helm_ctx ctx, const helm_request* req, uint64
         req->gmres.restart < 1 || req->gmres.restart > 200 || req->gmres.maxit < 1 ||
         (req->gmres.basis_prec != HELM_PREC_FP64 && req->gmres.basis_prec != HELM_PREC_FP32))
         return set_error(ctx, HELM_EINVAL, "helm_submit: malformed request");
+    if (req->gmres.use_x0) return set_error(ctx, HELM_EINVAL, "helm_submit: warm starts are for gmres_solve only");
     SRequest* r = new SRequest();
     r->req = *req;
     r->t_submit = Clock::now();

@@ -183,21 +183,16 @@ __global__ void __launch_bounds__(CO_THREADS, 1) coarse_sweeps(const BoxInfo* __
                 const int rbase = i0 + half * 4;   // first of this lane's 4 rows (tile-local)
                 // lanes rl >= rn accumulate values that are never written out
                 const c64* bcol = rs + rl;
-                if (rbase + 3 < nrow) {
-                    const c64* g = gsm + (size_t)rbase * gp;
+                // every lane runs the same loop: rows past the CTA's last are clamped onto it (their sums are
+                // never written), so the two half-warps never diverge
+                const c64* g[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) g[i] = gsm + (size_t)min(rbase + i, nrow - 1) * gp;
 #pragma unroll 4
-                    for (int q = q0; q < q1; ++q) {
-                        const c64 bv = bcol[(size_t)q * CO_RN];
+                for (int q = q0; q < q1; ++q) {
+                    const c64 bv = bcol[(size_t)q * CO_RN];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) cmac(acc[i], g[(size_t)i * gp + q], bv);
-                    }
-                } else {
-                    for (int q = q0; q < q1; ++q) {
-                        const c64 bv = bcol[(size_t)q * CO_RN];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (rbase + i < nrow) cmac(acc[i], gsm[(size_t)(rbase + i) * gp + q], bv);
-                    }
+                    for (int i = 0; i < 4; ++i) cmac(acc[i], g[i][q], bv);
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) red[(wid * CO_ROWS + half * 4 + i) * CO_RN + rl] = acc[i];

@@ -54,7 +54,7 @@ class OrasDesc(C.Structure):
 
 class GmresDesc(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("flexible", C.c_int),
-                ("basis_prec", C.c_int)]
+                ("basis_prec", C.c_int), ("use_x0", C.c_int)]
 
 
 class RhsStats(C.Structure):
@@ -299,14 +299,16 @@ class Oras:
         return out
 
     def solve(self, b, x=None, tol=1e-6, restart=30, maxit=1000, flexible=True, basis_prec=PREC_FP64,
-              allow_notconv=False):
-        """``gmres_solve``; b is complex128 ``[nz, ny, nx, nrhs]`` (CUDA or pinned/pageable CPU tensor)."""
+              allow_notconv=False, warm=False):
+        """``gmres_solve``; b is complex128 ``[nz, ny, nx, nrhs]`` (CUDA or pinned/pageable CPU tensor).
+        ``warm=True``: ``x`` (required) holds the initial guess on entry."""
         import torch
         assert b.dtype == torch.complex128 and b.is_contiguous()
         nrhs = b.numel() // self.grid.n
         if x is None:
+            assert not warm, "a warm start needs x"
             x = torch.empty_like(b)
-        d = GmresDesc(tol, restart, maxit, 1 if flexible else 0, basis_prec)
+        d = GmresDesc(tol, restart, maxit, 1 if flexible else 0, basis_prec, 1 if warm else 0)
         stats = (RhsStats * max(nrhs, 1))()
         st = lib().gmres_solve(self._h, _ptr(b), _ptr(x), nrhs, C.byref(d), stats)
         if st and not (allow_notconv and st == ENOTCONV):

@@ -224,3 +224,48 @@ def test_adaptive_weights_two_level_solve(ctx):
         assert st[r]["converged"]
         assert _residual(prob, x[..., r], b[..., r]) <= tol
         assert _rel(x[..., r], xs[..., r]) <= 10 * tol
+
+
+def test_warm_start_from_neighbouring_frequency(ctx):
+    """Warm starts (use_x0): the solution at 5.0 Hz as the initial guess at 5.2 Hz.  The GPU FP64 GMRES
+    from that guess converges with the oracle's FP64 residual <= tol, within 10 x tol of the direct
+    solution, in the oracle's iteration count (+-1) from the same guess; restarting from its own result
+    takes no iteration and returns it unchanged; a b = 0 column returns 0 whatever the guess."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (24, 22, 20)
+    pos = [(12, 11, 3), (5, 17, 9), (18, 6, 4)]
+    b = synth.point_sources(*dims, 25.0, pos)
+    b[..., 2] = 0.0
+    tol = 1e-8
+    grid0, _ = _problem(ctx, dims, f=5.0)
+    x0, _ = helm.Oras(grid0, (2, 2, 2), 2).solve(torch.from_numpy(b).cuda(), tol=tol, restart=30)
+    x0[..., 2] = 1.0 + 1.0j                        # a guess for the zero column that must be ignored
+    grid, prob = _problem(ctx, dims, f=5.2)
+    o = helm.Oras(grid, (2, 2, 2), 2)
+    _, cold = o.solve(torch.from_numpy(b).cuda(), tol=tol, restart=30)
+    x = x0.clone()
+    _, st = o.solve(torch.from_numpy(b).cuda(), x, tol=tol, restart=30, warm=True)
+    xh = x.cpu().numpy()
+    xs = direct_solve_planes(prob, b.reshape(-1, 3)).reshape(b.shape)
+    M = ORAS(prob, (2, 2, 2), 2)
+    A = assemble_A(prob)
+    x0h = x0.cpu().numpy()
+    for r in range(2):
+        assert st[r]["converged"]
+        assert _residual(prob, xh[..., r], b[..., r]) <= tol
+        assert _rel(xh[..., r], xs[..., r]) <= 10 * tol
+        _, info = gmres(lambda v: A @ v, b[..., r].ravel(), M.apply, tol=tol, restart=30,
+                        x0=x0h[..., r].ravel())
+        assert abs(st[r]["iterations"] - info["iterations"]) <= 1
+        assert st[r]["iterations"] < cold[r]["iterations"]
+    assert st[2]["iterations"] == 0 and torch.all(x[..., 2] == 0)
+    x2 = x.clone()
+    _, st2 = o.solve(torch.from_numpy(b).cuda(), x2, tol=tol, restart=30, warm=True)
+    assert all(s["iterations"] == 0 and s["converged"] for s in st2)
+    assert torch.equal(x2, x)
+    with pytest.raises(helm.HelmError) as e:           # nonfinite guess
+        x3 = x.clone()
+        x3[0, 0, 0, 0] = complex("nan")
+        o.solve(torch.from_numpy(b).cuda(), x3, tol=tol, warm=True)
+    assert e.value.status == helm.ENONFINITE

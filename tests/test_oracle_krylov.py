@@ -69,3 +69,22 @@ def test_restarted_and_flexible_agree_with_direct_solve():
 def test_zero_rhs_gives_zero():
     x, info = gmres(lambda v: v, np.zeros(4, complex))
     assert np.all(x == 0) and info["iterations"] == 0
+
+
+def test_initial_guess():
+    """From x0 = the solution: no iteration, x0 returned; from a restarted iterate: the method continues the
+    same solve (one restart cycle of GMRES(m) from x_m is the next cycle of the restarted run); b = 0 gives
+    x = 0 whatever x0."""
+    n = 60
+    A = _rand_matrix(n, 21, shift=2.5)
+    b = synth.random_complex((n,), 22)
+    xs = np.linalg.solve(A, b)
+    x, info = gmres(lambda v: A @ v, b, tol=1e-10, restart=10, x0=xs)
+    assert info["iterations"] == 0 and np.array_equal(x, xs)
+    x1, i1 = gmres(lambda v: A @ v, b, tol=1e-14, restart=8, maxit=8)          # one cycle, not converged
+    x2, i2 = gmres(lambda v: A @ v, b, tol=1e-14, restart=8, maxit=8, x0=x1)   # the second cycle
+    x12, i12 = gmres(lambda v: A @ v, b, tol=1e-14, restart=8, maxit=16)       # both cycles at once
+    assert np.allclose(x2, x12, rtol=0, atol=1e-12 * np.linalg.norm(x12))
+    assert np.isclose(i2["true_residual"], i12["true_residual"], rtol=1e-6)
+    x0, _ = gmres(lambda v: A @ v, np.zeros(n, complex), x0=xs)
+    assert not np.any(x0)
