@@ -113,11 +113,16 @@ helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launche
  * of the last gmres_solve on its ORAS handle (freed by oras_destroy, by a gmres_solve with
  * another slot count, restart, method or basis precision, or by setting this knob to 0) and
  * replays each Krylov iteration from a CUDA graph captured on its second use; 0 launches every
- * kernel from the host and frees the workspace after each call.  Returns HELM_EINVAL for an
- * unknown key or value out of range. */
+ * kernel from the host and frees the workspace after each call.  HELM_TUNE_TC_FLOW: 1 (default)
+ * runs both tensor-core sweeps of every box as one persistent launch that takes its work (row
+ * tiles of the products, tiles of the operand preparation) from a device queue, each box's next
+ * step queued as soon as its current one completes (an even number of right-hand sides and
+ * 16-byte aligned vectors; otherwise, and with 0, two launches per plane step).  Both give
+ * bit-identical results.  Returns HELM_EINVAL for an unknown key or value out of range. */
 #define HELM_TUNE_TC_STAGES 1
 #define HELM_TUNE_COARSE_COOP 2
 #define HELM_TUNE_GRAPHS 3
+#define HELM_TUNE_TC_FLOW 4
 helm_status helm_set_tuning(helm_ctx ctx, int key, int value);
 
 /* ------------------------------------------------------------ grid / model */

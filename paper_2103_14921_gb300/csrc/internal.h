@@ -73,6 +73,7 @@ struct helm_ctx_s {
     int tc_stages = 0;         // tuning: pipeline stages of the tensor-core sweep (0 = automatic)
     int coarse_coop = 1;       // tuning: one cooperative launch for the complex64 coarse sweeps
     int use_graphs = 1;        // tuning: Krylov iterations replayed from captured CUDA graphs
+    int tc_flow = 1;           // tuning: tensor-core sweeps as one persistent launch with a work queue
     uint64_t graph_gen = 1;    // bumped when a setting that captured graphs depend on changes
     cudaStream_t cap_stream = nullptr;   // private stream graphs are captured on (the context's may be
                                          // the legacy default stream, which cannot be captured)
@@ -160,6 +161,20 @@ struct PlaneSet {
 
 struct KrylovEngine;
 
+// Work queue of the persistent tensor-core sweep (sweep_tc.cu), sized by the box geometry alone.
+// One allocation: ctl (head, tail, one counter per box) and flag (one per pushed item) first, reset
+// before every launch, then the initial items and the pushed items (int4 each).
+struct TcFlow {
+    void* mem = nullptr;
+    size_t bytes = 0;
+    size_t reset_bytes = 0;
+    int* ctl = nullptr;
+    int* flag = nullptr;
+    int4* init = nullptr;
+    int4* items = nullptr;
+    int ninit = 0, total = 0;
+};
+
 struct helm_oras_s {
     helm_grid g = nullptr;
     helm_oras_desc d{};
@@ -183,6 +198,7 @@ struct helm_oras_s {
     void* tcb = nullptr;        // tensor-core sweep operand B^T, [nbox][tc_npad][2 ld] fp32
     void* lb = nullptr;         // restricted right-hand sides of the tensor-core sweeps (same layout as loc)
     int tc_npad = 0;
+    TcFlow flow;                // persistent tensor-core sweep queue (fine set with the tile layout)
     int* dev_err = nullptr;     // device error code of bounded waits (0 = none)
     uint64_t scratch_gen = 0;   // bumped whenever the apply scratch is reallocated
     // inexact coarse solve (coarse_iters > 0): one-level ORAS on the coarse grid and inner GMRES
@@ -249,8 +265,11 @@ helm_status planeset_solve_coop(helm_ctx ctx, const PlaneSet& P, c64* loc, c64* 
 // tensor-core sweeps (sweep_tc.cu), complex64 local vectors, padded factor layout
 int tc_npad(int nrhs);
 // lb: the restricted right-hand sides b (read by the forward sweep); loc receives y, then x.
+// flow (may be null): the queue of the persistent single-launch sweep, used when the context allows it.
 helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb, void* loc, void* bt, int npad, int nrhs,
-                              cudaStream_t st, int* err);
+                              cudaStream_t st, int* err, const TcFlow* flow = nullptr);
+helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F);
+void tc_flow_free(helm_ctx ctx, TcFlow& F);
 // Device bytes an ORAS handle with this description will hold (factors, local operators,
 // coarse level) plus its apply scratch for nrhs columns; an estimate for admission control.
 size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int nrhs);

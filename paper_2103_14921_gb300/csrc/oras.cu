@@ -666,6 +666,7 @@ static void free_scratch(helm_oras o) {
     o->tcb = nullptr;
     o->lb = nullptr;
     o->tc_npad = 0;
+    tc_flow_free(ctx, o->flow);
     o->loc = o->rbuf = o->qf = o->tf = nullptr;
     o->cvec = o->crbuf = nullptr;
     dev_free(ctx, o->cy, (size_t)o->nc * R * sizeof(c128));
@@ -695,6 +696,7 @@ static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
         HELM_TRY(dev_alloc(ctx, &o->tcb, bytes, "tensor-core sweep operand"));
         HELM_CUDA(ctx, cudaMemsetAsync(o->tcb, 0, bytes, ctx->stream));
         HELM_TRY(dev_alloc(ctx, &o->lb, (size_t)o->fine.nloc * R * fe, "restricted right-hand sides"));
+        if (!o->flow.mem) HELM_TRY(tc_flow_alloc(ctx, o->fine, o->flow));
     }
     if (o->nc) {
         HELM_TRY(dev_alloc(ctx, (void**)&o->cvec, (size_t)o->nc * R * sizeof(c128), "coarse vector"));
@@ -787,7 +789,7 @@ helm_status apply_t(helm_oras o, const cplx<TV>* v, cplx<TV>* out, int nrhs) {
     prof_end(ctx, tr, lb);
     ctx->launches++;
     if (o->fine.padded)
-        HELM_TRY(planeset_solve_tc(ctx, o->fine, o->lb, o->loc, o->tcb, o->tc_npad, nrhs, st, o->dev_err));
+        HELM_TRY(planeset_solve_tc(ctx, o->fine, o->lb, o->loc, o->tcb, o->tc_npad, nrhs, st, o->dev_err, &o->flow));
     else
         HELM_TRY(planeset_solve(ctx, o->fine, o->loc, o->rbuf, nrhs, st));
     tr = prof_begin(ctx, "oras_transfer");

@@ -25,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <vector>
+
 #include "internal.h"
 #include "tc.cuh"
 
@@ -128,24 +130,23 @@ template <> struct Pair2<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat162 make(float a, float b) { return __floats2bfloat162_rn(a, b); }
 };
 
-template <typename E>
-__global__ void __launch_bounds__(512) tc_prep2(const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
-                                                const c64* __restrict__ lb, const c64* __restrict__ loc,
-                                                E* __restrict__ bt, int ld2, int npad, int nrhs, int s, int fwd) {
-    extern __shared__ __align__(16) unsigned char prep_smem[];
-    c64* tile = reinterpret_cast<c64*>(prep_smem);   // [nrhs][PREP2_TP + 1]
-    const BoxInfo B = boxes[blockIdx.y];
+// One tile of tpn plane nodes of box B (index box) for step s: thread per (node, column pair), any
+// block size; tile is [nrhs][tpn + 1] complex64 in shared memory.
+template <typename E, bool CG = false>
+__device__ __forceinline__ void prep_tile(const BoxInfo& B, int box, int t, int tpn, const c64* __restrict__ coef,
+                                          const c64* __restrict__ lb, const c64* __restrict__ loc,
+                                          E* __restrict__ bt, int ld2, int npad, int nrhs, int s, int fwd, c64* tile) {
     const int m = B.m, bz = B.dims[2], bx = B.dims[0], by = B.dims[1];
     const int k = fwd ? s : bz - 1 - s;
     if (k < 0 || k >= bz || (!fwd && k == bz - 1)) return;
-    const int p0 = blockIdx.x * PREP2_TP;
+    const int p0 = t * tpn;
     if (p0 >= m) return;
     const int npair = nrhs >> 1;
     const long long plane = B.loc_off + (long long)k * m;
     const long long nbr = fwd ? plane - m : plane + m;
     const int off = fwd ? 0 : 18;
     const bool couple = !(fwd && k == 0);
-    for (int e = threadIdx.x; e < PREP2_TP * npair; e += blockDim.x) {
+    for (int e = threadIdx.x; e < tpn * npair; e += blockDim.x) {
         const int pr = e % npair, pl = e / npair, p = p0 + pl;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);   // columns 2 pr and 2 pr + 1: (re, im, re, im)
         if (p < m) {
@@ -161,7 +162,8 @@ __global__ void __launch_bounds__(512) tc_prep2(const BoxInfo* __restrict__ boxe
                 for (int d = 0; d < 9; ++d) {
                     const int qx = min(max(px + d % 3 - 1, 0), bx - 1), qy = min(max(py + d / 3 - 1, 0), by - 1);
                     c[d] = cp[d];
-                    v[d] = *reinterpret_cast<const float4*>(loc + (nbr + qy * bx + qx) * nrhs + 2 * pr);
+                    const float4* src = reinterpret_cast<const float4*>(loc + (nbr + qy * bx + qx) * nrhs + 2 * pr);
+                    v[d] = CG ? __ldcg(src) : *src;
                 }
 #pragma unroll
                 for (int d = 0; d < 9; ++d) {
@@ -174,19 +176,125 @@ __global__ void __launch_bounds__(512) tc_prep2(const BoxInfo* __restrict__ boxe
                 }
             }
         }
-        tile[(2 * pr) * (PREP2_TP + 1) + pl] = mk<float>(acc.x, acc.y);
-        tile[(2 * pr + 1) * (PREP2_TP + 1) + pl] = mk<float>(acc.z, acc.w);
+        tile[(2 * pr) * (tpn + 1) + pl] = mk<float>(acc.x, acc.y);
+        tile[(2 * pr + 1) * (tpn + 1) + pl] = mk<float>(acc.z, acc.w);
     }
     __syncthreads();
-    E* bb = bt + (size_t)blockIdx.y * npad * ld2;
+    E* bb = bt + (size_t)box * npad * ld2;
     typedef typename Pair2<E>::type P2;
-    for (int e = threadIdx.x; e < nrhs * PREP2_TP; e += blockDim.x) {
-        const int r = e / PREP2_TP, pl = e % PREP2_TP, p = p0 + pl;
+    for (int e = threadIdx.x; e < nrhs * tpn; e += blockDim.x) {
+        const int r = e / tpn, pl = e % tpn, p = p0 + pl;
         if (p >= m) continue;
-        const c64 a = tile[r * (PREP2_TP + 1) + pl];
+        const c64 a = tile[r * (tpn + 1) + pl];
         *reinterpret_cast<P2*>(bb + (size_t)(2 * r) * ld2 + 2 * p) = Pair2<E>::make(a.x, -a.y);
         *reinterpret_cast<P2*>(bb + (size_t)(2 * r + 1) * ld2 + 2 * p) = Pair2<E>::make(a.y, a.x);
     }
+}
+
+// prep_tile for the persistent sweep.  One round of independent loads (8 per thread in flight) brings into
+// shared memory the tile's neighbour rows (a contiguous stretch of the neighbour plane, read from L2),
+// its 9 coupling coefficients per node and, forward, its right-hand sides; every value is then formed
+// from shared memory with the same operations in the same order as prep_tile, by a thread per
+// (node, column pair) with the node fastest, and written straight into its four B^T rows (coalesced
+// along the node).  Node rows are padded to npair + 1 float4 against bank conflicts.  Plane 0 of the
+// forward sweep (no coupling) and tiles whose data exceed smem_bytes use prep_tile.
+template <typename E>
+__device__ __forceinline__ void prep_tile_staged(const BoxInfo& B, int box, int t, int tpn,
+                                                 const c64* __restrict__ coef, const c64* __restrict__ lb,
+                                                 const c64* __restrict__ loc, E* __restrict__ bt, int ld2, int npad,
+                                                 int nrhs, int s, int fwd, unsigned char* smem, int smem_bytes) {
+    const int m = B.m, bz = B.dims[2], bx = B.dims[0], by = B.dims[1];
+    const int k = fwd ? s : bz - 1 - s;
+    if (k < 0 || k >= bz || (!fwd && k == bz - 1)) return;
+    const int p0 = t * tpn;
+    if (p0 >= m) return;
+    const int np = min(tpn, m - p0);
+    const int r_lo = max(p0 / bx - 1, 0), r_hi = min((p0 + np - 1) / bx + 1, by - 1);
+    const int ns = (r_hi - r_lo + 1) * bx;   // staged neighbour nodes
+    const int npair = nrhs >> 1, sp = npair + 1;
+    const int n1 = ns * npair, n2 = fwd ? np * npair : 0, n3 = np * 9;
+    const size_t need = ((size_t)ns * sp + (size_t)(fwd ? np : 0) * sp) * sizeof(float4) + (size_t)n3 * sizeof(float2);
+    if ((fwd && k == 0) || need > (size_t)smem_bytes) {
+        prep_tile<E, true>(B, box, t, tpn, coef, lb, loc, bt, ld2, npad, nrhs, s, fwd, reinterpret_cast<c64*>(smem));
+        return;
+    }
+    const long long plane = B.loc_off + (long long)k * m;
+    const long long nbr = fwd ? plane - m : plane + m;
+    const int off = fwd ? 0 : 18;
+    float4* stg = reinterpret_cast<float4*>(smem);            // [ns][sp]
+    float4* lbs = stg + (size_t)ns * sp;                        // [np][sp] (forward)
+    float2* cfs = reinterpret_cast<float2*>(lbs + (size_t)(fwd ? np : 0) * sp);   // [np][9]
+    const float4* nsrc = reinterpret_cast<const float4*>(loc + (nbr + (long long)r_lo * bx) * nrhs);
+    const float4* lsrc = reinterpret_cast<const float4*>(lb + (plane + p0) * nrhs);
+    const float2* csrc = reinterpret_cast<const float2*>(coef + (plane + p0) * 27 + off);
+    const int N = n1 + n2 + n3;
+    constexpr int U = 8;
+    for (int e0 = threadIdx.x; e0 < N; e0 += blockDim.x * U) {
+        float4 r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < n1) {
+                r[u] = __ldcg(nsrc + e);
+            } else if (e < n1 + n2) {
+                r[u] = lsrc[e - n1];
+            } else if (e < N) {
+                const int q = e - n1 - n2;
+                const float2 c = csrc[(q / 9) * 27 + q % 9];
+                r[u] = make_float4(c.x, c.y, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < n1)
+                stg[(e / npair) * sp + e % npair] = r[u];
+            else if (e < n1 + n2)
+                lbs[((e - n1) / npair) * sp + (e - n1) % npair] = r[u];
+            else if (e < N)
+                cfs[e - n1 - n2] = make_float2(r[u].x, r[u].y);
+        }
+    }
+    __syncthreads();
+    E* bb = bt + (size_t)box * npad * ld2;
+    typedef typename Pair2<E>::type P2;
+    for (int e = threadIdx.x; e < np * npair; e += blockDim.x) {
+        const int pl = e % np, pr = e / np, p = p0 + pl;
+        float4 acc = fwd ? lbs[pl * sp + pr] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int px = p % bx, py = p / bx;
+        float2 c[9];
+        float4 v[9];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+            const int qx = min(max(px + d % 3 - 1, 0), bx - 1), qy = min(max(py + d / 3 - 1, 0), by - 1);
+            c[d] = cfs[pl * 9 + d];
+            v[d] = stg[((qy - r_lo) * bx + qx) * sp + pr];
+        }
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+            const float sr = fwd ? -c[d].x : c[d].x, si = fwd ? -c[d].y : c[d].y;
+            acc.x = fmaf(sr, v[d].x, fmaf(-si, v[d].y, acc.x));
+            acc.y = fmaf(sr, v[d].y, fmaf(si, v[d].x, acc.y));
+            acc.z = fmaf(sr, v[d].z, fmaf(-si, v[d].w, acc.z));
+            acc.w = fmaf(sr, v[d].w, fmaf(si, v[d].z, acc.w));
+        }
+        // columns 2 pr (acc.x, acc.y) and 2 pr + 1 (acc.z, acc.w): B^T rows 4 pr .. 4 pr + 3 at entries 2p, 2p + 1
+        E* row = bb + (size_t)(4 * pr) * ld2 + 2 * p;
+        *reinterpret_cast<P2*>(row) = Pair2<E>::make(acc.x, -acc.y);
+        *reinterpret_cast<P2*>(row + ld2) = Pair2<E>::make(acc.y, acc.x);
+        *reinterpret_cast<P2*>(row + 2 * (size_t)ld2) = Pair2<E>::make(acc.z, -acc.w);
+        *reinterpret_cast<P2*>(row + 3 * (size_t)ld2) = Pair2<E>::make(acc.w, acc.z);
+    }
+}
+
+template <typename E>
+__global__ void __launch_bounds__(512) tc_prep2(const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
+                                                const c64* __restrict__ lb, const c64* __restrict__ loc,
+                                                E* __restrict__ bt, int ld2, int npad, int nrhs, int s, int fwd) {
+    extern __shared__ __align__(16) unsigned char prep_smem[];
+    const BoxInfo B = boxes[blockIdx.y];
+    prep_tile<E>(B, blockIdx.y, blockIdx.x, PREP2_TP, coef, lb, loc, bt, ld2, npad, nrhs, s, fwd,
+                 reinterpret_cast<c64*>(prep_smem));
 }
 
 template <typename E, int NPAD, int NST>
@@ -200,53 +308,73 @@ struct TcCfg {
     static constexpr int SMEM = STAGES * STAGE + (2 * STAGES + 1) * 8 + 16 + 1024;
 };
 
+// Position of a CTA in its operand ring: chunks issued so far (stage = g mod NST, phase = g / NST)
+// and the phase of the accumulator-ready barrier.  Carried across the row tiles a persistent CTA takes.
+struct Ring {
+    uint32_t g = 0;
+    uint32_t dphase = 0;
+};
+
+// mbarriers, tensor-map prefetch and the TMEM accumulator of one CTA; returns the TMEM address.
 template <typename E, int NPAD, int NST>
-__global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ CUtensorMap mapA,
-                                                        const __grid_constant__ CUtensorMap mapA32,
-                                                        const __grid_constant__ CUtensorMap mapB,
-                                                        const BoxInfo* __restrict__ boxes, c64* __restrict__ loc,
-                                                        int nrhs, int s, int fwd, int nkc, int* __restrict__ err) {
+__device__ __forceinline__ uint32_t gemm_setup(const CUtensorMap* mapA, const CUtensorMap* mapA32,
+                                               const CUtensorMap* mapB, unsigned char* base) {
     using Cfg = TcCfg<E, NPAD, NST>;
-    constexpr int TC_STAGES = Cfg::STAGES;
-    constexpr int TC_BK = Cfg::BK;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                           ~static_cast<uintptr_t>(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + TC_STAGES * Cfg::STAGE);
-    uint64_t* empty = full + TC_STAGES;
-    uint64_t* done = empty + TC_STAGES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * Cfg::STAGE);
+    uint64_t* empty = full + NST;
+    uint64_t* done = empty + NST;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-
-    const BoxInfo B = boxes[blockIdx.y];
-    const int m = B.m, bz = B.dims[2];
-    const int k = fwd ? s : bz - 1 - s;
-    if (k < 0 || k >= bz) return;
-    if (!fwd && k == bz - 1) return;
-    const int row0 = blockIdx.x * TC_BM;
-    if (row0 >= m) return;
-    const int nK = (2 * m + TC_BK - 1) / TC_BK;
-    const int plane = B.plane0 + k;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) {
+        for (int i = 0; i < NST; ++i) {
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&empty[i], 1);
         }
         tc::mbar_init(done, 1);
         tc::fence_barrier_init();
-        tc::prefetch_tmap(&mapA);
-        tc::prefetch_tmap(&mapA32);
-        tc::prefetch_tmap(&mapB);
+        tc::prefetch_tmap(mapA);
+        tc::prefetch_tmap(mapA32);
+        tc::prefetch_tmap(mapB);
     }
-    if (warp == 1) {
+    if ((threadIdx.x >> 5) == 1) {
         tc::tmem_alloc(tmem_slot, Cfg::TCOLS);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tmem_slot;
+    return *tmem_slot;
+}
+
+template <typename E, int NPAD, int NST>
+__device__ __forceinline__ void gemm_teardown(uint32_t tmem) {
+    using Cfg = TcCfg<E, NPAD, NST>;
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, Cfg::TCOLS);
+    }
+}
+
+// Row tile t of box (index box) at plane k: y_k rows (forward) or x_k = y_k - G_k R rows (backward).
+// base: 1024-aligned dynamic shared memory (NST stages, then the barriers).  All 128 threads call it;
+// it ends with a CTA barrier after the accumulator has been read, so the next tile may reuse TMEM and
+// the stages.  A wait that gives up leaves an error code in *err.
+template <typename E, int NPAD, int NST>
+__device__ __forceinline__ void gemm_core(const CUtensorMap* mapA, const CUtensorMap* mapA32, const CUtensorMap* mapB,
+                                          const BoxInfo& B, int box, int t, int k, c64* __restrict__ loc, int nrhs,
+                                          int fwd, int nkc, int* __restrict__ err, unsigned char* base, uint32_t tmem,
+                                          Ring& R) {
+    using Cfg = TcCfg<E, NPAD, NST>;
+    constexpr int TC_BK = Cfg::BK;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * Cfg::STAGE);
+    uint64_t* empty = full + NST;
+    uint64_t* done = empty + NST;
+    const int m = B.m;
+    const int row0 = t * TC_BM;
+    const int nK = (2 * m + TC_BK - 1) / TC_BK;
+    const int plane = B.plane0 + k;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0 && lane == 0) {
         // TMA producer.  A tile (rows row0.., chunk kc): 16 KB contiguous in the tile layout; the last,
@@ -255,25 +383,36 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
         const int rows = min(TC_BM, m - row0);
         const int nsub = rows >= TC_BM ? 0 : (rows + 31) / 32;
         const uint32_t a_bytes = nsub ? (uint32_t)nsub * 32 * 128 : (uint32_t)Cfg::A_BYTES;
+        int issued = 0;
         for (int kc = 0; kc < nK; ++kc) {
-            const int st = kc % TC_STAGES;
-            if (kc >= TC_STAGES && !tc::mbar_wait(&empty[st], ((kc / TC_STAGES) - 1) & 1, err, 1)) break;
+            const uint32_t gi = R.g + kc;
+            const int st = gi % NST;
+            if (gi >= NST && !tc::mbar_wait(&empty[st], ((gi / NST) - 1) & 1, err, 1)) break;
             unsigned char* sa = base + st * Cfg::STAGE;
             tc::mbar_arrive_expect_tx(&full[st], a_bytes + Cfg::B_BYTES);
-            const int line = (blockIdx.x * nkc + kc) * TC_BM;
+            const int line = (t * nkc + kc) * TC_BM;
             if (nsub == 0)
-                tc::tma_load_3d(sa, &mapA, 0, line, plane, &full[st]);
+                tc::tma_load_3d(sa, mapA, 0, line, plane, &full[st]);
             else
-                for (int q = 0; q < nsub; ++q) tc::tma_load_3d(sa + q * 4096, &mapA32, 0, line + 32 * q, plane, &full[st]);
-            tc::tma_load_3d(sa + Cfg::A_BYTES, &mapB, kc * TC_BK, 0, blockIdx.y, &full[st]);
+                for (int q = 0; q < nsub; ++q) tc::tma_load_3d(sa + q * 4096, mapA32, 0, line + 32 * q, plane, &full[st]);
+            tc::tma_load_3d(sa + Cfg::A_BYTES, mapB, kc * TC_BK, 0, box, &full[st]);
+            ++issued;
+        }
+        if (issued < nK) {
+            // gave up: let the copies already issued land (bounded) before the stages are left
+            for (int kc = max(0, issued - NST); kc < issued; ++kc) {
+                const uint32_t gi = R.g + kc;
+                tc::mbar_drain(&full[gi % NST], (gi / NST) & 1);
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         constexpr bool BF = sizeof(E) == 2;
         constexpr uint32_t idesc = BF ? tc::idesc_bf16(TC_BM, NPAD) : tc::idesc_tf32(TC_BM, NPAD);
         for (int kc = 0; kc < nK; ++kc) {
-            const int st = kc % TC_STAGES;
-            if (!tc::mbar_wait(&full[st], (kc / TC_STAGES) & 1, err, 2)) break;
+            const uint32_t gi = R.g + kc;
+            const int st = gi % NST;
+            if (!tc::mbar_wait(&full[st], (gi / NST) & 1, err, 2)) break;
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_u32(base + st * Cfg::STAGE);
             const uint32_t sb = sa + Cfg::A_BYTES;
@@ -290,7 +429,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
     __syncwarp();
 
     // epilogue: thread t of warp w owns TMEM lane 32 w + t = output row row0 + 32 w + t
-    const bool ok = tc::mbar_wait(done, 0, err, 3);
+    const bool ok = tc::mbar_wait(done, R.dphase, err, 3);
     tc::fence_after_sync();
     if (ok) {
         const int row = row0 + warp * 32 + lane;
@@ -309,7 +448,8 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
                         if (fwd) {
                             dst[r] = mk<float>(re, im);
                         } else {
-                            const c64 o = dst[r];
+                            // y_k may come from another CTA of a persistent launch: read it from L2
+                            const float2 o = __ldcg(reinterpret_cast<const float2*>(dst + r));
                             dst[r] = mk<float>(o.x - re, o.y - im);
                         }
                     }
@@ -317,12 +457,173 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
             }
         }
     }
+    R.g += nK;
+    R.dphase ^= 1u;
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 1) {
-        tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, Cfg::TCOLS);
+    tc::fence_after_sync();
+}
+
+__device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
+    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~static_cast<uintptr_t>(1023));
+}
+
+template <typename E, int NPAD, int NST>
+__global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapA32,
+                                                        const __grid_constant__ CUtensorMap mapB,
+                                                        const BoxInfo* __restrict__ boxes, c64* __restrict__ loc,
+                                                        int nrhs, int s, int fwd, int nkc, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const BoxInfo B = boxes[blockIdx.y];
+    const int bz = B.dims[2];
+    const int k = fwd ? s : bz - 1 - s;
+    if (k < 0 || k >= bz || (!fwd && k == bz - 1) || (int)blockIdx.x * TC_BM >= B.m) return;
+    unsigned char* base = align1024(smem_raw);
+    const uint32_t tmem = gemm_setup<E, NPAD, NST>(&mapA, &mapA32, &mapB, base);
+    Ring R;
+    gemm_core<E, NPAD, NST>(&mapA, &mapA32, &mapB, B, blockIdx.y, blockIdx.x, k, loc, nrhs, fwd, nkc, err, base, tmem,
+                            R);
+    gemm_teardown<E, NPAD, NST>(tmem);
+}
+
+// ---------------------------------------------------------------- persistent dataflow sweep
+//
+// Both sweeps of every box in one launch.  Box b runs the chain of operations
+//   prep(0), gemm(0), prep(1), gemm(1), ..., prep(2 n_z - 2), gemm(2 n_z - 2)
+// (steps 0..n_z-1 forward, then n_z-1 backward steps), each operation split into items: row tiles of
+// 128 for a product, tiles of FLOW_TPN nodes for an operand preparation.  Items wait in a queue: the
+// preparations of step 0 are there at the start (init), and the CTA that completes the last item of an
+// operation appends the items of the box's next operation.  Each CTA takes the next queue slot, waits
+// until that slot has been written, runs the item and counts it done.  A slot is written only after
+// everything its item depends on has completed, and a CTA waits only for slots, so as long as one CTA
+// runs, work advances (no co-residency is assumed).  Every wait is bounded (HELM_ETIMEOUT).
+//
+// Ordering across CTAs: an item's global writes (loc, the B operand) are made visible with a gpu-scope
+// fence (and a generic-to-async proxy fence, since the next product reads the B operand by TMA) before
+// its completion is counted; queue slots are published with release stores and read with acquire loads;
+// values other CTAs wrote in this launch are read through L2 (ld.cg), never a stale L1 line.
+constexpr int FLOW_TPN = 128;
+constexpr uint64_t FLOW_WAIT_NS = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
+    int old;
+    asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+constexpr int FLOW_QT = 96;   // the thread that handles the queue (warp 3, lane 0)
+
+// The item in queue slot `slot` (bounded wait until it has been published); x = -1 when the queue is
+// exhausted or a wait anywhere gave up.
+__device__ __forceinline__ int4 flow_fetch(int slot, const int4* __restrict__ init, int ninit, const int4* items,
+                                           const int* flag, int total, int* err) {
+    if (slot >= total || *reinterpret_cast<volatile int*>(err) != 0) return make_int4(-1, 0, 0, 0);
+    if (slot < ninit) return init[slot];
+    const int q = slot - ninit;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
+        if (ld_acquire_gpu(flag + q)) return __ldcg(items + q);
+        if ((i & 255) == 255) {
+            if (*reinterpret_cast<volatile int*>(err) != 0) break;
+            if (global_ns() - t0 > FLOW_WAIT_NS) {
+                atomicExch(err, 4);
+                break;
+            }
+        }
+        __nanosleep(32);
     }
+    return make_int4(-1, 0, 0, 0);
+}
+
+// ops in box b's chain, and the items of operation j
+__device__ __host__ __forceinline__ int flow_chain(int bz) { return 2 * (2 * bz - 1); }
+__device__ __host__ __forceinline__ int flow_tiles(int m, int j) {
+    return (j & 1) ? (m + TC_BM - 1) / TC_BM : (m + FLOW_TPN - 1) / FLOW_TPN;
+}
+
+template <typename E, int NPAD, int NST>
+__global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapA32,
+                                                        const __grid_constant__ CUtensorMap mapB,
+                                                        const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
+                                                        const c64* __restrict__ lb, c64* __restrict__ loc,
+                                                        E* __restrict__ bt, int ld2, int nrhs, int nkc,
+                                                        const int4* __restrict__ init, int ninit, int4* items,
+                                                        int* flag, int total, int* ctl, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int4 cur;
+    unsigned char* base = align1024(smem_raw);
+    int* head = ctl;
+    int* tail = ctl + 1;
+    int* cnt = ctl + 2;   // per box: items of its current operation completed
+    const uint32_t tmem = gemm_setup<E, NPAD, NST>(&mapA, &mapA32, &mapB, base);
+    Ring R;
+    // Queue work is done by thread FLOW_QT (idle in a product's main loop): it takes the next slot while
+    // the current item runs, and after the item counts it done, publishes the box's next operation if
+    // the item was the operation's last, and waits for the next slot's item.
+    int slot = 0;
+    if (threadIdx.x == FLOW_QT) {
+        slot = atomicAdd(head, 1);
+        cur = flow_fetch(slot, init, ninit, items, flag, total, err);
+    }
+    for (;;) {
+        __syncthreads();
+        const int4 it = cur;
+        if (it.x < 0) break;
+        // the product's TMA reads the B operand another CTA wrote: generic-to-async proxy order after the
+        // acquire that FLOW_QT made before the barrier above
+        if (threadIdx.x == 0) fence_proxy_async_global();
+        if (threadIdx.x == FLOW_QT) slot = atomicAdd(head, 1);
+        const int box = it.x, j = it.y, t = it.z;
+        const BoxInfo B = boxes[box];
+        const int bz = B.dims[2];
+        const int q = j >> 1;
+        const int fwd = q < bz;
+        const int s = fwd ? q : q - bz + 1;
+        if (j & 1) {
+            const int k = fwd ? s : bz - 1 - s;
+            gemm_core<E, NPAD, NST>(&mapA, &mapA32, &mapB, B, box, t, k, loc, nrhs, fwd, nkc, err, base, tmem, R);
+        } else {
+            prep_tile_staged<E>(B, box, t, FLOW_TPN, coef, lb, loc, bt, ld2, NPAD, nrhs, s, fwd, base,
+                                NST * TcCfg<E, NPAD, NST>::STAGE);
+            tc::fence_proxy_async_smem();   // the stages are TMA destinations again in a later product
+            fence_proxy_async_global();     // B operand written here, read by TMA in another CTA
+        }
+        __syncthreads();
+        if (threadIdx.x == FLOW_QT) {
+            // acq_rel: releases this CTA's writes (ordered before by the barrier) and, for the operation's
+            // last item, acquires the other items' writes so that the publication below carries them
+            if (atom_add_acq_rel_gpu(cnt + box, 1) == flow_tiles(B.m, j) - 1) {
+                atomicExch(cnt + box, 0);
+                if (j + 1 < flow_chain(bz)) {
+                    const int n = flow_tiles(B.m, j + 1);
+                    const int q0 = atomicAdd(tail, n);
+                    for (int i = 0; i < n && ninit + q0 + i < total; ++i) items[q0 + i] = make_int4(box, j + 1, i, 0);
+                    for (int i = 0; i < n && ninit + q0 + i < total; ++i) st_release_gpu(flag + q0 + i, 1);
+                }
+            }
+            cur = flow_fetch(slot, init, ninit, items, flag, total, err);
+        }
+    }
+    gemm_teardown<E, NPAD, NST>(tmem);
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up through the runtime so that the
@@ -357,7 +658,7 @@ bool encode_3d(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t 
 
 template <typename E, int NPAD, int NST>
 helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* bt, int nrhs, cudaStream_t st,
-                   int* err) {
+                   int* err, const TcFlow* flow) {
     using Cfg = TcCfg<E, NPAD, NST>;
     constexpr bool BF = sizeof(E) == 2;
     CUtensorMap mapA, mapA32, mapB;
@@ -373,14 +674,33 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
                    Cfg::BK, NPAD, BF))
         return set_error(ctx, HELM_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
     static bool attr = false;
+    static int flow_occ = 0;
     if (!attr) {
         cudaFuncSetAttribute(tc_sweep_gemm<E, NPAD, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        cudaFuncSetAttribute(tc_sweep_flow<E, NPAD, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        // all of the unified L1 as shared memory, so that as many persistent CTAs fit per SM as its 228 KB allow
+        cudaFuncSetAttribute(tc_sweep_flow<E, NPAD, NST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        // persistent CTAs per SM from the kernel's shared memory, registers and TMEM columns (the
+        // occupancy calculator reports 1 for these tcgen05 kernels, while two of them run side by side)
+        int dev = 0, smem_sm = 0, regs_sm = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, tc_sweep_flow<E, NPAD, NST>) == cudaSuccess) {
+            const int per_block = Cfg::SMEM + (int)fa.sharedSizeBytes + 1024;   // + the 1 KB reserved per block
+            const int regs = (fa.numRegs + 7) / 8 * 8 * 128;
+            flow_occ = std::min(std::min(smem_sm / per_block, regs_sm / std::max(1, regs)),
+                                std::min(512 / (int)Cfg::TCOLS, 8));
+        }
         cudaFuncSetAttribute(tc_prep2<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(128 * (PREP2_TP + 1) * sizeof(c64)));
         attr = true;
     }
     const int m = P.m_max;
-    const dim3 ggrid((m + TC_BM - 1) / TC_BM, P.nbox);
+    const int gtiles = (m + TC_BM - 1) / TC_BM;
+    const dim3 ggrid(gtiles, P.nbox);
     const dim3 pgrid((unsigned)((m + PREP_TP - 1) / PREP_TP), P.nbox);
     const dim3 pgrid2((unsigned)((m + PREP2_TP - 1) / PREP2_TP), P.nbox);
     const size_t psmem2 = (size_t)nrhs * (PREP2_TP + 1) * sizeof(c64);
@@ -388,9 +708,11 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
     const c64* coef = (const c64*)P.coef;
     const double es = sizeof(c64);
     const double fs = 2.0 * sizeof(E);   // bytes of one stored complex factor entry
-    auto bytes = [&](int s, bool fwd, double& gemm, double& prep) {
+    // algorithmic bytes of the product and of the operand preparation of step (s, fwd) over boxes [b0, b1)
+    auto bytes = [&](int s, bool fwd, int b0, int b1, double& gemm, double& prep) {
         gemm = prep = 0;
-        for (const auto& b : P.hbox) {
+        for (int i = b0; i < b1; ++i) {
+            const auto& b = P.hbox[i];
             const int bz = b.dims[2];
             const bool act = fwd ? s < bz : (s >= 1 && s <= bz - 1);
             if (!act) continue;
@@ -399,10 +721,28 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
         }
     };
     double gb, pb;
+    if (flow && flow->mem && ctx->tc_flow && vec2 && flow_occ > 0 &&
+        (size_t)nrhs * (FLOW_TPN + 1) * sizeof(c64) <= (size_t)NST * Cfg::STAGE) {
+        double all = 0;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int s = pass == 0 ? 0 : 1; s < P.bz_max; ++s) {
+                bytes(s, pass == 0, 0, P.nbox, gb, pb);
+                all += gb + pb;
+            }
+        const int grid = std::max(1, std::min(flow->total, flow_occ * std::max(1, ctx->sm_count)));
+        HELM_CUDA(ctx, cudaMemsetAsync(flow->mem, 0, flow->reset_bytes, st));
+        const int t = prof_begin(ctx, "sweep_flow");
+        tc_sweep_flow<E, NPAD, NST><<<grid, 128, Cfg::SMEM, st>>>(mapA, mapA32, mapB, P.dbox, coef, lb, loc, bt, 2 * ld,
+                                                                   nrhs, P.pk_chunks, flow->init, flow->ninit,
+                                                                   flow->items, flow->flag, flow->total, flow->ctl, err);
+        prof_end(ctx, t, all);
+        ctx->launches++;
+        return cuda_check(ctx, cudaGetLastError(), "tensor-core plane sweeps (persistent)");
+    }
     for (int pass = 0; pass < 2; ++pass) {
         const int fwd = pass == 0;
         for (int s = fwd ? 0 : 1; s < P.bz_max; ++s) {
-            bytes(s, fwd, gb, pb);
+            bytes(s, fwd, 0, P.nbox, gb, pb);
             int t = prof_begin(ctx, "sweep_prep");
             if (vec2)
                 tc_prep2<E><<<pgrid2, 512, psmem2, st>>>(P.dbox, coef, lb, loc, bt, 2 * ld, NPAD, nrhs, s, fwd);
@@ -421,24 +761,24 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
 
 template <typename E, int NPAD>
 helm_status dispatch_stages(helm_ctx ctx, const PlaneSet& P, const c64* lb, void* loc, void* bt, int ns, int nrhs,
-                            cudaStream_t st, int* err) {
+                            cudaStream_t st, int* err, const TcFlow* flow) {
     switch (ns) {
-        case 2: return run_tc<E, NPAD, 2>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err);
-        case 3: return run_tc<E, NPAD, 3>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err);
-        case 4: return run_tc<E, NPAD, 4>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err);
-        default: return run_tc<E, NPAD, (NPAD >= 256 ? 4 : 5)>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err);
+        case 2: return run_tc<E, NPAD, 2>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err, flow);
+        case 3: return run_tc<E, NPAD, 3>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err, flow);
+        case 4: return run_tc<E, NPAD, 4>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err, flow);
+        default: return run_tc<E, NPAD, (NPAD >= 256 ? 4 : 5)>(ctx, P, lb, (c64*)loc, (E*)bt, nrhs, st, err, flow);
     }
 }
 
 template <typename E>
 helm_status dispatch_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, void* loc, void* bt, int npad, int ns,
-                        int nrhs, cudaStream_t st, int* err) {
+                        int nrhs, cudaStream_t st, int* err, const TcFlow* flow) {
     switch (npad) {
-        case 16: return dispatch_stages<E, 16>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
-        case 32: return dispatch_stages<E, 32>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
-        case 64: return dispatch_stages<E, 64>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
-        case 128: return dispatch_stages<E, 128>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
-        default: return dispatch_stages<E, 256>(ctx, P, lb, loc, bt, ns, nrhs, st, err);
+        case 16: return dispatch_stages<E, 16>(ctx, P, lb, loc, bt, ns, nrhs, st, err, flow);
+        case 32: return dispatch_stages<E, 32>(ctx, P, lb, loc, bt, ns, nrhs, st, err, flow);
+        case 64: return dispatch_stages<E, 64>(ctx, P, lb, loc, bt, ns, nrhs, st, err, flow);
+        case 128: return dispatch_stages<E, 128>(ctx, P, lb, loc, bt, ns, nrhs, st, err, flow);
+        default: return dispatch_stages<E, 256>(ctx, P, lb, loc, bt, ns, nrhs, st, err, flow);
     }
 }
 
@@ -518,7 +858,7 @@ int tc_npad(int nrhs) {
 }
 
 helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb_, void* loc, void* bt, int npad,
-                              int nrhs, cudaStream_t st, int* err) {
+                              int nrhs, cudaStream_t st, int* err, const TcFlow* flow) {
     const c64* lb = (const c64*)lb_;
     if (nrhs > 128 || tc_npad(nrhs) > npad) return set_error(ctx, HELM_EINVAL, "tensor-core sweep: too many rhs");
     // pipeline depth: the context's tuning value, else 4 stages (3 for N = 256); measured at 112^3 x 16 RHS:
@@ -526,7 +866,38 @@ helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb_, 
     int ns = ctx->tc_stages;
     if (ns < 2 || ns > 5) ns = npad >= 256 ? 3 : 4;
     if (npad >= 256 && ns > 4) ns = 4;   // shared memory: 5 x 48 KB does not fit
-    if (P.prec == HELM_PREC_BF16) return dispatch_tc<__nv_bfloat16>(ctx, P, lb, loc, bt, npad, ns, nrhs, st, err);
-    return dispatch_tc<float>(ctx, P, lb, loc, bt, npad, ns, nrhs, st, err);
+    if (P.prec == HELM_PREC_BF16)
+        return dispatch_tc<__nv_bfloat16>(ctx, P, lb, loc, bt, npad, ns, nrhs, st, err, flow);
+    return dispatch_tc<float>(ctx, P, lb, loc, bt, npad, ns, nrhs, st, err, flow);
 }
 
+helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F) {
+    tc_flow_free(ctx, F);
+    std::vector<int4> init;
+    long long total = 0;
+    for (int b = 0; b < P.nbox; ++b) {
+        const BoxInfo& B = P.hbox[b];
+        for (int j = 0; j < flow_chain(B.dims[2]); ++j) total += flow_tiles(B.m, j);
+        for (int i = 0; i < flow_tiles(B.m, 0); ++i) init.push_back(make_int4(b, 0, i, 0));
+    }
+    if (total >= (1ll << 30)) return set_error(ctx, HELM_EINVAL, "tensor-core sweep: too many queue items");
+    const size_t nctl = ((size_t)P.nbox + 2 + 3) / 4 * 4;   // ints, padded to 16 bytes
+    const size_t nflag = ((size_t)total + 3) / 4 * 4;
+    F.reset_bytes = (nctl + nflag) * sizeof(int);
+    F.bytes = F.reset_bytes + (size_t)total * sizeof(int4);
+    HELM_TRY(dev_alloc(ctx, &F.mem, F.bytes, "tensor-core sweep queue"));
+    F.ctl = (int*)F.mem;
+    F.flag = F.ctl + nctl;
+    F.init = (int4*)(F.flag + nflag);
+    F.ninit = (int)init.size();
+    F.items = F.init + F.ninit;
+    F.total = (int)total;
+    HELM_CUDA(ctx, cudaMemcpyAsync(F.init, init.data(), init.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    HELM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return HELM_OK;
+}
+
+void tc_flow_free(helm_ctx ctx, TcFlow& F) {
+    if (F.mem) dev_free(ctx, F.mem, F.bytes);
+    F = TcFlow{};
+}

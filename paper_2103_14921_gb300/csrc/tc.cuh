@@ -61,6 +61,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     return false;
 }
 
+// Bounded wait that ignores the error flag: used after a give-up, to let copies already issued land
+// before their shared-memory stages are left.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return;
+        if (i > 64) __nanosleep(32);
+    }
+}
+
 // 3-D tiled TMA load into shared memory, completing on `bar` (transaction bytes).
 __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* map, int x, int y, int z,
                                             uint64_t* bar) {

@@ -153,11 +153,11 @@ def test_graph_replayed_iterations_equal_eager_launches(ctx):
     kw = dict(tol=1e-6, restart=8, basis_prec=helm.PREC_FP32)
 
     def run():
-        ctx.profile(True, only=["sweep_gemm_tc", "coarse_sweep"])
+        ctx.profile(True, only=["sweep_flow", "coarse_sweep"])
         l0 = ctx.launches
         x, st = o.solve(b, **kw)
         n = ctx.launches - l0
-        prof = {f: ctx.profile_query(f) for f in ("sweep_gemm_tc", "coarse_sweep")}
+        prof = {f: ctx.profile_query(f) for f in ("sweep_flow", "coarse_sweep")}
         ctx.profile(False)
         return x, [s["iterations"] for s in st], n, prof
 

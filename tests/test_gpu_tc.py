@@ -130,3 +130,39 @@ def test_tf32_fgmres_converges_to_the_direct_solution(ctx):
         res = np.linalg.norm(apply_A(prob, x[..., r]) - b[..., r]) / np.linalg.norm(b[..., r])
         assert res <= 1e-6
         assert np.linalg.norm(x[..., r] - xs[..., r]) <= 1e-5 * np.linalg.norm(xs[..., r])
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("parts,nrhs", [((3, 2, 2), 16), ((3, 1, 1), 2), ((2, 2, 2), 40), ((2, 1, 2), 3)])
+def test_persistent_sweep_equals_per_step_launches(ctx, prec, parts, nrhs):
+    """Both sweeps of every box as one persistent launch fed by a device work queue, against one
+    preparation and one product launch per plane step: the same arithmetic on every element, so the
+    preconditioner outputs are bit-identical.  Ragged boxes with unequal plane counts, a single-box
+    row, 40 columns (N = 128) and an odd column count (which keeps the per-step launches).  Launches:
+    one persistent (family sweep_flow), or 2 n_z - 1 of each kind; repeated applies reuse the queue."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    dims = (21, 18, 17)
+    nx, ny, nz = dims
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 1.0)
+    grid = helm.Grid(ctx, nx, ny, nz, 25.0, 5.0, c, npml=3, weights=helm.fit_weights())
+    fp = helm.PREC_TF32 if prec == "tf32" else helm.PREC_BF16
+    o = helm.Oras(grid, parts, 2, factor_prec=fp)
+    v = torch.from_numpy(synth.random_complex((nz, ny, nx, nrhs), 63)).cuda()
+    bz = max(o.box_info(b)[2][2] for b in range(o.box_info(0)[0]))
+    steps = 2 * bz - 1
+    got, counts = {}, {}
+    fams = ("sweep_prep", "sweep_gemm_tc", "sweep_flow")
+    for flow in (1, 0):
+        ctx.set_tuning(helm.TUNE_TC_FLOW, flow)
+        ctx.profile(True, only=list(fams))
+        got[flow] = o.apply(v)
+        counts[flow] = tuple((ctx.profile_query(f) or (0,))[0] for f in fams)
+        ctx.profile(False)
+    ctx.set_tuning(helm.TUNE_TC_FLOW, 1)
+    again = o.apply(v)
+    assert torch.equal(got[1], got[0])
+    assert torch.equal(again, got[1])
+    assert torch.isfinite(torch.view_as_real(got[1])).all()
+    assert counts[0] == (steps, steps, 0)
+    assert counts[1] == ((0, 0, 1) if nrhs % 2 == 0 else (steps, steps, 0))
