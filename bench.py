@@ -446,9 +446,10 @@ def run_gpu(args, W):
 
     peaks, src = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    # DRAM traffic per launch relative to the algorithmic bytes, from the ncu capture summarised in
-    # profiles/tc_sweep_gemm_slab112.md (dram__bytes_read.sum + dram__bytes_write.sum = 1.037 x algorithmic)
-    traffic_ratio = {"sweep_gemm_tc": 1.037}.get(roof_fam) if args.factor_prec == "tf32" else None
+    # DRAM traffic per launch relative to the algorithmic bytes, from the ncu captures summarised in
+    # profiles/tc_sweep_flow_slab112.md (dram__bytes_read.sum + dram__bytes_write.sum = 0.994 x algorithmic)
+    # and profiles/tc_sweep_gemm_slab112.md (per-step product launches: 1.037 x)
+    traffic_ratio = {"sweep_flow": 0.994, "sweep_gemm_tc": 1.037}.get(roof_fam) if args.factor_prec == "tf32" else None
     roof = None
     fam = roof_fam
     g = roof_meas
@@ -457,7 +458,8 @@ def run_gpu(args, W):
         ach = by / (ms / 1000.0) / 1e9
         roof = {"kernel": fam, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": (traffic_ratio * by / nl) if traffic_ratio else None,
-                "traffic_source": "ncu 112x112x24 slab capture scaled by algorithmic bytes" if traffic_ratio else None,
+                "traffic_source": ("ncu 112x112x24 slab capture of the same kernel, scaled by algorithmic bytes"
+                                   if traffic_ratio else None),
                 "peak_source": src, "launches": nl,
                 "avg_launch_us": 1000.0 * ms / nl, "algorithmic_bytes_per_launch": by / nl}
     kernels = {}
