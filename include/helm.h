@@ -118,11 +118,15 @@ helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launche
  * tiles of the products, tiles of the operand preparation) from a device queue, each box's next
  * step queued as soon as its current one completes (an even number of right-hand sides and
  * 16-byte aligned vectors; otherwise, and with 0, two launches per plane step).  Both give
- * bit-identical results.  Returns HELM_EINVAL for an unknown key or value out of range. */
+ * bit-identical results.  HELM_TUNE_STENCIL_MARCH: 1 (default) applies complex64 stencils with 16
+ * right-hand sides and constant weights by walking z-planes (the in-plane terms of a plane are formed
+ * once and reused by the three output planes it touches); 0 uses the per-node kernel.  The two agree
+ * to FP32 rounding.  Returns HELM_EINVAL for an unknown key or value out of range. */
 #define HELM_TUNE_TC_STAGES 1
 #define HELM_TUNE_COARSE_COOP 2
 #define HELM_TUNE_GRAPHS 3
 #define HELM_TUNE_TC_FLOW 4
+#define HELM_TUNE_STENCIL_MARCH 5
 helm_status helm_set_tuning(helm_ctx ctx, int key, int value);
 
 /* ------------------------------------------------------------ grid / model */

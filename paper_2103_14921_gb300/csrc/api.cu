@@ -115,6 +115,12 @@ extern "C" helm_status helm_set_tuning(helm_ctx ctx, int key, int value) {
         ctx->graph_gen++;
         return HELM_OK;
     }
+    if (key == HELM_TUNE_STENCIL_MARCH) {
+        if (value != 0 && value != 1) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: stencil_march must be 0 or 1");
+        ctx->stencil_march = value;
+        ctx->graph_gen++;
+        return HELM_OK;
+    }
     return set_error(ctx, HELM_EINVAL, "helm_set_tuning: unknown key %d", key);
 }
 extern "C" uint64_t helm_launch_count(helm_ctx ctx) { return ctx ? ctx->launches : 0; }

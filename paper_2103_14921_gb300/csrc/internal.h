@@ -74,6 +74,7 @@ struct helm_ctx_s {
     int coarse_coop = 1;       // tuning: one cooperative launch for the complex64 coarse sweeps
     int use_graphs = 1;        // tuning: Krylov iterations replayed from captured CUDA graphs
     int tc_flow = 1;           // tuning: tensor-core sweeps as one persistent launch with a work queue
+    int stencil_march = 1;     // tuning: complex64 16-column stencils walk z-planes (in-plane terms reused)
     uint64_t graph_gen = 1;    // bumped when a setting that captured graphs depend on changes
     cudaStream_t cap_stream = nullptr;   // private stream graphs are captured on (the context's may be
                                          // the legacy default stream, which cannot be captured)

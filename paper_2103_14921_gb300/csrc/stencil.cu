@@ -181,6 +181,205 @@ __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict_
     *reinterpret_cast<CPack<T, RCH>*>(y + p * nrhs + (long long)ch * RCH) = out;
 }
 
+// ---------------------------------------------------------------- z-march (complex64, 16 columns)
+//
+// The same operator grouped by z-planes: with D_a the stretched and P_a the plain second differences,
+//   A u = h^-2 [S0 + D_z S1] + [T0 + P_z T1],
+//   S0 = (D_x + D_y) u + a2 D_x D_y u,   S1 = u + a2 (D_x + D_y) u + a3 D_x D_y u,
+//   T0 = m0 v + m1 (P_x + P_y) v + m2 P_x P_y v,   T1 = m1 v + m2 (P_x + P_y) v + m3 P_x P_y v,   v = k^2 u,
+// where S0, S1, T0, T1 are in-plane.  A thread owns MN consecutive x-nodes of one row j and one column pair
+// and walks a chunk of MZC output planes: for every plane q it loads the (MN + 2) x 3 in-plane neighbourhood
+// once, forms the in-plane terms of its nodes, and adds their contributions to the outputs q - 1 (last
+// term, then stored), q and q + 1 (first term).  Each output therefore costs (MN + 2) * 3 / MN vector loads
+// instead of 27.  Blocks whose rows all have plain (1, -2, 1) 1-D coefficients take the real-coefficient
+// path; the others use the complex table coefficients.  Ghost nodes contribute zero.
+constexpr int MN = 4;      // x-nodes per thread
+constexpr int MZC = 16;    // output planes per block
+constexpr int MNP = 8;     // column pairs (16 columns)
+
+struct PlainRange {
+    int lo[3], hi[3];   // per axis: indices whose stretched coefficients are exactly (1, -2, 1)
+};
+
+__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+// a + s b (s real)
+__device__ __forceinline__ float4 axpy4(float s, float4 b, float4 a) {
+    return make_float4(fmaf(s, b.x, a.x), fmaf(s, b.y, a.y), fmaf(s, b.z, a.z), fmaf(s, b.w, a.w));
+}
+// a + c b (c complex, b two complex values)
+__device__ __forceinline__ float4 caxpy4(c64 c, float4 b, float4 a) {
+    return make_float4(fmaf(c.x, b.x, fmaf(-c.y, b.y, a.x)), fmaf(c.x, b.y, fmaf(c.y, b.x, a.y)),
+                       fmaf(c.x, b.z, fmaf(-c.y, b.w, a.z)), fmaf(c.x, b.w, fmaf(c.y, b.z, a.w)));
+}
+// the 3-point second difference c0 x0 + c1 x1 + c2 x2, plain (1, -2, 1) or with complex coefficients
+template <bool PLAIN>
+__device__ __forceinline__ float4 d3(const c64* c, float4 x0, float4 x1, float4 x2) {
+    if (PLAIN) return axpy4(-2.f, x1, add4(x0, x2));
+    return caxpy4(c[2], x2, caxpy4(c[1], x1, caxpy4(c[0], x0, f4(0.f))));
+}
+
+// The block's planes pass through shared memory: a 128-thread block covers 16 x-nodes x 4 rows x 16
+// columns, and plane q's neighbourhood (18 nodes x 6 rows, all columns, and k^2) is copied in with cp.async
+// two planes ahead of the one computed (three buffers; ghost nodes are zero-filled by the copy).
+constexpr int MTX = (32 / MNP) * MN;       // x-nodes per block (16)
+constexpr int MTY = 4;                     // rows per block (one warp each)
+constexpr int MBX = MTX + 2, MBY = MTY + 2;
+constexpr int MBUF_U = MBX * MBY * MNP;    // float4 entries of one plane buffer
+constexpr int MBUF_K = MBX * MBY;          // float2 entries (k^2) of one plane buffer
+constexpr int MNBUF = 3;                   // plane buffers: q is computed while q + 1 and q + 2 arrive
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, bool valid) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// issue the copies of plane q (rows j0-1..j0+MTY, nodes i0-1..i0+MTX); out-of-grid entries become zero
+__device__ __forceinline__ void march_stage(float4* su, float2* sk, const c64* __restrict__ u,
+                                            const c64* __restrict__ k2, int nx, int ny, int nz, int i0, int j0,
+                                            int q) {
+    const bool qin = q >= 0 && q < nz;
+    for (int e = threadIdx.x; e < MBUF_U; e += blockDim.x) {
+        const int pc = e % MNP, xn = (e / MNP) % MBX, yr = e / (MNP * MBX);
+        const int ii = i0 + xn - 1, jj = j0 + yr - 1;
+        const bool ok = qin && ii >= 0 && ii < nx && jj >= 0 && jj < ny;
+        const long long node = ok ? ((long long)q * ny + jj) * nx + ii : 0;
+        cp_async16(su + e, reinterpret_cast<const float4*>(u + node * (2 * MNP)) + pc, ok);
+    }
+    for (int e = threadIdx.x; e < MBUF_K; e += blockDim.x) {
+        const int xn = e % MBX, yr = e / MBX;
+        const int ii = i0 + xn - 1, jj = j0 + yr - 1;
+        const bool ok = qin && ii >= 0 && ii < nx && jj >= 0 && jj < ny;
+        const long long node = ok ? ((long long)q * ny + jj) * nx + ii : 0;
+        cp_async8(sk + e, k2 + node, ok);
+    }
+}
+
+template <bool SUB, bool REALK, bool PLAIN>
+__device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* __restrict__ b, c64* __restrict__ y,
+                                          const c64* __restrict__ k2, const c64* __restrict__ tab, int nx, int ny,
+                                          int nz, const StencilW& w, int i0, int j0, int k0, int k1, float4* su,
+                                          float2* sk) {
+    const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
+    const int pc = lane % MNP, g = lane / MNP;
+    const int j = j0 + wr, xb = g * MN, ib = i0 + xb;
+    const bool live = j < ny;
+    const float ih2 = (float)w.inv_h2, a2 = (float)w.a2, a3 = (float)w.a3;
+    const float m0 = (float)w.m0, m1 = (float)w.m1, m2 = (float)w.m2, m3 = (float)w.m3;
+    c64 X[MN][3], Y[3];
+    if (!PLAIN) {
+#pragma unroll
+        for (int c = 0; c < MN; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) X[c][d] = ib + c < nx ? tab[3 * (ib + c) + d] : mk<float>(0, 0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Y[d] = live ? tab[3 * (nx + j) + d] : mk<float>(0, 0);
+    }
+    const c64* tz = tab + 3 * (nx + ny);
+    float4 P[MN], N[MN];   // outputs q and q + 1, partial
+#pragma unroll
+    for (int c = 0; c < MN; ++c) P[c] = N[c] = f4(0.f);
+    march_stage(su, sk, u, k2, nx, ny, nz, i0, j0, k0 - 1);
+    cp_async_commit();
+    march_stage(su + MBUF_U, sk + MBUF_K, u, k2, nx, ny, nz, i0, j0, k0);
+    cp_async_commit();
+    for (int q = k0 - 1, buf = 0; q <= k1; ++q, buf = buf == MNBUF - 1 ? 0 : buf + 1) {
+        // prefetch plane q + 2 into the buffer plane q - 1 used (free since the barrier ending the last step)
+        const int nb = buf >= 1 ? buf - 1 : MNBUF - 1;
+        if (q + 2 <= k1) march_stage(su + nb * MBUF_U, sk + nb * MBUF_K, u, k2, nx, ny, nz, i0, j0, q + 2);
+        cp_async_commit();
+        cp_async_wait<2>();
+        __syncthreads();
+        const float4* cu = su + buf * MBUF_U;
+        const float2* ck = sk + buf * MBUF_K;
+        const bool qin = q >= 0 && q < nz;
+        c64 zm = mk<float>(1.f, 0.f), zc = mk<float>(-2.f, 0.f), zp = mk<float>(1.f, 0.f);
+        if (!PLAIN) {
+            zm = q - 1 >= 0 && q - 1 < nz ? tz[3 * (q - 1) + 2] : mk<float>(0, 0);
+            zc = qin ? tz[3 * q + 1] : mk<float>(0, 0);
+            zp = q + 1 >= 0 && q + 1 < nz ? tz[3 * (q + 1) + 0] : mk<float>(0, 0);
+        }
+        // sliding window over the columns n = c, c + 1, c + 2 of node c (column n = block node xb + n - 1):
+        // D_y u, P_y v, v and u on row j
+        float4 DyU[3], PyV[3], V1[3], U1[3];
+        auto column = [&](int n, int slot) {
+            float4 Ur[3], V[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int sidx = (wr + r) * MBX + xb + n;
+                Ur[r] = cu[sidx * MNP + pc];
+                const float2 kk = ck[sidx];
+                if (REALK) V[r] = make_float4(kk.x * Ur[r].x, kk.x * Ur[r].y, kk.x * Ur[r].z, kk.x * Ur[r].w);
+                else V[r] = caxpy4(mk<float>(kk.x, kk.y), Ur[r], f4(0.f));
+            }
+            DyU[slot] = d3<PLAIN>(Y, Ur[0], Ur[1], Ur[2]);
+            PyV[slot] = d3<true>(nullptr, V[0], V[1], V[2]);
+            V1[slot] = V[1];
+            U1[slot] = Ur[1];
+        };
+        column(0, 0);
+        column(1, 1);
+#pragma unroll
+        for (int c = 0; c < MN; ++c) {
+            column(c + 2, (c + 2) % 3);
+            const int s0 = c % 3, s1 = (c + 1) % 3, s2 = (c + 2) % 3;
+            const float4 u0 = U1[s1];
+            const float4 Eu = add4(d3<PLAIN>(PLAIN ? nullptr : X[c], U1[s0], U1[s1], U1[s2]), DyU[s1]);
+            const float4 Fu = d3<PLAIN>(PLAIN ? nullptr : X[c], DyU[s0], DyU[s1], DyU[s2]);
+            const float4 v0 = V1[s1];
+            const float4 Ev = add4(d3<true>(nullptr, V1[s0], V1[s1], V1[s2]), PyV[s1]);
+            const float4 Fv = d3<true>(nullptr, PyV[s0], PyV[s1], PyV[s2]);
+            const float4 S0 = axpy4(a2, Fu, Eu);
+            const float4 S1 = axpy4(a3, Fu, axpy4(a2, Eu, u0));
+            const float4 T0 = axpy4(m2, Fv, axpy4(m1, Ev, make_float4(m0 * v0.x, m0 * v0.y, m0 * v0.z, m0 * v0.w)));
+            const float4 T1 = axpy4(m3, Fv, axpy4(m2, Ev, make_float4(m1 * v0.x, m1 * v0.y, m1 * v0.z, m1 * v0.w)));
+            const float4 hS1 = make_float4(ih2 * S1.x, ih2 * S1.y, ih2 * S1.z, ih2 * S1.w);
+            // output q - 1: its last term
+            const int i = ib + c;
+            if (live && q - 1 >= k0 && i < nx) {
+                float4 o = add4(PLAIN ? add4(P[c], hS1) : caxpy4(zm, hS1, P[c]), T1);
+                const long long node = ((long long)(q - 1) * ny + j) * nx + i;
+                float4* dst = reinterpret_cast<float4*>(y + node * (2 * MNP)) + pc;
+                if (SUB) {
+                    const float4 bb = __ldg(reinterpret_cast<const float4*>(b + node * (2 * MNP)) + pc);
+                    o = make_float4(bb.x - o.x, bb.y - o.y, bb.z - o.z, bb.w - o.w);
+                }
+                __stcs(dst, o);
+            }
+            // output q: the centre term; output q + 1: its first term
+            float4 pn = add4(N[c], axpy4(ih2, S0, axpy4(-2.f, T1, T0)));
+            pn = PLAIN ? axpy4(-2.f, hS1, pn) : caxpy4(zc, hS1, pn);
+            N[c] = add4(PLAIN ? hS1 : caxpy4(zp, hS1, f4(0.f)), T1);
+            P[c] = pn;
+        }
+        __syncthreads();   // buffer buf is refilled by the next step's prefetch
+    }
+    cp_async_wait<0>();
+}
+
+template <bool SUB, bool REALK>
+__global__ void __launch_bounds__(128, 3) stencil_march(const c64* __restrict__ u, const c64* __restrict__ b,
+                                                     c64* __restrict__ y, const c64* __restrict__ k2,
+                                                     const c64* __restrict__ tab, int nx, int ny, int nz, StencilW w,
+                                                     PlainRange pl) {
+    __shared__ float4 su[MNBUF * MBUF_U];
+    __shared__ float2 sk[MNBUF * MBUF_K];
+    const int i0 = blockIdx.x * MTX, j0 = blockIdx.y * MTY;
+    const int k0 = blockIdx.z * MZC, k1 = min(k0 + MZC, nz);
+    // block-uniform path choice: every row the block writes has plain coefficients on every axis
+    const bool plain = i0 >= pl.lo[0] && min(i0 + MTX, nx) - 1 <= pl.hi[0] && j0 >= pl.lo[1] &&
+                       min(j0 + MTY, ny) - 1 <= pl.hi[1] && k0 >= pl.lo[2] && k1 - 1 <= pl.hi[2];
+    if (plain) march_run<SUB, REALK, true>(u, b, y, k2, tab, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
+    else march_run<SUB, REALK, false>(u, b, y, k2, tab, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
+}
+
 struct RowW {
     const StencilW* wtab;
     const unsigned char* wbin;
@@ -247,6 +446,34 @@ Interior interior_of(helm_grid g) {
     return in;
 }
 
+// Per axis, the index range whose complex64 stretched coefficients are exactly (1, -2, 1) (the table is
+// contiguous-plain in the middle and stretched in the absorbing layers); empty if not contiguous.
+PlainRange plain_range(helm_grid g) {
+    PlainRange r;
+    const int n[3] = {g->d.nx, g->d.ny, g->d.nz};
+    int base = 0;
+    for (int a = 0; a < 3; ++a) {
+        auto plain = [&](int i) {
+            const c128* c = &g->htab[3 * (base + i)];
+            return (float)c[0].x == 1.f && (float)c[0].y == 0.f && (float)c[1].x == -2.f && (float)c[1].y == 0.f &&
+                   (float)c[2].x == 1.f && (float)c[2].y == 0.f;
+        };
+        int lo = 0, hi = n[a] - 1;
+        while (lo < n[a] && !plain(lo)) ++lo;
+        while (hi >= 0 && !plain(hi)) --hi;
+        for (int i = lo; i <= hi; ++i)
+            if (!plain(i)) {
+                lo = 1;
+                hi = 0;
+                break;
+            }
+        r.lo[a] = lo;
+        r.hi[a] = hi;
+        base += n[a];
+    }
+    return r;
+}
+
 template <bool SUB>
 helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void* y, int nrhs, cudaStream_t s) {
     if (nrhs <= 0) return HELM_OK;
@@ -256,9 +483,20 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
     const int tok = prof_begin(g->ctx, prec == HELM_PREC_FP64 ? "stencil64" : "stencil");
     const Interior in = interior_of(g);
     const RowW rw{g->wtab, g->wbin};
+    const uintptr_t al = (uintptr_t)u | (uintptr_t)y | (SUB ? (uintptr_t)b : 0);
     if (prec == HELM_PREC_FP64) {
         dispatch<double, SUB>((const c128*)u, (const c128*)b, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, in,
                               g->k2_real, rw, s);
+    } else if (g->ctx->stencil_march && nrhs == 2 * MNP && !g->wtab && (al & 15) == 0) {
+        const PlainRange pl = plain_range(g);
+        const dim3 grid((unsigned)((g->d.nx + (32 / MNP) * MN - 1) / ((32 / MNP) * MN)), (unsigned)((g->d.ny + 3) / 4),
+                        (unsigned)((g->d.nz + MZC - 1) / MZC));
+        if (g->k2_real)
+            stencil_march<SUB, true><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
+                                                          g->d.nx, g->d.ny, g->d.nz, g->w, pl);
+        else
+            stencil_march<SUB, false><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
+                                                           g->d.nx, g->d.ny, g->d.nz, g->w, pl);
     } else {
         dispatch<float, SUB>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, in,
                              g->k2_real, rw, s);

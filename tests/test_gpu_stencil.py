@@ -145,3 +145,66 @@ def test_apply_rejects_overlap_and_bad_prec(ctx):
     assert e.value.status == helm.EINVAL
     st = helm.lib().helm_apply(grid._h, 7, helm._ptr(u), helm._ptr(torch.empty_like(u)), 1)
     assert st == helm.EINVAL
+
+
+@pytest.mark.parametrize("case", [
+    # nx, ny, nz, npml, top_pml, Q
+    (37, 35, 33, 8, False, None),     # ragged against the 16 x 4 x 16 blocks; absorbing layers
+    (24, 20, 18, 4, True, 60.0),      # complex k^2, absorbing top
+    (64, 40, 20, 0, False, None),     # no absorbing layers: every block takes the plain path
+    (17, 5, 3, 2, False, 80.0),       # fewer planes than a block's chunk
+])
+def test_stencil_zmarch_matches_per_node_kernel_and_oracle(ctx, case):
+    """The z-marching complex64 stencil (16 columns, constant weights) against the per-node kernel (the
+    tuning switch selects the path) and the FP64 oracle: the same operator summed in another order, so
+    the two agree to FP32 rounding (1e-6 relative L2) and both match the oracle (1e-5)."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    nx, ny, nz, npml, top, Q = case
+    h, f, nrhs = 25.0, 5.0, 16
+    c = synth.linear_gradient(nx, ny, nz, h, 1500.0, 2.0, Q=Q)
+    w = synth.random_weights(nx + 1)
+    grid = helm.Grid(ctx, nx, ny, nz, h, f, c, npml=npml, top_bc=helm.TOP_PML if top else helm.TOP_DIRICHLET,
+                     weights=w)
+    prob = Problem(nx, ny, nz, h, f, c, npml=npml, top_pml=top, weights=w)
+    u = synth.random_complex((nz, ny, nx, nrhs), 2000 + nx)
+    want = apply_A(prob, u)
+    u32 = torch.from_numpy(u.astype(np.complex64)).cuda()
+    got = {}
+    for march in (1, 0):
+        ctx.set_tuning(helm.TUNE_STENCIL_MARCH, march)
+        ctx.profile(True, only=["stencil"])
+        got[march] = grid.apply(u32, prec=helm.PREC_FP32).cpu().numpy().astype(np.complex128)
+        assert ctx.profile_query("stencil")[0] == 1
+        ctx.profile(False)
+    ctx.set_tuning(helm.TUNE_STENCIL_MARCH, 1)
+    assert _rel(got[1], got[0]) <= 1e-6
+    for m in (1, 0):
+        assert _rel(got[m], want) <= 1e-5
+
+
+def test_stencil_zmarch_residual_path_in_fgmres(ctx):
+    """The z-march's b - A u form (the two-level preconditioner's t = v - A q with a complex64 basis): the
+    16-column two-level FGMRES converges with either stencil kernel, within one iteration of each other,
+    and the oracle's FP64 residual of both results is <= tol."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    nx, ny, nz, h, f, tol = 28, 26, 24, 25.0, 6.0, 1e-6
+    c = synth.linear_gradient(nx, ny, nz, h, 1500.0, 0.6, Q=100.0)
+    w = helm.fit_weights()
+    grid = helm.Grid(ctx, nx, ny, nz, h, f, c, npml=4, weights=w)
+    prob = Problem(nx, ny, nz, h, f, c, npml=4, weights=w)
+    b = synth.point_sources(nx, ny, nz, h, synth.source_plane_positions(nx, ny, 4, 3, 16, 17))
+    o = helm.Oras(grid, (2, 2, 2), 2, coarse_ratio=4, factor_prec=helm.PREC_TF32)
+    its = {}
+    for march in (1, 0):
+        ctx.set_tuning(helm.TUNE_STENCIL_MARCH, march)
+        x, st = o.solve(torch.from_numpy(b).cuda(), tol=tol, restart=30, basis_prec=helm.PREC_FP32)
+        its[march] = [s["iterations"] for s in st]
+        x = x.cpu().numpy()
+        for r in (0, 15):
+            assert st[r]["converged"]
+            res = np.linalg.norm(apply_A(prob, x[..., r]) - b[..., r]) / np.linalg.norm(b[..., r])
+            assert res <= tol
+    ctx.set_tuning(helm.TUNE_STENCIL_MARCH, 1)
+    assert max(abs(a - c_) for a, c_ in zip(its[1], its[0])) <= 1
