@@ -81,10 +81,11 @@ template <> struct RAcc<double> {
 
 // partial[blk][i][r] = sum over this block's elements of conj(V_i[e]) w[e], i in [i0, i0+ni),
 // and with npart also |w|^2.  Runs on the reduction grid (grid stride a multiple of nrhs, so each
-// thread keeps one column).  Two elements per loop trip and IC basis vectors per pass keep 2 * (IC+1)
-// independent loads in flight; products in the basis precision are summed in groups of up to 8
-// before they are added to the thread's accumulator (CAcc); one FP64 block-wide reduction per pass.
-template <typename T>
+// thread keeps one column).  EPT elements per loop trip and IC basis vectors per pass keep EPT * (IC+1)
+// independent loads in flight (EPT = 8 for bases of up to 2 vectors, else 2); products in the basis
+// precision are summed in groups of up to 8 before they are added to the thread's accumulator (CAcc);
+// one FP64 block-wide reduction per pass.
+template <typename T, int EPT = 2>
 __global__ void __launch_bounds__(RED_THREADS, 2) dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
                                                               const cplx<T>* __restrict__ w, long long n_el, int nrhs,
                                                               int i0, int ni, c128* __restrict__ partial, int ldp,
@@ -106,26 +107,27 @@ __global__ void __launch_bounds__(RED_THREADS, 2) dots_kernel(const cplx<T>* __r
         T pn = (T)0;
         int cnt = 0;
         const cplx<T>* Vb = V + (long long)(i0 + ib) * vstride;
+        constexpr int QL = EPT > 2 ? 2 : IC;   // basis vectors loaded per trip (IC, or 2 with 8 elements)
         long long e = t;
-        for (; e + stride < n_el; e += 2 * stride) {
-            const cplx<T> w0 = w[e], w1 = w[e + stride];
-            cplx<T> a[IC], b[IC];
+        for (; e + (EPT - 1) * stride < n_el; e += EPT * stride) {
+            cplx<T> wv[EPT];
+            cplx<T> a[EPT][QL];
 #pragma unroll
-            for (int q = 0; q < IC; ++q) {
-                if (q < nq) {
-                    a[q] = Vb[(long long)q * vstride + e];
-                    b[q] = Vb[(long long)q * vstride + e + stride];
-                }
-            }
+            for (int u = 0; u < EPT; ++u) wv[u] = w[e + u * stride];
 #pragma unroll
-            for (int q = 0; q < IC; ++q) {
-                if (q < nq) {
-                    cmac_conj(part[q], a[q], w0);
-                    cmac_conj(part[q], b[q], w1);
-                }
-            }
-            if (with_norm) pn += w0.x * w0.x + w0.y * w0.y + w1.x * w1.x + w1.y * w1.y;
-            if ((cnt += 2) >= 8) {
+            for (int u = 0; u < EPT; ++u)
+#pragma unroll
+                for (int q = 0; q < QL; ++q)
+                    if (q < nq) a[u][q] = Vb[(long long)q * vstride + e + u * stride];
+#pragma unroll
+            for (int u = 0; u < EPT; ++u)
+#pragma unroll
+                for (int q = 0; q < QL; ++q)
+                    if (q < nq) cmac_conj(part[q], a[u][q], wv[u]);
+            if (with_norm)
+#pragma unroll
+                for (int u = 0; u < EPT; ++u) pn += wv[u].x * wv[u].x + wv[u].y * wv[u].y;
+            if ((cnt += EPT) >= 8) {
 #pragma unroll
                 for (int q = 0; q < IC; ++q) {
                     if (q < nq) acc[q].add(part[q]);
@@ -136,10 +138,11 @@ __global__ void __launch_bounds__(RED_THREADS, 2) dots_kernel(const cplx<T>* __r
                 cnt = 0;
             }
         }
-        if (e < n_el) {
+        // the last, partial trip: at most EPT - 1 elements, each product added once
+        for (int u = 0; u < (EPT == 2 ? 1 : EPT - 1) && e < n_el; ++u, e += stride) {
             const cplx<T> w0 = w[e];
 #pragma unroll
-            for (int q = 0; q < IC; ++q)
+            for (int q = 0; q < QL; ++q)
                 if (q < nq) cmac_conj(part[q], Vb[(long long)q * vstride + e], w0);
             if (with_norm) pn += w0.x * w0.x + w0.y * w0.y;
         }
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(RED_THREADS, 2) update_norm_kernel(const cplx<
 // |w'|^2 (compensated) are reduced per block.  Runs on the reduction grid (one column per thread), one
 // resident block per SM.
 template <typename T, int IM>
-__global__ void __launch_bounds__(RED_THREADS, 1) update_dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
+__global__ void __launch_bounds__(RED_THREADS, IM <= 4 ? 2 : 1) update_dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
                                                                     cplx<T>* __restrict__ w, long long n_el, int nrhs,
                                                                     int ni, const c128* __restrict__ hsrc,
                                                                     c128* __restrict__ partial, int ldp,
@@ -300,7 +303,9 @@ __global__ void __launch_bounds__(RED_THREADS, 1) update_dots_kernel(const cplx<
     RAcc<T> nrm;
     // EPT elements per trip (e, e + stride, ...: the same column), so that every trip keeps the same number
     // of basis loads in flight whatever IM is
-    constexpr int EPT = (sizeof(T) == 4 ? 32 : 16) / IM > 0 ? (sizeof(T) == 4 ? 32 : 16) / IM : 1;
+    // (bases of up to 4 vectors: 8 elements (8 / IM in FP64), two blocks per SM)
+    constexpr int EPT = IM <= 4 ? (sizeof(T) == 4 ? 8 : 8 / IM)
+                                : ((sizeof(T) == 4 ? 32 : 16) / IM > 0 ? (sizeof(T) == 4 ? 32 : 16) / IM : 1);
     for (long long e0 = t; e0 < n_el; e0 += EPT * stride) {
         cplx<T> v[EPT][IM];
         cplx<T> x[EPT];
@@ -338,7 +343,7 @@ __global__ void __launch_bounds__(RED_THREADS, 1) update_dots_kernel(const cplx<
         if (q0 >= ni) break;
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 8; ++q) s[q][threadIdx.x] = widen(acc[q0 + q]);
+        for (int q = 0; q < 8; ++q) s[q][threadIdx.x] = q0 + q < IM ? widen(acc[min(q0 + q, IM - 1)]) : mk<double>(0, 0);
         __syncthreads();
         const int nq = min(8, ni - q0);
         for (int o = threadIdx.x; o < nq * nr; o += RED_THREADS) {
@@ -359,8 +364,9 @@ __global__ void __launch_bounds__(RED_THREADS, 1) update_dots_kernel(const cplx<
 }
 
 // Second update of CGS2 fused with the normalisation: out = (w' - V h2) * inv[r] (inv = 0 writes zeros, for
-// the columns whose cycle has stopped).  Two elements per trip, batches of 8 basis loads.
-template <typename T>
+// the columns whose cycle has stopped).  EPT elements per trip and batches of QB basis loads (EPT * QB = 16,
+// more elements for fewer basis vectors, so that short bases still keep 16 loads in flight per thread).
+template <typename T, int EPT, int QB>
 __global__ void __launch_bounds__(RED_THREADS, 2) update_scale_kernel(const cplx<T>* __restrict__ V, long long vstride,
                                                                      const cplx<T>* __restrict__ w,
                                                                      cplx<T>* __restrict__ out, long long n_el,
@@ -374,30 +380,39 @@ __global__ void __launch_bounds__(RED_THREADS, 2) update_scale_kernel(const cplx
     for (int e = threadIdx.x; e < ni * nrhs; e += RED_THREADS) hs[e] = mk<T>((T)hsrc[e].x, (T)hsrc[e].y);
     __syncthreads();
     const T sc = (T)inv[r];
-    for (long long e = t; e < n_el; e += 2 * stride) {
-        const bool two = e + stride < n_el;
-        const long long e1 = two ? e + stride : e;
-        cplx<T> acc0 = w[e], acc1 = w[e1];
-        for (int i0 = 0; i0 < ni; i0 += 8) {
-            cplx<T> v0[8], v1[8];
+    for (long long e0 = t; e0 < n_el; e0 += EPT * stride) {
+        cplx<T> acc[EPT];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (i0 + q < ni) {
-                    v0[q] = V[(long long)(i0 + q) * vstride + e];
-                    v1[q] = V[(long long)(i0 + q) * vstride + e1];
-                }
+        for (int u = 0; u < EPT; ++u) {
+            const long long e = e0 + u * stride;
+            acc[u] = w[e < n_el ? e : e0];
+        }
+        for (int i0 = 0; i0 < ni; i0 += QB) {
+            cplx<T> v[EPT][QB];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+            for (int u = 0; u < EPT; ++u) {
+                const long long e = e0 + u * stride;
+                const long long ec = e < n_el ? e : e0;
+#pragma unroll
+                for (int q = 0; q < QB; ++q)
+                    if (i0 + q < ni) v[u][q] = V[(long long)(i0 + q) * vstride + ec];
+            }
+#pragma unroll
+            for (int q = 0; q < QB; ++q)
                 if (i0 + q < ni) {
                     const cplx<T> h = hs[(i0 + q) * nrhs + r];
-                    acc0.x -= h.x * v0[q].x - h.y * v0[q].y;
-                    acc0.y -= h.x * v0[q].y + h.y * v0[q].x;
-                    acc1.x -= h.x * v1[q].x - h.y * v1[q].y;
-                    acc1.y -= h.x * v1[q].y + h.y * v1[q].x;
+#pragma unroll
+                    for (int u = 0; u < EPT; ++u) {
+                        acc[u].x -= h.x * v[u][q].x - h.y * v[u][q].y;
+                        acc[u].y -= h.x * v[u][q].y + h.y * v[u][q].x;
+                    }
                 }
         }
-        out[e] = mk<T>(acc0.x * sc, acc0.y * sc);
-        if (two) out[e1] = mk<T>(acc1.x * sc, acc1.y * sc);
+#pragma unroll
+        for (int u = 0; u < EPT; ++u) {
+            const long long e = e0 + u * stride;
+            if (e < n_el) out[e] = mk<T>(acc[u].x * sc, acc[u].y * sc);
+        }
     }
 }
 
@@ -802,7 +817,10 @@ struct Krylov final : KrylovEngine {
     // kernels return at once when no column needs it, so that the first family's bandwidth is exact)
     void dots_pass(const cplx<T>* Vb, const cplx<T>* vec, int ni, double* npart, const int* anyp) {
         const int tk = prof_begin(ctx, anyp ? "arnoldi_reorth" : "arnoldi");
-        dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, S, 0, ni, part, ldp, npart, anyp);
+        if (ni <= 2)
+            dots_kernel<T, 8><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, S, 0, ni, part, ldp, npart, anyp);
+        else
+            dots_kernel<T><<<nblk, RED_THREADS, 0, st>>>(Vb, nel, vec, nel, S, 0, ni, part, ldp, npart, anyp);
         prof_end(ctx, tk, (double)(ni + 1 + (npart ? 1 : 0)) * nel * sizeof(cplx<T>));
         ctx->launches++;
     }
@@ -889,17 +907,23 @@ struct Krylov final : KrylovEngine {
     // v_{j+1} = (w' - V h2) / H[j+1][j] fused with the second update.
     helm_status cgs2_fused(int j) {
         const int ni = j + 1;
-        // one resident block per SM for the fused kernel: the largest multiple of q <= the SM count
+        // resident blocks per SM for the fused kernel (two for bases of up to 4 vectors, whose smaller register
+        // arrays allow it), as the largest multiple of q <= that many blocks
         int a = RED_THREADS, bq = S;
         while (bq) { const int t = a % bq; a = bq; bq = t; }
         const int q = S / a;
-        const int nb1 = std::min(nblk, std::max(q, (std::max(1, ctx->sm_count) / q) * q));
+        const int per_sm = ni <= 4 ? 2 : 1;
+        const int nb1 = std::min(nblk, std::max(q, (per_sm * std::max(1, ctx->sm_count) / q) * q));
         dots_pass(V, w, ni, nullptr, nullptr);
         finish_into(ni, hpass, S, 1, 0, 0, nullptr, nullptr);
         finish_into(ni, H, m, (m + 1) * m, j, 0, nullptr, nullptr);
         {
             const int tk = prof_begin(ctx, "arnoldi");
-            if (ni <= 8)
+            if (ni <= 2)
+                update_dots_kernel<T, 2><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
+            else if (ni <= 4)
+                update_dots_kernel<T, 4><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
+            else if (ni <= 8)
                 update_dots_kernel<T, 8><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
             else if (ni <= 16 || sizeof(T) == 8)
                 update_dots_kernel<T, 16><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
@@ -917,8 +941,15 @@ struct Krylov final : KrylovEngine {
         givens_step<<<rg, 128, 0, st>>>(Sd, H, cs, sn, gv, hn, inv, j, m, S, running);
         {
             const int tk = prof_begin(ctx, "arnoldi");
-            update_scale_kernel<T><<<nblk, RED_THREADS, (size_t)ni * S * sizeof(cplx<T>), st>>>(
-                V, nel, w, V + (long long)(j + 1) * nel, nel, S, ni, hpass, inv);
+            const size_t hsm = (size_t)ni * S * sizeof(cplx<T>);
+            cplx<T>* vn = V + (long long)(j + 1) * nel;
+            if (ni <= 2)
+                update_scale_kernel<T, (sizeof(T) == 4 ? 8 : 4), (sizeof(T) == 4 ? 2 : 4)><<<nblk, RED_THREADS, hsm, st>>>(
+                    V, nel, w, vn, nel, S, ni, hpass, inv);
+            else if (ni <= 4)
+                update_scale_kernel<T, 4, 4><<<nblk, RED_THREADS, hsm, st>>>(V, nel, w, vn, nel, S, ni, hpass, inv);
+            else
+                update_scale_kernel<T, 2, 8><<<nblk, RED_THREADS, hsm, st>>>(V, nel, w, vn, nel, S, ni, hpass, inv);
             prof_end(ctx, tk, (double)(ni + 2) * nel * sizeof(cplx<T>));
         }
         ctx->launches += 2;
