@@ -407,6 +407,26 @@ def run_gpu(args, W):
                                           "max_true_relres": max(s_["true_relres"] for s_ in sti),
                                           "rel_l2_vs_exact_coarse_solution": err}
             del oi, xi
+        # a frequency sweep of the same model and sources (three neighbouring frequencies): warm starts from
+        # the previous frequency, and the next frequency's grid and factors built on a second context while
+        # the current one is solved; wall time includes every set-up
+        fs = [W["f"] - 0.1, W["f"], W["f"] + 0.1]
+        sweep_kw = dict(npml=W["npml"], weights=weights, coarse_ratio=W["coarse"], factor_prec=helm.PREC_TF32,
+                        tol=W["tol"], restart=W["restart"], basis_prec=helm.PREC_FP32)
+        sweep = {"freqs_hz": fs}
+        for name, warm, ov in (("overlap_warm", True, True), ("sequential_warm", True, False),
+                               ("overlap_cold", False, True)):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            xs_, st_, su_ = helm.frequency_sweep(ctx, n, n, nz, W["h"], fs, velocity(W), b, W["parts"],
+                                                 W["overlap"], warm=warm, overlap_factor=ov, **sweep_kw)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t
+            sweep[name] = {"wall_s": wall, "rhs_per_s_incl_setup": len(fs) * nrhs / wall, "setup_s": su_,
+                           "iterations_max": [max(s_["iterations"] for s_ in f_) for f_ in st_],
+                           "iterations_total": [sum(s_["iterations"] for s_ in f_) for f_ in st_]}
+            del xs_
+        variants["freq_sweep"] = sweep
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     bh = torch.from_numpy(b_host).pin_memory()

@@ -270,6 +270,37 @@ typedef struct {
 helm_status gmres_solve(helm_oras o, const void* b, void* x, int nrhs, const helm_gmres_desc* desc,
                         helm_rhs_stats* stats);
 
+/* -------------------------------------------------------------- frequency sweeps
+ *
+ * Several frequencies of one model and one set of sources (the paper's forward problem is solved for many
+ * frequencies and sources per model, section 1).  For each frequency f_i the driver builds the grid
+ * (helm_setup_grid with desc.grid and freq_hz = freqs[i]) and the ORAS factors (oras_factor), solves
+ * (gmres_solve) and frees the factors again, so that at most two factor sets are resident.
+ *   warm = 1: frequency i > 0 starts from the solution at frequency i - 1 (use_x0; the solution of a
+ *             neighbouring frequency is close when the frequencies are close);
+ *   overlap = 1: the factors of frequency i + 1 are built on a second stream by a second host thread
+ *             (with a context of its own, created and destroyed by the call) while frequency i is
+ *             solved; 0 runs everything in order on ctx's stream.  Both give bit-identical x.
+ * c: wave speed complex128 [nz][ny][nx] (device or host), read once per frequency.  b: complex128
+ * [N][nrhs], the same right-hand sides at every frequency; x: complex128 [nfreq][N][nrhs]; b and x both
+ * device or both host.  stats (host, may be NULL): [nfreq][nrhs].  setup_s (host, may be NULL): [nfreq],
+ * the wall time of each frequency's grid set-up and factorisation.  desc.gmres.use_x0 is ignored.
+ * Returns the first error (later frequencies are then not solved), else HELM_ENOTCONV if some column of
+ * some frequency missed tol (every frequency is still solved), else HELM_OK.  The serving loop must not
+ * be active on ctx. */
+typedef struct {
+    helm_grid_desc  grid;     /* freq_hz is ignored: each frequency comes from freqs */
+    helm_oras_desc  oras;
+    helm_gmres_desc gmres;
+    int             nfreq;    /* 1 .. 64 */
+    const double*   freqs;    /* host array of nfreq frequencies in Hz (> 0) */
+    int             warm;     /* 0 or 1 */
+    int             overlap;  /* 0 or 1 */
+} helm_sweep_desc;
+
+helm_status helm_frequency_sweep(helm_ctx ctx, const helm_sweep_desc* desc, const void* c, const void* b, void* x,
+                                 int nrhs, helm_rhs_stats* stats, double* setup_s);
+
 /* -------------------------------------------------------------- serving
  *
  * A request loop on one context (BASELINE serving pattern; the paper's

@@ -64,6 +64,11 @@ class RhsStats(C.Structure):
                 ("est_relres", C.c_double)]
 
 
+class SweepDesc(C.Structure):
+    _fields_ = [("grid", GridDesc), ("oras", OrasDesc), ("gmres", GmresDesc), ("nfreq", C.c_int),
+                ("freqs", C.POINTER(C.c_double)), ("warm", C.c_int), ("overlap", C.c_int)]
+
+
 class Request(C.Structure):
     _fields_ = [("model_id", C.c_uint64), ("grid", GridDesc), ("c", C.c_void_p), ("oras", OrasDesc),
                 ("gmres", GmresDesc), ("nrhs", C.c_int), ("b", C.c_void_p), ("x", C.c_void_p)]
@@ -108,6 +113,8 @@ def lib():
         "oras_setup_seconds": (C.c_double, [vp]),
         "oras_estimate_bytes_c": (st, [C.POINTER(GridDesc), C.POINTER(OrasDesc), i32, C.POINTER(C.c_size_t)]),
         "gmres_solve": (st, [vp, vp, vp, i32, C.POINTER(GmresDesc), C.POINTER(RhsStats)]),
+        "helm_frequency_sweep": (st, [vp, C.POINTER(SweepDesc), vp, vp, vp, i32, C.POINTER(RhsStats),
+                                      C.POINTER(C.c_double)]),
         "helm_serve_start": (st, [vp, i32]),
         "helm_submit": (st, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
         "helm_poll": (st, [vp, C.c_uint64, C.POINTER(i32), C.POINTER(RequestStats)]),
@@ -399,3 +406,37 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def frequency_sweep(ctx: Context, nx, ny, nz, h, freqs, c, b, parts, overlap, x=None, npml=8,
+                    top_bc=TOP_DIRICHLET, pml_R=1e-3, weights=None, weight_bins=0, coarse_ratio=0, interface_bc=0,
+                    factor_prec=PREC_FP64, coarse_iters=0, coarse_overlap=1, tol=1e-6, restart=30, maxit=1000,
+                    flexible=True, basis_prec=PREC_FP64, warm=True, overlap_factor=True, allow_notconv=False):
+    """``helm_frequency_sweep``: b complex128 ``[nz, ny, nx, nrhs]`` (the sources of every frequency);
+    returns x ``[nfreq, nz, ny, nx, nrhs]``, per-frequency stats and set-up seconds."""
+    import torch
+    if weights is None:
+        weights = fit_weights()
+    nf = len(freqs)
+    gd = GridDesc(nx, ny, nz, h, 0.0, npml, pml_R, top_bc, (C.c_double * 7)(*weights), weight_bins)
+    od = OrasDesc(parts[0], parts[1], parts[2], overlap, coarse_ratio, interface_bc, factor_prec, coarse_iters,
+                  coarse_overlap)
+    gm = GmresDesc(tol, restart, maxit, 1 if flexible else 0, basis_prec, 0)
+    fa = (C.c_double * nf)(*freqs)
+    d = SweepDesc(gd, od, gm, nf, fa, 1 if warm else 0, 1 if overlap_factor else 0)
+    if isinstance(c, np.ndarray):
+        c = torch.from_numpy(np.ascontiguousarray(c, dtype=np.complex128))
+    c = c.contiguous()
+    assert b.dtype == torch.complex128 and b.is_contiguous()
+    n = nx * ny * nz
+    nrhs = b.numel() // n
+    if x is None:
+        x = torch.empty((nf,) + tuple(b.shape), dtype=b.dtype, device=b.device)
+    stats = (RhsStats * (nf * nrhs))()
+    setup = (C.c_double * nf)()
+    st = lib().helm_frequency_sweep(ctx._h, C.byref(d), _ptr(c), _ptr(b), _ptr(x), nrhs, stats, setup)
+    if st and not (allow_notconv and st == ENOTCONV):
+        ctx.check(st, "helm_frequency_sweep")
+    out = [[dict(iterations=stats[f * nrhs + r].iterations, converged=bool(stats[f * nrhs + r].converged),
+                 true_relres=stats[f * nrhs + r].true_relres) for r in range(nrhs)] for f in range(nf)]
+    return x, out, list(setup)
