@@ -225,6 +225,121 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_panel(const BoxInfo* __restrict
     }
 }
 
+// gj_panel with the panel held in shared memory: NB columns of all m rows (column-major, m * NB complex
+// values), 1024 threads.  The same pivots (largest modulus, ties to the smallest row) and the same
+// per-entry operations as gj_panel; the row swaps of the columns outside the panel are recorded and
+// applied to the matrix, in order, after the panel, which gives the rows gj_panel's whole-row swaps
+// leave (nothing else touches those columns in between).
+constexpr int GJS_THREADS = 1024;
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(GJS_THREADS) gj_panel_smem(const BoxInfo* __restrict__ boxes, cplx<T>* __restrict__ S,
+                                                             int* __restrict__ perm, cplx<T>* __restrict__ rows,
+                                                             int* __restrict__ flag, int m_max, int j0, int k) {
+    extern __shared__ __align__(16) unsigned char gjs_smem[];
+    cplx<T>* P = reinterpret_cast<cplx<T>*>(gjs_smem);   // [NB][m]: column-major, a warp reads 32 consecutive rows
+    const BoxInfo B = boxes[blockIdx.x];
+    const int m = B.m;
+    if (k >= B.dims[2] || j0 >= m) return;
+    const int nbw = min(NB, m - j0);
+    cplx<T>* A = S + (size_t)blockIdx.x * m_max * m_max;
+    int* pv = perm + (size_t)blockIdx.x * m_max;
+    __shared__ T s_val[GJS_THREADS / 32];
+    __shared__ int s_idx[GJS_THREADS / 32];
+    __shared__ int s_piv[NB];
+    __shared__ cplx<T> s_row[NB];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int e = tid; e < m * NB; e += GJS_THREADS) {
+        const int r = e / NB, c = e % NB;
+        P[c * m + r] = c < nbw ? A[(size_t)r * m + j0 + c] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    for (int cc = 0; cc < nbw; ++cc) {
+        const int c = j0 + cc;
+        T best = (T)-1;
+        int bi = m;
+        for (int r = c + tid; r < m; r += GJS_THREADS) {
+            const T v = cabs2(P[cc * m + r]);
+            if (v > best) { best = v; bi = r; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            T bv = s_val[0];
+            int bidx = s_idx[0];
+            for (int w = 1; w < GJS_THREADS / 32; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bidx)) { bv = s_val[w]; bidx = s_idx[w]; }
+            if (!(bv > (T)0) || bidx >= m) {
+                atomicOr(flag, 1);
+                bidx = c;
+            }
+            s_piv[cc] = bidx;
+            pv[c] = bidx;
+        }
+        __syncthreads();
+        const int p = s_piv[cc];
+        if (p != c && tid < NB) {
+            const cplx<T> t = P[tid * m + c];
+            P[tid * m + c] = P[tid * m + p];
+            P[tid * m + p] = t;
+        }
+        __syncthreads();
+        cplx<T> piv = P[cc * m + c];
+        if (!(cabs2(piv) > (T)0)) piv = mk<T>((T)1, (T)0);   // singular: flagged above, keep going finite
+        const cplx<T> inv = cinv(piv);
+        if (tid < nbw) s_row[tid] = (tid == cc) ? inv : P[tid * m + c] * inv;
+        __syncthreads();
+        for (int r = tid; r < m; r += GJS_THREADS) {
+            if (r == c) {
+                for (int jj = 0; jj < nbw; ++jj) P[jj * m + r] = s_row[jj];
+                continue;
+            }
+            const cplx<T> f = P[cc * m + r];
+            for (int jj = 0; jj < nbw; ++jj) {
+                cplx<T>& x = P[jj * m + r];
+                if (jj == cc) {
+                    const cplx<T> v = f * inv;
+                    x = mk<T>(-v.x, -v.y);
+                } else {
+                    const cplx<T> sv = s_row[jj];
+                    x.x -= f.x * sv.x - f.y * sv.y;
+                    x.y -= f.x * sv.y + f.y * sv.x;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // the recorded row swaps, in order, on the columns outside the panel
+    for (int cc = 0; cc < nbw; ++cc) {
+        const int c = j0 + cc, p = s_piv[cc];
+        if (p != c)
+            for (int j = tid; j < m; j += GJS_THREADS) {
+                if (j >= j0 && j < j0 + nbw) continue;
+                const cplx<T> t = A[(size_t)c * m + j];
+                A[(size_t)c * m + j] = A[(size_t)p * m + j];
+                A[(size_t)p * m + j] = t;
+            }
+        __syncthreads();
+    }
+    // the panel back, and rows j0..j0+nbw (all columns) for the trailing update
+    for (int e = tid; e < m * NB; e += GJS_THREADS) {
+        const int r = e / NB, c = e % NB;
+        if (c < nbw) A[(size_t)r * m + j0 + c] = P[c * m + r];
+    }
+    __syncthreads();
+    cplx<T>* Rb = rows + (size_t)blockIdx.x * 64 * m_max;
+    for (long long e = tid; e < (long long)nbw * m; e += GJS_THREADS) {
+        const int i = (int)(e / m), j = (int)(e % m);
+        Rb[(size_t)i * m + j] = (j >= j0 && j < j0 + nbw) ? P[(j - j0) * m + j0 + i] : A[(size_t)(j0 + i) * m + j];
+    }
+}
+
 // Columns outside the panel: A[r][j] = [r not in panel] A[r][j] + sum_c W[r][c] Rows[c][j].
 // 64 x 64 output tile per CTA, 16 x 16 threads, 4 x 4 outputs per thread.
 template <typename T, int NB>
@@ -516,6 +631,17 @@ helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
     const unsigned eblocks = (unsigned)std::min<long long>(((long long)m * m + 255) / 256, 4096);
     const dim3 egrid(eblocks, P.nbox);
     const int tiles = (m + 63) / 64;
+    // complex64: 24-column panels held in shared memory while they fit (m * 24 * 8 bytes, m <= 1066);
+    // else the global-memory panel of nb columns
+    constexpr int NBS = 24;
+    const size_t psm = (size_t)m * NBS * sizeof(cplx<T>);
+    static bool psm_attr = false;
+    if (sizeof(T) == 4 && !psm_attr) {
+        cudaFuncSetAttribute(gj_panel_smem<T, NBS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        psm_attr = true;
+    }
+    const bool smem_panel = sizeof(T) == 4 && psm <= 200 * 1024;
+    const int nbk = smem_panel ? NBS : nb;
     for (int k = 0; k < P.bz_max; ++k) {
         if (k == 0) {
             schur_init<T><<<egrid, 256, 0, st>>>(P.dbox, coef, S, m, k);
@@ -528,12 +654,17 @@ helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
         double ub = 0;
         for (const auto& b : P.hbox)
             if (k < b.dims[2]) ub += 2.0 * b.m * b.m * sizeof(cplx<T>);
-        for (int j0 = 0; j0 < m; j0 += nb) {
+        for (int j0 = 0; j0 < m; j0 += nbk) {
             int t = prof_begin(ctx, "gj_panel");
-            gj_panel<T><<<P.nbox, GJ_THREADS, 0, st>>>(P.dbox, S, perm, rows, flag, m, nb, j0, k);
+            if (smem_panel)
+                gj_panel_smem<T, NBS><<<P.nbox, GJS_THREADS, psm, st>>>(P.dbox, S, perm, rows, flag, m, j0, k);
+            else
+                gj_panel<T><<<P.nbox, GJ_THREADS, 0, st>>>(P.dbox, S, perm, rows, flag, m, nb, j0, k);
             prof_end(ctx, t, 0.0);
             t = prof_begin(ctx, "gj_update");
-            if (sizeof(T) == 4)
+            if (sizeof(T) == 4 && smem_panel)
+                gj_update<T, NBS><<<dim3(tiles, tiles, P.nbox), 256, 0, st>>>(P.dbox, S, rows, m, j0, k);
+            else if (sizeof(T) == 4)
                 gj_update<T, 32><<<dim3(tiles, tiles, P.nbox), 256, 0, st>>>(P.dbox, S, rows, m, j0, k);
             else
                 gj_update<T, 16><<<dim3(tiles, tiles, P.nbox), 256, 0, st>>>(P.dbox, S, rows, m, j0, k);
