@@ -163,16 +163,15 @@ struct PlaneSet {
 struct KrylovEngine;
 
 // Work queue of the persistent tensor-core sweep (sweep_tc.cu), sized by the box geometry alone.
-// One allocation: ctl (head, tail, one counter per box) and flag (one per pushed item) first, reset
-// before every launch, then the initial items and the pushed items (int4 each).
+// One allocation: ctl (head, tail, one counter per box) and flag (one per pushed slot: the slot's packed
+// item once published, 0 before) first, reset before every launch, then the initial items (packed).
 struct TcFlow {
     void* mem = nullptr;
     size_t bytes = 0;
     size_t reset_bytes = 0;
     int* ctl = nullptr;
     int* flag = nullptr;
-    int4* init = nullptr;
-    int4* items = nullptr;
+    int* init = nullptr;
     int ninit = 0, total = 0;
 };
 

@@ -297,6 +297,17 @@ __device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* 
         cp_async_commit();
         cp_async_wait<2>();
         __syncthreads();
+        // b of the output plane q - 1, loaded now so that its latency overlaps this step's arithmetic
+        float4 bq[MN];
+        if (SUB) {
+#pragma unroll
+            for (int c = 0; c < MN; ++c) {
+                bq[c] = f4(0.f);
+                if (live && q - 1 >= k0 && ib + c < nx)
+                    bq[c] = __ldg(reinterpret_cast<const float4*>(b + (((long long)(q - 1) * ny + j) * nx + ib + c) *
+                                                                     (2 * MNP)) + pc);
+            }
+        }
         const float4* cu = su + buf * MBUF_U;
         const float2* ck = sk + buf * MBUF_K;
         const bool qin = q >= 0 && q < nz;
@@ -347,10 +358,7 @@ __device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* 
                 float4 o = add4(PLAIN ? add4(P[c], hS1) : caxpy4(zm, hS1, P[c]), T1);
                 const long long node = ((long long)(q - 1) * ny + j) * nx + i;
                 float4* dst = reinterpret_cast<float4*>(y + node * (2 * MNP)) + pc;
-                if (SUB) {
-                    const float4 bb = __ldg(reinterpret_cast<const float4*>(b + node * (2 * MNP)) + pc);
-                    o = make_float4(bb.x - o.x, bb.y - o.y, bb.z - o.z, bb.w - o.w);
-                }
+                if (SUB) o = make_float4(bq[c].x - o.x, bq[c].y - o.y, bq[c].z - o.z, bq[c].w - o.w);
                 __stcs(dst, o);
             }
             // output q: the centre term; output q + 1: its first term

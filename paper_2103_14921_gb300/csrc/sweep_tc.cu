@@ -531,26 +531,35 @@ __device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
 
 constexpr int FLOW_QT = 96;   // the thread that handles the queue (warp 3, lane 0)
 
+// A queue item packed in one int: box (11 bits), operation (10 bits), tile (10 bits), stored + 1 so that a
+// published slot is never 0 (the flag of a slot is its item).
+__device__ __host__ __forceinline__ int flow_pack(int box, int j, int t) { return ((box << 20) | (j << 10) | t) + 1; }
+
 // The item in queue slot `slot` (bounded wait until it has been published); x = -1 when the queue is
 // exhausted or a wait anywhere gave up.
-__device__ __forceinline__ int4 flow_fetch(int slot, const int4* __restrict__ init, int ninit, const int4* items,
-                                           const int* flag, int total, int* err) {
+__device__ __forceinline__ int4 flow_fetch(int slot, const int* __restrict__ init, int ninit, const int* flag, int total,
+                                           int* err) {
     if (slot >= total || *reinterpret_cast<volatile int*>(err) != 0) return make_int4(-1, 0, 0, 0);
-    if (slot < ninit) return init[slot];
-    const int q = slot - ninit;
-    const uint64_t t0 = global_ns();
-    for (uint32_t i = 0;; ++i) {
-        if (ld_acquire_gpu(flag + q)) return __ldcg(items + q);
-        if ((i & 255) == 255) {
-            if (*reinterpret_cast<volatile int*>(err) != 0) break;
-            if (global_ns() - t0 > FLOW_WAIT_NS) {
-                atomicExch(err, 4);
-                break;
+    int v = 0;
+    if (slot < ninit) {
+        v = init[slot];
+    } else {
+        const int q = slot - ninit;
+        const uint64_t t0 = global_ns();
+        for (uint32_t i = 0;; ++i) {
+            if ((v = ld_acquire_gpu(flag + q)) != 0) break;
+            if ((i & 255) == 255) {
+                if (*reinterpret_cast<volatile int*>(err) != 0) return make_int4(-1, 0, 0, 0);
+                if (global_ns() - t0 > FLOW_WAIT_NS) {
+                    atomicExch(err, 4);
+                    return make_int4(-1, 0, 0, 0);
+                }
             }
+            __nanosleep(32);
         }
-        __nanosleep(32);
     }
-    return make_int4(-1, 0, 0, 0);
+    --v;
+    return make_int4(v >> 20, (v >> 10) & 1023, v & 1023, 0);
 }
 
 // ops in box b's chain, and the items of operation j
@@ -566,8 +575,8 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
                                                         const BoxInfo* __restrict__ boxes, const c64* __restrict__ coef,
                                                         const c64* __restrict__ lb, c64* __restrict__ loc,
                                                         E* __restrict__ bt, int ld2, int nrhs, int nkc,
-                                                        const int4* __restrict__ init, int ninit, int4* items,
-                                                        int* flag, int total, int* ctl, int* __restrict__ err) {
+                                                        const int* __restrict__ init, int ninit, int* flag, int total,
+                                                        int* ctl, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int4 cur;
     unsigned char* base = align1024(smem_raw);
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
     int slot = 0;
     if (threadIdx.x == FLOW_QT) {
         slot = atomicAdd(head, 1);
-        cur = flow_fetch(slot, init, ninit, items, flag, total, err);
+        cur = flow_fetch(slot, init, ninit, flag, total, err);
     }
     for (;;) {
         __syncthreads();
@@ -616,11 +625,11 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
                 if (j + 1 < flow_chain(bz)) {
                     const int n = flow_tiles(B.m, j + 1);
                     const int q0 = atomicAdd(tail, n);
-                    for (int i = 0; i < n && ninit + q0 + i < total; ++i) items[q0 + i] = make_int4(box, j + 1, i, 0);
-                    for (int i = 0; i < n && ninit + q0 + i < total; ++i) st_release_gpu(flag + q0 + i, 1);
+                    for (int i = 0; i < n && ninit + q0 + i < total; ++i)
+                        st_release_gpu(flag + q0 + i, flow_pack(box, j + 1, i));
                 }
             }
-            cur = flow_fetch(slot, init, ninit, items, flag, total, err);
+            cur = flow_fetch(slot, init, ninit, flag, total, err);
         }
     }
     gemm_teardown<E, NPAD, NST>(tmem);
@@ -734,7 +743,7 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
         const int t = prof_begin(ctx, "sweep_flow");
         tc_sweep_flow<E, NPAD, NST><<<grid, 128, Cfg::SMEM, st>>>(mapA, mapA32, mapB, P.dbox, coef, lb, loc, bt, 2 * ld,
                                                                    nrhs, P.pk_chunks, flow->init, flow->ninit,
-                                                                   flow->items, flow->flag, flow->total, flow->ctl, err);
+                                                                   flow->flag, flow->total, flow->ctl, err);
         prof_end(ctx, t, all);
         ctx->launches++;
         return cuda_check(ctx, cudaGetLastError(), "tensor-core plane sweeps (persistent)");
@@ -873,26 +882,29 @@ helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb_, 
 
 helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F) {
     tc_flow_free(ctx, F);
-    std::vector<int4> init;
+    std::vector<int> init;
     long long total = 0;
+    // the packed items hold box < 2048, operation < 1024 (n_z <= 256) and tile < 1024; otherwise no queue
+    // (the sweep then runs as per-step launches)
+    if (P.nbox >= 2048) return HELM_OK;
     for (int b = 0; b < P.nbox; ++b) {
         const BoxInfo& B = P.hbox[b];
+        if (flow_chain(B.dims[2]) > 1024 || flow_tiles(B.m, 0) > 1024 || flow_tiles(B.m, 1) > 1024) return HELM_OK;
         for (int j = 0; j < flow_chain(B.dims[2]); ++j) total += flow_tiles(B.m, j);
-        for (int i = 0; i < flow_tiles(B.m, 0); ++i) init.push_back(make_int4(b, 0, i, 0));
+        for (int i = 0; i < flow_tiles(B.m, 0); ++i) init.push_back(flow_pack(b, 0, i));
     }
-    if (total >= (1ll << 30)) return set_error(ctx, HELM_EINVAL, "tensor-core sweep: too many queue items");
+    if (total >= (1ll << 30)) return HELM_OK;
     const size_t nctl = ((size_t)P.nbox + 2 + 3) / 4 * 4;   // ints, padded to 16 bytes
     const size_t nflag = ((size_t)total + 3) / 4 * 4;
     F.reset_bytes = (nctl + nflag) * sizeof(int);
-    F.bytes = F.reset_bytes + (size_t)total * sizeof(int4);
+    F.bytes = F.reset_bytes + init.size() * sizeof(int);
     HELM_TRY(dev_alloc(ctx, &F.mem, F.bytes, "tensor-core sweep queue"));
     F.ctl = (int*)F.mem;
     F.flag = F.ctl + nctl;
-    F.init = (int4*)(F.flag + nflag);
+    F.init = F.flag + nflag;
     F.ninit = (int)init.size();
-    F.items = F.init + F.ninit;
     F.total = (int)total;
-    HELM_CUDA(ctx, cudaMemcpyAsync(F.init, init.data(), init.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    HELM_CUDA(ctx, cudaMemcpyAsync(F.init, init.data(), init.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     HELM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return HELM_OK;
 }
