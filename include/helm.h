@@ -92,8 +92,10 @@ size_t      helm_bytes_in_use(helm_ctx ctx);
 uint64_t    helm_launch_count(helm_ctx ctx);
 
 /* Per-kernel-family timing with CUDA events recorded on the context's stream
- * around every launch of the instrumented families ("stencil", "sweep_gemv",
- * "sweep_prep", "gj_update", "gj_panel", "arnoldi").  on = 1 enables (and
+ * around every launch of the instrumented families ("stencil", "stencil64", "sweep_flow" (the persistent
+ * tensor-core sweep), "sweep_gemm_tc", "sweep_prep", "sweep_gemv", "coarse_sweep", "coarse_prep",
+ * "coarse_restrict", "coarse_prolong", "coarse_inner", "oras_transfer", "gj_panel", "gj_update", "arnoldi",
+ * "arnoldi_reorth", "krylov_misc").  on = 1 enables (and
  * clears the counters), 0 disables.  helm_profile_query synchronizes the
  * stream and returns, for family `name`, the launches recorded, their summed
  * device time in milliseconds and their summed algorithmic bytes (the data a
