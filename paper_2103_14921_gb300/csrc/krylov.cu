@@ -274,7 +274,9 @@ __global__ void __launch_bounds__(RED_THREADS, 2) update_norm_kernel(const cplx<
 // projection's coefficients, plain FP32 sums per thread: they only correct rounding-level remainders) and of
 // |w'|^2 (compensated) are reduced per block.  Runs on the reduction grid (one column per thread), one
 // resident block per SM.
-template <typename T, int IM>
+// HS: the coefficients h are read from shared memory at every use instead of being held in registers
+// (needs ni * nrhs <= 16 IM); the freed registers carry twice as many elements per trip.
+template <typename T, int IM, bool HS = false>
 __global__ void __launch_bounds__(RED_THREADS, IM <= 4 ? 2 : 1) update_dots_kernel(const cplx<T>* __restrict__ V, long long vstride,
                                                                     cplx<T>* __restrict__ w, long long n_el, int nrhs,
                                                                     int ni, const c128* __restrict__ hsrc,
@@ -290,13 +292,15 @@ __global__ void __launch_bounds__(RED_THREADS, IM <= 4 ? 2 : 1) update_dots_kern
     if (hsm)
         for (int e = threadIdx.x; e < ni * nrhs; e += RED_THREADS) hs[e] = mk<T>((T)hsrc[e].x, (T)hsrc[e].y);
     __syncthreads();
-    cplx<T> h[IM];
+    cplx<T> h[HS ? 1 : IM];
+    if (!HS) {
 #pragma unroll
-    for (int q = 0; q < IM; ++q)
-        if (q < ni) {
-            if (hsm) h[q] = hs[q * nrhs + r];
-            else h[q] = mk<T>((T)hsrc[(long long)q * nrhs + r].x, (T)hsrc[(long long)q * nrhs + r].y);
-        }
+        for (int q = 0; q < IM; ++q)
+            if (q < ni) {
+                if (hsm) h[q] = hs[q * nrhs + r];
+                else h[q] = mk<T>((T)hsrc[(long long)q * nrhs + r].x, (T)hsrc[(long long)q * nrhs + r].y);
+            }
+    }
     cplx<T> acc[IM];
 #pragma unroll
     for (int q = 0; q < IM; ++q) acc[q] = mk<T>(0, 0);
@@ -304,8 +308,9 @@ __global__ void __launch_bounds__(RED_THREADS, IM <= 4 ? 2 : 1) update_dots_kern
     // EPT elements per trip (e, e + stride, ...: the same column), so that every trip keeps the same number
     // of basis loads in flight whatever IM is
     // (bases of up to 4 vectors: 8 elements (8 / IM in FP64), two blocks per SM)
-    constexpr int EPT = IM <= 4 ? (sizeof(T) == 4 ? 8 : 8 / IM)
-                                : ((sizeof(T) == 4 ? 32 : 16) / IM > 0 ? (sizeof(T) == 4 ? 32 : 16) / IM : 1);
+    constexpr int EPT0 = IM <= 4 ? (sizeof(T) == 4 ? 8 : 8 / IM)
+                                 : ((sizeof(T) == 4 ? 32 : 16) / IM > 0 ? (sizeof(T) == 4 ? 32 : 16) / IM : 1);
+    constexpr int EPT = HS ? 2 * EPT0 : EPT0;
     for (long long e0 = t; e0 < n_el; e0 += EPT * stride) {
         cplx<T> v[EPT][IM];
         cplx<T> x[EPT];
@@ -325,8 +330,9 @@ __global__ void __launch_bounds__(RED_THREADS, IM <= 4 ? 2 : 1) update_dots_kern
 #pragma unroll
             for (int q = 0; q < IM; ++q)
                 if (q < ni) {
-                    x[u].x -= h[q].x * v[u][q].x - h[q].y * v[u][q].y;
-                    x[u].y -= h[q].x * v[u][q].y + h[q].y * v[u][q].x;
+                    const cplx<T> hq = HS ? hs[q * nrhs + r] : h[HS ? 0 : q];
+                    x[u].x -= hq.x * v[u][q].x - hq.y * v[u][q].y;
+                    x[u].y -= hq.x * v[u][q].y + hq.y * v[u][q].x;
                 }
             w[e] = x[u];
             nrm.add(x[u].x * x[u].x + x[u].y * x[u].y);
@@ -927,6 +933,9 @@ struct Krylov final : KrylovEngine {
                 update_dots_kernel<T, 8><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
             else if (ni <= 16 || sizeof(T) == 8)
                 update_dots_kernel<T, 16><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
+            else if (S <= 16)
+                update_dots_kernel<T, (sizeof(T) == 4 ? 32 : 16), true><<<nb1, RED_THREADS, 0, st>>>(
+                    V, nel, w, nel, S, ni, hpass, part, ldp, dpart);
             else
                 update_dots_kernel<T, (sizeof(T) == 4 ? 32 : 16)><<<nb1, RED_THREADS, 0, st>>>(V, nel, w, nel, S, ni,
                                                                                            hpass, part, ldp, dpart);
