@@ -659,11 +659,6 @@ __global__ void accum_widen(const cplx<T>* __restrict__ u, c128* __restrict__ x,
         x[e] = x[e] + widen(u[e]);
 }
 
-__global__ void finite_check(const c128* __restrict__ v, long long n_el, int* __restrict__ bad) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (long long)gridDim.x * blockDim.x)
-        if (!isfinite(v[e].x) || !isfinite(v[e].y)) atomicOr(bad, 1);
-}
-
 // column-masked set-up of new columns: x = 0, r = b (mask[r] != 0)
 __global__ void start_columns_kernel(const c128* __restrict__ B, c128* __restrict__ X, c128* __restrict__ R,
                                      const int* __restrict__ mask, long long n_el, int nrhs) {

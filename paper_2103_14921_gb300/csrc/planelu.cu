@@ -636,9 +636,11 @@ helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
     constexpr int NBS = 24;
     const size_t psm = (size_t)m * NBS * sizeof(cplx<T>);
     static bool psm_attr = false;
-    if (sizeof(T) == 4 && !psm_attr) {
-        cudaFuncSetAttribute(gj_panel_smem<T, NBS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        psm_attr = true;
+    if constexpr (sizeof(T) == 4) {
+        if (!psm_attr) {
+            cudaFuncSetAttribute(gj_panel_smem<T, NBS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            psm_attr = true;
+        }
     }
     const bool smem_panel = sizeof(T) == 4 && psm <= 200 * 1024;
     const int nbk = smem_panel ? NBS : nb;
@@ -656,10 +658,14 @@ helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
             if (k < b.dims[2]) ub += 2.0 * b.m * b.m * sizeof(cplx<T>);
         for (int j0 = 0; j0 < m; j0 += nbk) {
             int t = prof_begin(ctx, "gj_panel");
-            if (smem_panel)
-                gj_panel_smem<T, NBS><<<P.nbox, GJS_THREADS, psm, st>>>(P.dbox, S, perm, rows, flag, m, j0, k);
-            else
+            if constexpr (sizeof(T) == 4) {
+                if (smem_panel)
+                    gj_panel_smem<T, NBS><<<P.nbox, GJS_THREADS, psm, st>>>(P.dbox, S, perm, rows, flag, m, j0, k);
+                else
+                    gj_panel<T><<<P.nbox, GJ_THREADS, 0, st>>>(P.dbox, S, perm, rows, flag, m, nb, j0, k);
+            } else {
                 gj_panel<T><<<P.nbox, GJ_THREADS, 0, st>>>(P.dbox, S, perm, rows, flag, m, nb, j0, k);
+            }
             prof_end(ctx, t, 0.0);
             t = prof_begin(ctx, "gj_update");
             if (sizeof(T) == 4 && smem_panel)
