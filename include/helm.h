@@ -305,7 +305,7 @@ helm_status helm_frequency_sweep(helm_ctx ctx, const helm_sweep_desc* desc, cons
 
 /* -------------------------------------------------------------- serving
  *
- * A request loop on one context (BASELINE serving pattern; the paper's
+ * A request loop on one context (the serving pattern: the paper's
  * forward problem with many right-hand sides per frequency arriving over
  * time).  A worker thread owns the context's stream: factors are built on
  * first use and kept resident in a cache keyed by (model_id, grid
