@@ -16,8 +16,9 @@ measured beside it.  Every factor plane is read twice per preconditioner
 application and the factors (~15 GB) are far larger than L2, so no L2 flush
 is needed between steps.
 
-``--impl reference`` times the FP64 CPU oracle on the same workload on the
-host cores instead (a bounded sample scaled to RHS/s).
+``--impl reference`` solves the same workload with the FP64 CPU oracle on
+the host cores instead (right-hand sides solved in full; one step = one
+oracle FGMRES iteration).
 """
 from __future__ import annotations
 
@@ -32,6 +33,11 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+if "reference" in sys.argv or "--impl=reference" in sys.argv:
+    # the oracle arm: single-threaded BLAS in this process (set before numpy loads); its parallelism is the
+    # process pool of local solves
+    for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(_v, "1")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -39,6 +45,8 @@ from paper_2103_14921_gb300 import synth  # noqa: E402
 
 # the headline metric, the same on the library's line and the reference (oracle) line
 METRIC = "RHS solved/s to rel-res 1e-6 (mixed batched vs FP64 plain GPU)"
+# DRAM bytes per launch over algorithmic bytes, per kernel family (ncu, TF32 factors)
+TRAFFIC_RATIO = {"sweep_flow": 0.994, "sweep_gemm_tc": 1.037}
 
 WORKLOADS = {
     "lg112": dict(desc="linear-gradient 112^3, 5 Hz, 16 RHS, two-level ORAS 4x4x4 ov2 r4, FGMRES(30) tol 1e-6",
@@ -250,32 +258,188 @@ def run_serving(helm, device, stream, weights, args):
                    "TF32 factors"}
 
 
+def _host_info():
+    """Host CPU description: logical CPUs, the ones this process may run on, and the model name."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "affinity_cpus": len(os.sched_getaffinity(0)), "cpu_model": model}
+
+
+def _threads(pids):
+    out = []
+    for pid in pids:
+        try:
+            out += [int(t) for t in os.listdir(f"/proc/{pid}/task")]
+        except OSError:
+            pass
+    return out
+
+
+def _pin_all_threads(cpus, pids=()):
+    """Restrict every thread of this process and of the processes `pids` to `cpus`; returns the previous
+    sets."""
+    prev = {}
+    for tid in _threads(["self", *pids]):
+        try:
+            prev[tid] = os.sched_getaffinity(tid)
+            os.sched_setaffinity(tid, cpus)
+        except OSError:
+            pass
+    return prev
+
+
+def _unpin_all_threads(prev, default):
+    for tid, cpus in prev.items():
+        try:
+            os.sched_setaffinity(tid, cpus or default)
+        except OSError:
+            pass
+
+
+def _cpu_seconds(pids):
+    """User + system CPU seconds of this process and of the processes `pids` (from /proc)."""
+    tot = time.process_time()
+    tick = os.sysconf("SC_CLK_TCK")
+    for pid in pids:
+        try:
+            f = open(f"/proc/{pid}/stat").read().rsplit(")", 1)[1].split()
+            tot += (int(f[11]) + int(f[12])) / tick
+        except (OSError, IndexError, ValueError):
+            pass
+    return tot
+
+
+def oracle_timed_solve(prob, M, b, tol, restart, flexible, maxit=1000):
+    """One oracle (F)GMRES solve with a timestamp at every preconditioner application: returns the
+    solution, the oracle's info, the wall time, the per-iteration times and the cores used (process CPU
+    time over wall time)."""
+    from oracle.discretization import apply_A
+    from oracle.krylov import gmres
+    shape = (prob.nz, prob.ny, prob.nx)
+    marks = []
+
+    def aM(v):
+        marks.append(time.perf_counter())
+        return M.apply(v)
+
+    def aA(u):
+        return apply_A(prob, u.reshape(shape)).ravel()
+
+    pids = M.pool.pids() if M.pool is not None else []
+    cpu0, t0 = _cpu_seconds(pids), time.perf_counter()
+    x, info = gmres(aA, b.ravel(), aM, tol=tol, restart=restart, maxit=maxit, flexible=flexible)
+    t1 = time.perf_counter()
+    cores = (_cpu_seconds(pids) - cpu0) / max(t1 - t0, 1e-9)
+    its = [marks[i + 1] - marks[i] for i in range(len(marks) - 1)] + ([t1 - marks[-1]] if marks else [])
+    return x, info, t1 - t0, its, cores
+
+
 def run_reference(args, W):
+    """The FP64 CPU oracle solving the workload on the host cores (the reference has no installable
+    implementation: it is a paper).  Nothing from the library is imported or loaded here: weights, operator,
+    ORAS set-up (splu local solves, exact coarse solve) and FGMRES are all the oracle's.
+
+    One step = one oracle FGMRES iteration of a real solve of the workload (one two-level preconditioner
+    application with its coarse solve, one matrix-free A u, the Arnoldi and Givens work); the warm-up and
+    timed steps are consecutive iterations of solves of the workload's right-hand sides, each run to
+    convergence.  value = right-hand sides solved / their total solve wall time (set-up reported apart).
+    Beside it: the same solve's iterations on one core, and the plain-method workload (48^3, FP64,
+    one-level ORAS 2x2x2, GMRES(30)) solved in full on all cores and on one core."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    from paper_2103_14921_gb300 import helm  # weights only (host code); no GPU work
     import numpy as np
+    from oracle.discretization import Problem, apply_A
+    from oracle.schwarz import ORAS
+    from oracle.weights import fit_weights
+
+    host = _host_info()
+    all_cpus = os.sched_getaffinity(0)
+    weights = fit_weights()
+    n, nz = W["n"], W.get("nz", W["n"])
+    prob = Problem(n, n, nz, W["h"], W["f"], velocity(W), npml=W["npml"], weights=weights)
+    b_all = synth.point_sources(n, n, nz, W["h"], sources(W))
+    nrhs = b_all.shape[-1]
+    workers = len(all_cpus)
+    t = time.perf_counter()
+    M = ORAS(prob, W["parts"], W["overlap"], coarse_ratio=W["coarse"], local="splu", workers=workers)
+    setup_s = time.perf_counter() - t
+    flexible = W["coarse"] > 0
+    need = args.warmup + args.steps
+    its_all, solves = [], []
+    col = 0
+    while col < nrhs and (len(its_all) < need or not solves):
+        x, info, wall, its, cores = oracle_timed_solve(prob, M, b_all[..., col], W["tol"], W["restart"], flexible)
+        solves.append({"column": col, "wall_s": wall, "iterations": info["iterations"],
+                       "true_relres": info["true_residual"], "converged": info["converged"], "cores": cores})
+        its_all += its
+        col += 1
+    timed = its_all[args.warmup:need] or its_all[-args.steps:]
+    value = len(solves) / sum(s_["wall_s"] for s_ in solves)
+    cores_used = max(1, round(statistics.median(s_["cores"] for s_ in solves)))
+    # the same iterations with every thread of the process on one CPU
+    one = None
     try:
-        weights = helm.fit_weights()
-    except Exception:
-        from oracle.weights import fit_weights
-        weights = fit_weights()
-    iters = args.ref_iters
-    samples = []
-    for s in range(args.warmup + args.steps):
-        r = oracle_sample(W, iters, weights)
-        if s >= args.warmup:
-            samples.append(r)
-    vals = [r["value"] for r in samples]
-    value = statistics.median(vals)
-    cb = dict(samples[-1])
-    cb["value"] = value
+        prev = _pin_all_threads({min(all_cpus)}, M.pool.pids() if M.pool is not None else ())
+        try:
+            _, _, _, its1, _ = oracle_timed_solve(prob, M, b_all[..., col % nrhs], W["tol"], W["restart"],
+                                                  flexible, maxit=3)
+        finally:
+            _unpin_all_threads(prev, all_cpus)
+        it1 = statistics.median(its1)
+        one = {"cores": 1, "s_per_iteration": it1, "iterations_timed": len(its1),
+               "rhs_per_s_at_all_core_iteration_count": 1.0 / (it1 * statistics.mean(s_["iterations"] for s_ in solves))}
+    except Exception as exc:
+        one = {"error": repr(exc)}
+    M.close()
+    del M
+    # the plain-method workload in full (48^3, FP64, one-level ORAS 2x2x2, GMRES(30)), all cores and one core
+    plain = None
+    try:
+        W1 = WORKLOADS["lg48"]
+        if W1 is W:
+            raise LookupError("the plain-method workload is the timed workload itself")
+        p1 = Problem(W1["n"], W1["n"], W1["n"], W1["h"], W1["f"], velocity(W1), npml=W1["npml"], weights=weights)
+        b1 = synth.point_sources(W1["n"], W1["n"], W1["n"], W1["h"], sources(W1))[..., 0]
+        t = time.perf_counter()
+        M1 = ORAS(p1, W1["parts"], W1["overlap"], coarse_ratio=0, local="splu", workers=workers)
+        su1 = time.perf_counter() - t
+        _, inf1, wall1, _, c1 = oracle_timed_solve(p1, M1, b1, W1["tol"], W1["restart"], False)
+        prev = _pin_all_threads({min(all_cpus)}, M1.pool.pids() if M1.pool is not None else ())
+        try:
+            _, inf1b, wall1b, _, _ = oracle_timed_solve(p1, M1, b1, W1["tol"], W1["restart"], False)
+        finally:
+            _unpin_all_threads(prev, all_cpus)
+            M1.close()
+        plain = {"workload": W1["desc"], "setup_s": su1, "solve_s": wall1, "iterations": inf1["iterations"],
+                 "true_relres": inf1["true_residual"], "rhs_per_s": 1.0 / wall1, "cores": max(1, round(c1)),
+                 "one_core": {"solve_s": wall1b, "iterations": inf1b["iterations"], "rhs_per_s": 1.0 / wall1b}}
+    except Exception as exc:
+        plain = {"error": repr(exc)}
+    sample = (f"oracle FP64 two-level ORAS-FGMRES (splu local solves in {workers} worker processes, exact "
+              f"coarse solve) solving "
+              f"{len(solves)} of the workload's right-hand sides in full on the host cores: "
+              f"{sum(s_['iterations'] for s_ in solves)} iterations in {sum(s_['wall_s'] for s_ in solves):.1f} s "
+              f"(set-up {setup_s:.1f} s apart); a step is one of those iterations")
+    try:
+        maps = open("/proc/self/maps").read()
+    except OSError:
+        maps = ""
+    cb = {"value": value, "unit": "RHS/s", "cores": cores_used, "kind": "oracle", "sample": sample, "workers": workers,
+          "setup_s": setup_s, "solves": solves, "one_core": one, "plain_method_48": plain, "host": host,
+          "product_library_loaded": "libhelm" in maps}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * W["nrhs"] / value, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 * statistics.mean(timed), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": W["desc"], "grid": [W["n"]] * 3, "nrhs": W["nrhs"]},
+            "config": {"workload": W["desc"], "grid": [n, n, nz], "nrhs": W["nrhs"]},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -472,10 +636,9 @@ def run_gpu(args, W):
 
     peaks, src = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    # DRAM traffic per launch relative to the algorithmic bytes, from the ncu captures summarised in
-    # profiles/tc_sweep_flow_slab112.md (dram__bytes_read.sum + dram__bytes_write.sum = 0.994 x algorithmic)
-    # and profiles/tc_sweep_gemm_slab112.md (per-step product launches: 1.037 x)
-    traffic_ratio = {"sweep_flow": 0.994, "sweep_gemm_tc": 1.037}.get(roof_fam) if args.factor_prec == "tf32" else None
+    # DRAM traffic per launch relative to the algorithmic bytes (dram__bytes_read.sum + dram__bytes_write.sum
+    # over the kernel's own byte count), measured by ncu on a 112 x 112 x 24 slab of the same kernels
+    traffic_ratio = TRAFFIC_RATIO.get(roof_fam) if args.factor_prec == "tf32" else None
     roof = None
     fam = roof_fam
     g = roof_meas
@@ -504,7 +667,8 @@ def run_gpu(args, W):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         try:
-            cpu = oracle_sample(W, float(np.mean(iters)), weights)
+            from oracle.weights import fit_weights as oracle_fit_weights
+            cpu = oracle_sample(W, float(np.mean(iters)), oracle_fit_weights())
         except Exception as exc:  # keep the GPU line even if the oracle leg fails
             cpu = {"error": repr(exc)}
     line = {
@@ -544,8 +708,6 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the bf16-factor variant measurement")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate, requests/s")
-    ap.add_argument("--ref-iters", type=float, default=32.0,
-                    help="iterations per RHS used to scale the oracle's per-iteration time (reference arm)")
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -305,22 +305,113 @@ class CoarseGMRES:
 # The preconditioner
 # ---------------------------------------------------------------------------
 
+def _local_solve_worker(conn, prob, boxes, mode):
+    """Worker process of :class:`LocalSolvePool`: factor its boxes' ``A_i`` with ``splu`` and answer solve
+    requests ``{box index: right-hand side}`` until it receives ``None``."""
+    coef = neighbour_coefficients(prob)
+    lus = {i: spla.splu(local_operator(prob, box, mode, coef).tocsc()) for i, box in boxes}
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            break
+        conn.send({i: lus[i].solve(r) for i, r in msg.items()})
+    conn.close()
+
+
+class LocalSolvePool:
+    """The exact local solves ``A_i^{-1}`` of Eq. (oras) by ``splu``, as ``ORAS(local="splu")`` computes them,
+    with the boxes shared out over spawned worker processes (each builds and keeps the factors of its own
+    boxes; single-threaded BLAS in the workers).  Only where the work runs differs: every box's solve is the
+    same ``splu`` factorisation and solve."""
+
+    def __init__(self, prob: Problem, boxes, mode, workers):
+        import dataclasses
+        import multiprocessing as mp
+        import os
+        order = sorted(range(len(boxes)), key=lambda i: -boxes[i].size)
+        share = [[] for _ in range(workers)]
+        load = [0] * workers
+        for i in order:                       # largest boxes first, each to the least-loaded worker
+            w = load.index(min(load))
+            share[w].append((i, boxes[i]))
+            load[w] += boxes[i].size
+        lean = dataclasses.replace(prob, _cache={})
+        ctx = mp.get_context("spawn")
+        saved = {v: os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"
+        self.procs, self.conns = [], []
+        try:
+            for w in range(workers):
+                if not share[w]:
+                    continue
+                a, b = ctx.Pipe()
+                pr = ctx.Process(target=_local_solve_worker, args=(b, lean, share[w], mode), daemon=True)
+                pr.start()
+                self.procs.append(pr)
+                self.conns.append((a, [i for i, _ in share[w]]))
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
+        for a, _ in self.conns:
+            if a.recv() != "ready":
+                raise RuntimeError("local solve worker failed")
+
+    def solve(self, rhs):
+        """``{box index: A_i^{-1} r}`` for ``rhs = {box index: r}``."""
+        for a, idx in self.conns:
+            a.send({i: rhs[i] for i in idx})
+        out = {}
+        for a, _ in self.conns:
+            out.update(a.recv())
+        return out
+
+    def pids(self):
+        return [p.pid for p in self.procs]
+
+    def close(self):
+        for a, _ in self.conns:
+            try:
+                a.send(None)
+            except (OSError, BrokenPipeError):
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.terminate()
+        self.procs, self.conns = [], []
+
+
 class ORAS:
-    """``M^{-1}`` of Eq. (2lvl) (or Eq. (oras) alone when ``coarse_ratio == 0``)."""
+    """``M^{-1}`` of Eq. (2lvl) (or Eq. (oras) alone when ``coarse_ratio == 0``).
+
+    ``workers = k > 1`` (with ``local="splu"``) runs the local solves in a :class:`LocalSolvePool` of k
+    processes; the result is the same."""
 
     def __init__(self, prob: Problem, parts, overlap, coarse_ratio=0, mode="oras", local="splu",
-                 coarse_solve="exact", coarse_iters=10, coarse_overlap=1):
+                 coarse_solve="exact", coarse_iters=10, coarse_overlap=1, workers=0):
         self.prob = prob
         self.dims = (prob.nx, prob.ny, prob.nz)
         self.boxes = decompose(self.dims, parts, overlap)
         coef = neighbour_coefficients(prob)
         self.A = assemble_A(prob)
         self.local = local
+        self.pool = None
+        if workers and workers > 1:
+            if local != "splu":
+                raise ValueError("a worker pool runs splu local solves")
+            self.pool = LocalSolvePool(prob, self.boxes, mode, min(workers, len(self.boxes)))
         self.idx, self.pu, self.Ai, self.solvers = [], [], [], []
         for box in self.boxes:
-            Ai = local_operator(prob, box, mode, coef)
             self.idx.append(box_global_indices(box, self.dims))
             self.pu.append(partition_of_unity(box))
+            if self.pool is not None:
+                continue
+            Ai = local_operator(prob, box, mode, coef)
             self.Ai.append(Ai)
             if local == "splu":
                 self.solvers.append(spla.splu(Ai.tocsc()))
@@ -351,11 +442,19 @@ class ORAS:
     def apply_one_level(self, v):
         """``sum_i R_i^T D_i A_i^{-1} R_i v`` for ``v`` of shape ``[N]`` or ``[N, nrhs]``."""
         out = np.zeros(v.shape, dtype=np.complex128)
+        if self.pool is not None:
+            xs = self.pool.solve({i: np.ascontiguousarray(v[self.idx[i]]) for i in range(len(self.boxes))})
         for i in range(len(self.boxes)):
-            xi = self.local_solve(i, np.ascontiguousarray(v[self.idx[i]]))
+            xi = xs[i] if self.pool is not None else self.local_solve(i, np.ascontiguousarray(v[self.idx[i]]))
             d = self.pu[i] if v.ndim == 1 else self.pu[i][:, None]
             out[self.idx[i]] += d * xi
         return out
+
+    def close(self):
+        """Stop the worker pool, if any."""
+        if self.pool is not None:
+            self.pool.close()
+            self.pool = None
 
     def coarse_correction(self, v):
         """``Q v = Z E^{-1} Z^T v`` (the inner GMRES approximation of ``E^{-1}`` with ``coarse_solve="gmres"``,

@@ -1,6 +1,7 @@
 """The reference (oracle) line of bench.py keeps the JSON contract on the host cores (no GPU): one line with
-the library line's metric, the oracle as cpu_baseline with its measured core count, and an e2e object
-without host-device copies.  Runs the small 48^3 workload (about 30 s)."""
+the library line's metric, the oracle as cpu_baseline (a real solve of the workload's right-hand side, its
+measured core count, a one-core sample, nothing of the library loaded), and an e2e object without
+host-device copies.  Runs the small 48^3 workload."""
 import json
 import os
 import subprocess
@@ -26,6 +27,10 @@ def test_reference_line_contract():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["unit"] == "RHS/s" and cb["sample"]
     assert 1 <= cb["cores"] <= (os.cpu_count() or 1)
+    assert cb["product_library_loaded"] is False          # the oracle arm loads nothing of the library
+    assert cb["solves"] and all(s["converged"] for s in cb["solves"])
+    assert cb["one_core"]["cores"] == 1 and cb["one_core"]["s_per_iteration"] > 0
+    assert cb["host"]["nproc"] >= 1
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == "RHS/s"
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

@@ -259,3 +259,19 @@ def test_inexact_two_level_fgmres_reaches_direct_solution():
     x, info = gmres(lambda v: A @ v, b, M.apply, tol=1e-8, restart=30, flexible=True)
     assert info["converged"]
     assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+def test_worker_pool_local_solves_equal_the_serial_route():
+    """Local solves farmed to spawned worker processes (splu in each worker) give the same preconditioner
+    as the serial splu route: the same factorisations of the same local operators, up to the summation
+    order of the BLAS inside SuperLU (single-threaded in the workers), so to 1e-13 relative."""
+    prob = _prob(15, 13, 12)
+    v = synth.random_complex((prob.n, 2), 17)
+    serial = ORAS(prob, (2, 2, 2), 2, coarse_ratio=4)
+    pooled = ORAS(prob, (2, 2, 2), 2, coarse_ratio=4, workers=3)
+    try:
+        assert len(pooled.pool.pids()) == 3
+        for a, b in ((pooled.apply(v), serial.apply(v)), (pooled.apply(v[:, 0]), serial.apply(v[:, 0]))):
+            assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+    finally:
+        pooled.close()
