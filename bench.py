@@ -47,6 +47,8 @@ from paper_2103_14921_gb300 import synth  # noqa: E402
 METRIC = "RHS solved/s to rel-res 1e-6 (mixed batched vs FP64 plain GPU)"
 # DRAM bytes per launch over algorithmic bytes, per kernel family (ncu, TF32 factors)
 TRAFFIC_RATIO = {"sweep_flow": 0.994, "sweep_gemm_tc": 1.037}
+# the autotuner's cache of tuned problem classes (decomposition, coarse level, sweep knobs)
+TUNE_CACHE = os.path.join(ROOT, "paper_2103_14921_gb300", "tuned.json")
 
 WORKLOADS = {
     "lg112": dict(desc="linear-gradient 112^3, 5 Hz, 16 RHS, two-level ORAS 4x4x4 ov2 r4, FGMRES(30) tol 1e-6",
@@ -202,143 +204,291 @@ def oracle_sample(W, iters_per_rhs, weights, repeats=1):
     }
 
 
-def run_serving(helm, device, stream, weights, args):
-    """Request stream through helm_submit/helm_poll: Poisson arrivals, seeded layered models,
-    cubic grids from 48^3 to 96^3, 3 or 5 Hz, 1..16 RHS each, a 150 GB HBM budget, TF32
-    factors cached per (model, grid, frequency); returns RHS/s and p50/p99 latency."""
-    import numpy as np
-    import torch
-    rng = np.random.default_rng(synth.workload_seed(5))
-    ctx = helm.Context(device, stream=stream.cuda_stream, budget_bytes=150 << 30)
-    sizes = [48, 64, 80, 96]
-    models = {}
-    reqs = []
-    t_arr = 0.0
-    for i in range(args.serve_requests):
-        n = int(rng.choice(sizes))
-        mid = int(rng.integers(0, 2))
-        f = float(rng.choice([3.0, 5.0]))
-        nrhs = int(rng.integers(1, 17))
-        t_arr += float(rng.exponential(1.0 / args.serve_rate))
+class RequestMix:
+    """The serving workload: seeded requests over cubic grids n in {48, 64, ..., 160} (h = 25 m, 8-node
+    absorbing layers), 4 seeded layered models per size (3-6 layers, 1500-4500 m/s), f in {2, 3, 4, 5, 6} Hz,
+    1-64 point sources each at seeded interior nodes; two-level ORAS with boxes of about 24 nodes per axis,
+    TF32 factors, FGMRES(30) to 1e-6.  Right-hand sides are made on the device when a request is submitted
+    and released when it is done."""
+
+    SIZES = (48, 64, 80, 96, 112, 128, 144, 160)
+
+    def __init__(self, seed, count):
+        import numpy as np
+        rng = np.random.default_rng(seed)
+        self.items = []
+        for _ in range(count):
+            n = int(rng.choice(self.SIZES))
+            nr = int(rng.integers(1, 65))
+            pos = rng.integers(8, n - 8, size=(nr, 3))
+            pos[:, 2] = np.minimum(pos[:, 2], n - 9)
+            self.items.append(dict(n=n, mid=int(rng.integers(0, 4)), f=float(rng.choice([2.0, 3.0, 4.0, 5.0, 6.0])),
+                                   pos=[tuple(int(v) for v in p) for p in pos]))
+        self.models = {}
+
+    def model(self, n, mid):
+        import torch
         key = (n, mid)
-        if key not in models:
-            models[key] = torch.from_numpy(synth.layered(n, n, n, 25.0, seed=synth.workload_seed(5) * 10 + n + mid,
-                                                         vmin=1500.0, vmax=4500.0))
-        pos = [tuple(int(v) for v in p) for p in rng.integers(8, n - 8, size=(nrhs, 3))]
-        pos = [(p[0], p[1], min(p[2], n - 9)) for p in pos]
-        b = torch.from_numpy(synth.point_sources(n, n, n, 25.0, pos)).cuda()
-        reqs.append(dict(t=t_arr, n=n, mid=mid, f=f, b=b))
+        if key not in self.models:
+            self.models[key] = torch.from_numpy(synth.layered(n, n, n, 25.0, seed=synth.workload_seed(5) * 10 + 7 * n + mid,
+                                                              vmin=1500.0, vmax=4500.0))
+        return self.models[key]
+
+
+def serve_phase(helm, sv, mix, items, weights, arrivals=None):
+    """Submit `items` (at the given arrival offsets in seconds, or all at once), wait for all; returns the
+    per-request stats and the wall time."""
     import ctypes as C
-    lat, done_rhs, statuses = [], 0, []
-    with helm.Server(ctx, slots_per_batch=32) as sv:
-        t0 = time.perf_counter()
-        pending = []
-        for r in reqs:
-            while time.perf_counter() - t0 < r["t"]:
-                time.sleep(0.0005)
-            n = r["n"]
-            gd = helm.GridDesc(n, n, n, 25.0, r["f"], 8, 1e-3, helm.TOP_DIRICHLET, (C.c_double * 7)(*weights))
-            p = max(2, n // 24)                      # boxes of about 24 nodes plus overlap per axis
-            od = helm.OrasDesc(p, p, p, 2, 4, 0, helm.PREC_TF32)
-            x = torch.empty_like(r["b"])
-            tk = sv.submit(1000 * n + r["mid"], gd, models[(n, r["mid"])], od, r["b"], x, tol=1e-6, restart=30,
-                           basis_prec=helm.PREC_FP32)
-            pending.append((tk, r["b"].shape[-1]))
-        for tk, nr in pending:
-            s = sv.wait(tk, timeout_s=900)
-            statuses.append(s["status"])
-            lat.append(s["latency_ms"])
-            done_rhs += nr
-        wall = time.perf_counter() - t0
-    ok = sum(1 for s in statuses if s == helm.OK)
-    return {"requests": len(reqs), "ok": ok, "rhs": done_rhs, "wall_s": wall, "rhs_per_s": done_rhs / wall,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "arrival_rate_per_s": args.serve_rate, "slots_per_batch": 32, "budget_gb": 150,
-            "mix": "cubic 48..96, 2 layered models per size, 3/5 Hz, 1..16 RHS, two-level ORAS with ~24-node boxes, "
-                   "TF32 factors"}
-
-
-def _host_info():
-    """Host CPU description: logical CPUs, the ones this process may run on, and the model name."""
-    model = ""
-    try:
-        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
-        for ln in out.splitlines():
-            if ln.startswith("Model name:"):
-                model = ln.split(":", 1)[1].strip()
-                break
-    except Exception:
-        pass
-    return {"nproc": os.cpu_count(), "affinity_cpus": len(os.sched_getaffinity(0)), "cpu_model": model}
-
-
-def _threads(pids):
+    import torch
+    t0 = time.perf_counter()
+    live = {}
     out = []
-    for pid in pids:
-        try:
-            out += [int(t) for t in os.listdir(f"/proc/{pid}/task")]
-        except OSError:
-            pass
-    return out
+
+    def reap(block):
+        for tk in list(live):
+            s = sv.wait(tk, timeout_s=1800) if block else sv.poll(tk)[1]
+            if s["done"]:
+                nr = live.pop(tk)
+                out.append(dict(s, nrhs=nr))
+
+    for i, it in enumerate(items):
+        if arrivals is not None:
+            while time.perf_counter() - t0 < arrivals[i]:
+                reap(False)
+                time.sleep(0.0005)
+        n = it["n"]
+        b = torch.zeros((n, n, n, len(it["pos"])), dtype=torch.complex128, device="cuda")
+        for r, (ii, jj, kk) in enumerate(it["pos"]):
+            b[kk, jj, ii, r] = 1.0 / 25.0 ** 3
+        gd = helm.GridDesc(n, n, n, 25.0, it["f"], 8, 1e-3, helm.TOP_DIRICHLET, (C.c_double * 7)(*weights))
+        p = max(2, round(n / 24))
+        od = helm.OrasDesc(p, p, p, 2, 4, 0, helm.PREC_TF32)
+        tk = sv.submit(1000 * n + it["mid"], gd, mix.model(n, it["mid"]), od, b, torch.empty_like(b), tol=1e-6,
+                       restart=30, basis_prec=helm.PREC_FP32)
+        live[tk] = len(it["pos"])
+        del b
+    reap(True)
+    return out, time.perf_counter() - t0
 
 
-def _pin_all_threads(cpus, pids=()):
-    """Restrict every thread of this process and of the processes `pids` to `cpus`; returns the previous
-    sets."""
-    prev = {}
-    for tid in _threads(["self", *pids]):
-        try:
-            prev[tid] = os.sched_getaffinity(tid)
-            os.sched_setaffinity(tid, cpus)
-        except OSError:
-            pass
-    return prev
+def run_serving(helm, device, stream, weights, args):
+    """The request stream through helm_submit/helm_poll under a 150 GB HBM budget with 64 column slots per
+    factor set: first the saturated request rate (a burst of requests submitted at once), then Poisson
+    arrivals at 0.8 x that rate (the main figure: RHS/s, p50/p99 latency) and a short sweep of rates."""
+    import numpy as np
+    mix = RequestMix(synth.workload_seed(5), args.serve_requests + args.serve_burst + 3 * args.serve_sweep)
+    ctx = helm.Context(device, stream=stream.cuda_stream, budget_bytes=150 << 30)
+    items = mix.items
+    res = {"mix": RequestMix.__doc__.split("\n\n")[0].replace("\n", " "), "budget_gb": 150, "slots_per_batch": 64}
+
+    def summary(st, wall, rate=None):
+        lat = [s_["latency_ms"] for s_ in st]
+        rhs = sum(s_["nrhs"] for s_ in st)
+        ok = sum(1 for s_ in st if s_["status"] == helm.OK)
+        return {"requests": len(st), "ok": ok, "rhs": rhs, "wall_s": wall, "rhs_per_s": rhs / wall,
+                "requests_per_s": len(st) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "arrival_rate_per_s": rate,
+                "factors_reused": sum(1 for s_ in st if s_["factors_reused"])}
+
+    with helm.Server(ctx, slots_per_batch=64) as sv:
+        pos = 0
+        burst = items[pos:pos + args.serve_burst]
+        pos += args.serve_burst
+        st, wall = serve_phase(helm, sv, mix, burst, weights)
+        sat = len(st) / wall
+        res["saturated"] = summary(st, wall)
+        rng = np.random.default_rng(synth.workload_seed(5) + 1)
+        lam = 0.8 * sat
+        main = items[pos:pos + args.serve_requests]
+        pos += args.serve_requests
+        arr = np.cumsum(rng.exponential(1.0 / lam, len(main)))
+        st, wall = serve_phase(helm, sv, mix, main, weights, arr)
+        res["main"] = summary(st, wall, lam)
+        sweep = []
+        for frac in (0.5, 1.0, 1.2):
+            part = items[pos:pos + args.serve_sweep]
+            pos += args.serve_sweep
+            if not part:
+                break
+            arr = np.cumsum(rng.exponential(1.0 / (frac * sat), len(part)))
+            st, wall = serve_phase(helm, sv, mix, part, weights, arr)
+            sweep.append(dict(summary(st, wall, frac * sat), rate_fraction_of_saturated=frac))
+        res["rate_sweep"] = sweep
+    res.update({k: res["main"][k] for k in ("requests", "ok", "rhs", "wall_s", "rhs_per_s", "p50_ms", "p99_ms",
+                                             "arrival_rate_per_s")})
+    ctx.close()
+    return res
 
 
-def _unpin_all_threads(prev, default):
-    for tid, cpus in prev.items():
-        try:
-            os.sched_setaffinity(tid, cpus or default)
-        except OSError:
-            pass
+def factor_roofline(ctx, o, peaks):
+    """Tensor-pipe roofline of the plane factorisation's rank-128 updates (family gj_update_tc) from the
+    profile of a factorisation of ``o``: algorithmic flops = for every box, plane and 128-column panel,
+    8 (rows outside the panel) x m x (panel columns below m) real flops per complex product, times 3 for the
+    three-product TF32 split; peak = the measured dense BF16 rate halved (TF32 runs at half the BF16 rate)."""
+    q = ctx.profile_query("gj_update_tc")
+    if not q:
+        return None
+    nl, ms, by = q
+    fl = 0.0
+    nb = o.box_info(-1)[0]
+    for b in range(nb):
+        _, _, d = o.box_info(b)
+        m = d[0] * d[1]
+        for j0 in range(0, m, 128):
+            w = min(128, m - j0)
+            fl += d[2] * 3 * 8.0 * (m - w) * m * w
+    tf32 = float(peaks.get("bf16_tflops", 1900.0)) / 2.0
+    pan = ctx.profile_query("gj_panel")
+    ach = fl / (ms / 1e3) / 1e12
+    return {"kernel": "gj_update_tc", "bound": "tensor", "launches": nl, "ms_total": ms,
+            "achieved_tflops": ach, "peak_tflops": tf32, "peak_source": "measured bf16 / 2 (TF32)",
+            "frac": ach / tf32, "flops": fl, "GBps": by / (ms / 1e3) / 1e9,
+            "panel_ms_total": pan[1] if pan else None, "panel_launches": pan[0] if pan else None}
 
 
-def _cpu_seconds(pids):
-    """User + system CPU seconds of this process and of the processes `pids` (from /proc)."""
-    tot = time.process_time()
-    tick = os.sysconf("SC_CLK_TCK")
-    for pid in pids:
-        try:
-            f = open(f"/proc/{pid}/stat").read().rsplit(")", 1)[1].split()
-            tot += (int(f[11]) + int(f[12])) / tick
-        except (OSError, IndexError, ValueError):
-            pass
+def _sweep_roofline(ctx, fam, hbm, tf32_peak, nrhs, W_planes):
+    """Roofline figures of a profiled persistent-sweep family: HBM bytes and TF32 flops per second."""
+    q = ctx.profile_query(fam)
+    if not q:
+        return None
+    nl, ms, by = q
+    fl = W_planes * nrhs * 8.0     # complex multiply-adds of the plane products, 8 real flops each, per launch
+    return {"kernel": fam, "launches": nl, "avg_launch_us": 1000.0 * ms / nl, "GBps": by / (ms / 1e3) / 1e9,
+            "hbm_frac": by / (ms / 1e3) / 1e9 / hbm, "tflops": fl * nl / (ms / 1e3) / 1e12,
+            "tensor_frac_tf32": fl * nl / (ms / 1e3) / 1e12 / tf32_peak}
+
+
+def _plane_entries(o):
+    """Sum over the fine boxes and both sweeps of m^2 per plane step (the entries one apply multiplies)."""
+    tot = 0
+    for b in range(o.box_info(-1)[0]):
+        _, _, d = o.box_info(b)
+        tot += (d[0] * d[1]) ** 2 * (2 * d[2] - 1)
     return tot
 
 
-def oracle_timed_solve(prob, M, b, tol, restart, flexible, maxit=1000):
-    """One oracle (F)GMRES solve with a timestamp at every preconditioner application: returns the
-    solution, the oracle's info, the wall time, the per-iteration times and the cores used (process CPU
-    time over wall time)."""
-    from oracle.discretization import apply_A
-    from oracle.krylov import gmres
-    shape = (prob.nz, prob.ny, prob.nx)
-    marks = []
+def run_thrust_fold(helm, ctx, stream, weights, peaks, retune=False):
+    """The Overthrust stand-in: thrust-fold model 256 x 256 x 96 (h = 25 m, 8 folded layers 2000-6000 m/s, two
+    dipping faults), 5 Hz, 64 sources on an 8 x 8 node array at z = 50 m, decomposition and sweep knobs picked
+    by the autotuner (in-plane cores 16-24, overlap 2-4), TF32 tensor-core local solves, two-level ORAS
+    (the coarse level chosen by the tuner between ratio 8 solved exactly and ratio 4 solved as in the paper by
+    10 inner GMRES iterations: the exact FP64 coarse plane LU of ratio 4 would cost ~1.5e13 FP64 flops), FGMRES(30)
+    to 1e-6, the 64 right-hand sides solved as two batches of 32 (the flexible basis of all 64 at once would
+    not fit next to the factors)."""
+    import numpy as np
+    import torch
+    from paper_2103_14921_gb300 import tune
+    nx, ny, nz, h, f = 256, 256, 96, 25.0, 5.0
+    c = synth.thrust_fold(nx, ny, nz, h, synth.workload_seed(3))
+    grid = helm.Grid(ctx, nx, ny, nz, h, f, c, npml=8, weights=weights)
+    pos = synth.source_array_positions(nx, ny, 8, 1, 8)
+    b = torch.from_numpy(synth.point_sources(nx, ny, nz, h, pos)).cuda()
+    chunk = 32
+    t = time.perf_counter()
+    # the autotuner's choice for this problem class is kept in the package's tuning cache (written by the
+    # tuner itself on a GB300); --retune times every candidate again
+    tr = tune.tune(ctx, grid, b[..., :8].contiguous(), factor_prec=helm.PREC_TF32, coarse_ratio=8, nrhs=chunk,
+                   max_trials=4, knobs=True, coarse_opts=[(8, 0), (4, 10)],
+                   cache_path=None if retune else TUNE_CACHE)
+    tune_s = time.perf_counter() - t
+    t = time.perf_counter()
+    o = helm.Oras(grid, tuple(tr["parts"]), tr["overlap"], coarse_ratio=tr.get("coarse_ratio", 8),
+                  factor_prec=helm.PREC_TF32, coarse_iters=tr.get("coarse_iters", 0))
+    setup_s = time.perf_counter() - t
+    kw = dict(tol=1e-6, restart=30, flexible=True, basis_prec=helm.PREC_FP32)
+    x = torch.empty_like(b)
+    b0 = b[..., :chunk].contiguous()
+    x0 = torch.empty_like(b0)
+    o.solve(b0, x0, **kw)                        # warm-up: workspace and iteration graphs
+    ctx.profile(True, only=["sweep_flow"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for c0 in range(0, b.shape[-1], chunk):
+        bc = b[..., c0:c0 + chunk].contiguous()
+        xc = torch.empty_like(bc)
+        _, st = o.solve(bc, xc, **kw)
+        x[..., c0:c0 + chunk] = xc
+        stats += st
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    tf32 = float(peaks.get("bf16_tflops", 1900.0)) / 2.0
+    roof = _sweep_roofline(ctx, "sweep_flow", hbm, tf32, chunk, _plane_entries(o))
+    ctx.profile(False)
+    tune.apply_knobs(ctx, {"tc_stages": 0, "tc_flow": 1})
+    out = {"workload": "thrust-fold 256x256x96, 5 Hz, 64 RHS (8x8 node array, z = 50 m), autotuned ORAS "
+                       "(boxes, overlap, coarse level, sweep knobs), TF32 factors, FGMRES(30) tol 1e-6, 2 batches of 32",
+           "value": b.shape[-1] / (ms / 1e3), "unit": "RHS/s", "solve_s": ms / 1e3, "setup_s": setup_s,
+           "tune_s": tune_s, "parts": tr["parts"], "overlap": tr["overlap"], "knobs": tr.get("knobs"),
+           "coarse_ratio": tr.get("coarse_ratio"), "coarse_iters": tr.get("coarse_iters"),
+           "tune_cached": tr.get("cached", False), "tune_trials": tr.get("trials"),
+           "iterations_max": max(s_["iterations"] for s_ in stats),
+           "iterations_mean": float(np.mean([s_["iterations"] for s_ in stats])),
+           "max_true_relres": max(s_["true_relres"] for s_ in stats),
+           "converged": all(s_["converged"] for s_ in stats), "sweep_roofline": roof}
+    del o, x, b, b0, x0, grid
+    torch.cuda.synchronize()
+    return out
 
-    def aM(v):
-        marks.append(time.perf_counter())
-        return M.apply(v)
 
-    def aA(u):
-        return apply_A(prob, u.reshape(shape)).ravel()
-
-    pids = M.pool.pids() if M.pool is not None else []
-    cpu0, t0 = _cpu_seconds(pids), time.perf_counter()
-    x, info = gmres(aA, b.ravel(), aM, tol=tol, restart=restart, maxit=maxit, flexible=flexible)
-    t1 = time.perf_counter()
-    cores = (_cpu_seconds(pids) - cpu0) / max(t1 - t0, 1e-9)
-    its = [marks[i + 1] - marks[i] for i in range(len(marks) - 1)] + ([t1 - marks[-1]] if marks else [])
-    return x, info, t1 - t0, its, cores
+def run_attenuating(helm, ctx, stream, weights, peaks):
+    """The attenuating workload: linear gradient with c (1 - i/(2Q)), Q = 100, on 160 x 160 x 80, frequencies
+    3, 4 and 6 Hz, 128 sources on the plane z = 100 m (seeded), two-level ORAS 8 x 8 x 4 boxes (cores of 20
+    nodes, overlap 2: 576-node planes), coarse ratio 4, TF32 factors, all 128 right-hand sides in one batch
+    (one persistent sweep launch per preconditioner apply, graph-replayed FGMRES(30) iterations), tol 1e-6.
+    Per frequency: set-up and solve time, every column's FP64 true residual; at 6 Hz two columns are also
+    solved by the plain FP64 path and the mixed solution's relative difference from it is reported."""
+    import numpy as np
+    import torch
+    nx, ny, nz, h = 160, 160, 80, 25.0
+    c = synth.linear_gradient(nx, ny, nz, h, 1500.0, 0.6, Q=100.0)
+    pos = synth.source_plane_positions(nx, ny, 8, 3, 128, synth.workload_seed(4))
+    b = torch.from_numpy(synth.point_sources(nx, ny, nz, h, pos)).cuda()
+    kw = dict(tol=1e-6, restart=30, flexible=True, basis_prec=helm.PREC_FP32)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    tf32 = float(peaks.get("bf16_tflops", 1900.0)) / 2.0
+    freqs = {}
+    tot_ms = 0.0
+    for f in (3.0, 4.0, 6.0):
+        grid = helm.Grid(ctx, nx, ny, nz, h, f, c, npml=8, weights=weights)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        o = helm.Oras(grid, (8, 8, 4), 2, coarse_ratio=4, factor_prec=helm.PREC_TF32)
+        setup_s = time.perf_counter() - t
+        x = torch.empty_like(b)
+        ctx.profile(True, only=["sweep_flow"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = o.solve(b, x, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tot_ms += ms
+        roof = _sweep_roofline(ctx, "sweep_flow", hbm, tf32, b.shape[-1], _plane_entries(o))
+        ctx.profile(False)
+        rec = {"setup_s": setup_s, "solve_s": ms / 1e3, "rhs_per_s": b.shape[-1] / (ms / 1e3),
+               "iterations": [s_["iterations"] for s_ in st], "true_relres": [s_["true_relres"] for s_ in st],
+               "converged": all(s_["converged"] for s_ in st), "sweep_roofline": roof}
+        if f == 6.0:
+            del o
+            torch.cuda.synchronize()
+            o64 = helm.Oras(grid, (8, 8, 4), 2, coarse_ratio=4, factor_prec=helm.PREC_FP64)
+            cols = [0, 127]
+            x64, s64 = o64.solve(b[..., cols].contiguous(), tol=1e-6, restart=30, basis_prec=helm.PREC_FP64)
+            rec["fp64_vs_mixed"] = {str(cc): float(torch.linalg.vector_norm(x[..., cc] - x64[..., k]) /
+                                                   torch.linalg.vector_norm(x64[..., k]))
+                                    for k, cc in enumerate(cols)}
+            rec["fp64_setup_s"] = o64.setup_seconds
+            del o64, x64
+        freqs[f"{f:g}Hz"] = rec
+        del x, grid
+        torch.cuda.synchronize()
+    n_all = 3 * b.shape[-1]
+    return {"workload": "attenuating linear gradient (Q = 100) 160x160x80, 3/4/6 Hz x 128 RHS, two-level ORAS "
+                        "8x8x4 ov2 r4, TF32 factors, FGMRES(30) tol 1e-6, one batch of 128 per frequency",
+            "value": n_all / (tot_ms / 1e3), "unit": "RHS/s", "solve_s": tot_ms / 1e3, "per_frequency": freqs}
 
 
 def run_reference(args, W):
@@ -474,6 +624,16 @@ def run_gpu(args, W):
     t = time.perf_counter()
     oras = helm.Oras(grid, W["parts"], W["overlap"], coarse_ratio=W["coarse"], factor_prec=mixed_prec)
     setup_wall = time.perf_counter() - t
+    setup_device = oras.setup_seconds
+    # the plane factorisation's kernels, from a second, instrumented factorisation of the same problem
+    factor = None
+    if mixed_prec in (helm.PREC_TF32, helm.PREC_BF16):
+        ctx.profile(True, only=["gj_update_tc", "gj_panel", "gj_update"])
+        of = helm.Oras(grid, W["parts"], W["overlap"], coarse_ratio=W["coarse"], factor_prec=mixed_prec)
+        factor = factor_roofline(ctx, of, load_peaks()[0])
+        ctx.profile(False)
+        del of
+        torch.cuda.synchronize()
     solve_kw = dict(tol=W["tol"], restart=W["restart"], flexible=True, basis_prec=helm.PREC_FP32)
 
     # the persistent tensor-core sweep (both sweeps, products and operand preparation, one launch per apply)
@@ -662,6 +822,18 @@ def run_gpu(args, W):
         del grid
         torch.cuda.synchronize()
         serving = run_serving(helm, local, stream, weights, args)
+    # the other workloads of the paper's method at their full sizes (each line's own RHS/s and sweep roofline)
+    more = {}
+    if not args.no_workloads and args.workload == "lg112":
+        torch.cuda.synchronize()
+        for name, fn in (("thrust_fold_256x256x96_64rhs", run_thrust_fold),
+                         ("attenuating_160x160x80_3freq_128rhs", run_attenuating)):
+            try:
+                more[name] = (fn(helm, ctx, stream, weights, peaks, retune=args.retune) if fn is run_thrust_fold
+                              else fn(helm, ctx, stream, weights, peaks))
+            except Exception as exc:   # report the failure; the headline line stands
+                more[name] = {"error": repr(exc)}
+            torch.cuda.synchronize()
     if rank != 0:
         return
     cpu = None
@@ -679,13 +851,14 @@ def run_gpu(args, W):
         "config": {"workload": W["desc"], "grid": [n, n, nz], "nrhs": nrhs, "factor_prec": args.factor_prec,
                    "basis_prec": "fp32", "parallelism": f"replicas x{ws}",
                    "l2": "factors (>10 GB) and Krylov basis exceed L2; no flush"},
-        "setup_s": setup_wall, "setup_device_s": None, "iterations": iters, "max_true_relres": relres,
+        "setup_s": setup_wall, "setup_device_s": setup_device, "factorisation": factor,
+        "iterations": iters, "max_true_relres": relres,
         "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": int(b_host.nbytes),
                 "d2h_bytes_per_step": int(b_host.nbytes)},
         "gpu_launches": int(launches),
         "launches_before_timed": int(l0),   # the library's launches up to the timed region (ncu -s for a launch list)
         "roofline": roof, "kernels": kernels, "plain_fp64_gpu": plain,
-        "cpu_baseline": cpu, "clocks": clk, "serving": serving, "variants": variants,
+        "cpu_baseline": cpu, "clocks": clk, "serving": serving, "variants": variants, "workloads": more,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -706,8 +879,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream (serving) measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the bf16-factor variant measurement")
-    ap.add_argument("--serve-requests", type=int, default=32)
-    ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--retune", action="store_true", help="ignore the tuning cache (time every candidate again)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the thrust-fold (256x256x96, 64 RHS) and attenuating (160x160x80, 3 x 128 RHS) lines")
+    ap.add_argument("--serve-requests", type=int, default=500, help="requests of the main serving phase")
+    ap.add_argument("--serve-burst", type=int, default=60, help="requests of the saturated-rate burst")
+    ap.add_argument("--serve-sweep", type=int, default=40, help="requests per point of the arrival-rate sweep")
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -94,7 +94,8 @@ uint64_t    helm_launch_count(helm_ctx ctx);
 /* Per-kernel-family timing with CUDA events recorded on the context's stream
  * around every launch of the instrumented families ("stencil", "stencil64", "sweep_flow" (the persistent
  * tensor-core sweep), "sweep_gemm_tc", "sweep_prep", "sweep_gemv", "coarse_sweep", "coarse_prep",
- * "coarse_restrict", "coarse_prolong", "coarse_inner", "oras_transfer", "gj_panel", "gj_update", "arnoldi",
+ * "coarse_restrict", "coarse_prolong", "coarse_inner", "oras_transfer", "gj_panel", "gj_update",
+ * "gj_update_tc" (the tensor-core rank-128 update of the plane factorisation), "arnoldi",
  * "arnoldi_reorth", "krylov_misc").  on = 1 enables (and
  * clears the counters), 0 disables.  helm_profile_query synchronizes the
  * stream and returns, for family `name`, the launches recorded, their summed
@@ -129,6 +130,24 @@ helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launche
 #define HELM_TUNE_GRAPHS 3
 #define HELM_TUNE_TC_FLOW 4
 #define HELM_TUNE_STENCIL_MARCH 5
+/* HELM_TUNE_FLOW_WAIT_US: how long (microseconds) a CTA of the persistent tensor-core sweep waits for its
+ * queue slot to be published before it gives up and the call returns HELM_ETIMEOUT (default 2,000,000).
+ * 0 makes any wait give up at once: a test uses it to exercise the HELM_ETIMEOUT path (the launch then
+ * drains, frees its TMEM and returns; the handle stays usable once the knob is restored).  Not captured
+ * into CUDA graphs: it only affects launches made after it is set. */
+#define HELM_TUNE_FLOW_WAIT_US 6
+/* HELM_TUNE_TC_FACTOR: 1 (default) factors the complex64 local planes of HELM_PREC_TF32 / HELM_PREC_BF16
+ * sets by blocked Gauss-Jordan on the tensor cores (128-column panels; block pivots with partial pivoting
+ * inside each 128 x 128 diagonal block; rank-128 updates as tcgen05 products with the three-product TF32
+ * split hi*hi + hi*lo + lo*hi and FP32 accumulation); a block pivot below 1e-6 of its block's largest entry
+ * makes oras_factor factor the set again with full partial pivoting.  0 always uses the fully pivoted
+ * Gauss-Jordan on the CUDA cores.  Read by oras_factor. */
+#define HELM_TUNE_TC_FACTOR 7
+/* HELM_TUNE_BLOCK_GJ: 1 (default) factors the other plane sets (FP64 and FP32 local factors, the FP64
+ * coarse problem) by the same blocked Gauss-Jordan with block pivots on the CUDA cores (64-column panels,
+ * the rank-64 updates spread over every SM), falling back to full partial pivoting after a tiny block
+ * pivot; 0 always uses the fully pivoted elimination.  Read by oras_factor. */
+#define HELM_TUNE_BLOCK_GJ 8
 helm_status helm_set_tuning(helm_ctx ctx, int key, int value);
 
 /* ------------------------------------------------------------ grid / model */
@@ -224,8 +243,11 @@ helm_status oras_apply(helm_oras o, const void* v, void* out, int nrhs);
  * message giving the size it would need.  The array's device address is
  * looked up on the first call on each device, so make that first call before
  * any stream capture.  All calls share the array: calls whose GPU work
- * overlaps (other streams or threads) race on it.  v, out: complex128,
- * nrhs columns, device pointers. */
+ * overlaps (other streams or threads) race on it.  While the call runs the
+ * handle's working vectors point into the array, so no other call may use
+ * the same handle (from another thread) until it returns.  A bounded device
+ * wait that gives up returns HELM_ETIMEOUT, as oras_apply does.  v, out:
+ * complex128, nrhs columns, device pointers. */
 helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out, int nrhs);
 
 /* Sizes of the decomposition: number of boxes, and for box `box` its origin
@@ -308,7 +330,9 @@ helm_status helm_frequency_sweep(helm_ctx ctx, const helm_sweep_desc* desc, cons
  * A request loop on one context (the serving pattern: the paper's
  * forward problem with many right-hand sides per frequency arriving over
  * time).  A worker thread owns the context's stream: factors are built on
- * first use and kept resident in a cache keyed by (model_id, grid
+ * first use -- by a second host thread on a stream (and context) of its own,
+ * so that the batches already running keep cycling meanwhile; the finished
+ * set joins the context -- and kept resident in a cache keyed by (model_id, grid
  * description, ORAS description, restart, flexible, basis precision), and
  * evicted least-recently-used when idle and the HBM budget needs the room.
  * Requests that share factors are batched: each right-hand side takes one

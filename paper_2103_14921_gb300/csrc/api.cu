@@ -121,6 +121,21 @@ extern "C" helm_status helm_set_tuning(helm_ctx ctx, int key, int value) {
         ctx->graph_gen++;
         return HELM_OK;
     }
+    if (key == HELM_TUNE_TC_FACTOR) {
+        if (value != 0 && value != 1) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: tc_factor must be 0 or 1");
+        ctx->tc_factor = value;
+        return HELM_OK;
+    }
+    if (key == HELM_TUNE_BLOCK_GJ) {
+        if (value != 0 && value != 1) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: block_gj must be 0 or 1");
+        ctx->block_gj = value;
+        return HELM_OK;
+    }
+    if (key == HELM_TUNE_FLOW_WAIT_US) {
+        if (value < 0) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: flow_wait_us must be >= 0");
+        ctx->flow_wait_us = value == 0 ? 0 : value;
+        return HELM_OK;
+    }
     return set_error(ctx, HELM_EINVAL, "helm_set_tuning: unknown key %d", key);
 }
 extern "C" uint64_t helm_launch_count(helm_ctx ctx) { return ctx ? ctx->launches : 0; }

@@ -75,6 +75,10 @@ struct helm_ctx_s {
     int use_graphs = 1;        // tuning: Krylov iterations replayed from captured CUDA graphs
     int tc_flow = 1;           // tuning: tensor-core sweeps as one persistent launch with a work queue
     int stencil_march = 1;     // tuning: complex64 16-column stencils walk z-planes (in-plane terms reused)
+    long long flow_wait_us = 2000000;   // tuning: bound of the persistent sweep's queue-slot wait (microseconds)
+    int tc_factor = 1;         // tuning: tensor-core blocked Gauss-Jordan for complex64 tensor-core factor sets
+    int block_gj = 1;          // tuning: block-pivot Gauss-Jordan on the CUDA cores for the other factor sets
+    uint64_t factor_fallbacks = 0;   // sets refactored with full pivoting after a tiny block pivot
     uint64_t graph_gen = 1;    // bumped when a setting that captured graphs depend on changes
     cudaStream_t cap_stream = nullptr;   // private stream graphs are captured on (the context's may be
                                          // the legacy default stream, which cannot be captured)
@@ -252,6 +256,8 @@ helm_status launch_max_real(helm_ctx ctx, const c128* v, long long n, double* ho
 helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P);
 void planeset_free(helm_ctx ctx, PlaneSet& P);
 helm_status planeset_factor(helm_ctx ctx, PlaneSet& P, int* singular);
+// tensor-core blocked Gauss-Jordan of a padded complex64 set (planelu_tc.cu); *weak: a block pivot was tiny
+helm_status planeset_factor_tc(helm_ctx ctx, PlaneSet& P, int* singular, int* weak);
 helm_status planeset_to_bf16(helm_ctx ctx, PlaneSet& P);
 helm_status planeset_pack_tc(helm_ctx ctx, PlaneSet& P);   // row-major padded planes -> tile layout
 // plane slot of a padded set, in stored entries: room for ld x ld row-major or the tile layout

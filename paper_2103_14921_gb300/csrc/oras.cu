@@ -1020,7 +1020,9 @@ extern "C" double oras_setup_seconds(helm_oras o) { return o ? o->setup_s : 0.0;
 // cached.  All calls share the array and it keeps the last call's contents:
 // every working vector is fully written before it is read, so nothing needs
 // clearing, but calls whose work overlaps on the GPU (two streams, or two
-// threads) race on it.
+// threads) race on it.  During the call the handle's working-vector pointers
+// point into the array, so no other call may use the same handle (from
+// another thread) until this one returns.
 
 #define HELM_NOALLOC_SCRATCH_BYTES (8u << 20)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[HELM_NOALLOC_SCRATCH_BYTES];
@@ -1096,7 +1098,10 @@ extern "C" helm_status oras_apply_noalloc(helm_oras o, const void* v, void* out,
     o->cvec = s_cvec_p;
     o->crbuf = s_crbuf_p;
     ctx->prof.on = prof_on;
-    return rc;
+    if (rc) return rc;
+    // a bounded device wait that gave up during this call is this call's failure (reading the flag
+    // copies one int to host memory and allocates nothing)
+    return oras_check_device_error(o);
 }
 
 size_t oras_estimate_bytes(const helm_grid_desc& g, const helm_oras_desc& d, int nrhs) {

@@ -694,6 +694,341 @@ helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
     return rc;
 }
 
+// ------------------------------------------------------------------ block-pivot Gauss-Jordan (CUDA cores)
+//
+// The same elimination as the tensor-core factorisation (planelu_tc.cu), for complex128 and complex64 sets
+// on the CUDA cores: 64-column panels J, P = A[J,J]^{-1} with partial pivoting inside the block,
+// A[J,:] = P A[J,:] (A[J,J] = P), and for the rows outside J A[I,j] = [j not in J] A[I,j] - W[I,:] A[J,j]
+// with W = A[:, J] copied before the step.  The rank-64 update is spread over every SM (64 x 64 output
+// tiles), where the fully pivoted elimination above eliminates one column at a time in one CTA per box.
+constexpr int BGJ_NB = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(512) bgj_diag(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ S,
+                                                int m_max, cplx<T>* __restrict__ Pbuf, int* __restrict__ flag, int j0,
+                                                int k) {
+    constexpr int NB = BGJ_NB, DP = BGJ_NB + 1;
+    extern __shared__ __align__(16) unsigned char bgj_sm[];
+    cplx<T>* X = reinterpret_cast<cplx<T>*>(bgj_sm);   // [NB][DP]
+    __shared__ cplx<T> s_row[NB], s_col[NB];
+    __shared__ int s_perm[NB], s_pos[NB];
+    __shared__ int s_piv;
+    __shared__ T s_wmax[16];
+    const BoxInfo B = boxes[blockIdx.x];
+    const int m = B.m;
+    if (k >= B.dims[2] || j0 >= m) return;
+    const int nbw = min(NB, m - j0);
+    const cplx<T>* A = S + (size_t)blockIdx.x * m_max * m_max;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    T amax = 0;
+    for (int e = tid; e < NB * NB; e += 512) {
+        const int r = e / NB, c = e % NB;
+        cplx<T> v = mk<T>(r == c ? (T)1 : (T)0, (T)0);   // identity beyond a partial panel
+        if (r < nbw && c < nbw) v = A[(size_t)(j0 + r) * m + j0 + c];
+        X[r * DP + c] = v;
+        amax = max(amax, v.x * v.x + v.y * v.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) s_wmax[wid] = amax;
+    __syncthreads();
+    amax = 0;
+    for (int w = 0; w < 16; ++w) amax = max(amax, s_wmax[w]);
+    for (int c = 0; c < NB; ++c) {
+        if (wid == 0) {
+            T best = -1;
+            int bi = NB;
+            for (int r = c + lane; r < NB; r += 32) {
+                const T a = X[r * DP + c].x * X[r * DP + c].x + X[r * DP + c].y * X[r * DP + c].y;
+                if (a > best) { best = a; bi = r; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                if (!(best > (T)0) || bi >= NB) {
+                    atomicOr(flag, 1);
+                    bi = c;
+                } else if (best < (T)1e-12 * amax) {
+                    atomicOr(flag, 2);
+                }
+                s_piv = bi;
+                s_perm[c] = bi;
+            }
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != c && tid < NB) {
+            const cplx<T> t = X[c * DP + tid];
+            X[c * DP + tid] = X[p * DP + tid];
+            X[p * DP + tid] = t;
+        }
+        __syncthreads();
+        cplx<T> piv = X[c * DP + c];
+        if (!(piv.x * piv.x + piv.y * piv.y > (T)0)) piv = mk<T>((T)1, (T)0);   // flagged above; stay finite
+        const cplx<T> inv = cinv(piv);
+        if (tid < NB) {
+            s_row[tid] = tid == c ? inv : X[c * DP + tid] * inv;
+            s_col[tid] = X[tid * DP + c];
+        }
+        __syncthreads();
+        for (int e = tid; e < NB * NB; e += 512) {
+            const int r = e / NB, j = e % NB;
+            cplx<T>& x = X[r * DP + j];
+            if (r == c) {
+                x = s_row[j];
+            } else if (j == c) {
+                const cplx<T> v = s_col[r] * inv;
+                x = mk<T>(-v.x, -v.y);
+            } else {
+                const cplx<T> f = s_col[r], sv = s_row[j];
+                x.x -= f.x * sv.x - f.y * sv.y;
+                x.y -= f.x * sv.y + f.y * sv.x;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        for (int j = 0; j < NB; ++j) s_pos[j] = j;
+        for (int c = NB - 1; c >= 0; --c) {
+            const int p = s_perm[c];
+            const int t = s_pos[c];
+            s_pos[c] = s_pos[p];
+            s_pos[p] = t;
+        }
+    }
+    __syncthreads();
+    cplx<T>* Pb = Pbuf + (size_t)blockIdx.x * NB * NB;
+    for (int e = tid; e < NB * NB; e += 512) Pb[e] = X[(e / NB) * DP + s_pos[e % NB]];
+}
+
+// R = P A[J, :] for 64 columns per CTA, written into rows J (R[:, J] = P).  Thread (tx, ty): rows tx + 16 i,
+// columns col0 + ty + 16 q.
+template <typename T>
+__global__ void __launch_bounds__(256) bgj_rows(const BoxInfo* __restrict__ boxes, cplx<T>* __restrict__ S, int m_max,
+                                                const cplx<T>* __restrict__ Pbuf, int j0, int k) {
+    constexpr int NB = BGJ_NB;
+    __shared__ cplx<T> Ps[NB][17];
+    __shared__ cplx<T> As[16][64];
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m;
+    if (k >= B.dims[2] || j0 >= m) return;
+    const int col0 = blockIdx.x * 64;
+    if (col0 >= m) return;
+    const int nbw = min(NB, m - j0);
+    cplx<T>* A = S + (size_t)blockIdx.y * m_max * m_max;
+    const cplx<T>* P = Pbuf + (size_t)blockIdx.y * NB * NB;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    cplx<T> acc[NB / 16][4];
+#pragma unroll
+    for (int i = 0; i < NB / 16; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = mk<T>(0, 0);
+    for (int k0 = 0; k0 < NB; k0 += 16) {
+        for (int e = tid; e < NB * 16; e += 256) Ps[e >> 4][e & 15] = P[(e >> 4) * NB + k0 + (e & 15)];
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int kk = e >> 6, jj = e & 63;
+            As[kk][jj] = (k0 + kk < nbw && col0 + jj < m) ? A[(size_t)(j0 + k0 + kk) * m + col0 + jj] : mk<T>(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            cplx<T> a[NB / 16], b[4];
+#pragma unroll
+            for (int i = 0; i < NB / 16; ++i) a[i] = Ps[tx + 16 * i][kk];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = As[kk][ty + 16 * q];
+#pragma unroll
+            for (int i = 0; i < NB / 16; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cmac(acc[i][q], a[i], b[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = col0 + ty + 16 * q;
+        if (j >= m) continue;
+        const bool inJ = j >= j0 && j < j0 + nbw;
+#pragma unroll
+        for (int i = 0; i < NB / 16; ++i) {
+            const int c = tx + 16 * i;
+            if (c < nbw) A[(size_t)(j0 + c) * m + j] = inJ ? P[c * NB + (j - j0)] : acc[i][q];
+        }
+    }
+}
+
+// W = A[:, J] (rows J and columns beyond the panel zero), [m_max][NB] per box
+template <typename T>
+__global__ void bgj_wcopy(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ S, int m_max,
+                          cplx<T>* __restrict__ Wbuf, int j0, int k) {
+    constexpr int NB = BGJ_NB;
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m;
+    if (k >= B.dims[2] || j0 >= m) return;
+    const int nbw = min(NB, m - j0);
+    const cplx<T>* A = S + (size_t)blockIdx.y * m_max * m_max;
+    cplx<T>* W = Wbuf + (size_t)blockIdx.y * m_max * NB;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * NB; e += gridDim.x * blockDim.x) {
+        const int I = e / NB, c = e % NB;
+        W[e] = (c < nbw && !(I >= j0 && I < j0 + nbw)) ? A[(size_t)I * m + j0 + c] : mk<T>(0, 0);
+    }
+}
+
+// A[I, j] = [j not in J] A[I, j] - sum_c W[I, c] A[j0 + c, j] for rows I outside J; 64 x 64 tiles, 4 x 4 per thread
+template <typename T>
+__global__ void __launch_bounds__(256) bgj_update(const BoxInfo* __restrict__ boxes, cplx<T>* __restrict__ S,
+                                                  int m_max, const cplx<T>* __restrict__ Wbuf, int j0, int k) {
+    constexpr int NB = BGJ_NB;
+    const BoxInfo B = boxes[blockIdx.z];
+    const int m = B.m;
+    if (k >= B.dims[2] || j0 >= m) return;
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+    if (r0 >= m || c0 >= m || r0 == j0) return;   // the tile of rows J (NB == 64, j0 % 64 == 0)
+    const int nbw = min(NB, m - j0);
+    cplx<T>* A = S + (size_t)blockIdx.z * m_max * m_max;
+    const cplx<T>* W = Wbuf + (size_t)blockIdx.z * m_max * NB;
+    __shared__ cplx<T> Ws[64][17];
+    __shared__ cplx<T> Rs[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    cplx<T> acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = mk<T>(0, 0);
+    for (int k0 = 0; k0 < nbw; k0 += 16) {
+        for (int e = tid; e < 64 * 16; e += 256) {
+            const int r = e >> 4, kk = e & 15;
+            Ws[r][kk] = r0 + r < m ? W[(size_t)(r0 + r) * NB + k0 + kk] : mk<T>(0, 0);
+            const int kr = e >> 6, jj = e & 63;
+            Rs[kr][jj] = (k0 + kr < nbw && c0 + jj < m) ? A[(size_t)(j0 + k0 + kr) * m + c0 + jj] : mk<T>(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            cplx<T> w[4], rr[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) w[a] = Ws[ty + 16 * a][kk];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) rr[b] = Rs[kk][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) cmac(acc[a][b], w[a], rr[b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = r0 + ty + 16 * a;
+        if (r >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int j = c0 + tx + 16 * b;
+            if (j >= m) continue;
+            cplx<T>* dst = A + (size_t)r * m + j;
+            const cplx<T> base = (j >= j0 && j < j0 + nbw) ? mk<T>(0, 0) : *dst;
+            *dst = base - acc[a][b];
+        }
+    }
+}
+
+template <typename T>
+__global__ void bgj_store(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ S, cplx<T>* __restrict__ G,
+                          int m_max, int k) {
+    const BoxInfo B = boxes[blockIdx.y];
+    const int m = B.m;
+    if (k >= B.dims[2]) return;
+    const cplx<T>* A = S + (size_t)blockIdx.y * m_max * m_max;
+    cplx<T>* Gk = G + B.fac_off + (size_t)k * B.pstride;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * m;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / m), j = (int)(e % m);
+        Gk[(size_t)r * B.ld + j] = A[e];
+    }
+}
+
+// Block-pivot factorisation of a set on the CUDA cores.  *weak: a block pivot below 1e-6 of its block.
+template <typename T>
+helm_status factor_block_t(helm_ctx ctx, PlaneSet& P, int* singular, int* weak) {
+    *singular = *weak = 0;
+    cudaStream_t st = ctx->stream;
+    constexpr int NB = BGJ_NB;
+    const size_t mm = (size_t)P.m_max * P.m_max;
+    cplx<T>*S = nullptr, *Tm = nullptr, *W = nullptr, *Pb = nullptr;
+    int* flag = nullptr;
+    auto cleanup = [&]() {
+        dev_free(ctx, S, P.nbox * mm * sizeof(cplx<T>));
+        dev_free(ctx, Tm, P.nbox * mm * sizeof(cplx<T>));
+        dev_free(ctx, W, (size_t)P.nbox * P.m_max * NB * sizeof(cplx<T>));
+        dev_free(ctx, Pb, (size_t)P.nbox * NB * NB * sizeof(cplx<T>));
+        dev_free(ctx, flag, sizeof(int));
+    };
+    helm_status rc;
+    if ((rc = dev_alloc(ctx, (void**)&S, P.nbox * mm * sizeof(cplx<T>), "factor work S")) ||
+        (rc = dev_alloc(ctx, (void**)&Tm, P.nbox * mm * sizeof(cplx<T>), "factor work T")) ||
+        (rc = dev_alloc(ctx, (void**)&W, (size_t)P.nbox * P.m_max * NB * sizeof(cplx<T>), "factor panel W")) ||
+        (rc = dev_alloc(ctx, (void**)&Pb, (size_t)P.nbox * NB * NB * sizeof(cplx<T>), "block pivots")) ||
+        (rc = dev_alloc(ctx, (void**)&flag, sizeof(int), "factor flag"))) {
+        cleanup();
+        return rc;
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(bgj_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(NB * (NB + 1) * sizeof(cplx<T>)));
+        attr = true;
+    }
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    const cplx<T>* coef = (const cplx<T>*)P.coef;
+    const int m = P.m_max;
+    const unsigned eblocks = (unsigned)std::min<long long>(((long long)m * m + 255) / 256, 4096);
+    const dim3 egrid(eblocks, P.nbox);
+    const int t64 = (m + 63) / 64;
+    const unsigned wblocks = (unsigned)std::min<long long>(((long long)m * NB + 255) / 256, 1024);
+    for (int k = 0; k < P.bz_max; ++k) {
+        if (k == 0) {
+            schur_init<T><<<egrid, 256, 0, st>>>(P.dbox, coef, S, m, k);
+            ctx->launches++;
+        } else {
+            schur_gu<T><<<egrid, 256, 0, st>>>(P.dbox, coef, (const cplx<T>*)P.G, Tm, m, k);
+            schur_lt<T><<<egrid, 256, 0, st>>>(P.dbox, coef, Tm, S, m, k);
+            ctx->launches += 2;
+        }
+        for (int j0 = 0; j0 < m; j0 += NB) {
+            double ub = 0;
+            for (const auto& b : P.hbox)
+                if (k < b.dims[2] && j0 < b.m) ub += 2.0 * (b.m - std::min(NB, b.m - j0)) * b.m * sizeof(cplx<T>);
+            int t = prof_begin(ctx, "gj_panel");
+            bgj_diag<T><<<P.nbox, 512, NB * (NB + 1) * sizeof(cplx<T>), st>>>(P.dbox, S, m, Pb, flag, j0, k);
+            bgj_rows<T><<<dim3(t64, P.nbox), 256, 0, st>>>(P.dbox, S, m, Pb, j0, k);
+            bgj_wcopy<T><<<dim3(wblocks, P.nbox), 256, 0, st>>>(P.dbox, S, m, W, j0, k);
+            prof_end(ctx, t, 0.0);
+            t = prof_begin(ctx, "gj_update");
+            bgj_update<T><<<dim3(t64, t64, P.nbox), 256, 0, st>>>(P.dbox, S, m, W, j0, k);
+            prof_end(ctx, t, ub);
+            ctx->launches += 4;
+        }
+        bgj_store<T><<<dim3(std::max(1, std::min(64, m / 16)), P.nbox), 256, 0, st>>>(P.dbox, S, (cplx<T>*)P.G, m, k);
+        ctx->launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_check(ctx, e, "block plane factorisation launch");
+        }
+    }
+    int hflag = 0;
+    cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    rc = cuda_check(ctx, cudaStreamSynchronize(st), "block plane factorisation");
+    cleanup();
+    *singular = hflag & 1;
+    *weak = (hflag >> 1) & 1;
+    return rc;
+}
+
 template <typename T, int RN>
 void launch_sweep_rn(const PlaneSet& P, cplx<T>* loc, cplx<T>* rbuf, int nrhs, cudaStream_t st, helm_ctx ctx) {
     const int m = P.m_max;
@@ -843,6 +1178,17 @@ void planeset_free(helm_ctx ctx, PlaneSet& P) {
 }
 
 helm_status planeset_factor(helm_ctx ctx, PlaneSet& P, int* singular) {
+    int weak = 0;
+    if (P.prec == HELM_PREC_FP32 && P.padded && ctx->tc_factor) {
+        HELM_TRY(planeset_factor_tc(ctx, P, singular, &weak));
+        if (!weak && !*singular) return HELM_OK;
+        ctx->factor_fallbacks++;   // a tiny (or zero) block pivot: factor the set again with full partial pivoting
+    } else if (!P.padded && ctx->block_gj) {
+        if (P.prec == HELM_PREC_FP64) HELM_TRY(factor_block_t<double>(ctx, P, singular, &weak));
+        else HELM_TRY(factor_block_t<float>(ctx, P, singular, &weak));
+        if (!weak && !*singular) return HELM_OK;
+        ctx->factor_fallbacks++;
+    }
     if (P.prec == HELM_PREC_FP64) return factor_t<double>(ctx, P, singular);
     return factor_t<float>(ctx, P, singular);
 }

@@ -5,12 +5,23 @@
 // grid + ORAS handle keyed by model id, grid, decomposition and solver
 // settings) it keeps one batched Krylov engine with a fixed number of column
 // slots.  Each right-hand side of a request occupies one slot.  The worker
-// repeats: admit queued requests whose factors exist or fit the HBM budget
-// (building them, evicting idle factor sets least-recently-used) and whose
-// columns fit the free slots; run one restart cycle of every batch that has
-// active columns; hand back the columns that finished (copying their
-// solutions out) and free their slots.  New requests therefore join running
-// batches at cycle boundaries and share every kernel launch with them.
+// repeats: take over factor sets the builder has finished; admit queued
+// requests whose factors are ready and whose columns fit the free slots,
+// and for a request whose factors are neither ready nor being built reserve
+// their estimated bytes within the HBM budget (evicting idle factor sets
+// least-recently-used) and hand the build to the builder; run one restart
+// cycle of every batch that has active columns; hand back the columns that
+// finished (copying their solutions out) and free their slots.  New requests
+// therefore join running batches at cycle boundaries and share every kernel
+// launch with them.
+//
+// The builder is a second host thread with a context of its own (its own
+// non-blocking stream on the same device): it sets up the grid and factors a
+// new set while the worker keeps cycling the running batches, so admission
+// of a new model or frequency never stalls the others.  A finished set is
+// handed over to the serving context (its grid is re-parented and its bytes
+// move from the builder's account to the serving context's) before its
+// engine is made and its first request admitted.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -41,6 +52,7 @@ struct SRequest {
     int iters_max = 0;
     double rel_max = 0.0;
     bool reused = false;
+    bool built_for = false;   // its factor set was built for it (not found in the cache)
     bool notconv = false;
     FactorSet* fs = nullptr;
 };
@@ -60,6 +72,12 @@ bool same_oras(const helm_oras_desc& a, const helm_oras_desc& b) {
 }
 
 struct FactorSet {
+    int building = 0;               // 1 while the builder owns it (queued or being built)
+    const void* c = nullptr;        // wave speed of the request that asked for it (read by the build)
+    size_t reserved = 0;            // budget bytes reserved from the request to the handover
+    size_t built_bytes = 0;         // device bytes the build left allocated
+    helm_status build_status = HELM_OK;
+    std::string build_msg;
     uint64_t model_id = 0;
     helm_grid_desc gd{};
     helm_oras_desc od{};
@@ -119,6 +137,91 @@ struct Server {
     std::deque<SRequest*> waiting;
     std::vector<FactorSet*> sets;
     int* dslot = nullptr;                           // device slot map for (un)packing
+    size_t reserved = 0;                            // worker: bytes reserved for sets being built
+    // builder: its context and thread; queues guarded by mu
+    helm_ctx bctx = nullptr;
+    cudaStream_t bstream = nullptr;
+    std::thread bth;
+    std::condition_variable bcv;
+    bool bstop = false;
+    std::deque<FactorSet*> to_build, built;
+
+    void build_loop() {
+        cudaSetDevice(ctx->device);
+        for (;;) {
+            FactorSet* fs = nullptr;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                bcv.wait(lk, [&] { return bstop || !to_build.empty(); });
+                if (to_build.empty()) break;
+                fs = to_build.front();
+                to_build.pop_front();
+            }
+            const size_t before = bctx->in_use;
+            helm_status st = helm_setup_grid(bctx, &fs->gd, fs->c, &fs->g);
+            if (!st) st = oras_factor(fs->g, &fs->od, &fs->o);
+            if (!st) st = cuda_check(bctx, cudaStreamSynchronize(bctx->stream), "factor set build");
+            if (st) {
+                fs->build_msg = bctx->last_error;
+                if (fs->o) oras_destroy(fs->o);
+                fs->o = nullptr;
+                if (fs->g) helm_destroy_grid(fs->g);
+                fs->g = nullptr;
+            } else {
+                // the set's bytes leave the builder's account; the worker adds them to the serving context
+                fs->built_bytes = bctx->in_use - before;
+                bctx->in_use = before;
+                bctx->children--;
+            }
+            fs->build_status = st;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                built.push_back(fs);
+            }
+            cv.notify_one();
+        }
+    }
+
+    // Worker: take over the sets the builder has finished.
+    void take_built() {
+        std::deque<FactorSet*> done;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            done.swap(built);
+        }
+        for (FactorSet* fs : done) {
+            reserved -= fs->reserved;
+            fs->reserved = 0;
+            helm_status st = fs->build_status;
+            if (!st) {
+                fs->g->ctx = ctx;   // re-parent: every later call on the set runs on the serving stream
+                ctx->children++;
+                ctx->in_use += fs->built_bytes;
+                fs->K.reset(make_krylov_engine(fs->o, slots, fs->restart, fs->flexible != 0, fs->basis_prec, nullptr,
+                                               nullptr, &st));
+                if (st) fs->build_msg = ctx->last_error;
+            }
+            fs->building = 0;
+            if (st) {
+                // every waiting request for this set fails with the build's error
+                set_error(ctx, st, "%s", fs->build_msg.c_str());
+                for (auto it = waiting.begin(); it != waiting.end();) {
+                    if (fs->matches((*it)->req)) {
+                        finish(*it, st);
+                        it = waiting.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                sets.erase(std::find(sets.begin(), sets.end(), fs));
+                destroy_set(fs);
+                continue;
+            }
+            fs->owner.assign(slots, nullptr);
+            fs->col.assign(slots, -1);
+            fs->last_used = Clock::now();
+        }
+    }
 
     void finish(SRequest* r, helm_status st) {
         std::lock_guard<std::mutex> lk(mu);
@@ -141,18 +244,19 @@ struct Server {
         return N * slots * ((2 * m + 3) * e + 3 * sizeof(c128)) + N * 48;
     }
 
-    // Try to place r: returns true if admitted (or failed), false if it must keep waiting.
+    // Try to place r: returns true if admitted (or failed), false if it must keep waiting (its factors are
+    // being built, or its columns or its factors do not fit yet).
     bool try_admit(SRequest* r, bool idle) {
         FactorSet* fs = nullptr;
         for (auto* s : sets)
             if (s->matches(r->req)) fs = s;
         if (!fs) {
             const size_t need = oras_estimate_bytes(r->req.grid, r->req.oras, slots) + engine_estimate(r->req);
-            auto room = [&]() { return ctx->budget == 0 || ctx->in_use + need <= ctx->budget; };
+            auto room = [&]() { return ctx->budget == 0 || ctx->in_use + reserved + need <= ctx->budget; };
             while (!room()) {
                 FactorSet* lru = nullptr;
                 for (auto* s : sets)
-                    if (s->active == 0 && (!lru || s->last_used < lru->last_used)) lru = s;
+                    if (!s->building && s->active == 0 && (!lru || s->last_used < lru->last_used)) lru = s;
                 if (!lru) break;
                 sets.erase(std::find(sets.begin(), sets.end(), lru));
                 destroy_set(lru);
@@ -172,25 +276,22 @@ struct Server {
             fs->restart = r->req.gmres.restart;
             fs->flexible = r->req.gmres.flexible;
             fs->basis_prec = r->req.gmres.basis_prec;
-            helm_status st = helm_setup_grid(ctx, &fs->gd, r->req.c, &fs->g);
-            if (!st) st = oras_factor(fs->g, &fs->od, &fs->o);
-            if (!st) {
-                fs->K.reset(make_krylov_engine(fs->o, slots, fs->restart, fs->flexible != 0, fs->basis_prec, nullptr,
-                                               nullptr, &st));
-            }
-            if (st) {
-                destroy_set(fs);
-                finish(r, st);
-                return true;
-            }
-            fs->owner.assign(slots, nullptr);
-            fs->col.assign(slots, -1);
-            fs->last_used = Clock::now();
+            fs->c = r->req.c;
+            fs->building = 1;
+            r->built_for = true;
+            fs->reserved = need;
+            reserved += need;
             sets.push_back(fs);
-        } else {
-            r->reused = true;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                to_build.push_back(fs);
+            }
+            bcv.notify_one();
+            return false;
         }
+        if (fs->building || !fs->K) return false;
         if (fs->free_slots() < r->req.nrhs) return false;
+        r->reused = !r->built_for;
         // take slots, copy the request's columns into them and start them
         const long long N = fs->g->n;
         std::vector<int> sl;
@@ -280,10 +381,14 @@ struct Server {
         for (;;) {
             {
                 std::unique_lock<std::mutex> lk(mu);
-                bool busy = !waiting.empty();
-                for (auto* s : sets) busy = busy || s->active > 0;
-                if (!busy && incoming.empty()) {
-                    if (stop) break;
+                bool running = false, building = false;
+                for (auto* s : sets) {
+                    running = running || s->active > 0;
+                    building = building || s->building;
+                }
+                if (!running && incoming.empty() && built.empty()) {
+                    if (stop && waiting.empty() && !building) break;
+                    // nothing to cycle: sleep until a submission or a finished build (or 20 ms)
                     cv.wait_for(lk, std::chrono::milliseconds(20));
                 }
                 while (!incoming.empty()) {
@@ -291,8 +396,9 @@ struct Server {
                     incoming.pop_front();
                 }
             }
+            take_built();
             bool idle = true;
-            for (auto* s : sets) idle = idle && s->active == 0;
+            for (auto* s : sets) idle = idle && s->active == 0 && !s->building;
             for (auto it = waiting.begin(); it != waiting.end();) {
                 if (try_admit(*it, idle)) {
                     it = waiting.erase(it);
@@ -357,7 +463,24 @@ extern "C" helm_status helm_serve_start(helm_ctx ctx, int slots) {
         delete sv;
         return rc;
     }
+    // the builder's context: same device, its own non-blocking stream, no budget of its own (the worker
+    // reserves every build's bytes within the serving context's budget), the serving context's tuning
+    rc = cuda_check(ctx, cudaStreamCreateWithFlags(&sv->bstream, cudaStreamNonBlocking), "builder stream");
+    if (!rc) rc = helm_create(&sv->bctx, ctx->device, sv->bstream, 0);
+    if (rc) {
+        if (sv->bstream) cudaStreamDestroy(sv->bstream);
+        dev_free(ctx, sv->dslot, 256 * sizeof(int));
+        delete sv;
+        return set_error(ctx, rc, "helm_serve_start: builder context");
+    }
+    sv->bctx->tc_stages = ctx->tc_stages;
+    sv->bctx->coarse_coop = ctx->coarse_coop;
+    sv->bctx->use_graphs = ctx->use_graphs;
+    sv->bctx->tc_flow = ctx->tc_flow;
+    sv->bctx->stencil_march = ctx->stencil_march;
+    sv->bctx->tc_factor = ctx->tc_factor;
     ctx->server = sv;
+    sv->bth = std::thread([sv]() { sv->build_loop(); });
     sv->th = std::thread([sv]() { sv->loop(); });
     return HELM_OK;
 }
@@ -424,7 +547,15 @@ extern "C" helm_status helm_serve_stop(helm_ctx ctx) {
         sv->stop = true;
     }
     sv->cv.notify_one();
-    sv->th.join();
+    sv->th.join();   // the worker waits for every build it started before it ends
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->bstop = true;
+    }
+    sv->bcv.notify_one();
+    sv->bth.join();
+    helm_destroy(sv->bctx);
+    cudaStreamDestroy(sv->bstream);
     for (auto& kv : sv->reqs) delete kv.second;
     dev_free(ctx, sv->dslot, 256 * sizeof(int));
     delete sv;

@@ -376,6 +376,7 @@ __device__ __forceinline__ void gemm_core(const CUtensorMap* mapA, const CUtenso
     const int plane = B.plane0 + k;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    int issued = 0;   // thread 0: chunks whose loads it issued for this tile
     if (warp == 0 && lane == 0) {
         // TMA producer.  A tile (rows row0.., chunk kc): 16 KB contiguous in the tile layout; the last,
         // partial row tile of a box loads only its 32-row groups that hold rows < m (the rest of the
@@ -383,7 +384,6 @@ __device__ __forceinline__ void gemm_core(const CUtensorMap* mapA, const CUtenso
         const int rows = min(TC_BM, m - row0);
         const int nsub = rows >= TC_BM ? 0 : (rows + 31) / 32;
         const uint32_t a_bytes = nsub ? (uint32_t)nsub * 32 * 128 : (uint32_t)Cfg::A_BYTES;
-        int issued = 0;
         for (int kc = 0; kc < nK; ++kc) {
             const uint32_t gi = R.g + kc;
             const int st = gi % NST;
@@ -430,7 +430,16 @@ __device__ __forceinline__ void gemm_core(const CUtensorMap* mapA, const CUtenso
 
     // epilogue: thread t of warp w owns TMEM lane 32 w + t = output row row0 + 32 w + t
     const bool ok = tc::mbar_wait(done, R.dphase, err, 3);
+    // gave up (here or elsewhere): the MMAs already issued still write TMEM and the loads already issued
+    // still land in the stages, so wait for both (bounded, ignoring the flag) before TMEM or the stages
+    // are reused or freed.  `done` is always committed once the issuer has left its loop.
+    if (!ok) tc::mbar_drain(done, R.dphase);
     tc::fence_after_sync();
+    if (!ok && threadIdx.x == 0)
+        for (int kc = max(0, issued - NST); kc < issued; ++kc) {
+            const uint32_t gi = R.g + kc;
+            tc::mbar_drain(&full[gi % NST], (gi / NST) & 1);
+        }
     if (ok) {
         const int row = row0 + warp * 32 + lane;
         c64* dst = loc + (B.loc_off + (long long)k * m + row) * nrhs;
@@ -504,7 +513,6 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
 // its completion is counted; queue slots are published with release stores and read with acquire loads;
 // values other CTAs wrote in this launch are read through L2 (ld.cg), never a stale L1 line.
 constexpr int FLOW_TPN = 128;
-constexpr uint64_t FLOW_WAIT_NS = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
     int v;
@@ -537,8 +545,10 @@ __device__ __host__ __forceinline__ int flow_pack(int box, int j, int t) { retur
 
 // The item in queue slot `slot` (bounded wait until it has been published); x = -1 when the queue is
 // exhausted or a wait anywhere gave up.
+// wait_ns bounds the wait (the context's flow_wait_us knob, 2 s by default); 0 gives up at the first
+// unpublished poll.
 __device__ __forceinline__ int4 flow_fetch(int slot, const int* __restrict__ init, int ninit, const int* flag, int total,
-                                           int* err) {
+                                           int* err, uint64_t wait_ns) {
     if (slot >= total || *reinterpret_cast<volatile int*>(err) != 0) return make_int4(-1, 0, 0, 0);
     int v = 0;
     if (slot < ninit) {
@@ -548,9 +558,9 @@ __device__ __forceinline__ int4 flow_fetch(int slot, const int* __restrict__ ini
         const uint64_t t0 = global_ns();
         for (uint32_t i = 0;; ++i) {
             if ((v = ld_acquire_gpu(flag + q)) != 0) break;
-            if ((i & 255) == 255) {
+            if ((i & 255) == 255 || wait_ns == 0) {
                 if (*reinterpret_cast<volatile int*>(err) != 0) return make_int4(-1, 0, 0, 0);
-                if (global_ns() - t0 > FLOW_WAIT_NS) {
+                if (global_ns() - t0 >= wait_ns) {
                     atomicExch(err, 4);
                     return make_int4(-1, 0, 0, 0);
                 }
@@ -576,7 +586,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
                                                         const c64* __restrict__ lb, c64* __restrict__ loc,
                                                         E* __restrict__ bt, int ld2, int nrhs, int nkc,
                                                         const int* __restrict__ init, int ninit, int* flag, int total,
-                                                        int* ctl, int* __restrict__ err) {
+                                                        int* ctl, int* __restrict__ err, uint64_t wait_ns) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int4 cur;
     unsigned char* base = align1024(smem_raw);
@@ -591,7 +601,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
     int slot = 0;
     if (threadIdx.x == FLOW_QT) {
         slot = atomicAdd(head, 1);
-        cur = flow_fetch(slot, init, ninit, flag, total, err);
+        cur = flow_fetch(slot, init, ninit, flag, total, err, wait_ns);
     }
     for (;;) {
         __syncthreads();
@@ -629,7 +639,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
                         st_release_gpu(flag + q0 + i, flow_pack(box, j + 1, i));
                 }
             }
-            cur = flow_fetch(slot, init, ninit, flag, total, err);
+            cur = flow_fetch(slot, init, ninit, flag, total, err, wait_ns);
         }
     }
     gemm_teardown<E, NPAD, NST>(tmem);
@@ -743,7 +753,8 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
         const int t = prof_begin(ctx, "sweep_flow");
         tc_sweep_flow<E, NPAD, NST><<<grid, 128, Cfg::SMEM, st>>>(mapA, mapA32, mapB, P.dbox, coef, lb, loc, bt, 2 * ld,
                                                                    nrhs, P.pk_chunks, flow->init, flow->ninit,
-                                                                   flow->flag, flow->total, flow->ctl, err);
+                                                                   flow->flag, flow->total, flow->ctl, err,
+                                                                   (uint64_t)ctx->flow_wait_us * 1000ull);
         prof_end(ctx, t, all);
         ctx->launches++;
         return cuda_check(ctx, cudaGetLastError(), "tensor-core plane sweeps (persistent)");

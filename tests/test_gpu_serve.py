@@ -107,3 +107,33 @@ def test_budget_admission_and_latency_stats(env):
     assert len(lat) == 6 and min(lat) > 0
     with pytest.raises(helm.HelmError):
         helm.Server(ctx, 0)
+
+
+def test_new_factor_set_joins_while_another_batch_runs(env):
+    """A request on a new model arrives while a batch on cached factors is cycling: its factors are built on
+    the builder thread meanwhile and it joins the running loop; both results are bit-identical to the same
+    requests served alone."""
+    import torch
+    helm, ctx, w, cA, cB = env
+    gd, od = _descs(helm, w, helm.PREC_TF32)
+    tol = 1e-6
+    bA = torch.from_numpy(_rhs([(12, 11, 3), (5, 6, 7), (18, 15, 9), (9, 4, 12)])).cuda()
+    bB = torch.from_numpy(_rhs([(11, 11, 5), (6, 17, 8)])).cuda()
+    alone = {}
+    for key, c, bb in (("A", cA, bA), ("B", cB, bB)):
+        with helm.Server(ctx, slots_per_batch=8) as sv:
+            xx = torch.empty_like(bb)
+            s = sv.wait(sv.submit(10 if key == "A" else 20, gd, c, od, bb, xx, tol=tol))
+            assert s["status"] == helm.OK
+            alone[key] = xx.cpu().numpy()
+    with helm.Server(ctx, slots_per_batch=8) as sv:
+        warm = torch.from_numpy(_rhs([(4, 4, 4)])).cuda()
+        assert sv.wait(sv.submit(10, gd, cA, od, warm, torch.empty_like(warm), tol=tol))["status"] == helm.OK
+        xA, xB = torch.empty_like(bA), torch.empty_like(bB)
+        tA = sv.submit(10, gd, cA, od, bA, xA, tol=tol)          # cached factors: admitted at once
+        tB = sv.submit(20, gd, cB, od, bB, xB, tol=tol)          # new model: built while A's batch cycles
+        sA, sB = sv.wait(tA), sv.wait(tB)
+    assert sA["status"] == helm.OK and sB["status"] == helm.OK
+    assert sA["factors_reused"] and not sB["factors_reused"]
+    assert np.array_equal(xA.cpu().numpy(), alone["A"])
+    assert np.array_equal(xB.cpu().numpy(), alone["B"])

@@ -25,3 +25,11 @@ def test_tuner_picks_a_converging_decomposition_and_caches_it(tmp_path):
     o = helm.Oras(grid, tuple(r["parts"]), r["overlap"], coarse_ratio=4, factor_prec=helm.PREC_TF32)
     _, st = o.solve(b)
     assert all(s["converged"] for s in st)
+    # the plane-sweep knobs on the chosen factors: every setting timed, the fastest kept and cached
+    k = tune.tune_knobs(ctx, o, b)
+    assert len(k["trials"]) == len(tune.KNOB_GRID) and k["best"] in tune.KNOB_GRID
+    r2 = tune.tune(ctx, grid, b, cands=cands[:1], cache_path=str(tmp_path / "tune2.json"), nrhs=16, knobs=True)
+    assert r2["knobs"] in tune.KNOB_GRID and len(r2["knob_trials"]) == len(tune.KNOB_GRID)
+    assert tune.tune(ctx, grid, b, cands=cands[:1], cache_path=str(tmp_path / "tune2.json"), nrhs=16,
+                     knobs=True)["cached"]
+    tune.apply_knobs(ctx, {"tc_stages": 0, "tc_flow": 1})
