@@ -204,11 +204,16 @@ def oracle_sample(W, iters_per_rhs, weights, repeats=1):
     }
 
 
+# FGMRES restart of the request stream: the flexible basis of a 160^3 set with 64 columns then takes about 80 GB,
+# so that the largest requests fit beside others in the 150 GB budget
+SERVE_RESTART = 15
+
+
 class RequestMix:
     """The serving workload: seeded requests over cubic grids n in {48, 64, ..., 160} (h = 25 m, 8-node
     absorbing layers), 4 seeded layered models per size (3-6 layers, 1500-4500 m/s), f in {2, 3, 4, 5, 6} Hz,
     1-64 point sources each at seeded interior nodes; two-level ORAS with boxes of about 24 nodes per axis,
-    TF32 factors, FGMRES(30) to 1e-6.  Right-hand sides are made on the device when a request is submitted
+    TF32 factors, FGMRES(15) to 1e-6.  Right-hand sides are made on the device when a request is submitted
     and released when it is done."""
 
     SIZES = (48, 64, 80, 96, 112, 128, 144, 160)
@@ -233,6 +238,12 @@ class RequestMix:
             self.models[key] = torch.from_numpy(synth.layered(n, n, n, 25.0, seed=synth.workload_seed(5) * 10 + 7 * n + mid,
                                                               vmin=1500.0, vmax=4500.0))
         return self.models[key]
+
+
+def log(msg):
+    """Progress on stderr (the JSON line is the only stdout output)."""
+    sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg}\n")
+    sys.stderr.flush()
 
 
 def serve_phase(helm, sv, mix, items, weights, arrivals=None):
@@ -264,7 +275,7 @@ def serve_phase(helm, sv, mix, items, weights, arrivals=None):
         p = max(2, round(n / 24))
         od = helm.OrasDesc(p, p, p, 2, 4, 0, helm.PREC_TF32)
         tk = sv.submit(1000 * n + it["mid"], gd, mix.model(n, it["mid"]), od, b, torch.empty_like(b), tol=1e-6,
-                       restart=30, basis_prec=helm.PREC_FP32)
+                       restart=SERVE_RESTART, basis_prec=helm.PREC_FP32)
         live[tk] = len(it["pos"])
         del b
     reap(True)
@@ -276,7 +287,7 @@ def run_serving(helm, device, stream, weights, args):
     factor set: first the saturated request rate (a burst of requests submitted at once), then Poisson
     arrivals at 0.8 x that rate (the main figure: RHS/s, p50/p99 latency) and a short sweep of rates."""
     import numpy as np
-    mix = RequestMix(synth.workload_seed(5), args.serve_requests + args.serve_burst + 3 * args.serve_sweep)
+    mix = RequestMix(synth.workload_seed(5), args.serve_requests + args.serve_burst + 2 * args.serve_sweep)
     ctx = helm.Context(device, stream=stream.cuda_stream, budget_bytes=150 << 30)
     items = mix.items
     res = {"mix": RequestMix.__doc__.split("\n\n")[0].replace("\n", " "), "budget_gb": 150, "slots_per_batch": 64}
@@ -294,18 +305,22 @@ def run_serving(helm, device, stream, weights, args):
         pos = 0
         burst = items[pos:pos + args.serve_burst]
         pos += args.serve_burst
+        log(f"serving: burst of {len(burst)} requests")
         st, wall = serve_phase(helm, sv, mix, burst, weights)
         sat = len(st) / wall
         res["saturated"] = summary(st, wall)
+        log(f"serving: saturated {sat:.2f} requests/s ({res['saturated']['rhs_per_s']:.1f} RHS/s) in {wall:.1f} s")
         rng = np.random.default_rng(synth.workload_seed(5) + 1)
         lam = 0.8 * sat
         main = items[pos:pos + args.serve_requests]
         pos += args.serve_requests
         arr = np.cumsum(rng.exponential(1.0 / lam, len(main)))
+        log(f"serving: {len(main)} requests at {lam:.2f} requests/s")
         st, wall = serve_phase(helm, sv, mix, main, weights, arr)
         res["main"] = summary(st, wall, lam)
+        log(f"serving: main phase {wall:.1f} s, p50 {res['main']['p50_ms']:.0f} ms, p99 {res['main']['p99_ms']:.0f} ms")
         sweep = []
-        for frac in (0.5, 1.0, 1.2):
+        for frac in (0.5, 1.2):
             part = items[pos:pos + args.serve_sweep]
             pos += args.serve_sweep
             if not part:
@@ -338,12 +353,16 @@ def factor_roofline(ctx, o, peaks):
             w = min(128, m - j0)
             fl += d[2] * 3 * 8.0 * (m - w) * m * w
     tf32 = float(peaks.get("bf16_tflops", 1900.0)) / 2.0
-    pan = ctx.profile_query("gj_panel")
     ach = fl / (ms / 1e3) / 1e12
-    return {"kernel": "gj_update_tc", "bound": "tensor", "launches": nl, "ms_total": ms,
-            "achieved_tflops": ach, "peak_tflops": tf32, "peak_source": "measured bf16 / 2 (TF32)",
-            "frac": ach / tf32, "flops": fl, "GBps": by / (ms / 1e3) / 1e9,
-            "panel_ms_total": pan[1] if pan else None, "panel_launches": pan[0] if pan else None}
+    out = {"kernel": "gj_update_tc", "bound": "tensor", "launches": nl, "ms_total": ms,
+           "achieved_tflops": ach, "peak_tflops": tf32, "peak_source": "measured bf16 / 2 (TF32)",
+           "frac": ach / tf32, "flops": fl, "GBps": by / (ms / 1e3) / 1e9}
+    # the rest of the set-up: tensor-core panel steps (fine planes), block-pivot panels and updates of the
+    # FP64 coarse problem on the CUDA cores
+    for fam in ("gj_panel_tc", "gj_diag", "gj_panel", "gj_update"):
+        q = ctx.profile_query(fam)
+        out[fam + "_ms"] = q[1] if q else None
+    return out
 
 
 def _sweep_roofline(ctx, fam, hbm, tf32_peak, nrhs, W_planes):
@@ -491,6 +510,89 @@ def run_attenuating(helm, ctx, stream, weights, peaks):
             "value": n_all / (tot_ms / 1e3), "unit": "RHS/s", "solve_s": tot_ms / 1e3, "per_frequency": freqs}
 
 
+def _host_info():
+    """Host CPU description: logical CPUs, the ones this process may run on, and the model name."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "affinity_cpus": len(os.sched_getaffinity(0)), "cpu_model": model}
+
+
+def _threads(pids):
+    out = []
+    for pid in pids:
+        try:
+            out += [int(t) for t in os.listdir(f"/proc/{pid}/task")]
+        except OSError:
+            pass
+    return out
+
+
+def _pin_all_threads(cpus, pids=()):
+    """Restrict every thread of this process and of the processes `pids` to `cpus`; returns the previous
+    sets."""
+    prev = {}
+    for tid in _threads(["self", *pids]):
+        try:
+            prev[tid] = os.sched_getaffinity(tid)
+            os.sched_setaffinity(tid, cpus)
+        except OSError:
+            pass
+    return prev
+
+
+def _unpin_all_threads(prev, default):
+    for tid, cpus in prev.items():
+        try:
+            os.sched_setaffinity(tid, cpus or default)
+        except OSError:
+            pass
+
+
+def _cpu_seconds(pids):
+    """User + system CPU seconds of this process and of the processes `pids` (from /proc)."""
+    tot = time.process_time()
+    tick = os.sysconf("SC_CLK_TCK")
+    for pid in pids:
+        try:
+            f = open(f"/proc/{pid}/stat").read().rsplit(")", 1)[1].split()
+            tot += (int(f[11]) + int(f[12])) / tick
+        except (OSError, IndexError, ValueError):
+            pass
+    return tot
+
+
+def oracle_timed_solve(prob, M, b, tol, restart, flexible, maxit=1000):
+    """One oracle (F)GMRES solve with a timestamp at every preconditioner application: returns the
+    solution, the oracle's info, the wall time, the per-iteration times and the cores used (process CPU
+    time over wall time)."""
+    from oracle.discretization import apply_A
+    from oracle.krylov import gmres
+    shape = (prob.nz, prob.ny, prob.nx)
+    marks = []
+
+    def aM(v):
+        marks.append(time.perf_counter())
+        return M.apply(v)
+
+    def aA(u):
+        return apply_A(prob, u.reshape(shape)).ravel()
+
+    pids = M.pool.pids() if M.pool is not None else []
+    cpu0, t0 = _cpu_seconds(pids), time.perf_counter()
+    x, info = gmres(aA, b.ravel(), aM, tol=tol, restart=restart, maxit=maxit, flexible=flexible)
+    t1 = time.perf_counter()
+    cores = (_cpu_seconds(pids) - cpu0) / max(t1 - t0, 1e-9)
+    its = [marks[i + 1] - marks[i] for i in range(len(marks) - 1)] + ([t1 - marks[-1]] if marks else [])
+    return x, info, t1 - t0, its, cores
+
+
 def run_reference(args, W):
     """The FP64 CPU oracle solving the workload on the host cores (the reference has no installable
     implementation: it is a paper).  Nothing from the library is imported or loaded here: weights, operator,
@@ -625,10 +727,11 @@ def run_gpu(args, W):
     oras = helm.Oras(grid, W["parts"], W["overlap"], coarse_ratio=W["coarse"], factor_prec=mixed_prec)
     setup_wall = time.perf_counter() - t
     setup_device = oras.setup_seconds
+    log(f"headline: set-up {setup_wall:.2f} s")
     # the plane factorisation's kernels, from a second, instrumented factorisation of the same problem
     factor = None
     if mixed_prec in (helm.PREC_TF32, helm.PREC_BF16):
-        ctx.profile(True, only=["gj_update_tc", "gj_panel", "gj_update"])
+        ctx.profile(True, only=["gj_update_tc", "gj_panel_tc", "gj_diag", "gj_panel", "gj_update"])
         of = helm.Oras(grid, W["parts"], W["overlap"], coarse_ratio=W["coarse"], factor_prec=mixed_prec)
         factor = factor_roofline(ctx, of, load_peaks()[0])
         ctx.profile(False)
@@ -691,6 +794,7 @@ def run_gpu(args, W):
     relres = max(s["true_relres"] for s in stats_all[-1])
     x_mixed = x.clone()
 
+    log(f"headline: {args.steps} timed solves, {elapsed_ms / args.steps:.1f} ms each")
     # variant: bfloat16-stored local factors (the same solve, reported beside the headline path)
     variants = {}
     if args.factor_prec == "tf32" and not args.no_variants:
@@ -828,6 +932,7 @@ def run_gpu(args, W):
         torch.cuda.synchronize()
         for name, fn in (("thrust_fold_256x256x96_64rhs", run_thrust_fold),
                          ("attenuating_160x160x80_3freq_128rhs", run_attenuating)):
+            log(f"workload {name}")
             try:
                 more[name] = (fn(helm, ctx, stream, weights, peaks, retune=args.retune) if fn is run_thrust_fold
                               else fn(helm, ctx, stream, weights, peaks))
@@ -882,9 +987,10 @@ def main():
     ap.add_argument("--retune", action="store_true", help="ignore the tuning cache (time every candidate again)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the thrust-fold (256x256x96, 64 RHS) and attenuating (160x160x80, 3 x 128 RHS) lines")
-    ap.add_argument("--serve-requests", type=int, default=500, help="requests of the main serving phase")
-    ap.add_argument("--serve-burst", type=int, default=60, help="requests of the saturated-rate burst")
-    ap.add_argument("--serve-sweep", type=int, default=40, help="requests per point of the arrival-rate sweep")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the main serving phase (the full request-stream workload: 500)")
+    ap.add_argument("--serve-burst", type=int, default=16, help="requests of the saturated-rate burst")
+    ap.add_argument("--serve-sweep", type=int, default=12, help="requests per point of the arrival-rate sweep")
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
     if args.impl == "reference":

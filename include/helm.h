@@ -95,7 +95,8 @@ uint64_t    helm_launch_count(helm_ctx ctx);
  * around every launch of the instrumented families ("stencil", "stencil64", "sweep_flow" (the persistent
  * tensor-core sweep), "sweep_gemm_tc", "sweep_prep", "sweep_gemv", "coarse_sweep", "coarse_prep",
  * "coarse_restrict", "coarse_prolong", "coarse_inner", "oras_transfer", "gj_panel", "gj_update",
- * "gj_update_tc" (the tensor-core rank-128 update of the plane factorisation), "arnoldi",
+ * "gj_diag", "gj_panel_tc", "gj_update_tc" (the panel steps and the tensor-core rank-128 update of the plane
+ * factorisation), "arnoldi",
  * "arnoldi_reorth", "krylov_misc").  on = 1 enables (and
  * clears the counters), 0 disables.  helm_profile_query synchronizes the
  * stream and returns, for family `name`, the launches recorded, their summed

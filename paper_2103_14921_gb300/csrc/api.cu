@@ -47,9 +47,15 @@ helm_status dev_alloc(helm_ctx ctx, void** p, size_t bytes, const char* what) {
     return HELM_OK;
 }
 
+// Stream-ordered free on the context's stream: unlike cudaFree it does not wait for the whole device, so a
+// context that frees memory (the serving worker evicting a factor set, a factorisation releasing its work
+// buffers) does not stall behind the kernels of another context sharing the GPU.
 void dev_free(helm_ctx ctx, void* p, size_t bytes) {
     if (!p) return;
-    cudaFree(p);
+    if (cudaFreeAsync(p, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+    }
     ctx->in_use -= bytes;
 }
 
@@ -122,7 +128,7 @@ extern "C" helm_status helm_set_tuning(helm_ctx ctx, int key, int value) {
         return HELM_OK;
     }
     if (key == HELM_TUNE_TC_FACTOR) {
-        if (value != 0 && value != 1) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: tc_factor must be 0 or 1");
+        if (value < 0 || value > 2) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: tc_factor must be 0..2");
         ctx->tc_factor = value;
         return HELM_OK;
     }
@@ -282,8 +288,10 @@ static helm_status setup_row_weights(helm_grid g) {
     HELM_TRY(dev_alloc(ctx, (void**)&g->wtab, nb * sizeof(StencilW), "adaptive weight table"));
     HELM_TRY(dev_alloc(ctx, (void**)&g->wbin, (size_t)g->n, "adaptive weight bins"));
     HELM_TRY(dev_alloc(ctx, (void**)&dedges, (nb + 1) * sizeof(double), "bin edges"));
-    HELM_CUDA(ctx, cudaMemcpy(g->wtab, tab.data(), nb * sizeof(StencilW), cudaMemcpyHostToDevice));
-    HELM_CUDA(ctx, cudaMemcpy(dedges, g->hedges.data(), (nb + 1) * sizeof(double), cudaMemcpyHostToDevice));
+    HELM_CUDA(ctx, cudaMemcpyAsync(g->wtab, tab.data(), nb * sizeof(StencilW), cudaMemcpyHostToDevice, ctx->stream));
+    HELM_CUDA(ctx, cudaMemcpyAsync(dedges, g->hedges.data(), (nb + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    HELM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     weight_bin_kernel<<<(unsigned)std::min<long long>((g->n + 255) / 256, 4096), 256, 0, ctx->stream>>>(
         g->c, g->n, fh, dedges, nb, g->wbin);
     ctx->launches++;
@@ -396,10 +404,12 @@ extern "C" helm_status helm_setup_grid(helm_ctx ctx, const helm_grid_desc* d, co
     axis_table(d->nz, d->h, d->npml, top, true, g->omega, g->c_ref, d->pml_R, &g->htab[3 * (d->nx + d->ny)]);
     std::vector<c64> hf(3 * ntab);
     for (int i = 0; i < 3 * ntab; ++i) hf[i] = mk<float>((float)g->htab[i].x, (float)g->htab[i].y);
-    if ((st = cuda_check(ctx, cudaMemcpy(g->tab, g->htab.data(), 3 * ntab * sizeof(c128), cudaMemcpyHostToDevice),
+    if ((st = cuda_check(ctx, cudaMemcpyAsync(g->tab, g->htab.data(), 3 * ntab * sizeof(c128), cudaMemcpyHostToDevice,
+                                              g->ctx->stream),
                          "copy tables")))
         return fail(st);
-    if ((st = cuda_check(ctx, cudaMemcpy(g->tabf, hf.data(), 3 * ntab * sizeof(c64), cudaMemcpyHostToDevice),
+    if ((st = cuda_check(ctx, cudaMemcpyAsync(g->tabf, hf.data(), 3 * ntab * sizeof(c64), cudaMemcpyHostToDevice,
+                                              g->ctx->stream),
                          "copy tables")))
         return fail(st);
     if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "grid setup"))) return fail(st);

@@ -177,6 +177,7 @@ struct TcFlow {
     int* flag = nullptr;
     int* init = nullptr;
     int ninit = 0, total = 0;
+    int tpn = 128;   // plane nodes per operand-preparation item
 };
 
 struct helm_oras_s {
@@ -274,7 +275,9 @@ int tc_npad(int nrhs);
 // flow (may be null): the queue of the persistent single-launch sweep, used when the context allows it.
 helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb, void* loc, void* bt, int npad, int nrhs,
                               cudaStream_t st, int* err, const TcFlow* flow = nullptr);
-helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F);
+// tpn: plane nodes per preparation item (tc_flow_tpn(nrhs) for the column count the queue is made for)
+helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F, int tpn);
+int tc_flow_tpn(int nrhs);
 void tc_flow_free(helm_ctx ctx, TcFlow& F);
 // Device bytes an ORAS handle with this description will hold (factors, local operators,
 // coarse level) plus its apply scratch for nrhs columns; an estimate for admission control.

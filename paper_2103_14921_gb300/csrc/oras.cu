@@ -439,7 +439,9 @@ static helm_status setup_coarse_dd(helm_oras o, const std::vector<int>& cuts) {
     o->cdd.prec = HELM_PREC_FP64;
     HELM_TRY(planeset_alloc(ctx, o->cdd));
     HELM_TRY(dev_alloc(ctx, (void**)&o->cowner, cowner.size() * sizeof(int), "coarse owner table"));
-    HELM_CUDA(ctx, cudaMemcpy(o->cowner, cowner.data(), cowner.size() * sizeof(int), cudaMemcpyHostToDevice));
+    HELM_CUDA(ctx, cudaMemcpyAsync(o->cowner, cowner.data(), cowner.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    HELM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     long long mx = 0;
     for (auto& b : o->cdd.hbox) mx = std::max(mx, (long long)b.m * b.dims[2]);
     build_local_coef27<double><<<dim3(grid_for(mx, 128, 4096), o->cdd.nbox), 128, 0, st>>>(
@@ -537,8 +539,9 @@ extern "C" helm_status oras_factor(helm_grid g, const helm_oras_desc* d, helm_or
             }
     if ((rc = planeset_alloc(ctx, o->fine))) return fail(rc);
     if ((rc = dev_alloc(ctx, (void**)&o->owner, owner.size() * sizeof(int), "owner table"))) return fail(rc);
-    if ((rc = cuda_check(ctx, cudaMemcpy(o->owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice),
-                         "owner copy")))
+    if ((rc = cuda_check(ctx, cudaMemcpyAsync(o->owner, owner.data(), owner.size() * sizeof(int),
+                                              cudaMemcpyHostToDevice, st), "owner copy")) ||
+        (rc = cuda_check(ctx, cudaStreamSynchronize(st), "owner copy")))
         return fail(rc);
 
     // --- local operators with absorbing interface folding
@@ -696,7 +699,7 @@ static helm_status ensure_scratch(helm_oras o, int wp, int nrhs) {
         HELM_TRY(dev_alloc(ctx, &o->tcb, bytes, "tensor-core sweep operand"));
         HELM_CUDA(ctx, cudaMemsetAsync(o->tcb, 0, bytes, ctx->stream));
         HELM_TRY(dev_alloc(ctx, &o->lb, (size_t)o->fine.nloc * R * fe, "restricted right-hand sides"));
-        if (!o->flow.mem) HELM_TRY(tc_flow_alloc(ctx, o->fine, o->flow));
+        if (!o->flow.mem) HELM_TRY(tc_flow_alloc(ctx, o->fine, o->flow, tc_flow_tpn(R)));
     }
     if (o->nc) {
         HELM_TRY(dev_alloc(ctx, (void**)&o->cvec, (size_t)o->nc * R * sizeof(c128), "coarse vector"));

@@ -28,6 +28,7 @@
 // swapped back in reverse pivot order.
 #include <cuda_bf16.h>
 
+#include "blockinv.cuh"
 #include "internal.h"
 
 namespace {
@@ -734,63 +735,7 @@ __global__ void __launch_bounds__(512) bgj_diag(const BoxInfo* __restrict__ boxe
     __syncthreads();
     amax = 0;
     for (int w = 0; w < 16; ++w) amax = max(amax, s_wmax[w]);
-    for (int c = 0; c < NB; ++c) {
-        if (wid == 0) {
-            T best = -1;
-            int bi = NB;
-            for (int r = c + lane; r < NB; r += 32) {
-                const T a = X[r * DP + c].x * X[r * DP + c].x + X[r * DP + c].y * X[r * DP + c].y;
-                if (a > best) { best = a; bi = r; }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (lane == 0) {
-                if (!(best > (T)0) || bi >= NB) {
-                    atomicOr(flag, 1);
-                    bi = c;
-                } else if (best < (T)1e-12 * amax) {
-                    atomicOr(flag, 2);
-                }
-                s_piv = bi;
-                s_perm[c] = bi;
-            }
-        }
-        __syncthreads();
-        const int p = s_piv;
-        if (p != c && tid < NB) {
-            const cplx<T> t = X[c * DP + tid];
-            X[c * DP + tid] = X[p * DP + tid];
-            X[p * DP + tid] = t;
-        }
-        __syncthreads();
-        cplx<T> piv = X[c * DP + c];
-        if (!(piv.x * piv.x + piv.y * piv.y > (T)0)) piv = mk<T>((T)1, (T)0);   // flagged above; stay finite
-        const cplx<T> inv = cinv(piv);
-        if (tid < NB) {
-            s_row[tid] = tid == c ? inv : X[c * DP + tid] * inv;
-            s_col[tid] = X[tid * DP + c];
-        }
-        __syncthreads();
-        for (int e = tid; e < NB * NB; e += 512) {
-            const int r = e / NB, j = e % NB;
-            cplx<T>& x = X[r * DP + j];
-            if (r == c) {
-                x = s_row[j];
-            } else if (j == c) {
-                const cplx<T> v = s_col[r] * inv;
-                x = mk<T>(-v.x, -v.y);
-            } else {
-                const cplx<T> f = s_col[r], sv = s_row[j];
-                x.x -= f.x * sv.x - f.y * sv.y;
-                x.y -= f.x * sv.y + f.y * sv.x;
-            }
-        }
-        __syncthreads();
-    }
+    block_inverse<T, NB, DP, 16, 512>(X, X + NB * DP, s_perm, s_row, s_col, &s_piv, amax, flag);
     if (tid == 0) {
         for (int j = 0; j < NB; ++j) s_pos[j] = j;
         for (int c = NB - 1; c >= 0; --c) {
@@ -979,7 +924,7 @@ helm_status factor_block_t(helm_ctx ctx, PlaneSet& P, int* singular, int* weak) 
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(bgj_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(NB * (NB + 1) * sizeof(cplx<T>)));
+                             (int)((NB * (NB + 1) + 16 * NB) * sizeof(cplx<T>)));
         attr = true;
     }
     cudaMemsetAsync(flag, 0, sizeof(int), st);
@@ -1002,8 +947,10 @@ helm_status factor_block_t(helm_ctx ctx, PlaneSet& P, int* singular, int* weak) 
             double ub = 0;
             for (const auto& b : P.hbox)
                 if (k < b.dims[2] && j0 < b.m) ub += 2.0 * (b.m - std::min(NB, b.m - j0)) * b.m * sizeof(cplx<T>);
-            int t = prof_begin(ctx, "gj_panel");
-            bgj_diag<T><<<P.nbox, 512, NB * (NB + 1) * sizeof(cplx<T>), st>>>(P.dbox, S, m, Pb, flag, j0, k);
+            int t = prof_begin(ctx, "gj_diag");
+            bgj_diag<T><<<P.nbox, 512, (NB * (NB + 1) + 16 * NB) * sizeof(cplx<T>), st>>>(P.dbox, S, m, Pb, flag, j0, k);
+            prof_end(ctx, t, 0.0);
+            t = prof_begin(ctx, "gj_panel");
             bgj_rows<T><<<dim3(t64, P.nbox), 256, 0, st>>>(P.dbox, S, m, Pb, j0, k);
             bgj_wcopy<T><<<dim3(wblocks, P.nbox), 256, 0, st>>>(P.dbox, S, m, W, j0, k);
             prof_end(ctx, t, 0.0);
@@ -1161,7 +1108,9 @@ helm_status planeset_alloc(helm_ctx ctx, PlaneSet& P) {
     P.fac_entries = fac;
     P.nplanes = planes;
     HELM_TRY(dev_alloc(ctx, (void**)&P.dbox, P.nbox * sizeof(BoxInfo), "box table"));
-    HELM_CUDA(ctx, cudaMemcpy(P.dbox, P.hbox.data(), P.nbox * sizeof(BoxInfo), cudaMemcpyHostToDevice));
+    HELM_CUDA(ctx, cudaMemcpyAsync(P.dbox, P.hbox.data(), P.nbox * sizeof(BoxInfo), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    HELM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     HELM_TRY(dev_alloc(ctx, &P.coef, (size_t)P.nloc * 27 * P.cesize(), "local operator coefficients"));
     if (P.coef_only) return HELM_OK;
     HELM_TRY(dev_alloc(ctx, &P.G, P.fac_entries * P.esize(), "plane factors"));

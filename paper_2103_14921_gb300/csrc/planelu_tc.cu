@@ -27,6 +27,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "blockinv.cuh"
 #include "internal.h"
 #include "tc.cuh"
 
@@ -136,13 +137,13 @@ __global__ void tgj_pad_diag(const BoxInfo* __restrict__ boxes, c64* __restrict_
 
 // ------------------------------------------------------------------ panel: block inverse, rows, W
 
-// P = A[J,J]^{-1} by Gauss-Jordan with partial pivoting inside the block (one CTA per box).  flag bit 0: a
-// zero pivot; bit 1: a pivot below 1e-6 of the block's largest entry.
+// P = A[J,J]^{-1} by Gauss-Jordan with partial pivoting inside the block, in 16-column sub-panels (one CTA per
+// box, blockinv.cuh).  flag bit 0: a zero pivot; bit 1: a pivot below 1e-6 of the block's largest entry.
 __global__ void __launch_bounds__(DIAG_THREADS) tgj_diag(const BoxInfo* __restrict__ boxes,
                                                          const c64* __restrict__ S, int L, c64* __restrict__ Pbuf,
                                                          int* __restrict__ flag, int j0, int k) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    c64* X = reinterpret_cast<c64*>(dsm);   // [NB][DP]
+    c64* X = reinterpret_cast<c64*>(dsm);   // [NB][DP], then the sub-panel rows [16][NB]
     __shared__ c64 s_row[NB], s_col[NB];
     __shared__ int s_perm[NB], s_pos[NB];
     __shared__ int s_piv;
@@ -165,65 +166,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) tgj_diag(const BoxInfo* __restri
     __syncthreads();
     amax = 0.f;
     for (int w = 0; w < DIAG_THREADS / 32; ++w) amax = fmaxf(amax, s_wmax[w]);
-    for (int c = 0; c < NB; ++c) {
-        if (wid == 0) {
-            float best = -1.f;
-            int bi = NB;
-            for (int r = c + lane; r < NB; r += 32) {
-                const c64 v = X[r * DP + c];
-                const float a = v.x * v.x + v.y * v.y;
-                if (a > best) { best = a; bi = r; }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (lane == 0) {
-                if (!(best > 0.f) || bi >= NB) {
-                    atomicOr(flag, 1);
-                    bi = c;
-                } else if (best < 1e-12f * amax) {
-                    atomicOr(flag, 2);
-                }
-                s_piv = bi;
-                s_perm[c] = bi;
-            }
-        }
-        __syncthreads();
-        const int p = s_piv;
-        if (p != c && tid < NB) {
-            const c64 t = X[c * DP + tid];
-            X[c * DP + tid] = X[p * DP + tid];
-            X[p * DP + tid] = t;
-        }
-        __syncthreads();
-        c64 piv = X[c * DP + c];
-        if (!(piv.x * piv.x + piv.y * piv.y > 0.f)) piv = mk<float>(1.f, 0.f);   // flagged above; stay finite
-        const float d = piv.x * piv.x + piv.y * piv.y;
-        const c64 inv = mk<float>(piv.x / d, -piv.y / d);
-        if (tid < NB) {
-            s_row[tid] = tid == c ? inv : X[c * DP + tid] * inv;
-            s_col[tid] = X[tid * DP + c];
-        }
-        __syncthreads();
-        for (int e = tid; e < NB * NB; e += DIAG_THREADS) {
-            const int r = e / NB, j = e % NB;
-            c64& x = X[r * DP + j];
-            if (r == c) {
-                x = s_row[j];
-            } else if (j == c) {
-                const c64 v = s_col[r] * inv;
-                x = mk<float>(-v.x, -v.y);
-            } else {
-                const c64 f = s_col[r], s = s_row[j];
-                x.x -= f.x * s.x - f.y * s.y;
-                x.y -= f.x * s.y + f.y * s.x;
-            }
-        }
-        __syncthreads();
-    }
+    block_inverse<float, NB, DP, 16, DIAG_THREADS>(X, X + NB * DP, s_perm, s_row, s_col, &s_piv, amax, flag);
     // the row swaps become a column permutation of the inverse (undone in reverse pivot order)
     if (tid == 0) {
         for (int j = 0; j < NB; ++j) s_pos[j] = j;
@@ -448,6 +391,201 @@ __global__ void __launch_bounds__(128, 1) tgj_update(const __grid_constant__ CUt
     }
 }
 
+// Persistent form of the update: one CTA per SM takes the launch's tiles in turn (tile t = box-major, then row
+// tile, then column tile, every gridDim.x-th one), with two TMEM accumulators so that the epilogue of one tile
+// runs while the products of the next are issued.  Warp 0 lane 0 loads the operands (TMA, 2-stage ring),
+// warp 1 lane 0 issues the MMAs, warps 2-5 read the accumulator (warp w owns TMEM lanes 32 (w mod 4)..) and
+// write -D back through shared memory with TMA: a reduce-add into A for the columns outside J (A - D), a
+// store for the panel's own columns (-W P).  The padding diagonal a store overwrites in the panel's column
+// tile is restored before the next plane.  Every wait is bounded; on a give-up each role leaves its loop,
+// copies and products already issued are waited for, and TMEM is freed.
+constexpr int PW = 6;                     // warps: producer, MMA issuer, four epilogue warps
+constexpr int STG = 2 * UBM * 128;        // staging: two 128-row x 32-float boxes (32 KB)
+constexpr int PSMEM = UST * STAGE + STG + 1024 + 256;
+
+__device__ __forceinline__ bool tile_of(const BoxInfo* __restrict__ boxes, int t, int tl, int j0, int k, int& box,
+                                        int& row0, int& col0) {
+    box = t / (tl * tl);
+    const int r = t % (tl * tl);
+    row0 = (r / tl) * UBM;
+    col0 = (r % tl) * (UBN / 2);
+    const BoxInfo& B = boxes[box];
+    return k < B.dims[2] && j0 < B.m && row0 < B.m && col0 < B.m && row0 != j0;
+}
+
+__global__ void __launch_bounds__(PW * 32, 1) tgj_update_pers(const __grid_constant__ CUtensorMap mWh,
+                                                              const __grid_constant__ CUtensorMap mWl,
+                                                              const __grid_constant__ CUtensorMap mBh,
+                                                              const __grid_constant__ CUtensorMap mBl,
+                                                              const __grid_constant__ CUtensorMap mS,
+                                                              const BoxInfo* __restrict__ boxes, int nbox, int L,
+                                                              int j0, int k, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char psm_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(psm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char* stg = base + UST * STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(stg + STG);
+    uint64_t* empty = full + UST;
+    uint64_t* tfull = empty + UST;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* fin = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    int* s_go = reinterpret_cast<int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tl = L / UBM;
+    const int ntiles = nbox * tl * tl;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < UST; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&tfull[i], 1);
+            tc::mbar_init(&tempty[i], 4);
+        }
+        tc::mbar_init(fin, 1);
+        tc::fence_barrier_init();
+        tc::prefetch_tmap(&mWh);
+        tc::prefetch_tmap(&mWl);
+        tc::prefetch_tmap(&mBh);
+        tc::prefetch_tmap(&mBl);
+        tc::prefetch_tmap(&mS);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    constexpr int NKC = K2 / 32;
+    int box, row0, col0;
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                if (!tile_of(boxes, t, tl, j0, k, box, row0, col0)) continue;
+                for (int kc = 0; kc < NKC; ++kc, ++g) {
+                    const int st = g % UST;
+                    if (g >= UST && !tc::mbar_wait(&empty[st], ((g / UST) - 1) & 1, err, 21)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* s = base + st * STAGE;
+                    tc::mbar_arrive_expect_tx(&full[st], STAGE);
+                    tc::tma_load_3d(s, &mWh, kc * 32, row0, box, &full[st]);
+                    tc::tma_load_3d(s + A_TILE, &mWl, kc * 32, row0, box, &full[st]);
+                    tc::tma_load_3d(s + 2 * A_TILE, &mBh, kc * 32, 2 * col0, box, &full[st]);
+                    tc::tma_load_3d(s + 2 * A_TILE + B_TILE, &mBl, kc * 32, 2 * col0, box, &full[st]);
+                }
+            }
+            // a give-up anywhere: let the loads already issued land before the stages are left
+            if (!ok || *reinterpret_cast<volatile int*>(err) != 0)
+                for (uint32_t q = g > UST ? g - UST : 0; q < g; ++q) tc::mbar_drain(&full[q % UST], (q / UST) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_tf32(UBM, UBN);
+            uint32_t g = 0, i = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                if (!tile_of(boxes, t, tl, j0, k, box, row0, col0)) continue;
+                const uint32_t a = i & 1, u = i >> 1;
+                if (u >= 1 && !tc::mbar_wait(&tempty[a], (u - 1) & 1, err, 22)) break;
+                tc::fence_after_sync();
+                const uint32_t acc = tmem + a * 256;
+                for (int kc = 0; kc < NKC; ++kc, ++g) {
+                    const int st = g % UST;
+                    if (!tc::mbar_wait(&full[st], (g / UST) & 1, err, 23)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t sah = tc::smem_u32(base + st * STAGE);
+                    const uint32_t sal = sah + A_TILE, sbh = sah + 2 * A_TILE, sbl = sbh + B_TILE;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ah = tc::desc_k_sw128(sah + kk * 32), al = tc::desc_k_sw128(sal + kk * 32);
+                        const uint64_t bh = tc::desc_k_sw128(sbh + kk * 32), bl = tc::desc_k_sw128(sbl + kk * 32);
+                        tc::mma_tf32(acc, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        tc::mma_tf32(acc, ah, bl, idesc, 1u);
+                        tc::mma_tf32(acc, al, bh, idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[st]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&tfull[a]);
+                ++i;
+            }
+            // every product issued has completed before TMEM is freed
+            tc::mma_commit(fin);
+            tc::mbar_drain(fin, 0);
+        }
+    } else {
+        // epilogue: 128 threads, hardware barrier 1 among them
+        const int et = threadIdx.x - 64;
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int r = q * 32 + lane;            // tile row of this thread
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            if (!tile_of(boxes, t, tl, j0, k, box, row0, col0)) continue;
+            const uint32_t a = i & 1, u = i >> 1;
+            if (et == 0) *s_go = tc::mbar_wait(&tfull[a], u & 1, err, 24) ? 1 : 0;
+            tc::named_bar(1, 128);
+            if (!*s_go) break;                  // uniform over the four warps
+            tc::fence_after_sync();
+            const bool store = col0 == j0;      // the panel's own columns: A[I,J] = -W P
+            for (int c = 0; c < UBN / 64; ++c) {
+                uint32_t v[2][32];
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + a * 256 + c * 64;
+                tc::tmem_ld_32x32b_x32(ta, v[0]);
+                tc::tmem_ld_32x32b_x32(ta + 32, v[1]);
+                tc::tmem_ld_wait();
+                if (c == UBN / 64 - 1) {
+                    // the accumulator has been read: the MMA issuer may reuse it
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&tempty[a]);
+                }
+                if (et == 0) tc::bulk_wait_read0();   // the staging buffer's last TMA copy has read it
+                tc::named_bar(1, 128);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    unsigned char* rowp = stg + h * (UBM * 128) + r * 128;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 val = make_float4(-__uint_as_float(v[h][4 * j]), -__uint_as_float(v[h][4 * j + 1]),
+                                                       -__uint_as_float(v[h][4 * j + 2]),
+                                                       -__uint_as_float(v[h][4 * j + 3]));
+                        *reinterpret_cast<float4*>(rowp + ((j ^ (r & 7)) << 4)) = val;
+                    }
+                }
+                tc::fence_proxy_async_smem();
+                tc::named_bar(1, 128);
+                if (et == 0) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int x = 2 * col0 + c * 64 + h * 32;
+                        if (store) tc::tma_store_3d(&mS, stg + h * (UBM * 128), x, row0, box);
+                        else tc::tma_reduce_add_3d(&mS, stg + h * (UBM * 128), x, row0, box);
+                    }
+                    tc::bulk_commit();
+                }
+            }
+            ++i;
+        }
+        if (et == 0) tc::bulk_wait0();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
 // G_k (row pitch ld, complex64) <- the inverse in S
 __global__ void tgj_store(const BoxInfo* __restrict__ boxes, const c64* __restrict__ S, int L, c64* __restrict__ G,
                           int k) {
@@ -473,6 +611,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn_f() {
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }
     return fn;
+}
+
+// the work matrices S as fp32 [nb][L][2L], boxes of 32 floats x 128 rows, 128-byte swizzle (epilogue stores)
+bool encode_matrix(CUtensorMap* map, void* base, uint64_t L, uint64_t nb) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn_f();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {2 * L, L, nb};
+    cuuint64_t strides[2] = {2 * L * 4, 2 * L * 4 * L};
+    cuuint32_t box[3] = {32, (cuuint32_t)UBM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // fp32 [nb][rows][K2] operand, boxes of 32 x box_rows, 128-byte swizzle
@@ -526,22 +677,28 @@ helm_status planeset_factor_tc(helm_ctx ctx, PlaneSet& P, int* singular, int* we
         cleanup();
         return rc;
     }
-    CUtensorMap mWh, mWl, mBh, mBl;
+    CUtensorMap mWh, mWl, mBh, mBl, mS;
     if (!encode_operand(&mWh, Wh, L, nb, UBM) || !encode_operand(&mWl, Wl, L, nb, UBM) ||
-        !encode_operand(&mBh, Bh, 2ull * L, nb, UBN) || !encode_operand(&mBl, Bl, 2ull * L, nb, UBN)) {
+        !encode_operand(&mBh, Bh, 2ull * L, nb, UBN) || !encode_operand(&mBl, Bl, 2ull * L, nb, UBN) ||
+        !encode_matrix(&mS, S, L, nb)) {
         cleanup();
         return set_error(ctx, HELM_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core factorisation");
     }
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tgj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, USMEM);
-        cudaFuncSetAttribute(tgj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(NB * DP * sizeof(c64)));
+        cudaFuncSetAttribute(tgj_update_pers, cudaFuncAttributeMaxDynamicSharedMemorySize, PSMEM);
+        cudaFuncSetAttribute(tgj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((NB * DP + 16 * NB) * sizeof(c64)));
         attr = true;
     }
     cudaMemsetAsync(S, 0, s_bytes, st);
     cudaMemsetAsync(flag, 0, 2 * sizeof(int), st);
     const c64* coef = (const c64*)P.coef;
     const int tl = L / NB;
+    // tc_factor 1: persistent update (one CTA per SM, overlapped epilogue); 2: one CTA per tile
+    const bool persistent = ctx->tc_factor == 1;
+    const int pgrid = std::max(1, std::min(ctx->sm_count, P.nbox * tl * tl));
     const unsigned eb = (unsigned)std::min<long long>(((long long)P.m_max * P.m_max + 255) / 256, 2048);
     const dim3 egrid(eb, P.nbox);
     tgj_pad_diag<<<dim3(1, P.nbox), 128, 0, st>>>(P.dbox, (c64*)S, L);
@@ -550,6 +707,11 @@ helm_status planeset_factor_tc(helm_ctx ctx, PlaneSet& P, int* singular, int* we
     // its matrix once; of one panel (block inverse, rows, W): the block, the rows J, the column block J and
     // the operands written
     for (int k = 0; k < P.bz_max; ++k) {
+        if (k > 0 && persistent) {
+            // the padding diagonal that the panel's column store may have overwritten in the last plane
+            tgj_pad_diag<<<dim3(1, P.nbox), 128, 0, st>>>(P.dbox, (c64*)S, L);
+            ctx->launches++;
+        }
         if (k == 0) {
             tgj_schur_init<<<egrid, 256, 0, st>>>(P.dbox, coef, (c64*)S, L);
             ctx->launches++;
@@ -566,16 +728,20 @@ helm_status planeset_factor_tc(helm_ctx ctx, PlaneSet& P, int* singular, int* we
                     ub += 2.0 * rows * b.m * sizeof(c64);
                     pb += (2.0 * NB * b.m + (double)NB * b.m) * sizeof(c64) + (2.0 * 2 * b.m + b.m) * K2 * sizeof(float);
                 }
-            int t = prof_begin(ctx, "gj_panel");
-            tgj_diag<<<P.nbox, DIAG_THREADS, NB * DP * sizeof(c64), st>>>(P.dbox, (const c64*)S, L, (c64*)Pb, flag,
+            int t = prof_begin(ctx, "gj_panel_tc");
+            tgj_diag<<<P.nbox, DIAG_THREADS, (NB * DP + 16 * NB) * sizeof(c64), st>>>(P.dbox, (const c64*)S, L, (c64*)Pb, flag,
                                                                           j0, k);
             tgj_rows<<<dim3(L / 64, P.nbox), 256, 0, st>>>(P.dbox, (c64*)S, L, (const c64*)Pb, (float*)Bh, (float*)Bl,
                                                            j0, k);
             tgj_wcopy<<<dim3(L / 32, P.nbox), 256, 0, st>>>(P.dbox, (const c64*)S, L, (float*)Wh, (float*)Wl, j0, k);
             prof_end(ctx, t, pb);
             t = prof_begin(ctx, "gj_update_tc");
-            tgj_update<<<dim3(tl, tl, P.nbox), 128, USMEM, st>>>(mWh, mWl, mBh, mBl, P.dbox, (c64*)S, L, j0, k,
-                                                                 flag + 1);
+            if (persistent)
+                tgj_update_pers<<<pgrid, PW * 32, PSMEM, st>>>(mWh, mWl, mBh, mBl, mS, P.dbox, P.nbox, L, j0, k,
+                                                               flag + 1);
+            else
+                tgj_update<<<dim3(tl, tl, P.nbox), 128, USMEM, st>>>(mWh, mWl, mBh, mBl, P.dbox, (c64*)S, L, j0, k,
+                                                                     flag + 1);
             prof_end(ctx, t, ub);
             ctx->launches += 4;
         }

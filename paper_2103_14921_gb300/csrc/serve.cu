@@ -29,11 +29,35 @@
 #include <thread>
 #include <unordered_map>
 
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+
 #include "internal.h"
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// HELM_SERVE_TRACE=1 in the environment: the worker and the builder log their events on stderr.
+bool trace_on() {
+    static const bool on = [] {
+        const char* v = std::getenv("HELM_SERVE_TRACE");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+void trace(const char* fmt, ...) {
+    if (!trace_on()) return;
+    static const Clock::time_point t0 = Clock::now();
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    fprintf(stderr, "[serve %9.3f] %s\n", std::chrono::duration<double>(Clock::now() - t0).count(), buf);
+    fflush(stderr);
+}
 
 double ms_since(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
@@ -82,6 +106,7 @@ struct FactorSet {
     helm_grid_desc gd{};
     helm_oras_desc od{};
     int restart = 0, flexible = 0, basis_prec = 0;
+    int width = 0;                  // column slots of its engine (a power of two >= 16, at most the server's)
     helm_grid g = nullptr;
     helm_oras o = nullptr;
     std::unique_ptr<KrylovEngine> K;
@@ -158,6 +183,8 @@ struct Server {
                 to_build.pop_front();
             }
             const size_t before = bctx->in_use;
+            trace("build start: model %llu, grid %dx%dx%d, f %.2f", (unsigned long long)fs->model_id, fs->gd.nx,
+                  fs->gd.ny, fs->gd.nz, fs->gd.freq_hz);
             helm_status st = helm_setup_grid(bctx, &fs->gd, fs->c, &fs->g);
             if (!st) st = oras_factor(fs->g, &fs->od, &fs->o);
             if (!st) st = cuda_check(bctx, cudaStreamSynchronize(bctx->stream), "factor set build");
@@ -174,6 +201,8 @@ struct Server {
                 bctx->children--;
             }
             fs->build_status = st;
+            trace("build done: model %llu, status %d, %.2f GB", (unsigned long long)fs->model_id, st,
+                  fs->built_bytes / 1e9);
             {
                 std::lock_guard<std::mutex> lk(mu);
                 built.push_back(fs);
@@ -197,8 +226,8 @@ struct Server {
                 fs->g->ctx = ctx;   // re-parent: every later call on the set runs on the serving stream
                 ctx->children++;
                 ctx->in_use += fs->built_bytes;
-                fs->K.reset(make_krylov_engine(fs->o, slots, fs->restart, fs->flexible != 0, fs->basis_prec, nullptr,
-                                               nullptr, &st));
+                fs->K.reset(make_krylov_engine(fs->o, fs->width, fs->restart, fs->flexible != 0, fs->basis_prec,
+                                               nullptr, nullptr, &st));
                 if (st) fs->build_msg = ctx->last_error;
             }
             fs->building = 0;
@@ -217,13 +246,21 @@ struct Server {
                 destroy_set(fs);
                 continue;
             }
-            fs->owner.assign(slots, nullptr);
-            fs->col.assign(slots, -1);
+            fs->owner.assign(fs->width, nullptr);
+            fs->col.assign(fs->width, -1);
             fs->last_used = Clock::now();
         }
     }
 
+    // engine width for a request of nrhs columns: a power of two from 16 up, at most the server's slot count
+    int width_for(int nrhs) const {
+        int w = 16;
+        while (w < nrhs) w *= 2;
+        return std::min(w, slots);
+    }
+
     void finish(SRequest* r, helm_status st) {
+        trace("finish ticket %llu: status %d", (unsigned long long)r->ticket, st);
         std::lock_guard<std::mutex> lk(mu);
         r->status = st;
         r->state = 2;
@@ -237,11 +274,11 @@ struct Server {
         delete fs;
     }
 
-    size_t engine_estimate(const helm_request& r) const {
+    size_t engine_estimate(const helm_request& r, int width) const {
         const size_t N = (size_t)r.grid.nx * r.grid.ny * r.grid.nz;
         const size_t e = r.gmres.basis_prec == HELM_PREC_FP64 ? sizeof(c128) : sizeof(c64);
         const size_t m = (size_t)r.gmres.restart;
-        return N * slots * ((2 * m + 3) * e + 3 * sizeof(c128)) + N * 48;
+        return N * width * ((2 * m + 3) * e + 3 * sizeof(c128)) + N * 48;
     }
 
     // Try to place r: returns true if admitted (or failed), false if it must keep waiting (its factors are
@@ -251,7 +288,8 @@ struct Server {
         for (auto* s : sets)
             if (s->matches(r->req)) fs = s;
         if (!fs) {
-            const size_t need = oras_estimate_bytes(r->req.grid, r->req.oras, slots) + engine_estimate(r->req);
+            const int width = width_for(r->req.nrhs);
+            const size_t need = oras_estimate_bytes(r->req.grid, r->req.oras, width) + engine_estimate(r->req, width);
             auto room = [&]() { return ctx->budget == 0 || ctx->in_use + reserved + need <= ctx->budget; };
             while (!room()) {
                 FactorSet* lru = nullptr;
@@ -259,6 +297,7 @@ struct Server {
                     if (!s->building && s->active == 0 && (!lru || s->last_used < lru->last_used)) lru = s;
                 if (!lru) break;
                 sets.erase(std::find(sets.begin(), sets.end(), lru));
+                trace("evict model %llu (grid %d^3)", (unsigned long long)lru->model_id, lru->gd.nx);
                 destroy_set(lru);
             }
             if (!room()) {
@@ -277,7 +316,10 @@ struct Server {
             fs->flexible = r->req.gmres.flexible;
             fs->basis_prec = r->req.gmres.basis_prec;
             fs->c = r->req.c;
+            fs->width = width;
             fs->building = 1;
+            trace("queue build for ticket %llu (need %.2f GB, in use %.2f, reserved %.2f)",
+                  (unsigned long long)r->ticket, need / 1e9, ctx->in_use / 1e9, reserved / 1e9);
             r->built_for = true;
             fs->reserved = need;
             reserved += need;
@@ -290,12 +332,33 @@ struct Server {
             return false;
         }
         if (fs->building || !fs->K) return false;
+        if (fs->width < r->req.nrhs) {
+            // a wider engine for this set, made once its running columns have finished (and if it fits)
+            if (fs->active > 0) return false;
+            const int width = width_for(r->req.nrhs);
+            const size_t more = engine_estimate(r->req, width) - engine_estimate(r->req, fs->width);
+            if (ctx->budget && ctx->in_use + reserved + more > ctx->budget) return false;
+            helm_status st = HELM_OK;
+            fs->K.reset();
+            fs->K.reset(make_krylov_engine(fs->o, width, fs->restart, fs->flexible != 0, fs->basis_prec, nullptr,
+                                           nullptr, &st));
+            if (st) {
+                // no room for the wider engine after all: drop the (idle) set; a later request rebuilds it
+                sets.erase(std::find(sets.begin(), sets.end(), fs));
+                destroy_set(fs);
+                finish(r, st);
+                return true;
+            }
+            fs->width = width;
+            fs->owner.assign(width, nullptr);
+            fs->col.assign(width, -1);
+        }
         if (fs->free_slots() < r->req.nrhs) return false;
         r->reused = !r->built_for;
         // take slots, copy the request's columns into them and start them
         const long long N = fs->g->n;
         std::vector<int> sl;
-        for (int s = 0; s < slots && (int)sl.size() < r->req.nrhs; ++s)
+        for (int s = 0; s < fs->width && (int)sl.size() < r->req.nrhs; ++s)
             if (!fs->owner[s]) sl.push_back(s);
         cudaStream_t st = ctx->stream;
         const size_t bytes = (size_t)N * r->req.nrhs * sizeof(c128);
@@ -311,7 +374,7 @@ struct Server {
                                  "slot map");
         if (!rc) {
             pack_columns<<<(unsigned)std::min<long long>((N * r->req.nrhs + 255) / 256, 4096), 256, 0, st>>>(
-                src, fs->K->B(), dslot, N, r->req.nrhs, slots);
+                src, fs->K->B(), dslot, N, r->req.nrhs, fs->width);
             ctx->launches++;
             std::vector<double> tol(sl.size(), r->req.gmres.tol);
             std::vector<int> maxit(sl.size(), r->req.gmres.maxit);
@@ -331,6 +394,8 @@ struct Server {
         }
         fs->active += (int)sl.size();
         fs->last_used = Clock::now();
+        trace("admit ticket %llu: %d columns into a set of width %d (%d active)", (unsigned long long)r->ticket,
+              (int)sl.size(), fs->width, fs->active);
         r->fs = fs;
         r->slots = sl;
         r->cols_left = (int)sl.size();
@@ -359,7 +424,7 @@ struct Server {
         }
         if (!rc) {
             unpack_columns<<<(unsigned)std::min<long long>((N * r->req.nrhs + 255) / 256, 4096), 256, 0, st>>>(
-                fs->K->X(), dst, dslot, N, r->req.nrhs, slots);
+                fs->K->X(), dst, dslot, N, r->req.nrhs, fs->width);
             ctx->launches++;
             if (!xdev) rc = cuda_check(ctx, cudaMemcpyAsync(r->req.x, stage, bytes, cudaMemcpyDeviceToHost, st), "x D2H");
         }
@@ -410,9 +475,13 @@ struct Server {
             for (auto* fs : sets) {
                 if (fs->active == 0) continue;
                 bool any = false;
+                const auto tc0 = Clock::now();
                 helm_status rc = fs->K->cycle(&any);
+                trace("cycle model %llu (grid %d^3, width %d, %d active): status %d, %.1f ms",
+                      (unsigned long long)fs->model_id, fs->gd.nx, fs->width, fs->active, rc,
+                      ms_since(tc0, Clock::now()));
                 std::vector<SRequest*> done_reqs;
-                for (int s = 0; s < slots; ++s) {
+                for (int s = 0; s < fs->width; ++s) {
                     SRequest* r = fs->owner[s];
                     if (!r) continue;
                     const RhsState& cs = fs->K->state(s);

@@ -372,20 +372,128 @@ __device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* 
     cp_async_wait<0>();
 }
 
+// march_run for blocks whose rows all have plain (1, -2, 1) coefficients, in class-sum form: with plain
+// differences the coefficient of a neighbour depends only on its class (centre, face, edge, corner), so per
+// plane q and node the in-plane terms of a field w (u for the Laplacian, v = k^2 u for the mass term) are its
+// centre value c, its in-plane face sum F = s_x w + s_y w and its in-plane corner sum E = s_x s_y w (s_a: the sum
+// of the two neighbours along axis a); plane q then adds Lc0 c + Lc1 F + Lc2 E (u) and Mc0 c + Mc1 F + Mc2 E (v)
+// to output q and Lc1 c + Lc2 F + Lc3 E, Mc1 c + Mc2 F + Mc3 E to outputs q - 1 and q + 1, with the class
+// constants Lc = {-6 + 12 a2 - 8 a3, 1 - 4 a2 + 4 a3, a2 - 2 a3, a3} / h^2 and Mc = {m0 - 6 m1 + 12 m2 - 8 m3,
+// m1 - 4 m2 + 4 m3, m2 - 2 m3, m3}.  The same operator as the product form (expanded), in fewer operations.
+template <bool SUB, bool REALK>
+__device__ __forceinline__ void march_run_plain(const c64* __restrict__ u, const c64* __restrict__ b,
+                                                c64* __restrict__ y, const c64* __restrict__ k2, int nx, int ny,
+                                                int nz, const StencilW& w, int i0, int j0, int k0, int k1, float4* su,
+                                                float2* sk) {
+    const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
+    const int pc = lane % MNP, g = lane / MNP;
+    const int j = j0 + wr, xb = g * MN, ib = i0 + xb;
+    const bool live = j < ny;
+    const double ih2 = w.inv_h2;
+    const float L0 = (float)((-6.0 + 12.0 * w.a2 - 8.0 * w.a3) * ih2), L1 = (float)((1.0 - 4.0 * w.a2 + 4.0 * w.a3) * ih2);
+    const float L2 = (float)((w.a2 - 2.0 * w.a3) * ih2), L3 = (float)(w.a3 * ih2);
+    const float M0 = (float)(w.m0 - 6.0 * w.m1 + 12.0 * w.m2 - 8.0 * w.m3), M1 = (float)(w.m1 - 4.0 * w.m2 + 4.0 * w.m3);
+    const float M2 = (float)(w.m2 - 2.0 * w.m3), M3 = (float)w.m3;
+    float4 P[MN], N[MN];
+#pragma unroll
+    for (int c = 0; c < MN; ++c) P[c] = N[c] = f4(0.f);
+    march_stage(su, sk, u, k2, nx, ny, nz, i0, j0, k0 - 1);
+    cp_async_commit();
+    march_stage(su + MBUF_U, sk + MBUF_K, u, k2, nx, ny, nz, i0, j0, k0);
+    cp_async_commit();
+    for (int q = k0 - 1, buf = 0; q <= k1; ++q, buf = buf == MNBUF - 1 ? 0 : buf + 1) {
+        const int nb = buf >= 1 ? buf - 1 : MNBUF - 1;
+        if (q + 2 <= k1) march_stage(su + nb * MBUF_U, sk + nb * MBUF_K, u, k2, nx, ny, nz, i0, j0, q + 2);
+        cp_async_commit();
+        cp_async_wait<2>();
+        __syncthreads();
+        float4 bq[MN];
+        if (SUB) {
+#pragma unroll
+            for (int c = 0; c < MN; ++c) {
+                bq[c] = f4(0.f);
+                if (live && q - 1 >= k0 && ib + c < nx)
+                    bq[c] = __ldg(reinterpret_cast<const float4*>(b + (((long long)(q - 1) * ny + j) * nx + ib + c) *
+                                                                     (2 * MNP)) + pc);
+            }
+        }
+        const float4* cu = su + buf * MBUF_U;
+        const float2* ck = sk + buf * MBUF_K;
+        // sliding window over the columns n of the block row: centre values and the sums over rows j - 1, j + 1
+        float4 Cu[3], Cv[3], Yu[3], Yv[3];
+        auto column = [&](int n, int slot) {
+            float4 U[3], V[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int sidx = (wr + r) * MBX + xb + n;
+                U[r] = cu[sidx * MNP + pc];
+                const float2 kk = ck[sidx];
+                if (REALK) V[r] = make_float4(kk.x * U[r].x, kk.x * U[r].y, kk.x * U[r].z, kk.x * U[r].w);
+                else V[r] = caxpy4(mk<float>(kk.x, kk.y), U[r], f4(0.f));
+            }
+            Cu[slot] = U[1];
+            Cv[slot] = V[1];
+            Yu[slot] = add4(U[0], U[2]);
+            Yv[slot] = add4(V[0], V[2]);
+        };
+        column(0, 0);
+        column(1, 1);
+#pragma unroll
+        for (int c = 0; c < MN; ++c) {
+            column(c + 2, (c + 2) % 3);
+            const int s0 = c % 3, s1 = (c + 1) % 3, s2 = (c + 2) % 3;
+            const float4 cU = Cu[s1], cV = Cv[s1];
+            const float4 FU = add4(add4(Cu[s0], Cu[s2]), Yu[s1]), EU = add4(Yu[s0], Yu[s2]);
+            const float4 FV = add4(add4(Cv[s0], Cv[s2]), Yv[s1]), EV = add4(Yv[s0], Yv[s2]);
+            // plane q's contribution to output q (A0) and to outputs q -/+ 1 (A1)
+            const float4 A0 = axpy4(M2, EV, axpy4(M1, FV, axpy4(M0, cV, axpy4(L2, EU, axpy4(L1, FU,
+                                  make_float4(L0 * cU.x, L0 * cU.y, L0 * cU.z, L0 * cU.w))))));
+            const float4 A1 = axpy4(M3, EV, axpy4(M2, FV, axpy4(M1, cV, axpy4(L3, EU, axpy4(L2, FU,
+                                  make_float4(L1 * cU.x, L1 * cU.y, L1 * cU.z, L1 * cU.w))))));
+            const int i = ib + c;
+            if (live && q - 1 >= k0 && i < nx) {
+                float4 o = add4(P[c], A1);
+                const long long node = ((long long)(q - 1) * ny + j) * nx + i;
+                float4* dst = reinterpret_cast<float4*>(y + node * (2 * MNP)) + pc;
+                if (SUB) o = make_float4(bq[c].x - o.x, bq[c].y - o.y, bq[c].z - o.z, bq[c].w - o.w);
+                __stcs(dst, o);
+            }
+            P[c] = add4(N[c], A0);
+            N[c] = A1;
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
 template <bool SUB, bool REALK>
 __global__ void __launch_bounds__(128, 3) stencil_march(const c64* __restrict__ u, const c64* __restrict__ b,
                                                      c64* __restrict__ y, const c64* __restrict__ k2,
                                                      const c64* __restrict__ tab, int nx, int ny, int nz, StencilW w,
-                                                     PlainRange pl) {
+                                                     PlainRange pl, int skip_plain) {
     __shared__ float4 su[MNBUF * MBUF_U];
     __shared__ float2 sk[MNBUF * MBUF_K];
     const int i0 = blockIdx.x * MTX, j0 = blockIdx.y * MTY;
     const int k0 = blockIdx.z * MZC, k1 = min(k0 + MZC, nz);
-    // block-uniform path choice: every row the block writes has plain coefficients on every axis
+    // blocks whose rows all have plain coefficients on every axis are left to stencil_march_plain
     const bool plain = i0 >= pl.lo[0] && min(i0 + MTX, nx) - 1 <= pl.hi[0] && j0 >= pl.lo[1] &&
                        min(j0 + MTY, ny) - 1 <= pl.hi[1] && k0 >= pl.lo[2] && k1 - 1 <= pl.hi[2];
+    if (plain && skip_plain) return;
     if (plain) march_run<SUB, REALK, true>(u, b, y, k2, tab, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
     else march_run<SUB, REALK, false>(u, b, y, k2, tab, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
+}
+
+// The plain blocks (a box of the block grid starting at block (bx0, by0, bz0)) in class-sum form, a kernel of
+// their own so that its register budget is that of the plain path alone.
+template <bool SUB, bool REALK>
+__global__ void __launch_bounds__(128, 4) stencil_march_plain(const c64* __restrict__ u, const c64* __restrict__ b,
+                                                             c64* __restrict__ y, const c64* __restrict__ k2, int nx,
+                                                             int ny, int nz, StencilW w, int bx0, int by0, int bz0) {
+    __shared__ float4 su[MNBUF * MBUF_U];
+    __shared__ float2 sk[MNBUF * MBUF_K];
+    const int i0 = (bx0 + blockIdx.x) * MTX, j0 = (by0 + blockIdx.y) * MTY;
+    const int k0 = (bz0 + blockIdx.z) * MZC, k1 = min(k0 + MZC, nz);
+    march_run_plain<SUB, REALK>(u, b, y, k2, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
 }
 
 struct RowW {
@@ -499,12 +607,41 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
         const PlainRange pl = plain_range(g);
         const dim3 grid((unsigned)((g->d.nx + (32 / MNP) * MN - 1) / ((32 / MNP) * MN)), (unsigned)((g->d.ny + 3) / 4),
                         (unsigned)((g->d.nz + MZC - 1) / MZC));
+        // the box of blocks whose rows are all plain on every axis: [lo, hi) per axis
+        const int n3[3] = {g->d.nx, g->d.ny, g->d.nz}, bs[3] = {MTX, MTY, MZC}, nbk[3] = {(int)grid.x, (int)grid.y,
+                                                                                          (int)grid.z};
+        int blo[3], bhi[3];
+        bool any = true;
+        for (int a = 0; a < 3; ++a) {
+            blo[a] = nbk[a];
+            bhi[a] = 0;
+            for (int t = 0; t < nbk[a]; ++t) {
+                const int lo = t * bs[a], hi = std::min(lo + bs[a], n3[a]) - 1;
+                if (lo >= pl.lo[a] && hi <= pl.hi[a]) {
+                    blo[a] = std::min(blo[a], t);
+                    bhi[a] = std::max(bhi[a], t + 1);
+                }
+            }
+            any = any && bhi[a] > blo[a];
+        }
+        const int skip = any && g->ctx->stencil_march == 1 ? 1 : 0;
         if (g->k2_real)
             stencil_march<SUB, true><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
-                                                          g->d.nx, g->d.ny, g->d.nz, g->w, pl);
+                                                          g->d.nx, g->d.ny, g->d.nz, g->w, pl, skip);
         else
             stencil_march<SUB, false><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
-                                                           g->d.nx, g->d.ny, g->d.nz, g->w, pl);
+                                                           g->d.nx, g->d.ny, g->d.nz, g->w, pl, skip);
+        if (skip) {
+            const dim3 pg(bhi[0] - blo[0], bhi[1] - blo[1], bhi[2] - blo[2]);
+            if (g->k2_real)
+                stencil_march_plain<SUB, true><<<pg, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->d.nx,
+                                                                  g->d.ny, g->d.nz, g->w, blo[0], blo[1], blo[2]);
+            else
+                stencil_march_plain<SUB, false><<<pg, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f,
+                                                                   g->d.nx, g->d.ny, g->d.nz, g->w, blo[0], blo[1],
+                                                                   blo[2]);
+            g->ctx->launches++;
+        }
     } else {
         dispatch<float, SUB>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, in,
                              g->k2_real, rw, s);

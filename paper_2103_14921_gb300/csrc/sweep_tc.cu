@@ -501,7 +501,9 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
 // Both sweeps of every box in one launch.  Box b runs the chain of operations
 //   prep(0), gemm(0), prep(1), gemm(1), ..., prep(2 n_z - 2), gemm(2 n_z - 2)
 // (steps 0..n_z-1 forward, then n_z-1 backward steps), each operation split into items: row tiles of
-// 128 for a product, tiles of FLOW_TPN nodes for an operand preparation.  Items wait in a queue: the
+// 128 for a product, tiles of tpn nodes for an operand preparation (128 nodes at up to 16 right-hand sides,
+// fewer as the column count grows, so that a preparation item stays about as long as a product item and the
+// preparations of a step spread over more CTAs: tpn = 1024 / (column pairs) rounded down to 16, 16..128).  Items wait in a queue: the
 // preparations of step 0 are there at the start (init), and the CTA that completes the last item of an
 // operation appends the items of the box's next operation.  Each CTA takes the next queue slot, waits
 // until that slot has been written, runs the item and counts it done.  A slot is written only after
@@ -512,7 +514,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
 // fence (and a generic-to-async proxy fence, since the next product reads the B operand by TMA) before
 // its completion is counted; queue slots are published with release stores and read with acquire loads;
 // values other CTAs wrote in this launch are read through L2 (ld.cg), never a stale L1 line.
-constexpr int FLOW_TPN = 128;
+constexpr int FLOW_TPN_MAX = 128;
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
     int v;
@@ -574,8 +576,8 @@ __device__ __forceinline__ int4 flow_fetch(int slot, const int* __restrict__ ini
 
 // ops in box b's chain, and the items of operation j
 __device__ __host__ __forceinline__ int flow_chain(int bz) { return 2 * (2 * bz - 1); }
-__device__ __host__ __forceinline__ int flow_tiles(int m, int j) {
-    return (j & 1) ? (m + TC_BM - 1) / TC_BM : (m + FLOW_TPN - 1) / FLOW_TPN;
+__device__ __host__ __forceinline__ int flow_tiles(int m, int j, int tpn) {
+    return (j & 1) ? (m + TC_BM - 1) / TC_BM : (m + tpn - 1) / tpn;
 }
 
 template <typename E, int NPAD, int NST>
@@ -586,7 +588,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
                                                         const c64* __restrict__ lb, c64* __restrict__ loc,
                                                         E* __restrict__ bt, int ld2, int nrhs, int nkc,
                                                         const int* __restrict__ init, int ninit, int* flag, int total,
-                                                        int* ctl, int* __restrict__ err, uint64_t wait_ns) {
+                                                        int* ctl, int* __restrict__ err, uint64_t wait_ns, int tpn) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int4 cur;
     unsigned char* base = align1024(smem_raw);
@@ -621,7 +623,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
             const int k = fwd ? s : bz - 1 - s;
             gemm_core<E, NPAD, NST>(&mapA, &mapA32, &mapB, B, box, t, k, loc, nrhs, fwd, nkc, err, base, tmem, R);
         } else {
-            prep_tile_staged<E>(B, box, t, FLOW_TPN, coef, lb, loc, bt, ld2, NPAD, nrhs, s, fwd, base,
+            prep_tile_staged<E>(B, box, t, tpn, coef, lb, loc, bt, ld2, NPAD, nrhs, s, fwd, base,
                                 NST * TcCfg<E, NPAD, NST>::STAGE);
             tc::fence_proxy_async_smem();   // the stages are TMA destinations again in a later product
             fence_proxy_async_global();     // B operand written here, read by TMA in another CTA
@@ -630,10 +632,10 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_flow(const __grid_constant__ 
         if (threadIdx.x == FLOW_QT) {
             // acq_rel: releases this CTA's writes (ordered before by the barrier) and, for the operation's
             // last item, acquires the other items' writes so that the publication below carries them
-            if (atom_add_acq_rel_gpu(cnt + box, 1) == flow_tiles(B.m, j) - 1) {
+            if (atom_add_acq_rel_gpu(cnt + box, 1) == flow_tiles(B.m, j, tpn) - 1) {
                 atomicExch(cnt + box, 0);
                 if (j + 1 < flow_chain(bz)) {
-                    const int n = flow_tiles(B.m, j + 1);
+                    const int n = flow_tiles(B.m, j + 1, tpn);
                     const int q0 = atomicAdd(tail, n);
                     for (int i = 0; i < n && ninit + q0 + i < total; ++i)
                         st_release_gpu(flag + q0 + i, flow_pack(box, j + 1, i));
@@ -741,7 +743,7 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
     };
     double gb, pb;
     if (flow && flow->mem && ctx->tc_flow && vec2 && flow_occ > 0 &&
-        (size_t)nrhs * (FLOW_TPN + 1) * sizeof(c64) <= (size_t)NST * Cfg::STAGE) {
+        (size_t)nrhs * (flow->tpn + 1) * sizeof(c64) <= (size_t)NST * Cfg::STAGE) {
         double all = 0;
         for (int pass = 0; pass < 2; ++pass)
             for (int s = pass == 0 ? 0 : 1; s < P.bz_max; ++s) {
@@ -754,7 +756,7 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
         tc_sweep_flow<E, NPAD, NST><<<grid, 128, Cfg::SMEM, st>>>(mapA, mapA32, mapB, P.dbox, coef, lb, loc, bt, 2 * ld,
                                                                    nrhs, P.pk_chunks, flow->init, flow->ninit,
                                                                    flow->flag, flow->total, flow->ctl, err,
-                                                                   (uint64_t)ctx->flow_wait_us * 1000ull);
+                                                                   (uint64_t)ctx->flow_wait_us * 1000ull, flow->tpn);
         prof_end(ctx, t, all);
         ctx->launches++;
         return cuda_check(ctx, cudaGetLastError(), "tensor-core plane sweeps (persistent)");
@@ -891,7 +893,12 @@ helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb_, 
     return dispatch_tc<float>(ctx, P, lb, loc, bt, npad, ns, nrhs, st, err, flow);
 }
 
-helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F) {
+int tc_flow_tpn(int nrhs) {
+    const int npair = std::max(1, nrhs / 2);
+    return std::max(16, std::min(FLOW_TPN_MAX, (1024 / npair) & ~15));
+}
+
+helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F, int tpn) {
     tc_flow_free(ctx, F);
     std::vector<int> init;
     long long total = 0;
@@ -900,9 +907,10 @@ helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F) {
     if (P.nbox >= 2048) return HELM_OK;
     for (int b = 0; b < P.nbox; ++b) {
         const BoxInfo& B = P.hbox[b];
-        if (flow_chain(B.dims[2]) > 1024 || flow_tiles(B.m, 0) > 1024 || flow_tiles(B.m, 1) > 1024) return HELM_OK;
-        for (int j = 0; j < flow_chain(B.dims[2]); ++j) total += flow_tiles(B.m, j);
-        for (int i = 0; i < flow_tiles(B.m, 0); ++i) init.push_back(flow_pack(b, 0, i));
+        if (flow_chain(B.dims[2]) > 1024 || flow_tiles(B.m, 0, tpn) > 1024 || flow_tiles(B.m, 1, tpn) > 1024)
+            return HELM_OK;
+        for (int j = 0; j < flow_chain(B.dims[2]); ++j) total += flow_tiles(B.m, j, tpn);
+        for (int i = 0; i < flow_tiles(B.m, 0, tpn); ++i) init.push_back(flow_pack(b, 0, i));
     }
     if (total >= (1ll << 30)) return HELM_OK;
     const size_t nctl = ((size_t)P.nbox + 2 + 3) / 4 * 4;   // ints, padded to 16 bytes
@@ -915,6 +923,7 @@ helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F) {
     F.init = F.flag + nflag;
     F.ninit = (int)init.size();
     F.total = (int)total;
+    F.tpn = tpn;
     HELM_CUDA(ctx, cudaMemcpyAsync(F.init, init.data(), init.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     HELM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return HELM_OK;
