@@ -207,6 +207,8 @@ def oracle_sample(W, iters_per_rhs, weights, repeats=1):
 # FGMRES restart of the request stream: the flexible basis of a 160^3 set with 64 columns then takes about 80 GB,
 # so that the largest requests fit beside others in the 150 GB budget
 SERVE_RESTART = 15
+# a serving phase gives up waiting after this long (the requests still open are reported as timed out)
+SERVE_PHASE_LIMIT_S = 240.0
 
 
 class RequestMix:
@@ -252,12 +254,21 @@ def serve_phase(helm, sv, mix, items, weights, arrivals=None):
     import ctypes as C
     import torch
     t0 = time.perf_counter()
+    deadline = t0 + SERVE_PHASE_LIMIT_S
     live = {}
     out = []
 
     def reap(block):
         for tk in list(live):
-            s = sv.wait(tk, timeout_s=1800) if block else sv.poll(tk)[1]
+            if block:
+                try:
+                    s = sv.wait(tk, timeout_s=max(1.0, deadline - time.perf_counter()))
+                except TimeoutError:   # reported as not done; the phase ends
+                    s = dict(sv.poll(tk)[1], done=False)
+                    out.append(dict(s, nrhs=live.pop(tk), timed_out=True))
+                    continue
+            else:
+                s = sv.poll(tk)[1]
             if s["done"]:
                 nr = live.pop(tk)
                 out.append(dict(s, nrhs=nr))
@@ -293,11 +304,13 @@ def run_serving(helm, device, stream, weights, args):
     res = {"mix": RequestMix.__doc__.split("\n\n")[0].replace("\n", " "), "budget_gb": 150, "slots_per_batch": 64}
 
     def summary(st, wall, rate=None):
-        lat = [s_["latency_ms"] for s_ in st]
-        rhs = sum(s_["nrhs"] for s_ in st)
-        ok = sum(1 for s_ in st if s_["status"] == helm.OK)
-        return {"requests": len(st), "ok": ok, "rhs": rhs, "wall_s": wall, "rhs_per_s": rhs / wall,
-                "requests_per_s": len(st) / wall, "p50_ms": float(np.percentile(lat, 50)),
+        done = [s_ for s_ in st if not s_.get("timed_out")]
+        lat = [s_["latency_ms"] for s_ in done] or [float("nan")]
+        rhs = sum(s_["nrhs"] for s_ in done if s_["status"] == helm.OK)
+        ok = sum(1 for s_ in done if s_["status"] == helm.OK)
+        return {"requests": len(st), "ok": ok, "timed_out": sum(1 for s_ in st if s_.get("timed_out")),
+                "rhs": rhs, "wall_s": wall, "rhs_per_s": rhs / wall,
+                "requests_per_s": len(done) / wall, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "arrival_rate_per_s": rate,
                 "factors_reused": sum(1 for s_ in st if s_["factors_reused"])}
 
@@ -307,7 +320,7 @@ def run_serving(helm, device, stream, weights, args):
         pos += args.serve_burst
         log(f"serving: burst of {len(burst)} requests")
         st, wall = serve_phase(helm, sv, mix, burst, weights)
-        sat = len(st) / wall
+        sat = max(1e-3, sum(1 for s_ in st if not s_.get("timed_out")) / wall)
         res["saturated"] = summary(st, wall)
         log(f"serving: saturated {sat:.2f} requests/s ({res['saturated']['rhs_per_s']:.1f} RHS/s) in {wall:.1f} s")
         rng = np.random.default_rng(synth.workload_seed(5) + 1)
@@ -987,10 +1000,10 @@ def main():
     ap.add_argument("--retune", action="store_true", help="ignore the tuning cache (time every candidate again)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the thrust-fold (256x256x96, 64 RHS) and attenuating (160x160x80, 3 x 128 RHS) lines")
-    ap.add_argument("--serve-requests", type=int, default=48,
+    ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the main serving phase (the full request-stream workload: 500)")
-    ap.add_argument("--serve-burst", type=int, default=16, help="requests of the saturated-rate burst")
-    ap.add_argument("--serve-sweep", type=int, default=12, help="requests per point of the arrival-rate sweep")
+    ap.add_argument("--serve-burst", type=int, default=10, help="requests of the saturated-rate burst")
+    ap.add_argument("--serve-sweep", type=int, default=6, help="requests per point of the arrival-rate sweep")
     args = ap.parse_args()
     W = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -333,11 +333,31 @@ struct Server {
         }
         if (fs->building || !fs->K) return false;
         if (fs->width < r->req.nrhs) {
-            // a wider engine for this set, made once its running columns have finished (and if it fits)
+            // a wider engine for this set, made once its running columns have finished, with room made by
+            // evicting other idle sets if needed
             if (fs->active > 0) return false;
             const int width = width_for(r->req.nrhs);
             const size_t more = engine_estimate(r->req, width) - engine_estimate(r->req, fs->width);
-            if (ctx->budget && ctx->in_use + reserved + more > ctx->budget) return false;
+            auto room = [&]() { return ctx->budget == 0 || ctx->in_use + reserved + more <= ctx->budget; };
+            while (!room()) {
+                FactorSet* lru = nullptr;
+                for (auto* s2 : sets)
+                    if (s2 != fs && !s2->building && s2->active == 0 && (!lru || s2->last_used < lru->last_used))
+                        lru = s2;
+                if (!lru) break;
+                sets.erase(std::find(sets.begin(), sets.end(), lru));
+                trace("evict model %llu (grid %d^3) to widen", (unsigned long long)lru->model_id, lru->gd.nx);
+                destroy_set(lru);
+            }
+            if (!room()) {
+                bool others = false;
+                for (auto* s2 : sets) others = others || (s2 != fs && (s2->building || s2->active > 0));
+                if (others) return false;   // room comes back when the others finish
+                set_error(ctx, HELM_ENOMEM, "request needs about %zu more bytes than the HBM budget leaves", more);
+                finish(r, HELM_ENOMEM);
+                return true;
+            }
+            trace("widen model %llu to %d columns", (unsigned long long)fs->model_id, width);
             helm_status st = HELM_OK;
             fs->K.reset();
             fs->K.reset(make_krylov_engine(fs->o, width, fs->restart, fs->flexible != 0, fs->basis_prec, nullptr,
