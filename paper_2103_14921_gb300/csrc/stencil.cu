@@ -479,12 +479,12 @@ __global__ void __launch_bounds__(128, 3) stencil_march(const c64* __restrict__ 
     const bool plain = i0 >= pl.lo[0] && min(i0 + MTX, nx) - 1 <= pl.hi[0] && j0 >= pl.lo[1] &&
                        min(j0 + MTY, ny) - 1 <= pl.hi[1] && k0 >= pl.lo[2] && k1 - 1 <= pl.hi[2];
     if (plain && skip_plain) return;
-    if (plain) march_run<SUB, REALK, true>(u, b, y, k2, tab, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
+    if (plain) march_run_plain<SUB, REALK>(u, b, y, k2, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
     else march_run<SUB, REALK, false>(u, b, y, k2, tab, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
 }
 
-// The plain blocks (a box of the block grid starting at block (bx0, by0, bz0)) in class-sum form, a kernel of
-// their own so that its register budget is that of the plain path alone.
+// The plain blocks (a box of the block grid starting at block (bx0, by0, bz0)) in class-sum form as a kernel of
+// their own (register budget of the plain path alone); kept for the split launch, which is not the default.
 template <bool SUB, bool REALK>
 __global__ void __launch_bounds__(128, 4) stencil_march_plain(const c64* __restrict__ u, const c64* __restrict__ b,
                                                              c64* __restrict__ y, const c64* __restrict__ k2, int nx,
@@ -624,7 +624,10 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
             }
             any = any && bhi[a] > blo[a];
         }
-        const int skip = any && g->ctx->stencil_march == 1 ? 1 : 0;
+        // the plain blocks run inside the same launch (class-sum form); a launch of their own left the two
+        // kernels each with a partly filled GPU (measured slower at 112^3)
+        const int skip = 0;
+        (void)any;
         if (g->k2_real)
             stencil_march<SUB, true><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
                                                           g->d.nx, g->d.ny, g->d.nz, g->w, pl, skip);

@@ -501,9 +501,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_gemm(const __grid_constant__ 
 // Both sweeps of every box in one launch.  Box b runs the chain of operations
 //   prep(0), gemm(0), prep(1), gemm(1), ..., prep(2 n_z - 2), gemm(2 n_z - 2)
 // (steps 0..n_z-1 forward, then n_z-1 backward steps), each operation split into items: row tiles of
-// 128 for a product, tiles of tpn nodes for an operand preparation (128 nodes at up to 16 right-hand sides,
-// fewer as the column count grows, so that a preparation item stays about as long as a product item and the
-// preparations of a step spread over more CTAs: tpn = 1024 / (column pairs) rounded down to 16, 16..128).  Items wait in a queue: the
+// 128 for a product, tiles of tpn nodes (the queue's tpn, 128) for an operand preparation.  Items wait in a queue: the
 // preparations of step 0 are there at the start (init), and the CTA that completes the last item of an
 // operation appends the items of the box's next operation.  Each CTA takes the next queue slot, waits
 // until that slot has been written, runs the item and counts it done.  A slot is written only after
@@ -894,8 +892,10 @@ helm_status planeset_solve_tc(helm_ctx ctx, const PlaneSet& P, const void* lb_, 
 }
 
 int tc_flow_tpn(int nrhs) {
-    const int npair = std::max(1, nrhs / 2);
-    return std::max(16, std::min(FLOW_TPN_MAX, (1024 / npair) & ~15));
+    // 128 nodes at every column count: smaller tiles at 128 columns (16 nodes) stage about 4.5 times the neighbour
+    // rows they use and measured slower (53 vs 42 ms per launch on 160 x 160 x 80 with 128 columns)
+    (void)nrhs;
+    return FLOW_TPN_MAX;
 }
 
 helm_status tc_flow_alloc(helm_ctx ctx, const PlaneSet& P, TcFlow& F, int tpn) {
