@@ -145,8 +145,8 @@ helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launche
  * Gauss-Jordan on the CUDA cores.  Read by oras_factor. */
 #define HELM_TUNE_TC_FACTOR 7
 /* HELM_TUNE_BLOCK_GJ: 1 (default) factors the other plane sets (FP64 and FP32 local factors, the FP64
- * coarse problem) by the same blocked Gauss-Jordan with block pivots on the CUDA cores (64-column panels,
- * the rank-64 updates spread over every SM), falling back to full partial pivoting after a tiny block
+ * coarse problem) by the same blocked Gauss-Jordan with block pivots on the CUDA cores (64-column panels for
+ * complex64, 32 for complex128; the rank-NB updates spread over every SM), falling back to full partial pivoting after a tiny block
  * pivot; 0 always uses the fully pivoted elimination.  Read by oras_factor. */
 #define HELM_TUNE_BLOCK_GJ 8
 helm_status helm_set_tuning(helm_ctx ctx, int key, int value);

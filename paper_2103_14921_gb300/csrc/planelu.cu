@@ -698,17 +698,20 @@ helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
 // ------------------------------------------------------------------ block-pivot Gauss-Jordan (CUDA cores)
 //
 // The same elimination as the tensor-core factorisation (planelu_tc.cu), for complex128 and complex64 sets
-// on the CUDA cores: 64-column panels J, P = A[J,J]^{-1} with partial pivoting inside the block,
+// on the CUDA cores: NB-column panels J (BgjNB), P = A[J,J]^{-1} with partial pivoting inside the block,
 // A[J,:] = P A[J,:] (A[J,J] = P), and for the rows outside J A[I,j] = [j not in J] A[I,j] - W[I,:] A[J,j]
-// with W = A[:, J] copied before the step.  The rank-64 update is spread over every SM (64 x 64 output
+// with W = A[:, J] copied before the step.  The rank-NB update is spread over every SM (64 x 64 output
 // tiles), where the fully pivoted elimination above eliminates one column at a time in one CTA per box.
-constexpr int BGJ_NB = 64;
+// panel width: 64 columns for complex64 sets, 32 for complex128 (the block inverse's cost per panel grows as NB^3
+// and runs in one CTA per box on the FP64 pipe; the coarse problem is a single box)
+template <typename T> struct BgjNB { static constexpr int v = 64; };
+template <> struct BgjNB<double> { static constexpr int v = 32; };
 
 template <typename T>
 __global__ void __launch_bounds__(512) bgj_diag(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ S,
                                                 int m_max, cplx<T>* __restrict__ Pbuf, int* __restrict__ flag, int j0,
                                                 int k) {
-    constexpr int NB = BGJ_NB, DP = BGJ_NB + 1;
+    constexpr int NB = BgjNB<T>::v, DP = NB + 1;
     extern __shared__ __align__(16) unsigned char bgj_sm[];
     cplx<T>* X = reinterpret_cast<cplx<T>*>(bgj_sm);   // [NB][DP]
     __shared__ cplx<T> s_row[NB], s_col[NB];
@@ -755,7 +758,7 @@ __global__ void __launch_bounds__(512) bgj_diag(const BoxInfo* __restrict__ boxe
 template <typename T>
 __global__ void __launch_bounds__(256) bgj_rows(const BoxInfo* __restrict__ boxes, cplx<T>* __restrict__ S, int m_max,
                                                 const cplx<T>* __restrict__ Pbuf, int j0, int k) {
-    constexpr int NB = BGJ_NB;
+    constexpr int NB = BgjNB<T>::v;
     __shared__ cplx<T> Ps[NB][17];
     __shared__ cplx<T> As[16][64];
     const BoxInfo B = boxes[blockIdx.y];
@@ -810,7 +813,7 @@ __global__ void __launch_bounds__(256) bgj_rows(const BoxInfo* __restrict__ boxe
 template <typename T>
 __global__ void bgj_wcopy(const BoxInfo* __restrict__ boxes, const cplx<T>* __restrict__ S, int m_max,
                           cplx<T>* __restrict__ Wbuf, int j0, int k) {
-    constexpr int NB = BGJ_NB;
+    constexpr int NB = BgjNB<T>::v;
     const BoxInfo B = boxes[blockIdx.y];
     const int m = B.m;
     if (k >= B.dims[2] || j0 >= m) return;
@@ -827,13 +830,13 @@ __global__ void bgj_wcopy(const BoxInfo* __restrict__ boxes, const cplx<T>* __re
 template <typename T>
 __global__ void __launch_bounds__(256) bgj_update(const BoxInfo* __restrict__ boxes, cplx<T>* __restrict__ S,
                                                   int m_max, const cplx<T>* __restrict__ Wbuf, int j0, int k) {
-    constexpr int NB = BGJ_NB;
+    constexpr int NB = BgjNB<T>::v;
     const BoxInfo B = boxes[blockIdx.z];
     const int m = B.m;
     if (k >= B.dims[2] || j0 >= m) return;
     const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
-    if (r0 >= m || c0 >= m || r0 == j0) return;   // the tile of rows J (NB == 64, j0 % 64 == 0)
     const int nbw = min(NB, m - j0);
+    if (r0 >= m || c0 >= m || (r0 >= j0 && r0 + 64 <= j0 + nbw)) return;   // a tile of rows J only
     cplx<T>* A = S + (size_t)blockIdx.z * m_max * m_max;
     const cplx<T>* W = Wbuf + (size_t)blockIdx.z * m_max * NB;
     __shared__ cplx<T> Ws[64][17];
@@ -869,7 +872,7 @@ __global__ void __launch_bounds__(256) bgj_update(const BoxInfo* __restrict__ bo
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int r = r0 + ty + 16 * a;
-        if (r >= m) continue;
+        if (r >= m || (r >= j0 && r < j0 + nbw)) continue;   // rows J hold the panel's new rows
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int j = c0 + tx + 16 * b;
@@ -901,7 +904,7 @@ template <typename T>
 helm_status factor_block_t(helm_ctx ctx, PlaneSet& P, int* singular, int* weak) {
     *singular = *weak = 0;
     cudaStream_t st = ctx->stream;
-    constexpr int NB = BGJ_NB;
+    constexpr int NB = BgjNB<T>::v;
     const size_t mm = (size_t)P.m_max * P.m_max;
     cplx<T>*S = nullptr, *Tm = nullptr, *W = nullptr, *Pb = nullptr;
     int* flag = nullptr;
