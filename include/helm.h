@@ -149,6 +149,12 @@ helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launche
  * complex64, 32 for complex128; the rank-NB updates spread over every SM), falling back to full partial pivoting after a tiny block
  * pivot; 0 always uses the fully pivoted elimination.  Read by oras_factor. */
 #define HELM_TUNE_BLOCK_GJ 8
+/* HELM_TUNE_STENCIL_PLANES: output planes per block of the z-marching stencil (HELM_TUNE_STENCIL_MARCH);
+ * 0 (default) picks, per grid, the longest walks (at most 64 planes, at least 8) that still give every
+ * resident block slot two blocks or more; else 4..128.  The split decides which blocks
+ * lie wholly inside the interior (and take the cheaper class-sum form), so results differ with it by FP32
+ * rounding only.  Captured graphs are re-captured after a change. */
+#define HELM_TUNE_STENCIL_PLANES 9
 helm_status helm_set_tuning(helm_ctx ctx, int key, int value);
 
 /* ------------------------------------------------------------ grid / model */

@@ -132,6 +132,13 @@ extern "C" helm_status helm_set_tuning(helm_ctx ctx, int key, int value) {
         ctx->tc_factor = value;
         return HELM_OK;
     }
+    if (key == HELM_TUNE_STENCIL_PLANES) {
+        if (value != 0 && (value < 4 || value > 128))
+            return set_error(ctx, HELM_EINVAL, "helm_set_tuning: stencil_planes must be 0 or 4..128");
+        ctx->stencil_planes = value;
+        ctx->graph_gen++;
+        return HELM_OK;
+    }
     if (key == HELM_TUNE_BLOCK_GJ) {
         if (value != 0 && value != 1) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: block_gj must be 0 or 1");
         ctx->block_gj = value;

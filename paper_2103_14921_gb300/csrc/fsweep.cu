@@ -97,6 +97,7 @@ extern "C" helm_status helm_frequency_sweep(helm_ctx ctx, const helm_sweep_desc*
         ctx2->use_graphs = ctx->use_graphs;
         ctx2->tc_flow = ctx->tc_flow;
         ctx2->stencil_march = ctx->stencil_march;
+        ctx2->stencil_planes = ctx->stencil_planes;
     }
     auto ctx_of = [&](int i) { return (d->overlap && (i & 1)) ? ctx2 : ctx; };
 

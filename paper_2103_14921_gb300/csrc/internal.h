@@ -74,7 +74,8 @@ struct helm_ctx_s {
     int coarse_coop = 1;       // tuning: one cooperative launch for the complex64 coarse sweeps
     int use_graphs = 1;        // tuning: Krylov iterations replayed from captured CUDA graphs
     int tc_flow = 1;           // tuning: tensor-core sweeps as one persistent launch with a work queue
-    int stencil_march = 1;     // tuning: complex64 16-column stencils walk z-planes (in-plane terms reused)
+    int stencil_march = 1;     // tuning: complex64 stencils (16-column chunks) walk z-planes (in-plane terms reused)
+    int stencil_planes = 0;    // tuning: output planes per z-march block (0 = chosen per grid)
     long long flow_wait_us = 2000000;   // tuning: bound of the persistent sweep's queue-slot wait (microseconds)
     int tc_factor = 1;         // tuning: tensor-core blocked Gauss-Jordan for complex64 tensor-core factor sets
     int block_gj = 1;          // tuning: block-pivot Gauss-Jordan on the CUDA cores for the other factor sets

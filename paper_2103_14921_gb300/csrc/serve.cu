@@ -567,6 +567,7 @@ extern "C" helm_status helm_serve_start(helm_ctx ctx, int slots) {
     sv->bctx->use_graphs = ctx->use_graphs;
     sv->bctx->tc_flow = ctx->tc_flow;
     sv->bctx->stencil_march = ctx->stencil_march;
+    sv->bctx->stencil_planes = ctx->stencil_planes;
     sv->bctx->tc_factor = ctx->tc_factor;
     ctx->server = sv;
     sv->bth = std::thread([sv]() { sv->build_loop(); });

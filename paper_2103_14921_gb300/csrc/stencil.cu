@@ -181,42 +181,79 @@ __global__ void __launch_bounds__(128) stencil_kernel(const cplx<T>* __restrict_
     *reinterpret_cast<CPack<T, RCH>*>(y + p * nrhs + (long long)ch * RCH) = out;
 }
 
-// ---------------------------------------------------------------- z-march (complex64, 16 columns)
+// ---------------------------------------------------------------- z-march (complex64, columns in chunks of 16)
 //
 // The same operator grouped by z-planes: with D_a the stretched and P_a the plain second differences,
 //   A u = h^-2 [S0 + D_z S1] + [T0 + P_z T1],
 //   S0 = (D_x + D_y) u + a2 D_x D_y u,   S1 = u + a2 (D_x + D_y) u + a3 D_x D_y u,
 //   T0 = m0 v + m1 (P_x + P_y) v + m2 P_x P_y v,   T1 = m1 v + m2 (P_x + P_y) v + m3 P_x P_y v,   v = k^2 u,
 // where S0, S1, T0, T1 are in-plane.  A thread owns MN consecutive x-nodes of one row j and one column pair
-// and walks a chunk of MZC output planes: for every plane q it loads the (MN + 2) x 3 in-plane neighbourhood
+// and walks a chunk of output planes (a launch parameter): for every plane q it loads the (MN + 2) x 3 in-plane neighbourhood
 // once, forms the in-plane terms of its nodes, and adds their contributions to the outputs q - 1 (last
 // term, then stored), q and q + 1 (first term).  Each output therefore costs (MN + 2) * 3 / MN vector loads
 // instead of 27.  Blocks whose rows all have plain (1, -2, 1) 1-D coefficients take the real-coefficient
 // path; the others use the complex table coefficients.  Ghost nodes contribute zero.
 constexpr int MN = 4;      // x-nodes per thread
-constexpr int MZC = 16;    // output planes per block
 constexpr int MNP = 8;     // column pairs (16 columns)
 
 struct PlainRange {
     int lo[3], hi[3];   // per axis: indices whose stretched coefficients are exactly (1, -2, 1)
 };
 
+// Two complex64 values (re0, im0, re1, im1) in a float4, processed as two (re, im) pairs by the packed FP32
+// instructions (two lanes per instruction, each lane rounded like the scalar operation).
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float2 sw2(float2 a) { return make_float2(a.y, a.x); }
 __device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
-__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return cat4(__fadd2_rn(lo2(a), lo2(b)), __fadd2_rn(hi2(a), hi2(b)));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) {
+    const float2 m = make_float2(-1.f, -1.f);
+    return cat4(__ffma2_rn(m, lo2(b), lo2(a)), __ffma2_rn(m, hi2(b), hi2(a)));
+}
+// s b (s real)
+__device__ __forceinline__ float4 scal4(float s, float4 b) {
+    const float2 ss = make_float2(s, s);
+    return cat4(__fmul2_rn(ss, lo2(b)), __fmul2_rn(ss, hi2(b)));
+}
 // a + s b (s real)
 __device__ __forceinline__ float4 axpy4(float s, float4 b, float4 a) {
-    return make_float4(fmaf(s, b.x, a.x), fmaf(s, b.y, a.y), fmaf(s, b.z, a.z), fmaf(s, b.w, a.w));
+    const float2 ss = make_float2(s, s);
+    return cat4(__ffma2_rn(ss, lo2(b), lo2(a)), __ffma2_rn(ss, hi2(b), hi2(a)));
 }
-// a + c b (c complex, b two complex values)
+// a + c b (c complex, b two complex values): per value re = c.x b.re + (-c.y b.im + a.re),
+// im = c.x b.im + (c.y b.re + a.im)
 __device__ __forceinline__ float4 caxpy4(c64 c, float4 b, float4 a) {
-    return make_float4(fmaf(c.x, b.x, fmaf(-c.y, b.y, a.x)), fmaf(c.x, b.y, fmaf(c.y, b.x, a.y)),
-                       fmaf(c.x, b.z, fmaf(-c.y, b.w, a.z)), fmaf(c.x, b.w, fmaf(c.y, b.z, a.w)));
+    const float2 cr = make_float2(c.x, c.x), ci = make_float2(-c.y, c.y);
+    return cat4(__ffma2_rn(cr, lo2(b), __ffma2_rn(ci, sw2(lo2(b)), lo2(a))),
+                __ffma2_rn(cr, hi2(b), __ffma2_rn(ci, sw2(hi2(b)), hi2(a))));
 }
-// the 3-point second difference c0 x0 + c1 x1 + c2 x2, plain (1, -2, 1) or with complex coefficients
+// c b (c complex)
+__device__ __forceinline__ float4 cmul4(c64 c, float4 b) {
+    const float2 cr = make_float2(c.x, c.x), ci = make_float2(-c.y, c.y);
+    return cat4(__ffma2_rn(cr, lo2(b), __fmul2_rn(ci, sw2(lo2(b)))),
+                __ffma2_rn(cr, hi2(b), __fmul2_rn(ci, sw2(hi2(b)))));
+}
+// A complex coefficient c as the pairs (c.re, c.re, c.im, c.im) of one float4.
+__device__ __forceinline__ float4 cpair(c64 c) { return make_float4(c.x, c.x, c.y, c.y); }
+// the 3-point second difference c0 x0 + c1 x1 + c2 x2, plain (1, -2, 1) or with complex coefficients given as
+// pairs: per value the real-coefficient sum R = sum re(c_d) x_d and the imaginary one I = sum im(c_d) x_d are
+// formed first and combined once, R + i I = (R.re - I.im, R.im + I.re)
 template <bool PLAIN>
-__device__ __forceinline__ float4 d3(const c64* c, float4 x0, float4 x1, float4 x2) {
+__device__ __forceinline__ float4 d3(const float4* c, float4 x0, float4 x1, float4 x2) {
     if (PLAIN) return axpy4(-2.f, x1, add4(x0, x2));
-    return caxpy4(c[2], x2, caxpy4(c[1], x1, caxpy4(c[0], x0, f4(0.f))));
+    const float2 j = make_float2(-1.f, 1.f);
+    float2 r[2], im[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 v0 = h ? hi2(x0) : lo2(x0), v1 = h ? hi2(x1) : lo2(x1), v2 = h ? hi2(x2) : lo2(x2);
+        r[h] = __ffma2_rn(lo2(c[2]), v2, __ffma2_rn(lo2(c[1]), v1, __fmul2_rn(lo2(c[0]), v0)));
+        im[h] = __ffma2_rn(hi2(c[2]), v2, __ffma2_rn(hi2(c[1]), v1, __fmul2_rn(hi2(c[0]), v0)));
+    }
+    return cat4(__ffma2_rn(j, sw2(im[0]), r[0]), __ffma2_rn(j, sw2(im[1]), r[1]));
 }
 
 // The block's planes pass through shared memory: a 128-thread block covers 16 x-nodes x 4 rows x 16
@@ -242,16 +279,16 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // issue the copies of plane q (rows j0-1..j0+MTY, nodes i0-1..i0+MTX); out-of-grid entries become zero
-__device__ __forceinline__ void march_stage(float4* su, float2* sk, const c64* __restrict__ u,
-                                            const c64* __restrict__ k2, int nx, int ny, int nz, int i0, int j0,
-                                            int q) {
+__device__ __forceinline__ void march_stage(float4* su, float2* sk, const float4* __restrict__ u,
+                                            const c64* __restrict__ k2, int nx, int ny, int nz, int nrs, int i0,
+                                            int j0, int q) {
     const bool qin = q >= 0 && q < nz;
     for (int e = threadIdx.x; e < MBUF_U; e += blockDim.x) {
         const int pc = e % MNP, xn = (e / MNP) % MBX, yr = e / (MNP * MBX);
         const int ii = i0 + xn - 1, jj = j0 + yr - 1;
         const bool ok = qin && ii >= 0 && ii < nx && jj >= 0 && jj < ny;
         const long long node = ok ? ((long long)q * ny + jj) * nx + ii : 0;
-        cp_async16(su + e, reinterpret_cast<const float4*>(u + node * (2 * MNP)) + pc, ok);
+        cp_async16(su + e, u + node * nrs + pc, ok);
     }
     for (int e = threadIdx.x; e < MBUF_K; e += blockDim.x) {
         const int xn = e % MBX, yr = e / MBX;
@@ -262,38 +299,43 @@ __device__ __forceinline__ void march_stage(float4* su, float2* sk, const c64* _
     }
 }
 
-template <bool SUB, bool REALK, bool PLAIN>
-__device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* __restrict__ b, c64* __restrict__ y,
-                                          const c64* __restrict__ k2, const c64* __restrict__ tab, int nx, int ny,
-                                          int nz, const StencilW& w, int i0, int j0, int k0, int k1, float4* su,
-                                          float2* sk) {
+// march_run in product form for blocks in the absorbing layers; PX, PY, PZ: the block's rows have plain
+// (1, -2, 1) coefficients along that axis (a block in one layer only is stretched along one axis), so only the
+// stretched axes pay complex products.  The x coefficients of the block's 16 nodes sit in shared memory as
+// pairs (sx, filled before the first barrier of the plane loop), the row's y coefficients in registers.
+template <bool SUB, bool REALK, bool PX, bool PY, bool PZ>
+__device__ __forceinline__ void march_run(const float4* __restrict__ u, const float4* __restrict__ b,
+                                          float4* __restrict__ y, const c64* __restrict__ k2,
+                                          const c64* __restrict__ tab, int nx, int ny, int nz, int nrs,
+                                          const StencilW& w, int i0, int j0, int k0, int k1, float4* su, float2* sk,
+                                          float4* sx) {
     const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
     const int pc = lane % MNP, g = lane / MNP;
     const int j = j0 + wr, xb = g * MN, ib = i0 + xb;
     const bool live = j < ny;
     const float ih2 = (float)w.inv_h2, a2 = (float)w.a2, a3 = (float)w.a3;
     const float m0 = (float)w.m0, m1 = (float)w.m1, m2 = (float)w.m2, m3 = (float)w.m3;
-    c64 X[MN][3], Y[3];
-    if (!PLAIN) {
+    if (!PX && threadIdx.x < MTX * 3) {
+        const int n = threadIdx.x / 3, d = threadIdx.x % 3;
+        sx[threadIdx.x] = i0 + n < nx ? cpair(tab[3 * (i0 + n) + d]) : f4(0.f);
+    }
+    float4 Y[3];
+    if (!PY) {
 #pragma unroll
-        for (int c = 0; c < MN; ++c)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) X[c][d] = ib + c < nx ? tab[3 * (ib + c) + d] : mk<float>(0, 0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) Y[d] = live ? tab[3 * (nx + j) + d] : mk<float>(0, 0);
+        for (int d = 0; d < 3; ++d) Y[d] = live ? cpair(tab[3 * (nx + j) + d]) : f4(0.f);
     }
     const c64* tz = tab + 3 * (nx + ny);
     float4 P[MN], N[MN];   // outputs q and q + 1, partial
 #pragma unroll
     for (int c = 0; c < MN; ++c) P[c] = N[c] = f4(0.f);
-    march_stage(su, sk, u, k2, nx, ny, nz, i0, j0, k0 - 1);
+    march_stage(su, sk, u, k2, nx, ny, nz, nrs, i0, j0, k0 - 1);
     cp_async_commit();
-    march_stage(su + MBUF_U, sk + MBUF_K, u, k2, nx, ny, nz, i0, j0, k0);
+    march_stage(su + MBUF_U, sk + MBUF_K, u, k2, nx, ny, nz, nrs, i0, j0, k0);
     cp_async_commit();
     for (int q = k0 - 1, buf = 0; q <= k1; ++q, buf = buf == MNBUF - 1 ? 0 : buf + 1) {
         // prefetch plane q + 2 into the buffer plane q - 1 used (free since the barrier ending the last step)
         const int nb = buf >= 1 ? buf - 1 : MNBUF - 1;
-        if (q + 2 <= k1) march_stage(su + nb * MBUF_U, sk + nb * MBUF_K, u, k2, nx, ny, nz, i0, j0, q + 2);
+        if (q + 2 <= k1) march_stage(su + nb * MBUF_U, sk + nb * MBUF_K, u, k2, nx, ny, nz, nrs, i0, j0, q + 2);
         cp_async_commit();
         cp_async_wait<2>();
         __syncthreads();
@@ -304,15 +346,14 @@ __device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* 
             for (int c = 0; c < MN; ++c) {
                 bq[c] = f4(0.f);
                 if (live && q - 1 >= k0 && ib + c < nx)
-                    bq[c] = __ldg(reinterpret_cast<const float4*>(b + (((long long)(q - 1) * ny + j) * nx + ib + c) *
-                                                                     (2 * MNP)) + pc);
+                    bq[c] = __ldg(b + (((long long)(q - 1) * ny + j) * nx + ib + c) * nrs + pc);
             }
         }
         const float4* cu = su + buf * MBUF_U;
         const float2* ck = sk + buf * MBUF_K;
         const bool qin = q >= 0 && q < nz;
-        c64 zm = mk<float>(1.f, 0.f), zc = mk<float>(-2.f, 0.f), zp = mk<float>(1.f, 0.f);
-        if (!PLAIN) {
+        c64 zm = mk<float>(0, 0), zc = mk<float>(0, 0), zp = mk<float>(0, 0);
+        if (!PZ) {
             zm = q - 1 >= 0 && q - 1 < nz ? tz[3 * (q - 1) + 2] : mk<float>(0, 0);
             zc = qin ? tz[3 * q + 1] : mk<float>(0, 0);
             zp = q + 1 >= 0 && q + 1 < nz ? tz[3 * (q + 1) + 0] : mk<float>(0, 0);
@@ -327,10 +368,9 @@ __device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* 
                 const int sidx = (wr + r) * MBX + xb + n;
                 Ur[r] = cu[sidx * MNP + pc];
                 const float2 kk = ck[sidx];
-                if (REALK) V[r] = make_float4(kk.x * Ur[r].x, kk.x * Ur[r].y, kk.x * Ur[r].z, kk.x * Ur[r].w);
-                else V[r] = caxpy4(mk<float>(kk.x, kk.y), Ur[r], f4(0.f));
+                V[r] = REALK ? scal4(kk.x, Ur[r]) : cmul4(mk<float>(kk.x, kk.y), Ur[r]);
             }
-            DyU[slot] = d3<PLAIN>(Y, Ur[0], Ur[1], Ur[2]);
+            DyU[slot] = d3<PY>(Y, Ur[0], Ur[1], Ur[2]);
             PyV[slot] = d3<true>(nullptr, V[0], V[1], V[2]);
             V1[slot] = V[1];
             U1[slot] = Ur[1];
@@ -341,30 +381,34 @@ __device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* 
         for (int c = 0; c < MN; ++c) {
             column(c + 2, (c + 2) % 3);
             const int s0 = c % 3, s1 = (c + 1) % 3, s2 = (c + 2) % 3;
+            float4 X[3];
+            if (!PX) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) X[d] = sx[(xb + c) * 3 + d];
+            }
             const float4 u0 = U1[s1];
-            const float4 Eu = add4(d3<PLAIN>(PLAIN ? nullptr : X[c], U1[s0], U1[s1], U1[s2]), DyU[s1]);
-            const float4 Fu = d3<PLAIN>(PLAIN ? nullptr : X[c], DyU[s0], DyU[s1], DyU[s2]);
+            const float4 Eu = add4(d3<PX>(X, U1[s0], U1[s1], U1[s2]), DyU[s1]);
+            const float4 Fu = d3<PX>(X, DyU[s0], DyU[s1], DyU[s2]);
             const float4 v0 = V1[s1];
             const float4 Ev = add4(d3<true>(nullptr, V1[s0], V1[s1], V1[s2]), PyV[s1]);
             const float4 Fv = d3<true>(nullptr, PyV[s0], PyV[s1], PyV[s2]);
             const float4 S0 = axpy4(a2, Fu, Eu);
             const float4 S1 = axpy4(a3, Fu, axpy4(a2, Eu, u0));
-            const float4 T0 = axpy4(m2, Fv, axpy4(m1, Ev, make_float4(m0 * v0.x, m0 * v0.y, m0 * v0.z, m0 * v0.w)));
-            const float4 T1 = axpy4(m3, Fv, axpy4(m2, Ev, make_float4(m1 * v0.x, m1 * v0.y, m1 * v0.z, m1 * v0.w)));
-            const float4 hS1 = make_float4(ih2 * S1.x, ih2 * S1.y, ih2 * S1.z, ih2 * S1.w);
+            const float4 T0 = axpy4(m2, Fv, axpy4(m1, Ev, scal4(m0, v0)));
+            const float4 T1 = axpy4(m3, Fv, axpy4(m2, Ev, scal4(m1, v0)));
+            const float4 hS1 = scal4(ih2, S1);
             // output q - 1: its last term
             const int i = ib + c;
             if (live && q - 1 >= k0 && i < nx) {
-                float4 o = add4(PLAIN ? add4(P[c], hS1) : caxpy4(zm, hS1, P[c]), T1);
+                float4 o = add4(PZ ? add4(P[c], hS1) : caxpy4(zm, hS1, P[c]), T1);
                 const long long node = ((long long)(q - 1) * ny + j) * nx + i;
-                float4* dst = reinterpret_cast<float4*>(y + node * (2 * MNP)) + pc;
-                if (SUB) o = make_float4(bq[c].x - o.x, bq[c].y - o.y, bq[c].z - o.z, bq[c].w - o.w);
-                __stcs(dst, o);
+                if (SUB) o = sub4(bq[c], o);
+                __stcs(y + node * nrs + pc, o);
             }
             // output q: the centre term; output q + 1: its first term
             float4 pn = add4(N[c], axpy4(ih2, S0, axpy4(-2.f, T1, T0)));
-            pn = PLAIN ? axpy4(-2.f, hS1, pn) : caxpy4(zc, hS1, pn);
-            N[c] = add4(PLAIN ? hS1 : caxpy4(zp, hS1, f4(0.f)), T1);
+            pn = PZ ? axpy4(-2.f, hS1, pn) : caxpy4(zc, hS1, pn);
+            N[c] = add4(PZ ? hS1 : cmul4(zp, hS1), T1);
             P[c] = pn;
         }
         __syncthreads();   // buffer buf is refilled by the next step's prefetch
@@ -381,10 +425,10 @@ __device__ __forceinline__ void march_run(const c64* __restrict__ u, const c64* 
 // constants Lc = {-6 + 12 a2 - 8 a3, 1 - 4 a2 + 4 a3, a2 - 2 a3, a3} / h^2 and Mc = {m0 - 6 m1 + 12 m2 - 8 m3,
 // m1 - 4 m2 + 4 m3, m2 - 2 m3, m3}.  The same operator as the product form (expanded), in fewer operations.
 template <bool SUB, bool REALK>
-__device__ __forceinline__ void march_run_plain(const c64* __restrict__ u, const c64* __restrict__ b,
-                                                c64* __restrict__ y, const c64* __restrict__ k2, int nx, int ny,
-                                                int nz, const StencilW& w, int i0, int j0, int k0, int k1, float4* su,
-                                                float2* sk) {
+__device__ __forceinline__ void march_run_plain(const float4* __restrict__ u, const float4* __restrict__ b,
+                                                float4* __restrict__ y, const c64* __restrict__ k2, int nx, int ny,
+                                                int nz, int nrs, const StencilW& w, int i0, int j0, int k0, int k1,
+                                                float4* su, float2* sk) {
     const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
     const int pc = lane % MNP, g = lane / MNP;
     const int j = j0 + wr, xb = g * MN, ib = i0 + xb;
@@ -397,13 +441,13 @@ __device__ __forceinline__ void march_run_plain(const c64* __restrict__ u, const
     float4 P[MN], N[MN];
 #pragma unroll
     for (int c = 0; c < MN; ++c) P[c] = N[c] = f4(0.f);
-    march_stage(su, sk, u, k2, nx, ny, nz, i0, j0, k0 - 1);
+    march_stage(su, sk, u, k2, nx, ny, nz, nrs, i0, j0, k0 - 1);
     cp_async_commit();
-    march_stage(su + MBUF_U, sk + MBUF_K, u, k2, nx, ny, nz, i0, j0, k0);
+    march_stage(su + MBUF_U, sk + MBUF_K, u, k2, nx, ny, nz, nrs, i0, j0, k0);
     cp_async_commit();
     for (int q = k0 - 1, buf = 0; q <= k1; ++q, buf = buf == MNBUF - 1 ? 0 : buf + 1) {
         const int nb = buf >= 1 ? buf - 1 : MNBUF - 1;
-        if (q + 2 <= k1) march_stage(su + nb * MBUF_U, sk + nb * MBUF_K, u, k2, nx, ny, nz, i0, j0, q + 2);
+        if (q + 2 <= k1) march_stage(su + nb * MBUF_U, sk + nb * MBUF_K, u, k2, nx, ny, nz, nrs, i0, j0, q + 2);
         cp_async_commit();
         cp_async_wait<2>();
         __syncthreads();
@@ -413,8 +457,7 @@ __device__ __forceinline__ void march_run_plain(const c64* __restrict__ u, const
             for (int c = 0; c < MN; ++c) {
                 bq[c] = f4(0.f);
                 if (live && q - 1 >= k0 && ib + c < nx)
-                    bq[c] = __ldg(reinterpret_cast<const float4*>(b + (((long long)(q - 1) * ny + j) * nx + ib + c) *
-                                                                     (2 * MNP)) + pc);
+                    bq[c] = __ldg(b + (((long long)(q - 1) * ny + j) * nx + ib + c) * nrs + pc);
             }
         }
         const float4* cu = su + buf * MBUF_U;
@@ -428,8 +471,7 @@ __device__ __forceinline__ void march_run_plain(const c64* __restrict__ u, const
                 const int sidx = (wr + r) * MBX + xb + n;
                 U[r] = cu[sidx * MNP + pc];
                 const float2 kk = ck[sidx];
-                if (REALK) V[r] = make_float4(kk.x * U[r].x, kk.x * U[r].y, kk.x * U[r].z, kk.x * U[r].w);
-                else V[r] = caxpy4(mk<float>(kk.x, kk.y), U[r], f4(0.f));
+                V[r] = REALK ? scal4(kk.x, U[r]) : cmul4(mk<float>(kk.x, kk.y), U[r]);
             }
             Cu[slot] = U[1];
             Cv[slot] = V[1];
@@ -447,16 +489,15 @@ __device__ __forceinline__ void march_run_plain(const c64* __restrict__ u, const
             const float4 FV = add4(add4(Cv[s0], Cv[s2]), Yv[s1]), EV = add4(Yv[s0], Yv[s2]);
             // plane q's contribution to output q (A0) and to outputs q -/+ 1 (A1)
             const float4 A0 = axpy4(M2, EV, axpy4(M1, FV, axpy4(M0, cV, axpy4(L2, EU, axpy4(L1, FU,
-                                  make_float4(L0 * cU.x, L0 * cU.y, L0 * cU.z, L0 * cU.w))))));
+                                  scal4(L0, cU))))));
             const float4 A1 = axpy4(M3, EV, axpy4(M2, FV, axpy4(M1, cV, axpy4(L3, EU, axpy4(L2, FU,
-                                  make_float4(L1 * cU.x, L1 * cU.y, L1 * cU.z, L1 * cU.w))))));
+                                  scal4(L1, cU))))));
             const int i = ib + c;
             if (live && q - 1 >= k0 && i < nx) {
                 float4 o = add4(P[c], A1);
                 const long long node = ((long long)(q - 1) * ny + j) * nx + i;
-                float4* dst = reinterpret_cast<float4*>(y + node * (2 * MNP)) + pc;
-                if (SUB) o = make_float4(bq[c].x - o.x, bq[c].y - o.y, bq[c].z - o.z, bq[c].w - o.w);
-                __stcs(dst, o);
+                if (SUB) o = sub4(bq[c], o);
+                __stcs(y + node * nrs + pc, o);
             }
             P[c] = add4(N[c], A0);
             N[c] = A1;
@@ -466,34 +507,38 @@ __device__ __forceinline__ void march_run_plain(const c64* __restrict__ u, const
     cp_async_wait<0>();
 }
 
+// grid: (x-node blocks, row blocks, plane chunks x column chunks); the column chunk (16 columns) is the
+// fastest part of blockIdx.z, so the chunks of one node range run side by side
 template <bool SUB, bool REALK>
 __global__ void __launch_bounds__(128, 3) stencil_march(const c64* __restrict__ u, const c64* __restrict__ b,
                                                      c64* __restrict__ y, const c64* __restrict__ k2,
-                                                     const c64* __restrict__ tab, int nx, int ny, int nz, StencilW w,
-                                                     PlainRange pl, int skip_plain) {
+                                                     const c64* __restrict__ tab, int nx, int ny, int nz, int nrhs,
+                                                     int mzc, StencilW w, PlainRange pl) {
     __shared__ float4 su[MNBUF * MBUF_U];
     __shared__ float2 sk[MNBUF * MBUF_K];
+    __shared__ float4 sx[MTX * 3];
+    const int nrs = nrhs >> 1, ncc = nrs / MNP;   // float4 per node, column chunks
+    const int cc = blockIdx.z % ncc, zc = blockIdx.z / ncc;
     const int i0 = blockIdx.x * MTX, j0 = blockIdx.y * MTY;
-    const int k0 = blockIdx.z * MZC, k1 = min(k0 + MZC, nz);
-    // blocks whose rows all have plain coefficients on every axis are left to stencil_march_plain
+    const int k0 = zc * mzc, k1 = min(k0 + mzc, nz);
+    const float4* u4 = reinterpret_cast<const float4*>(u) + cc * MNP;
+    const float4* b4 = SUB ? reinterpret_cast<const float4*>(b) + cc * MNP : nullptr;
+    float4* y4 = reinterpret_cast<float4*>(y) + cc * MNP;
+    // blocks whose rows all have plain coefficients on every axis take the class-sum form
     const bool plain = i0 >= pl.lo[0] && min(i0 + MTX, nx) - 1 <= pl.hi[0] && j0 >= pl.lo[1] &&
                        min(j0 + MTY, ny) - 1 <= pl.hi[1] && k0 >= pl.lo[2] && k1 - 1 <= pl.hi[2];
-    if (plain && skip_plain) return;
-    if (plain) march_run_plain<SUB, REALK>(u, b, y, k2, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
-    else march_run<SUB, REALK, false>(u, b, y, k2, tab, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
-}
-
-// The plain blocks (a box of the block grid starting at block (bx0, by0, bz0)) in class-sum form as a kernel of
-// their own (register budget of the plain path alone); kept for the split launch, which is not the default.
-template <bool SUB, bool REALK>
-__global__ void __launch_bounds__(128, 4) stencil_march_plain(const c64* __restrict__ u, const c64* __restrict__ b,
-                                                             c64* __restrict__ y, const c64* __restrict__ k2, int nx,
-                                                             int ny, int nz, StencilW w, int bx0, int by0, int bz0) {
-    __shared__ float4 su[MNBUF * MBUF_U];
-    __shared__ float2 sk[MNBUF * MBUF_K];
-    const int i0 = (bx0 + blockIdx.x) * MTX, j0 = (by0 + blockIdx.y) * MTY;
-    const int k0 = (bz0 + blockIdx.z) * MZC, k1 = min(k0 + MZC, nz);
-    march_run_plain<SUB, REALK>(u, b, y, k2, nx, ny, nz, w, i0, j0, k0, k1, su, sk);
+    if (plain) {
+        march_run_plain<SUB, REALK>(u4, b4, y4, k2, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk);
+        return;
+    }
+    // per axis: the block's rows are plain along it
+    const bool px = i0 >= pl.lo[0] && min(i0 + MTX, nx) - 1 <= pl.hi[0];
+    const bool py = j0 >= pl.lo[1] && min(j0 + MTY, ny) - 1 <= pl.hi[1];
+    const bool pz = k0 >= pl.lo[2] && k1 - 1 <= pl.hi[2];
+    if (py && pz) march_run<SUB, REALK, false, true, true>(u4, b4, y4, k2, tab, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk, sx);
+    else if (px && pz) march_run<SUB, REALK, true, false, true>(u4, b4, y4, k2, tab, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk, sx);
+    else if (px && py) march_run<SUB, REALK, true, true, false>(u4, b4, y4, k2, tab, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk, sx);
+    else march_run<SUB, REALK, false, false, false>(u4, b4, y4, k2, tab, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk, sx);
 }
 
 struct RowW {
@@ -603,48 +648,36 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
     if (prec == HELM_PREC_FP64) {
         dispatch<double, SUB>((const c128*)u, (const c128*)b, (c128*)y, g->k2, g->tab, g->d, nrhs, g->w, in,
                               g->k2_real, rw, s);
-    } else if (g->ctx->stencil_march && nrhs == 2 * MNP && !g->wtab && (al & 15) == 0) {
+    } else if (g->ctx->stencil_march && nrhs % (2 * MNP) == 0 && !g->wtab && (al & 15) == 0) {
         const PlainRange pl = plain_range(g);
-        const dim3 grid((unsigned)((g->d.nx + (32 / MNP) * MN - 1) / ((32 / MNP) * MN)), (unsigned)((g->d.ny + 3) / 4),
-                        (unsigned)((g->d.nz + MZC - 1) / MZC));
-        // the box of blocks whose rows are all plain on every axis: [lo, hi) per axis
-        const int n3[3] = {g->d.nx, g->d.ny, g->d.nz}, bs[3] = {MTX, MTY, MZC}, nbk[3] = {(int)grid.x, (int)grid.y,
-                                                                                          (int)grid.z};
-        int blo[3], bhi[3];
-        bool any = true;
-        for (int a = 0; a < 3; ++a) {
-            blo[a] = nbk[a];
-            bhi[a] = 0;
-            for (int t = 0; t < nbk[a]; ++t) {
-                const int lo = t * bs[a], hi = std::min(lo + bs[a], n3[a]) - 1;
-                if (lo >= pl.lo[a] && hi <= pl.hi[a]) {
-                    blo[a] = std::min(blo[a], t);
-                    bhi[a] = std::max(bhi[a], t + 1);
-                }
+        const int gx = (g->d.nx + MTX - 1) / MTX, gy = (g->d.ny + MTY - 1) / MTY, ncc = nrhs / (2 * MNP);
+        int mzc = g->ctx->stencil_planes;
+        if (mzc == 0) {
+            // the fewest plane chunks (longest walks: less halo per output) of at most 64 planes that still give
+            // every resident block slot two blocks or more (measured: fewer blocks than that leave the launch
+            // short of latency hiding), chunks of 8 planes at least
+            static int per_sm = 0;
+            if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil_march<SUB, true>, 128,
+                                                                             0) != cudaSuccess)
+                per_sm = 0;
+            const long long slots = (long long)std::max(per_sm, 1) * std::max(g->ctx->sm_count, 1);
+            const long long xy = (long long)gx * gy * ncc;
+            const int nz = g->d.nz;
+            mzc = std::min(nz, 8);
+            for (int nch = 1; nch <= nz; ++nch) {
+                const int c = (nz + nch - 1) / nch;
+                if (c > 64) continue;
+                mzc = std::max(c, std::min(nz, 8));
+                if (c <= 8 || xy * ((nz + c - 1) / c) >= 2 * slots) break;
             }
-            any = any && bhi[a] > blo[a];
         }
-        // the plain blocks run inside the same launch (class-sum form); a launch of their own left the two
-        // kernels each with a partly filled GPU (measured slower at 112^3)
-        const int skip = 0;
-        (void)any;
+        const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((g->d.nz + mzc - 1) / mzc * ncc));
         if (g->k2_real)
             stencil_march<SUB, true><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
-                                                          g->d.nx, g->d.ny, g->d.nz, g->w, pl, skip);
+                                                          g->d.nx, g->d.ny, g->d.nz, nrhs, mzc, g->w, pl);
         else
             stencil_march<SUB, false><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
-                                                           g->d.nx, g->d.ny, g->d.nz, g->w, pl, skip);
-        if (skip) {
-            const dim3 pg(bhi[0] - blo[0], bhi[1] - blo[1], bhi[2] - blo[2]);
-            if (g->k2_real)
-                stencil_march_plain<SUB, true><<<pg, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->d.nx,
-                                                                  g->d.ny, g->d.nz, g->w, blo[0], blo[1], blo[2]);
-            else
-                stencil_march_plain<SUB, false><<<pg, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f,
-                                                                   g->d.nx, g->d.ny, g->d.nz, g->w, blo[0], blo[1],
-                                                                   blo[2]);
-            g->ctx->launches++;
-        }
+                                                           g->d.nx, g->d.ny, g->d.nz, nrhs, mzc, g->w, pl);
     } else {
         dispatch<float, SUB>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, in,
                              g->k2_real, rw, s);

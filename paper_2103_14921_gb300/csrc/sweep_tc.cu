@@ -191,13 +191,15 @@ __device__ __forceinline__ void prep_tile(const BoxInfo& B, int box, int t, int 
     }
 }
 
-// prep_tile for the persistent sweep.  One round of independent loads (8 per thread in flight) brings into
+// prep_tile for the persistent sweep.  One round of asynchronous copies (all in flight at once) brings into
 // shared memory the tile's neighbour rows (a contiguous stretch of the neighbour plane, read from L2),
 // its 9 coupling coefficients per node and, forward, its right-hand sides; every value is then formed
 // from shared memory with the same operations in the same order as prep_tile, by a thread per
 // (node, column pair) with the node fastest, and written straight into its four B^T rows (coalesced
-// along the node).  Node rows are padded to npair + 1 float4 against bank conflicts.  Plane 0 of the
-// forward sweep (no coupling) and tiles whose data exceed smem_bytes use prep_tile.
+// along the node).  Node rows are padded to one float4 more than a chunk against bank conflicts.  When
+// all column pairs do not fit in smem_bytes, they are staged and formed in chunks (the largest halving
+// of the pair count that fits; the coefficients are staged once).  Plane 0 of the forward sweep (no
+// coupling) and tiles whose data exceed smem_bytes even for one pair use prep_tile.
 template <typename E>
 __device__ __forceinline__ void prep_tile_staged(const BoxInfo& B, int box, int t, int tpn,
                                                  const c64* __restrict__ coef, const c64* __restrict__ lb,
@@ -211,79 +213,67 @@ __device__ __forceinline__ void prep_tile_staged(const BoxInfo& B, int box, int 
     const int np = min(tpn, m - p0);
     const int r_lo = max(p0 / bx - 1, 0), r_hi = min((p0 + np - 1) / bx + 1, by - 1);
     const int ns = (r_hi - r_lo + 1) * bx;   // staged neighbour nodes
-    const int npair = nrhs >> 1, sp = npair + 1;
-    const int n1 = ns * npair, n2 = fwd ? np * npair : 0, n3 = np * 9;
-    const size_t need = ((size_t)ns * sp + (size_t)(fwd ? np : 0) * sp) * sizeof(float4) + (size_t)n3 * sizeof(float2);
-    if ((fwd && k == 0) || need > (size_t)smem_bytes) {
+    const int npair = nrhs >> 1;
+    const int nl = fwd ? np : 0;              // staged right-hand-side nodes
+    auto need = [&](int cp) {
+        return ((size_t)ns + nl) * (cp + 1) * sizeof(float4) + (size_t)np * 9 * sizeof(float2);
+    };
+    int cp = npair;
+    while (cp > 1 && need(cp) > (size_t)smem_bytes) cp = (cp + 1) >> 1;
+    if ((fwd && k == 0) || need(cp) > (size_t)smem_bytes) {
         prep_tile<E, true>(B, box, t, tpn, coef, lb, loc, bt, ld2, npad, nrhs, s, fwd, reinterpret_cast<c64*>(smem));
         return;
     }
+    const int sp = cp + 1;
     const long long plane = B.loc_off + (long long)k * m;
     const long long nbr = fwd ? plane - m : plane + m;
     const int off = fwd ? 0 : 18;
     float4* stg = reinterpret_cast<float4*>(smem);            // [ns][sp]
     float4* lbs = stg + (size_t)ns * sp;                        // [np][sp] (forward)
-    float2* cfs = reinterpret_cast<float2*>(lbs + (size_t)(fwd ? np : 0) * sp);   // [np][9]
+    float2* cfs = reinterpret_cast<float2*>(lbs + (size_t)nl * sp);   // [np][9]
     const float4* nsrc = reinterpret_cast<const float4*>(loc + (nbr + (long long)r_lo * bx) * nrhs);
     const float4* lsrc = reinterpret_cast<const float4*>(lb + (plane + p0) * nrhs);
     const float2* csrc = reinterpret_cast<const float2*>(coef + (plane + p0) * 27 + off);
-    const int N = n1 + n2 + n3;
-    constexpr int U = 8;
-    for (int e0 = threadIdx.x; e0 < N; e0 += blockDim.x * U) {
-        float4 r[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < n1) {
-                r[u] = __ldcg(nsrc + e);
-            } else if (e < n1 + n2) {
-                r[u] = lsrc[e - n1];
-            } else if (e < N) {
-                const int q = e - n1 - n2;
-                const float2 c = csrc[(q / 9) * 27 + q % 9];
-                r[u] = make_float4(c.x, c.y, 0.f, 0.f);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < n1)
-                stg[(e / npair) * sp + e % npair] = r[u];
-            else if (e < n1 + n2)
-                lbs[((e - n1) / npair) * sp + (e - n1) % npair] = r[u];
-            else if (e < N)
-                cfs[e - n1 - n2] = make_float2(r[u].x, r[u].y);
-        }
-    }
-    __syncthreads();
     E* bb = bt + (size_t)box * npad * ld2;
     typedef typename Pair2<E>::type P2;
-    for (int e = threadIdx.x; e < np * npair; e += blockDim.x) {
-        const int pl = e % np, pr = e / np, p = p0 + pl;
-        float4 acc = fwd ? lbs[pl * sp + pr] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int px = p % bx, py = p / bx;
-        float2 c[9];
-        float4 v[9];
+    for (int c0 = 0; c0 < npair; c0 += cp) {
+        const int cw = min(cp, npair - c0);
+        const int n1 = ns * cw, n2 = nl * cw, n3 = c0 == 0 ? np * 9 : 0;
+        if (c0 > 0) __syncthreads();   // the previous chunk's values are read before they are replaced
+        for (int e = threadIdx.x; e < n1; e += blockDim.x)
+            tc::cp_async16(stg + (e / cw) * sp + e % cw, nsrc + (long long)(e / cw) * npair + c0 + e % cw);
+        for (int e = threadIdx.x; e < n2; e += blockDim.x)
+            tc::cp_async16(lbs + (e / cw) * sp + e % cw, lsrc + (long long)(e / cw) * npair + c0 + e % cw);
+        for (int e = threadIdx.x; e < n3; e += blockDim.x) tc::cp_async8(cfs + e, csrc + (e / 9) * 27 + e % 9);
+        tc::cp_async_wait_all();
+        __syncthreads();
+        for (int e = threadIdx.x; e < np * cw; e += blockDim.x) {
+            const int pl = e % np, pc = e / np, pr = c0 + pc, p = p0 + pl;
+            float4 acc = fwd ? lbs[pl * sp + pc] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int px = p % bx, py = p / bx;
+            float2 c[9];
+            float4 v[9];
 #pragma unroll
-        for (int d = 0; d < 9; ++d) {
-            const int qx = min(max(px + d % 3 - 1, 0), bx - 1), qy = min(max(py + d / 3 - 1, 0), by - 1);
-            c[d] = cfs[pl * 9 + d];
-            v[d] = stg[((qy - r_lo) * bx + qx) * sp + pr];
-        }
+            for (int d = 0; d < 9; ++d) {
+                const int qx = min(max(px + d % 3 - 1, 0), bx - 1), qy = min(max(py + d / 3 - 1, 0), by - 1);
+                c[d] = cfs[pl * 9 + d];
+                v[d] = stg[((qy - r_lo) * bx + qx) * sp + pc];
+            }
 #pragma unroll
-        for (int d = 0; d < 9; ++d) {
-            const float sr = fwd ? -c[d].x : c[d].x, si = fwd ? -c[d].y : c[d].y;
-            acc.x = fmaf(sr, v[d].x, fmaf(-si, v[d].y, acc.x));
-            acc.y = fmaf(sr, v[d].y, fmaf(si, v[d].x, acc.y));
-            acc.z = fmaf(sr, v[d].z, fmaf(-si, v[d].w, acc.z));
-            acc.w = fmaf(sr, v[d].w, fmaf(si, v[d].z, acc.w));
+            for (int d = 0; d < 9; ++d) {
+                const float sr = fwd ? -c[d].x : c[d].x, si = fwd ? -c[d].y : c[d].y;
+                acc.x = fmaf(sr, v[d].x, fmaf(-si, v[d].y, acc.x));
+                acc.y = fmaf(sr, v[d].y, fmaf(si, v[d].x, acc.y));
+                acc.z = fmaf(sr, v[d].z, fmaf(-si, v[d].w, acc.z));
+                acc.w = fmaf(sr, v[d].w, fmaf(si, v[d].z, acc.w));
+            }
+            // columns 2 pr (acc.x, acc.y) and 2 pr + 1 (acc.z, acc.w): B^T rows 4 pr .. 4 pr + 3 at entries 2p, 2p + 1
+            E* row = bb + (size_t)(4 * pr) * ld2 + 2 * p;
+            *reinterpret_cast<P2*>(row) = Pair2<E>::make(acc.x, -acc.y);
+            *reinterpret_cast<P2*>(row + ld2) = Pair2<E>::make(acc.y, acc.x);
+            *reinterpret_cast<P2*>(row + 2 * (size_t)ld2) = Pair2<E>::make(acc.z, -acc.w);
+            *reinterpret_cast<P2*>(row + 3 * (size_t)ld2) = Pair2<E>::make(acc.w, acc.z);
         }
-        // columns 2 pr (acc.x, acc.y) and 2 pr + 1 (acc.z, acc.w): B^T rows 4 pr .. 4 pr + 3 at entries 2p, 2p + 1
-        E* row = bb + (size_t)(4 * pr) * ld2 + 2 * p;
-        *reinterpret_cast<P2*>(row) = Pair2<E>::make(acc.x, -acc.y);
-        *reinterpret_cast<P2*>(row + ld2) = Pair2<E>::make(acc.y, acc.x);
-        *reinterpret_cast<P2*>(row + 2 * (size_t)ld2) = Pair2<E>::make(acc.z, -acc.w);
-        *reinterpret_cast<P2*>(row + 3 * (size_t)ld2) = Pair2<E>::make(acc.w, acc.z);
     }
 }
 

@@ -35,6 +35,7 @@ TUNE_STENCIL_MARCH = 5
 TUNE_FLOW_WAIT_US = 6
 TUNE_TC_FACTOR = 7
 TUNE_BLOCK_GJ = 8
+TUNE_STENCIL_PLANES = 9
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_TF32X3, PREC_BF16 = 0, 1, 2, 3, 4
 PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "tf32x3": PREC_TF32X3, "bf16": PREC_BF16}
 

@@ -148,20 +148,24 @@ def test_apply_rejects_overlap_and_bad_prec(ctx):
 
 
 @pytest.mark.parametrize("case", [
-    # nx, ny, nz, npml, top_pml, Q
-    (37, 35, 33, 8, False, None),     # ragged against the 16 x 4 x 16 blocks; absorbing layers
-    (24, 20, 18, 4, True, 60.0),      # complex k^2, absorbing top
-    (64, 40, 20, 0, False, None),     # no absorbing layers: every block takes the plain path
-    (17, 5, 3, 2, False, 80.0),       # fewer planes than a block's chunk
+    # nx, ny, nz, npml, top_pml, Q, columns
+    (37, 35, 33, 8, False, None, 16),     # ragged against the 16 x 4 x 16 blocks; absorbing layers
+    (24, 20, 18, 4, True, 60.0, 16),      # complex k^2, absorbing top
+    (64, 40, 20, 0, False, None, 16),     # no absorbing layers: every block takes the plain path
+    (17, 5, 3, 2, False, 80.0, 16),       # fewer planes than a block's chunk
+    (70, 45, 37, 10, False, None, 32),    # two column chunks; blocks stretched along one axis, two, three
+    (40, 36, 34, 6, True, 100.0, 48),     # three column chunks, complex k^2, absorbing top
 ])
 def test_stencil_zmarch_matches_per_node_kernel_and_oracle(ctx, case):
-    """The z-marching complex64 stencil (16 columns, constant weights) against the per-node kernel (the
-    tuning switch selects the path) and the FP64 oracle: the same operator summed in another order, so
-    the two agree to FP32 rounding (1e-6 relative L2) and both match the oracle (1e-5)."""
+    """The z-marching complex64 stencil (columns in chunks of 16, constant weights) against the per-node
+    kernel (the tuning switch selects the path) and the FP64 oracle: the same operator summed in another
+    order, so the two agree to FP32 rounding (1e-6 relative L2) and both match the oracle (1e-5).  Blocks
+    of the interior (class-sum form), of one absorbing layer (one stretched axis) and of edges and corners
+    (two or three) each take their own code path."""
     import torch
     from paper_2103_14921_gb300 import helm
-    nx, ny, nz, npml, top, Q = case
-    h, f, nrhs = 25.0, 5.0, 16
+    nx, ny, nz, npml, top, Q, nrhs = case
+    h, f = 25.0, 5.0
     c = synth.linear_gradient(nx, ny, nz, h, 1500.0, 2.0, Q=Q)
     w = synth.random_weights(nx + 1)
     grid = helm.Grid(ctx, nx, ny, nz, h, f, c, npml=npml, top_bc=helm.TOP_PML if top else helm.TOP_DIRICHLET,
@@ -181,6 +185,29 @@ def test_stencil_zmarch_matches_per_node_kernel_and_oracle(ctx, case):
     assert _rel(got[1], got[0]) <= 1e-6
     for m in (1, 0):
         assert _rel(got[m], want) <= 1e-5
+
+
+def test_stencil_zmarch_plane_chunks_do_not_change_results(ctx):
+    """The number of output planes per z-march block (HELM_TUNE_STENCIL_PLANES; 0 lets the library pick it
+    per grid) changes how the planes are split among blocks, and with it which outputs fall in blocks wholly
+    inside the interior (class-sum form) or in the absorbing layers (product form): the same operator
+    summed in another order, so the results agree to FP32 rounding (1e-6 relative L2)."""
+    import torch
+    from paper_2103_14921_gb300 import helm
+    nx, ny, nz, nrhs = 41, 30, 45, 32
+    c = synth.linear_gradient(nx, ny, nz, 25.0, 1500.0, 2.0)
+    grid = helm.Grid(ctx, nx, ny, nz, 25.0, 5.0, c, npml=6, weights=helm.fit_weights())
+    u = torch.from_numpy(synth.random_complex((nz, ny, nx, nrhs), 77).astype(np.complex64)).cuda()
+    got = []
+    for planes in (0, 4, 16, 50, 128):
+        ctx.set_tuning(helm.TUNE_STENCIL_PLANES, planes)
+        got.append(grid.apply(u, prec=helm.PREC_FP32))
+    ctx.set_tuning(helm.TUNE_STENCIL_PLANES, 0)
+    ref = got[0].cpu().numpy()
+    for g in got[1:]:
+        assert _rel(g.cpu().numpy(), ref) <= 1e-6
+    with pytest.raises(helm.HelmError):
+        ctx.set_tuning(helm.TUNE_STENCIL_PLANES, 3)
 
 
 def test_stencil_zmarch_residual_path_in_fgmres(ctx):

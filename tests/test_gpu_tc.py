@@ -133,12 +133,14 @@ def test_tf32_fgmres_converges_to_the_direct_solution(ctx):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
-@pytest.mark.parametrize("parts,nrhs", [((3, 2, 2), 16), ((3, 1, 1), 2), ((2, 2, 2), 40), ((2, 1, 2), 3)])
+@pytest.mark.parametrize("parts,nrhs", [((3, 2, 2), 16), ((3, 1, 1), 2), ((2, 2, 2), 40), ((2, 2, 2), 128),
+                                        ((2, 1, 2), 3)])
 def test_persistent_sweep_equals_per_step_launches(ctx, prec, parts, nrhs):
     """Both sweeps of every box as one persistent launch fed by a device work queue, against one
     preparation and one product launch per plane step: the same arithmetic on every element, so the
     preconditioner outputs are bit-identical.  Ragged boxes with unequal plane counts, a single-box
-    row, 40 columns (N = 128) and an odd column count (which keeps the per-step launches).  Launches:
+    row, 40 columns (N = 128), 128 columns (N = 256: the persistent launch stages its preparation tiles in
+    column chunks) and an odd column count (which keeps the per-step launches).  Launches:
     one persistent (family sweep_flow), or 2 n_z - 1 of each kind; repeated applies reuse the queue."""
     import torch
     from paper_2103_14921_gb300 import helm
