@@ -122,10 +122,12 @@ helm_status helm_profile_query(helm_ctx ctx, const char* name, uint64_t* launche
  * tiles of the products, tiles of the operand preparation) from a device queue, each box's next
  * step queued as soon as its current one completes (an even number of right-hand sides and
  * 16-byte aligned vectors; otherwise, and with 0, two launches per plane step).  Both give
- * bit-identical results.  HELM_TUNE_STENCIL_MARCH: 1 (default) applies complex64 stencils with 16
- * right-hand sides and constant weights by walking z-planes (the in-plane terms of a plane are formed
- * once and reused by the three output planes it touches); 0 uses the per-node kernel.  The two agree
- * to FP32 rounding.  Returns HELM_EINVAL for an unknown key or value out of range. */
+ * bit-identical results.  HELM_TUNE_STENCIL_MARCH: 1 (default) applies complex64 stencils whose column
+ * count is a multiple of 16, with constant weights, by walking z-planes (the in-plane terms of a plane are
+ * formed once and reused by the three output planes it touches; blocks wholly inside the interior take the
+ * class-sum form, the others the product form); 2 the same with the blocks of one absorbing layer (one
+ * stretched axis) in product forms specialised to that axis; 0 uses the per-node kernel.  All agree to
+ * FP32 rounding.  Returns HELM_EINVAL for an unknown key or value out of range. */
 #define HELM_TUNE_TC_STAGES 1
 #define HELM_TUNE_COARSE_COOP 2
 #define HELM_TUNE_GRAPHS 3

@@ -122,7 +122,7 @@ extern "C" helm_status helm_set_tuning(helm_ctx ctx, int key, int value) {
         return HELM_OK;
     }
     if (key == HELM_TUNE_STENCIL_MARCH) {
-        if (value != 0 && value != 1) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: stencil_march must be 0 or 1");
+        if (value < 0 || value > 2) return set_error(ctx, HELM_EINVAL, "helm_set_tuning: stencil_march must be 0..2");
         ctx->stencil_march = value;
         ctx->graph_gen++;
         return HELM_OK;

@@ -513,7 +513,7 @@ template <bool SUB, bool REALK>
 __global__ void __launch_bounds__(128, 3) stencil_march(const c64* __restrict__ u, const c64* __restrict__ b,
                                                      c64* __restrict__ y, const c64* __restrict__ k2,
                                                      const c64* __restrict__ tab, int nx, int ny, int nz, int nrhs,
-                                                     int mzc, StencilW w, PlainRange pl) {
+                                                     int mzc, StencilW w, PlainRange pl, int axis_variants) {
     __shared__ float4 su[MNBUF * MBUF_U];
     __shared__ float2 sk[MNBUF * MBUF_K];
     __shared__ float4 sx[MTX * 3];
@@ -531,10 +531,11 @@ __global__ void __launch_bounds__(128, 3) stencil_march(const c64* __restrict__ 
         march_run_plain<SUB, REALK>(u4, b4, y4, k2, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk);
         return;
     }
-    // per axis: the block's rows are plain along it
-    const bool px = i0 >= pl.lo[0] && min(i0 + MTX, nx) - 1 <= pl.hi[0];
-    const bool py = j0 >= pl.lo[1] && min(j0 + MTY, ny) - 1 <= pl.hi[1];
-    const bool pz = k0 >= pl.lo[2] && k1 - 1 <= pl.hi[2];
+    // per axis: the block's rows are plain along it (with axis_variants; else the general product form,
+    // which keeps the kernel's instruction footprint to two loop bodies)
+    const bool px = axis_variants && i0 >= pl.lo[0] && min(i0 + MTX, nx) - 1 <= pl.hi[0];
+    const bool py = axis_variants && j0 >= pl.lo[1] && min(j0 + MTY, ny) - 1 <= pl.hi[1];
+    const bool pz = axis_variants && k0 >= pl.lo[2] && k1 - 1 <= pl.hi[2];
     if (py && pz) march_run<SUB, REALK, false, true, true>(u4, b4, y4, k2, tab, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk, sx);
     else if (px && pz) march_run<SUB, REALK, true, false, true>(u4, b4, y4, k2, tab, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk, sx);
     else if (px && py) march_run<SUB, REALK, true, true, false>(u4, b4, y4, k2, tab, nx, ny, nz, nrs, w, i0, j0, k0, k1, su, sk, sx);
@@ -674,10 +675,12 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
         const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((g->d.nz + mzc - 1) / mzc * ncc));
         if (g->k2_real)
             stencil_march<SUB, true><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
-                                                          g->d.nx, g->d.ny, g->d.nz, nrhs, mzc, g->w, pl);
+                                                          g->d.nx, g->d.ny, g->d.nz, nrhs, mzc, g->w, pl,
+                                                          g->ctx->stencil_march == 2 ? 1 : 0);
         else
             stencil_march<SUB, false><<<grid, 128, 0, s>>>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf,
-                                                           g->d.nx, g->d.ny, g->d.nz, nrhs, mzc, g->w, pl);
+                                                           g->d.nx, g->d.ny, g->d.nz, nrhs, mzc, g->w, pl,
+                                                          g->ctx->stencil_march == 2 ? 1 : 0);
     } else {
         dispatch<float, SUB>((const c64*)u, (const c64*)b, (c64*)y, g->k2f, g->tabf, g->d, nrhs, g->w, in,
                              g->k2_real, rw, s);

@@ -157,8 +157,9 @@ def test_apply_rejects_overlap_and_bad_prec(ctx):
     (40, 36, 34, 6, True, 100.0, 48),     # three column chunks, complex k^2, absorbing top
 ])
 def test_stencil_zmarch_matches_per_node_kernel_and_oracle(ctx, case):
-    """The z-marching complex64 stencil (columns in chunks of 16, constant weights) against the per-node
-    kernel (the tuning switch selects the path) and the FP64 oracle: the same operator summed in another
+    """The z-marching complex64 stencil (columns in chunks of 16, constant weights; with and without the
+    one-axis absorbing-layer variants) against the per-node kernel (the tuning switch selects the path) and
+    the FP64 oracle: the same operator summed in another
     order, so the two agree to FP32 rounding (1e-6 relative L2) and both match the oracle (1e-5).  Blocks
     of the interior (class-sum form), of one absorbing layer (one stretched axis) and of edges and corners
     (two or three) each take their own code path."""
@@ -175,15 +176,16 @@ def test_stencil_zmarch_matches_per_node_kernel_and_oracle(ctx, case):
     want = apply_A(prob, u)
     u32 = torch.from_numpy(u.astype(np.complex64)).cuda()
     got = {}
-    for march in (1, 0):
+    for march in (1, 2, 0):
         ctx.set_tuning(helm.TUNE_STENCIL_MARCH, march)
         ctx.profile(True, only=["stencil"])
         got[march] = grid.apply(u32, prec=helm.PREC_FP32).cpu().numpy().astype(np.complex128)
         assert ctx.profile_query("stencil")[0] == 1
         ctx.profile(False)
     ctx.set_tuning(helm.TUNE_STENCIL_MARCH, 1)
-    assert _rel(got[1], got[0]) <= 1e-6
-    for m in (1, 0):
+    for m in (1, 2):
+        assert _rel(got[m], got[0]) <= 1e-6
+    for m in (1, 2, 0):
         assert _rel(got[m], want) <= 1e-5
 
 
