@@ -269,13 +269,12 @@ def serve_phase(helm, sv, mix, items, weights, arrivals=None):
                     s = sv.wait(tk, timeout_s=max(1.0, deadline - time.perf_counter()))
                 except TimeoutError:   # reported as not done; the phase ends
                     s = dict(sv.poll(tk)[1], done=False)
-                    out.append(dict(s, nrhs=live.pop(tk), timed_out=True))
+                    out.append(dict(s, **live.pop(tk), timed_out=True))
                     continue
             else:
                 s = sv.poll(tk)[1]
             if s["done"]:
-                nr = live.pop(tk)
-                out.append(dict(s, nrhs=nr))
+                out.append(dict(s, **live.pop(tk)))
 
     for i, it in enumerate(items):
         if arrivals is not None:
@@ -291,7 +290,7 @@ def serve_phase(helm, sv, mix, items, weights, arrivals=None):
         od = helm.OrasDesc(p, p, p, 2, 4, 0, helm.PREC_TF32, SERVE_COARSE_ITERS, 1)
         tk = sv.submit(1000 * n + it["mid"], gd, mix.model(n, it["mid"]), od, b, torch.empty_like(b), tol=1e-6,
                        restart=SERVE_RESTART, basis_prec=helm.PREC_FP32)
-        live[tk] = len(it["pos"])
+        live[tk] = dict(nrhs=len(it["pos"]), n=n, f=it["f"], model=it["mid"])
         del b
     reap(True)
     return out, time.perf_counter() - t0
@@ -316,7 +315,10 @@ def run_serving(helm, device, stream, weights, args):
                 "rhs": rhs, "wall_s": wall, "rhs_per_s": rhs / wall,
                 "requests_per_s": len(done) / wall, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "arrival_rate_per_s": rate,
-                "factors_reused": sum(1 for s_ in st if s_["factors_reused"])}
+                "factors_reused": sum(1 for s_ in st if s_["factors_reused"]),
+                "not_ok": [{k: s_[k] for k in ("n", "f", "model", "nrhs", "status", "iterations_max",
+                                               "true_relres_max", "latency_ms")}
+                           for s_ in done if s_["status"] != helm.OK]}
 
     with helm.Server(ctx, slots_per_batch=64) as sv:
         pos = 0

@@ -99,6 +99,8 @@ struct FactorSet {
     int building = 0;               // 1 while the builder owns it (queued or being built)
     const void* c = nullptr;        // wave speed of the request that asked for it (read by the build)
     size_t reserved = 0;            // budget bytes reserved from the request to the handover
+    size_t reserved_at_queue = 0;   // the same estimate (factors, solver workspace, apply scratch)
+    bool cycled = false;            // its first restart cycle has run (the apply scratch is allocated by then)
     size_t built_bytes = 0;         // device bytes the build left allocated
     helm_status build_status = HELM_OK;
     std::string build_msg;
@@ -226,9 +228,22 @@ struct Server {
                 fs->g->ctx = ctx;   // re-parent: every later call on the set runs on the serving stream
                 ctx->children++;
                 ctx->in_use += fs->built_bytes;
+                trace("take over model %llu: %.2f GB built against %.2f GB reserved", (unsigned long long)fs->model_id,
+                      fs->built_bytes / 1e9, fs->reserved_at_queue / 1e9);
+                const size_t in0 = ctx->in_use;
                 fs->K.reset(make_krylov_engine(fs->o, fs->width, fs->restart, fs->flexible != 0, fs->basis_prec,
                                                nullptr, nullptr, &st));
-                if (st) fs->build_msg = ctx->last_error;
+                if (!st) hold_residual(fs, fs->built_bytes + (ctx->in_use - in0));
+                if (st == HELM_ENOMEM) {
+                    // the budget has no room for the engine now (the factors took more than their estimate, or
+                    // other sets grew meanwhile): the set stays without one, and try_admit makes it once idle
+                    // sets can be evicted or running ones have finished
+                    trace("engine for model %llu deferred: no room in the budget", (unsigned long long)fs->model_id);
+                    fs->K.reset();
+                    st = HELM_OK;
+                } else if (st) {
+                    fs->build_msg = ctx->last_error;
+                }
             }
             fs->building = 0;
             if (st) {
@@ -268,6 +283,8 @@ struct Server {
     }
 
     void destroy_set(FactorSet* fs) {
+        reserved -= fs->reserved;   // a residual still held for its first cycle
+        fs->reserved = 0;
         fs->K.reset();
         if (fs->o) oras_destroy(fs->o);
         if (fs->g) helm_destroy_grid(fs->g);
@@ -281,6 +298,47 @@ struct Server {
         return N * width * ((2 * m + 3) * e + 3 * sizeof(c128)) + N * 48;
     }
 
+    // Evict idle factor sets other than keep (least recently used first) until `bytes` more fit the budget;
+    // returns whether they fit.
+    bool make_room(size_t bytes, FactorSet* keep) {
+        auto room = [&]() { return ctx->budget == 0 || ctx->in_use + reserved + bytes <= ctx->budget; };
+        while (!room()) {
+            FactorSet* lru = nullptr;
+            for (auto* s2 : sets)
+                if (s2 != keep && !s2->building && s2->active == 0 && !wanted(s2) &&
+                    (!lru || s2->last_used < lru->last_used))
+                    lru = s2;
+            if (!lru) break;
+            sets.erase(std::find(sets.begin(), sets.end(), lru));
+            trace("evict model %llu (grid %d^3)", (unsigned long long)lru->model_id, lru->gd.nx);
+            destroy_set(lru);
+        }
+        return room();
+    }
+
+    // Whether a queued request asks for this set (a set built for a request that is not admitted yet is not
+    // evicted for another's room: that would throw the build away and queue it again).
+    bool wanted(const FactorSet* fs) const {
+        for (const SRequest* w : waiting)
+            if (fs->matches(w->req)) return true;
+        return false;
+    }
+
+    // After a set's solver workspace is made: keep reserved what its estimate still expects (the apply scratch,
+    // allocated by its first restart cycle), so that other admissions do not spend it meanwhile.
+    void hold_residual(FactorSet* fs, size_t used) {
+        reserved -= fs->reserved;
+        fs->reserved = fs->reserved_at_queue > used ? fs->reserved_at_queue - used : 0;
+        reserved += fs->reserved;
+    }
+
+    // Whether a set other than fs is being built or has running columns (so that budget room will come back).
+    bool others_busy(const FactorSet* fs) const {
+        for (auto* s2 : sets)
+            if (s2 != fs && (s2->building || s2->active > 0)) return true;
+        return false;
+    }
+
     // Try to place r: returns true if admitted (or failed), false if it must keep waiting (its factors are
     // being built, or its columns or its factors do not fit yet).
     bool try_admit(SRequest* r, bool idle) {
@@ -290,17 +348,7 @@ struct Server {
         if (!fs) {
             const int width = width_for(r->req.nrhs);
             const size_t need = oras_estimate_bytes(r->req.grid, r->req.oras, width) + engine_estimate(r->req, width);
-            auto room = [&]() { return ctx->budget == 0 || ctx->in_use + reserved + need <= ctx->budget; };
-            while (!room()) {
-                FactorSet* lru = nullptr;
-                for (auto* s : sets)
-                    if (!s->building && s->active == 0 && (!lru || s->last_used < lru->last_used)) lru = s;
-                if (!lru) break;
-                sets.erase(std::find(sets.begin(), sets.end(), lru));
-                trace("evict model %llu (grid %d^3)", (unsigned long long)lru->model_id, lru->gd.nx);
-                destroy_set(lru);
-            }
-            if (!room()) {
+            if (!make_room(need, nullptr)) {
                 if (idle && sets.empty()) {
                     set_error(ctx, HELM_ENOMEM, "request needs about %zu bytes, more than the HBM budget", need);
                     finish(r, HELM_ENOMEM);
@@ -322,6 +370,7 @@ struct Server {
                   (unsigned long long)r->ticket, need / 1e9, ctx->in_use / 1e9, reserved / 1e9);
             r->built_for = true;
             fs->reserved = need;
+            fs->reserved_at_queue = need;
             reserved += need;
             sets.push_back(fs);
             {
@@ -331,25 +380,37 @@ struct Server {
             bcv.notify_one();
             return false;
         }
-        if (fs->building || !fs->K) return false;
+        if (fs->building) return false;
+        if (!fs->K) {
+            // the engine deferred at the handover: make it once the budget has room, evicting idle sets
+            const size_t eb = engine_estimate(r->req, fs->width);
+            if (!make_room(eb, fs)) {
+                if (others_busy(fs)) return false;   // room comes back when the others finish
+                set_error(ctx, HELM_ENOMEM, "request's solver workspace (about %zu bytes) does not fit the HBM budget",
+                          eb);
+                finish(r, HELM_ENOMEM);
+                return true;
+            }
+            helm_status st = HELM_OK;
+            const size_t in0 = ctx->in_use;
+            fs->K.reset(make_krylov_engine(fs->o, fs->width, fs->restart, fs->flexible != 0, fs->basis_prec, nullptr,
+                                           nullptr, &st));
+            if (st) {
+                fs->K.reset();
+                if (st == HELM_ENOMEM && others_busy(fs)) return false;
+                finish(r, st);
+                return true;
+            }
+            hold_residual(fs, fs->built_bytes + (ctx->in_use - in0));
+            trace("engine for model %llu made (%d columns)", (unsigned long long)fs->model_id, fs->width);
+        }
         if (fs->width < r->req.nrhs) {
             // a wider engine for this set, made once its running columns have finished, with room made by
             // evicting other idle sets if needed
             if (fs->active > 0) return false;
             const int width = width_for(r->req.nrhs);
             const size_t more = engine_estimate(r->req, width) - engine_estimate(r->req, fs->width);
-            auto room = [&]() { return ctx->budget == 0 || ctx->in_use + reserved + more <= ctx->budget; };
-            while (!room()) {
-                FactorSet* lru = nullptr;
-                for (auto* s2 : sets)
-                    if (s2 != fs && !s2->building && s2->active == 0 && (!lru || s2->last_used < lru->last_used))
-                        lru = s2;
-                if (!lru) break;
-                sets.erase(std::find(sets.begin(), sets.end(), lru));
-                trace("evict model %llu (grid %d^3) to widen", (unsigned long long)lru->model_id, lru->gd.nx);
-                destroy_set(lru);
-            }
-            if (!room()) {
+            if (!make_room(more, fs)) {
                 bool others = false;
                 for (auto* s2 : sets) others = others || (s2 != fs && (s2->building || s2->active > 0));
                 if (others) return false;   // room comes back when the others finish
@@ -497,6 +558,12 @@ struct Server {
                 bool any = false;
                 const auto tc0 = Clock::now();
                 helm_status rc = fs->K->cycle(&any);
+                if (!fs->cycled) {
+                    // the apply scratch exists now and is counted in use: the residual reservation is not needed
+                    fs->cycled = true;
+                    reserved -= fs->reserved;
+                    fs->reserved = 0;
+                }
                 trace("cycle model %llu (grid %d^3, width %d, %d active): status %d, %.1f ms",
                       (unsigned long long)fs->model_id, fs->gd.nx, fs->width, fs->active, rc,
                       ms_since(tc0, Clock::now()));
