@@ -137,3 +137,29 @@ def test_new_factor_set_joins_while_another_batch_runs(env):
     assert sA["factors_reused"] and not sB["factors_reused"]
     assert np.array_equal(xA.cpu().numpy(), alone["A"])
     assert np.array_equal(xB.cpu().numpy(), alone["B"])
+
+
+def test_burst_of_new_sets_under_a_tight_budget_all_complete(env):
+    """Four requests on four new models submitted at once under a budget that holds about two factor sets
+    with their solver workspace: the later ones wait for room (sets built for waiting requests are not
+    evicted for another's room, and each set's estimate stays reserved until its first cycle has allocated
+    its scratch), so every request completes with status OK and the tolerance, none with ENOMEM."""
+    import torch
+    helm, _, w, cA, _ = env
+    gd, od = _descs(helm, w, helm.PREC_TF32)
+    nx, ny, nz = DIMS
+    restart = 30
+    engine = nx * ny * nz * 16 * ((2 * restart + 3) * 8 + 3 * 16) + nx * ny * nz * 48   # FP32 basis, 16 slots
+    need = helm.estimate_bytes(gd, od, 16) + engine
+    tight = helm.Context(0, budget_bytes=int(2.5 * need))
+    tol = 1e-6
+    with helm.Server(tight, slots_per_batch=16) as sv:
+        jobs = []
+        for i in range(4):
+            bi = torch.from_numpy(_rhs([(6 + 3 * i, 7 + 2 * i, 4 + i), (15, 12, 9 + i)])).cuda()
+            jobs.append((sv.submit(100 + i, gd, cA, od, bi, torch.empty_like(bi), tol=tol, restart=restart), bi))
+        stats = [sv.wait(t) for t, _ in jobs]
+    for s in stats:
+        assert s["status"] == helm.OK, s
+        assert s["true_relres_max"] <= tol
+        assert not s["factors_reused"]
