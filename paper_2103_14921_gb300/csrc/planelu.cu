@@ -29,6 +29,8 @@
 #include <cuda_bf16.h>
 
 #include "blockinv.cuh"
+#include <atomic>
+
 #include "internal.h"
 
 namespace {
@@ -636,11 +638,11 @@ helm_status factor_t(helm_ctx ctx, PlaneSet& P, int* singular) {
     // else the global-memory panel of nb columns
     constexpr int NBS = 24;
     const size_t psm = (size_t)m * NBS * sizeof(cplx<T>);
-    static bool psm_attr = false;
+    static std::atomic<bool> psm_attr{false};
     if constexpr (sizeof(T) == 4) {
-        if (!psm_attr) {
+        if (!psm_attr.load(std::memory_order_acquire)) {
             cudaFuncSetAttribute(gj_panel_smem<T, NBS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            psm_attr = true;
+            psm_attr.store(true, std::memory_order_release);
         }
     }
     const bool smem_panel = sizeof(T) == 4 && psm <= 200 * 1024;
@@ -924,11 +926,11 @@ helm_status factor_block_t(helm_ctx ctx, PlaneSet& P, int* singular, int* weak) 
         cleanup();
         return rc;
     }
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};
+    if (!attr.load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(bgj_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((NB * (NB + 1) + 16 * NB) * sizeof(cplx<T>)));
-        attr = true;
+        attr.store(true, std::memory_order_release);
     }
     cudaMemsetAsync(flag, 0, sizeof(int), st);
     const cplx<T>* coef = (const cplx<T>*)P.coef;
@@ -992,11 +994,11 @@ void launch_sweep_rn(const PlaneSet& P, cplx<T>* loc, cplx<T>* rbuf, int nrhs, c
     const dim3 pgrid(pblocks, P.nbox);
     const cplx<T>* coef = (const cplx<T>*)P.coef;
     const cplx<T>* G = (const cplx<T>*)P.G;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[0]) {
+    static std::atomic<bool> attr_set{false};
+    if (!attr_set.load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(sweep_gemv<T, RN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(sweep_gemv<T, RN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set[0] = true;
+        attr_set.store(true, std::memory_order_release);
     }
     // algorithmic bytes of one step: every active box reads its m x m factor plane once,
     // the prepared plane (m x nrhs) and writes (backward: also reads) its output plane;
@@ -1020,10 +1022,10 @@ void launch_sweep_rn(const PlaneSet& P, cplx<T>* loc, cplx<T>* rbuf, int nrhs, c
         const dim3 sgrid((m + rows - 1) / rows, KSPLIT, (nrhs + RN - 1) / RN);
         const size_t ssm = (size_t)RN * kw * sizeof(cplx<T>);
         cplx<T>* part = rbuf + (size_t)m * nrhs;   // the caller sizes rbuf (1 + KSPLIT) planes deep
-        static bool sattr = false;
-        if (!sattr) {
+        static std::atomic<bool> sattr{false};
+        if (!sattr.load(std::memory_order_acquire)) {
             cudaFuncSetAttribute(sweep_gemv_splitk<T, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            sattr = true;
+            sattr.store(true, std::memory_order_release);
         }
         const unsigned rblocks = (unsigned)std::min<long long>(((long long)m * nrhs + 255) / 256, 512);
         for (int pass = 0; pass < 2; ++pass) {

@@ -28,6 +28,8 @@
 #include <cudaTypedefs.h>
 
 #include "blockinv.cuh"
+#include <atomic>
+
 #include "internal.h"
 #include "tc.cuh"
 
@@ -684,13 +686,13 @@ helm_status planeset_factor_tc(helm_ctx ctx, PlaneSet& P, int* singular, int* we
         cleanup();
         return set_error(ctx, HELM_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core factorisation");
     }
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};
+    if (!attr.load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(tgj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, USMEM);
         cudaFuncSetAttribute(tgj_update_pers, cudaFuncAttributeMaxDynamicSharedMemorySize, PSMEM);
         cudaFuncSetAttribute(tgj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((NB * DP + 16 * NB) * sizeof(c64)));
-        attr = true;
+        attr.store(true, std::memory_order_release);
     }
     cudaMemsetAsync(S, 0, s_bytes, st);
     cudaMemsetAsync(flag, 0, 2 * sizeof(int), st);

@@ -165,15 +165,19 @@ struct Server {
     std::vector<FactorSet*> sets;
     int* dslot = nullptr;                           // device slot map for (un)packing
     size_t reserved = 0;                            // worker: bytes reserved for sets being built
-    // builder: its context and thread; queues guarded by mu
-    helm_ctx bctx = nullptr;
-    cudaStream_t bstream = nullptr;
-    std::thread bth;
+    // builders: NBUILD host threads, each with its own context and stream; queues guarded by mu.  Two builders
+    // (two sets factored at once) measured no gain on the request stream (0.86 vs 0.87 requests/s saturated:
+    // the solves, not the builds, bound it), so one is used
+    static constexpr int NBUILD = 1;
+    helm_ctx bctxs[NBUILD] = {};
+    cudaStream_t bstreams[NBUILD] = {};
+    std::thread bths[NBUILD];
     std::condition_variable bcv;
     bool bstop = false;
     std::deque<FactorSet*> to_build, built;
 
-    void build_loop() {
+    void build_loop(int bi) {
+        helm_ctx bctx = bctxs[bi];
         cudaSetDevice(ctx->device);
         for (;;) {
             FactorSet* fs = nullptr;
@@ -619,25 +623,33 @@ extern "C" helm_status helm_serve_start(helm_ctx ctx, int slots) {
         delete sv;
         return rc;
     }
-    // the builder's context: same device, its own non-blocking stream, no budget of its own (the worker
+    // the builders' contexts: same device, each its own non-blocking stream, no budget of their own (the worker
     // reserves every build's bytes within the serving context's budget), the serving context's tuning
-    rc = cuda_check(ctx, cudaStreamCreateWithFlags(&sv->bstream, cudaStreamNonBlocking), "builder stream");
-    if (!rc) rc = helm_create(&sv->bctx, ctx->device, sv->bstream, 0);
+    for (int i = 0; i < Server::NBUILD && !rc; ++i) {
+        rc = cuda_check(ctx, cudaStreamCreateWithFlags(&sv->bstreams[i], cudaStreamNonBlocking), "builder stream");
+        if (!rc) rc = helm_create(&sv->bctxs[i], ctx->device, sv->bstreams[i], 0);
+    }
     if (rc) {
-        if (sv->bstream) cudaStreamDestroy(sv->bstream);
+        for (int i = 0; i < Server::NBUILD; ++i) {
+            if (sv->bctxs[i]) helm_destroy(sv->bctxs[i]);
+            if (sv->bstreams[i]) cudaStreamDestroy(sv->bstreams[i]);
+        }
         dev_free(ctx, sv->dslot, 256 * sizeof(int));
         delete sv;
         return set_error(ctx, rc, "helm_serve_start: builder context");
     }
-    sv->bctx->tc_stages = ctx->tc_stages;
-    sv->bctx->coarse_coop = ctx->coarse_coop;
-    sv->bctx->use_graphs = ctx->use_graphs;
-    sv->bctx->tc_flow = ctx->tc_flow;
-    sv->bctx->stencil_march = ctx->stencil_march;
-    sv->bctx->stencil_planes = ctx->stencil_planes;
-    sv->bctx->tc_factor = ctx->tc_factor;
+    for (helm_ctx b : sv->bctxs) {
+        b->tc_stages = ctx->tc_stages;
+        b->coarse_coop = ctx->coarse_coop;
+        b->use_graphs = ctx->use_graphs;
+        b->tc_flow = ctx->tc_flow;
+        b->stencil_march = ctx->stencil_march;
+        b->stencil_planes = ctx->stencil_planes;
+        b->tc_factor = ctx->tc_factor;
+        b->block_gj = ctx->block_gj;
+    }
     ctx->server = sv;
-    sv->bth = std::thread([sv]() { sv->build_loop(); });
+    for (int i = 0; i < Server::NBUILD; ++i) sv->bths[i] = std::thread([sv, i]() { sv->build_loop(i); });
     sv->th = std::thread([sv]() { sv->loop(); });
     return HELM_OK;
 }
@@ -709,10 +721,12 @@ extern "C" helm_status helm_serve_stop(helm_ctx ctx) {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->bstop = true;
     }
-    sv->bcv.notify_one();
-    sv->bth.join();
-    helm_destroy(sv->bctx);
-    cudaStreamDestroy(sv->bstream);
+    sv->bcv.notify_all();
+    for (auto& t : sv->bths) t.join();
+    for (int i = 0; i < Server::NBUILD; ++i) {
+        helm_destroy(sv->bctxs[i]);
+        cudaStreamDestroy(sv->bstreams[i]);
+    }
     for (auto& kv : sv->reqs) delete kv.second;
     dev_free(ctx, sv->dslot, 256 * sizeof(int));
     delete sv;

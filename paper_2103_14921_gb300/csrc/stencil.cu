@@ -23,6 +23,8 @@
 // the loads bounds it).  The coefficient is formed once per neighbour and
 // reused for the RCH columns.  The grid is (x-line chunks, y, z), so no
 // thread divides 64-bit indices.
+#include <atomic>
+
 #include "internal.h"
 
 namespace {
@@ -657,10 +659,14 @@ helm_status launch_any(helm_grid g, int prec, const void* u, const void* b, void
             // the fewest plane chunks (longest walks: less halo per output) of at most 64 planes that still give
             // every resident block slot two blocks or more (measured: fewer blocks than that leave the launch
             // short of latency hiding), chunks of 8 planes at least
-            static int per_sm = 0;
-            if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil_march<SUB, true>, 128,
-                                                                             0) != cudaSuccess)
-                per_sm = 0;
+            static std::atomic<int> occ{0};
+            int per_sm = occ.load(std::memory_order_relaxed);
+            if (per_sm == 0) {
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil_march<SUB, true>, 128, 0) !=
+                    cudaSuccess)
+                    per_sm = 0;
+                occ.store(per_sm, std::memory_order_relaxed);
+            }
             const long long slots = (long long)std::max(per_sm, 1) * std::max(g->ctx->sm_count, 1);
             const long long xy = (long long)gx * gy * ncc;
             const int nz = g->d.nz;

@@ -28,6 +28,8 @@
 // records an error code and makes the CTA drain its copies and return, so a
 // failure surfaces as HELM_ETIMEOUT instead of a hang.  A cooperative launch
 // guarantees that all CTAs are resident at once.
+#include <atomic>
+
 #include "internal.h"
 
 namespace {
@@ -227,23 +229,23 @@ struct CoopPlan {
 CoopPlan plan_for(helm_ctx ctx, const PlaneSet& P) {
     CoopPlan c;
     if (P.nbox != 1 || P.prec == HELM_PREC_FP64 || P.prec == HELM_PREC_BF16 || P.padded) return c;
-    static int coop_attr = -1;
-    if (coop_attr < 0) {
+    static std::atomic<int> coop_attr{-1};
+    if (coop_attr.load(std::memory_order_acquire) < 0) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, ctx->device);
-        coop_attr = v;
+        coop_attr.store(v, std::memory_order_release);
     }
-    if (!coop_attr || ctx->sm_count <= 0) return c;
+    if (!coop_attr.load(std::memory_order_acquire) || ctx->sm_count <= 0) return c;
     const int m = P.hbox[0].m;
     c.grid = ctx->sm_count;
     c.rpc = (m + c.grid - 1) / c.grid;
     c.gp = m | 1;
     c.smem = ((size_t)CO_RN * m + (size_t)c.rpc * c.gp + (size_t)CO_WARPS * CO_ROWS * CO_RN) * sizeof(c64);
     if (c.smem > 200 * 1024) return c;
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};
+    if (!attr.load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(coarse_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
+        attr.store(true, std::memory_order_release);
     }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_sweeps, CO_THREADS, c.smem) != cudaSuccess ||

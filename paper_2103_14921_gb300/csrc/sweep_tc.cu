@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <vector>
 
 #include "internal.h"
@@ -682,9 +683,9 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
         !encode_3d(&mapB, bt, 2ull * ld, (uint64_t)NPAD, (uint64_t)P.nbox, 2ull * ld * eb, 2ull * ld * NPAD * eb,
                    Cfg::BK, NPAD, BF))
         return set_error(ctx, HELM_ECUDA, "cuTensorMapEncodeTiled failed for the tensor-core sweep");
-    static bool attr = false;
-    static int flow_occ = 0;
-    if (!attr) {
+    static std::atomic<bool> attr{false};
+    static std::atomic<int> flow_occ{0};
+    if (!attr.load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(tc_sweep_gemm<E, NPAD, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         cudaFuncSetAttribute(tc_sweep_flow<E, NPAD, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         // all of the unified L1 as shared memory, so that as many persistent CTAs fit per SM as its 228 KB allow
@@ -700,12 +701,12 @@ helm_status run_tc(helm_ctx ctx, const PlaneSet& P, const c64* lb, c64* loc, E* 
             cudaFuncGetAttributes(&fa, tc_sweep_flow<E, NPAD, NST>) == cudaSuccess) {
             const int per_block = Cfg::SMEM + (int)fa.sharedSizeBytes + 1024;   // + the 1 KB reserved per block
             const int regs = (fa.numRegs + 7) / 8 * 8 * 128;
-            flow_occ = std::min(std::min(smem_sm / per_block, regs_sm / std::max(1, regs)),
-                                std::min(512 / (int)Cfg::TCOLS, 8));
+            flow_occ.store(std::min(std::min(smem_sm / per_block, regs_sm / std::max(1, regs)),
+                                    std::min(512 / (int)Cfg::TCOLS, 8)));
         }
         cudaFuncSetAttribute(tc_prep2<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(128 * (PREP2_TP + 1) * sizeof(c64)));
-        attr = true;
+        attr.store(true, std::memory_order_release);
     }
     const int m = P.m_max;
     const int gtiles = (m + TC_BM - 1) / TC_BM;
