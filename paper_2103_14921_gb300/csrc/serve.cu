@@ -413,11 +413,13 @@ struct Server {
             // evicting other idle sets if needed
             if (fs->active > 0) return false;
             const int width = width_for(r->req.nrhs);
-            const size_t more = engine_estimate(r->req, width) - engine_estimate(r->req, fs->width);
+            // the solver workspace grows now, the apply scratch at the set's next cycle (reserved until then)
+            const size_t s_new = oras_estimate_bytes(r->req.grid, r->req.oras, width);
+            const size_t s_old = oras_estimate_bytes(r->req.grid, r->req.oras, fs->width);
+            const size_t scratch = s_new > s_old ? s_new - s_old : 0;
+            const size_t more = engine_estimate(r->req, width) - engine_estimate(r->req, fs->width) + scratch;
             if (!make_room(more, fs)) {
-                bool others = false;
-                for (auto* s2 : sets) others = others || (s2 != fs && (s2->building || s2->active > 0));
-                if (others) return false;   // room comes back when the others finish
+                if (others_busy(fs)) return false;   // room comes back when the others finish
                 set_error(ctx, HELM_ENOMEM, "request needs about %zu more bytes than the HBM budget leaves", more);
                 finish(r, HELM_ENOMEM);
                 return true;
@@ -437,6 +439,10 @@ struct Server {
             fs->width = width;
             fs->owner.assign(width, nullptr);
             fs->col.assign(width, -1);
+            reserved -= fs->reserved;
+            fs->reserved = scratch;
+            reserved += scratch;
+            fs->cycled = false;
         }
         if (fs->free_slots() < r->req.nrhs) return false;
         r->reused = !r->built_for;
