@@ -42,3 +42,22 @@ def test_library_memory_estimate_grows_with_boxes_and_rhs():
     assert 0 < small < more_rhs and small < fp64
     # factors of 8 boxes of 34 x 34 x 34 nodes, padded rows of 1168 complex64: about 3 GB
     assert 2.5e9 < small < 6e9
+
+
+def test_package_cache_holds_the_benched_problem_classes():
+    """The tuning cache shipped in the package holds the autotuner's choices for the two benched workloads that
+    use it (thrust-fold 256 x 256 x 96 at 5 Hz in batches of 32, attenuating 160 x 160 x 80 tuned at 6 Hz for 128
+    columns), each among the decompositions that workload lets the tuner time, with its timed trials."""
+    import os
+
+    import bench
+    cache = tune.load_cache(bench.TUNE_CACHE)
+    assert os.path.dirname(bench.TUNE_CACHE).endswith("paper_2103_14921_gb300")
+    tf = cache[tune.problem_key(256, 256, 96, 5.0, 32, 2)]
+    assert (tuple(tf["parts"]), tf["overlap"]) in set(tune.candidates(256, 256, 96))
+    assert tf["coarse_iters"] in (0, 10) and tf["knobs"]["tc_flow"] in (0, 1)
+    at = cache[tune.problem_key(160, 160, 80, 6.0, 128, 2)]
+    assert (tuple(at["parts"]), at["overlap"]) in {(tuple(p), ov) for p, ov in bench.ATTEN_CANDS}
+    for entry in (tf, at):
+        good = [t for t in entry["trials"] if t.get("converged")]
+        assert good and entry["rhs_per_s"] == max(t["rhs_per_s"] for t in good)
