@@ -149,6 +149,38 @@ def test_stencil_coefficient_identities():
     assert a2 >= 0 and a3 >= 0
 
 
+def test_interior_row_depends_only_on_the_neighbour_class():
+    """Away from the absorbing layers the expanded 27-point row (Eq. eq1 in the product form of reading 2) gives
+    every neighbour a coefficient that depends only on its class (centre, face, edge, corner): the mass part is
+    exactly the paper's per-neighbour mass weight wm1..wm4 times k^2, and the Laplacian part is a consistent
+    second-order Laplacian whatever the weights -- zero on constants, exactly 2 on x^2 (and on y^2, z^2), zero
+    on xy -- with class values (-6 + 12 a2 - 8 a3, 1 - 4 a2 + 4 a3, a2 - 2 a3, a3) / h^2."""
+    w = synth.random_weights(31)
+    h = 25.0
+    rows = []
+    for f in (3.0, 7.0):
+        prob = _prob(n=(7, 7, 7), weights=w, npml=0, f=f, h=h)
+        rows.append((neighbour_coefficients(prob)[:, :, :, 3, 3, 3], prob.k2()[3, 3, 3]))
+    (c1, k1), (c2, k2) = rows
+    mass = (c1 - c2) / (k1 - k2)
+    lap = c1 - mass * k1
+    off = np.array([-1, 0, 1])
+    dz, dy, dx = np.meshgrid(off, off, off, indexing="ij")
+    cls = np.abs(dx) + np.abs(dy) + np.abs(dz)
+    a2, a3 = stencil_coefficients(w)[:2]
+    want_lap = np.array([-6 + 12 * a2 - 8 * a3, 1 - 4 * a2 + 4 * a3, a2 - 2 * a3, a3]) / h ** 2
+    want_mass = np.array(w[3:7])
+    for c in range(4):
+        assert np.allclose(mass[cls == c], want_mass[c], rtol=1e-12, atol=1e-15)
+        assert np.allclose(lap[cls == c], want_lap[c], rtol=1e-12, atol=1e-18)
+    # consistency of the Laplacian part, independently of the class formula
+    assert abs(lap.sum()) * h ** 2 < 1e-12
+    for d in (dx, dy, dz):
+        assert abs((lap * d ** 2).sum() * h ** 2 - 2.0) < 1e-12
+    assert abs((lap * dx * dy).sum()) * h ** 2 < 1e-12
+    assert abs(mass.sum() - 1.0) < 1e-12     # the mass weights of one row sum to one
+
+
 # --- adaptive stencil weights (each row with the weights matched to its own points per wavelength) ---
 
 def test_row_weights_rows_equal_their_constant_weight_rows():
