@@ -151,9 +151,10 @@ def _case(ctx, dims, parts, ov, npml, prec, nrhs, seed):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
-@pytest.mark.parametrize("nrhs", [16, 3])
+@pytest.mark.parametrize("nrhs", [16, 3, 128])
 def test_multiplane_tc_apply_matches_oracle(ctx, prec, nrhs):
-    """Ragged boxes of 9-11 planes; 16 columns take the persistent queue, 3 the per-step launches."""
+    """Ragged boxes of 9-11 planes; 16 columns take the persistent queue, 3 the per-step launches, 128 the
+    persistent queue with the preparation staged in column chunks (N = 256, one CTA per SM)."""
     _case(ctx, (21, 18, 17), (3, 2, 2), 2, 3, prec, nrhs, 71 + nrhs)
 
 
